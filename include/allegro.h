@@ -1,0 +1,165 @@
+/*
+ * allegro.h -- C ABI of the GB300 (sm_103a) Allegro edge hot path.
+ *
+ * Computes, for a set of atoms, the strictly local Allegro potential of
+ * arXiv 2304.10061: ordered neighbour pairs within r_c, Bessel x envelope
+ * radial basis, real spherical harmonics, the two-body MLP, per layer the
+ * env-weight projection, the environment sum and the Clebsch-Gordan tensor
+ * product (Eq. 1), the latent MLP, then the edge-energy MLP, the float64
+ * per-atom scale/shift/sum (Sec. "Allegro", "Mixed-precision calculations"),
+ * and, through a hand-written adjoint, forces F = -dE/dpos and the virial.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an allegro_status; no exception crosses the ABI.
+ *     On failure allegro_last_error(ctx) holds a one-line description.
+ *   - Input and output arrays are owned by the caller.  Each may live in host
+ *     memory or in device memory of the context's GPU; the library detects
+ *     which (cudaPointerGetAttributes) and copies as needed.  Host inputs are
+ *     copied before the call returns; host outputs are complete when it
+ *     returns.  Device outputs are complete when work queued on the
+ *     context's stream (allegro_set_stream) has finished; calls themselves
+ *     synchronise that stream before returning.
+ *   - Units: Angstrom, eV, eV/Angstrom.  All outputs are float64.
+ *   - A context is not thread safe; use one per host thread.
+ */
+#ifndef ALLEGRO_H
+#define ALLEGRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct allegro_ctx allegro_ctx;
+
+typedef enum {
+  ALLEGRO_OK = 0,
+  ALLEGRO_E_INVALID = 1,    /* bad argument: null pointer, bad size, unknown type, non-finite input, bad weights */
+  ALLEGRO_E_OOM = 2,        /* device memory could not be allocated */
+  ALLEGRO_E_CUDA = 3,       /* a CUDA runtime call failed */
+  ALLEGRO_E_CAPACITY = 4,   /* more edges than allegro_reserve(..., fixed=1) allows; last_error gives the need */
+  ALLEGRO_E_TIMEOUT = 5,    /* a bounded device-side wait ran out (kernel returned early, results invalid) */
+  ALLEGRO_E_NONFINITE = 6,  /* an output is NaN or Inf */
+  ALLEGRO_E_STATE = 7       /* call out of order (e.g. energy_forces before neighbors) */
+} allegro_status;
+
+typedef enum {
+  ALLEGRO_PREC_FP32 = 0,    /* all MLP GEMMs in float32 on the CUDA cores */
+  ALLEGRO_PREC_BF16 = 1     /* MLP GEMMs in bfloat16 on tcgen05 tensor cores, float32 accumulation */
+} allegro_precision;
+
+/*
+ * allegro_create -- load a model and bind a context to one GPU.
+ *   weights_blob/blob_bytes: host memory, an "ALGW" v1 weights image (header
+ *       with the architecture, then float32 weights and float64 per-species
+ *       scale sigma_Z / shift mu_Z of Sec. "Allegro": E = sum_i sigma_Z E_i + mu_Z).
+ *       Copied; the caller may free it after the call.
+ *   species_map[n_types]: maps the caller's atom type t to a model species
+ *       (0..n_species-1).  NULL means the identity (types are species).
+ *   r_c: neighbour cutoff in Angstrom; <= 0 takes the model's cutoff, any
+ *       other value must equal it (the radial basis and envelope vanish there).
+ *   precision: an allegro_precision.
+ *   device: CUDA device ordinal.  out: receives the context.
+ * Supported models: 1 or 2 layers, l_max 1 or 2, channels a power of two from
+ * 8 to 128, MLP widths up to 512.  Others return ALLEGRO_E_INVALID.
+ */
+allegro_status allegro_create(const void* weights_blob, size_t blob_bytes,
+                              const int32_t* species_map, int32_t n_types,
+                              double r_c, int32_t precision, int32_t device,
+                              allegro_ctx** out);
+
+/* allegro_set_stream -- queue all later device work on `cuda_stream` (a
+ * cudaStream_t of the context's device; NULL = the context's own stream). */
+allegro_status allegro_set_stream(allegro_ctx* ctx, void* cuda_stream);
+
+/*
+ * allegro_reserve -- pre-size the device arena for `atom_cap` atoms and
+ * `edge_cap` ordered edges (the role of the paper's 5 % input padding,
+ * Sec. "Optimized LAMMPS-Kokkos implementation": no reallocation while sizes
+ * fluctuate).  fixed = 0: later calls still grow the arena when needed (with
+ * 5 % headroom).  fixed = 1: a neighbour build needing more edges fails with
+ * ALLEGRO_E_CAPACITY and last_error states the required count.
+ * chunk_edges > 0 caps the edges evaluated per pass of the model (the
+ * activation working set scales with it); 0 = automatic.
+ */
+allegro_status allegro_reserve(allegro_ctx* ctx, int64_t atom_cap, int64_t edge_cap,
+                               int32_t fixed, int64_t chunk_edges);
+
+/*
+ * allegro_neighbors -- build the ordered neighbour list of one structure.
+ * An edge is (i, j, S), S in Z^3 an image shift, displacement
+ *   d = (pos_j + (S0 a + S1 b) + S2 c) - pos_i  evaluated in float64 in that
+ * order without fused multiply-add, kept iff |d|^2 < r_c^2 and not
+ * (i == j and S == 0) (Sec. "Allegro": per-ordered-pair energies E_ij).
+ *   n_atoms >= 0; pos[n_atoms*3] float64 (x,y,z per atom, any position, not
+ *   necessarily inside the cell); types[n_atoms] int32 caller types;
+ *   cell[9] float64 row-major with rows a, b, c, or NULL for no cell;
+ *   pbc[3] (0/1 per axis; NULL = all periodic if cell given, else none).
+ *   A periodic axis needs a cell.  n_edges_out (host, may be NULL): edges.
+ * The result is kept in the context for allegro_energy_forces.
+ */
+allegro_status allegro_neighbors(allegro_ctx* ctx, int64_t n_atoms, const double* pos,
+                                 const int32_t* types, const double* cell, const uint8_t* pbc,
+                                 int64_t* n_edges_out);
+
+/*
+ * allegro_neighbors_batched -- many independent structures in one packed
+ * list.  Structure b holds atoms [atom_offsets[b], atom_offsets[b+1]);
+ * atom_offsets[n_struct+1] int64 (host or device).  cells[n_struct*9] or
+ * NULL (no cells); pbc[n_struct*3] or NULL (periodic iff a cell is given).
+ * No edge joins two structures.  Intended for many small structures
+ * (each evaluated by all-pairs search over its image range).
+ */
+allegro_status allegro_neighbors_batched(allegro_ctx* ctx, int32_t n_struct,
+                                         const int64_t* atom_offsets, const double* pos,
+                                         const int32_t* types, const double* cells,
+                                         const uint8_t* pbc, int64_t* n_edges_out);
+
+/*
+ * allegro_energy_forces -- evaluate the model on the last neighbour list.
+ *   E_total: [1] (single structure) or [n_struct] (batched), per-structure
+ *            sum of sigma_Z E_i + mu_Z, float64.  Required.
+ *   E_atom:  [n_atoms] sigma_Z E_i + mu_Z or NULL.
+ *   F:       [n_atoms*3] forces -dE/dpos or NULL.
+ *   virial:  [9] or [n_struct*9] row-major W_ab = -sum_e d_{e,a} dE/dd_{e,b}, or NULL.
+ * The adjoint runs when F or virial is requested.
+ */
+allegro_status allegro_energy_forces(allegro_ctx* ctx, double* E_total, double* E_atom,
+                                     double* F, double* virial);
+
+/*
+ * allegro_get_neighbors -- copy the last neighbour list out, sorted by centre
+ * atom i (rows in ascending i; order inside a row is deterministic but
+ * unspecified).  i[cap], j[cap], shift[cap*3] int32 (any may be NULL);
+ * cap must be >= the edge count.
+ */
+allegro_status allegro_get_neighbors(allegro_ctx* ctx, int32_t* i, int32_t* j, int32_t* shift,
+                                     int64_t cap);
+
+/*
+ * allegro_profile -- enable (1) or disable (0) per-launch timing of the
+ * library's kernels with CUDA events on the context's stream; enabling clears
+ * earlier records.  Not part of the method: a tracing aid.
+ * allegro_profile_report -- writes a JSON object into buf[cap] (host):
+ *   {"<kernel>": {"launches": n, "ms": total, "flops": algorithmic FLOPs,
+ *                 "bytes": algorithmic bytes}, ...}
+ * over the launches recorded since profiling was enabled, and the number of
+ * kernel launches this context has issued since creation into *launches
+ * (may be NULL).  ALLEGRO_E_CAPACITY if cap is too small.
+ */
+allegro_status allegro_profile(allegro_ctx* ctx, int32_t enable);
+allegro_status allegro_profile_report(allegro_ctx* ctx, char* buf, size_t cap, int64_t* launches);
+
+/* allegro_last_error -- description of the last failure on ctx (never NULL). */
+const char* allegro_last_error(const allegro_ctx* ctx);
+
+/* allegro_destroy -- free the context and its device memory (NULL is a no-op). */
+void allegro_destroy(allegro_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALLEGRO_H */

@@ -10,8 +10,11 @@ fused multiply-add:
     r2     = (d[0]*d[0] + d[1]*d[1]) + d[2]*d[2]
 and the edge exists iff r2 < r_c*r_c (strict) and not (i == j and S == 0).
 Periodic self-images (i == j, S != 0) are edges when within the cutoff.
-S ranges over |S_k| <= ceil(r_c / w_k), w_k the perpendicular width of the
-cell along axis k.  numpy evaluates elementwise float64 operations without
+S ranges over |S_k| <= ceil(r_c / w_k + span_k), w_k the perpendicular width
+of the cell along axis k and span_k the spread of the atoms' fractional
+coordinates along k (positions need not be wrapped into the cell; for wrapped
+positions this is the usual ceil(r_c / w_k) plus one layer, which adds
+candidates, never edges).  numpy evaluates elementwise float64 operations without
 contraction, so the arithmetic above is what runs.
 
 `brute_force` is the definition, applied to every candidate.
@@ -36,15 +39,20 @@ def _widths(cell: np.ndarray) -> np.ndarray:
                      vol / np.linalg.norm(np.cross(a, b))])
 
 
-def image_range(cell, pbc, r_c):
+def image_range(cell, pbc, r_c, pos=None):
     if cell is None:
         return [0, 0, 0]
-    w = _widths(np.asarray(cell, dtype=np.float64))
-    return [int(math.ceil(r_c / w[k])) if pbc[k] else 0 for k in range(3)]
+    cell = np.asarray(cell, dtype=np.float64)
+    w = _widths(cell)
+    span = np.zeros(3)
+    if pos is not None and len(pos) > 1:
+        frac = np.asarray(pos, dtype=np.float64) @ np.linalg.inv(cell)
+        span = frac.max(0) - frac.min(0)
+    return [int(math.ceil(r_c / w[k] + span[k])) if pbc[k] else 0 for k in range(3)]
 
 
-def _images(cell, pbc, r_c):
-    n = image_range(cell, pbc, r_c)
+def _images(cell, pbc, r_c, pos=None):
+    n = image_range(cell, pbc, r_c, pos)
     return [S for S in itertools.product(*[range(-n[k], n[k] + 1) for k in range(3)])]
 
 
@@ -74,7 +82,7 @@ def brute_force(pos, cell, pbc, r_c, centers=None):
     centers = np.arange(n) if centers is None else np.asarray(centers, dtype=np.int64)
     rc2 = float(r_c) * float(r_c)
     I, J, SS = [], [], []
-    for S in _images(cell, pbc, r_c):
+    for S in _images(cell, pbc, r_c, pos):
         off = _offset(cell, S)
         ii = np.repeat(centers, n)
         jj = np.tile(np.arange(n), len(centers))
@@ -101,7 +109,7 @@ def neighbor_list(pos, cell, pbc, r_c, centers=None):
     lo = pos[centers].min(0) - rad
     hi = pos[centers].max(0) + rad
     pts, src, shf = [], [], []
-    for S in _images(cell, pbc, r_c):
+    for S in _images(cell, pbc, r_c, pos):
         off = _offset(cell, S)
         q = pos + off
         m = np.all((q >= lo) & (q <= hi), axis=1)

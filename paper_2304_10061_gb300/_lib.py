@@ -1,0 +1,54 @@
+"""ctypes binding of liballegro_gb300.so: the same entry points as include/allegro.h.
+
+Argument marshalling only; every step of the computation runs in the library's
+CUDA kernels.  Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "liballegro_gb300.so")
+
+ALLEGRO_OK = 0
+STATUS_NAMES = {
+    0: "ALLEGRO_OK", 1: "ALLEGRO_E_INVALID", 2: "ALLEGRO_E_OOM", 3: "ALLEGRO_E_CUDA",
+    4: "ALLEGRO_E_CAPACITY", 5: "ALLEGRO_E_TIMEOUT", 6: "ALLEGRO_E_NONFINITE", 7: "ALLEGRO_E_STATE",
+}
+PREC = {"fp32": 0, "bf16": 1}
+
+EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_reserve", "allegro_neighbors",
+           "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
+           "allegro_profile", "allegro_profile_report", "allegro_last_error", "allegro_destroy")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (once) and declare its prototypes."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, sz, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+    L.allegro_create.argtypes = [vp, sz, vp, i32, ctypes.c_double, i32, i32, ctypes.POINTER(vp)]
+    L.allegro_set_stream.argtypes = [vp, vp]
+    L.allegro_reserve.argtypes = [vp, i64, i64, i32, i64]
+    L.allegro_neighbors.argtypes = [vp, i64, dp, dp, dp, dp, ctypes.POINTER(i64)]
+    L.allegro_neighbors_batched.argtypes = [vp, i32, dp, dp, dp, dp, dp, ctypes.POINTER(i64)]
+    L.allegro_energy_forces.argtypes = [vp, dp, dp, dp, dp]
+    L.allegro_get_neighbors.argtypes = [vp, dp, dp, dp, i64]
+    L.allegro_profile.argtypes = [vp, i32]
+    L.allegro_profile_report.argtypes = [vp, ctypes.c_char_p, sz, ctypes.POINTER(i64)]
+    L.allegro_last_error.argtypes = [vp]
+    L.allegro_last_error.restype = ctypes.c_char_p
+    L.allegro_destroy.argtypes = [vp]
+    L.allegro_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("allegro_last_error", "allegro_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L

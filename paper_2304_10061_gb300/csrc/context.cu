@@ -1,0 +1,1331 @@
+// Host orchestration and the C ABI of liballegro_gb300 (include/allegro.h).
+//
+// The context owns the model (weights on the device as float32 and bfloat16,
+// forward and transposed), the tensor-product constants, and a device arena:
+// per-atom and per-edge arrays of the neighbour list, and a chunk workspace
+// for the per-edge activations.  Edges are evaluated in chunks of whole CSR
+// rows (every centre atom's environment sum is complete inside one chunk, the
+// strict locality of Eq. 1), so the activation working set is bounded by the
+// chunk size, not by the system size.
+//
+// One evaluation (Sec. "Allegro", Fig. "architecture"):
+//   geometry/basis -> two-body MLP -> [embedding | env weights 1]
+//   -> per layer: row kernel (environment sum, tensor product, scalars)
+//      -> latent MLP -> env weights of the next layer
+//   -> edge energy (linear edge MLP folded into one vector)
+// and the hand-written adjoint in reverse order down to dE/dd_e, then the
+// float64 per-atom reduction (energies, forces by row/column gathers, virial).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace alg;
+
+namespace {
+
+inline int pad8(int x) { return (x + 7) / 8 * 8; }
+inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// ------------------------------------------------------------------------
+// small kernels
+// ------------------------------------------------------------------------
+__global__ void map_types_kernel(const int* __restrict__ types, const double* __restrict__ pos, int n,
+                                 const int* __restrict__ map, int nmap, int* __restrict__ species,
+                                 int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int t = types[i];
+  bool bad = (t < 0 || t >= nmap);
+  int s = bad ? 0 : map[t];
+  if (s < 0) bad = true;
+  double x = pos[3 * (size_t)i], y = pos[3 * (size_t)i + 1], z = pos[3 * (size_t)i + 2];
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) bad = true;
+  if (bad) atomicOr(err, kErrBadInput);
+  species[i] = bad ? 0 : s;
+}
+
+__global__ void atom_struct_kernel(const int64_t* __restrict__ offs, int nstruct, int* __restrict__ atom_struct) {
+  int b = blockIdx.x;
+  if (b >= nstruct) return;
+  for (long long i = offs[b] + threadIdx.x; i < offs[b + 1]; i += blockDim.x) atom_struct[i] = b;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Per-launch timing of the library's kernels (CUDA events on the launching
+// stream) with the algorithmic FLOPs and bytes of each launch.
+struct ProfRec {
+  const char* name;
+  int ev;
+  double flops, bytes;
+  int launches;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;      // pairs: 2k = start, 2k+1 = stop
+  std::vector<ProfRec> recs;
+};
+
+// Capacity (elements) of each growable device buffer.
+struct Cap {
+  int64_t v = 0;
+};
+struct Caps {
+  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat;
+  Cap ej, ei, eS, ed, col_edge, Ee, g;
+  Cap cc, cs, ccur;
+  Cap offs, cells, pbc, nimg, Eout, Wout;
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// context
+// --------------------------------------------------------------------------
+struct allegro_ctx {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int prec = ALLEGRO_PREC_FP32;
+  Arch arch;
+  std::vector<int> species_map;
+  std::string err;
+
+  // model on the device
+  std::vector<Lin> tb;                     // two-body layers
+  Lin w01;                                 // [embedding ; env weights of layer 1]
+  Lin env2;                                // env weights of layer 2 (two-layer models)
+  std::vector<std::vector<Lin>> lat;       // latent MLP of layers 1..nl
+  float* d_v = nullptr;                    // folded edge-energy vector
+  double* d_sigma = nullptr;
+  double* d_mu = nullptr;
+  int* d_map = nullptr;
+  int nmap = 0;
+  TPConst tp{};
+  std::vector<void*> weight_allocs;
+
+  // state of the last neighbour build
+  bool have_nb = false;
+  int64_t n_atoms = 0, n_edges = 0;
+  int nstruct = 0;
+  bool batched = false;
+  std::vector<int> h_row_ptr;              // host copy of row_ptr (for chunking)
+
+  // capacities and policy
+  int64_t atom_cap = 0, edge_cap = 0;
+  bool fixed = false;
+  int64_t chunk_edges_user = 0;
+
+  // per-atom arrays
+  double* d_pos = nullptr;
+  int* d_types = nullptr;
+  int* d_species = nullptr;
+  int* d_row_ptr = nullptr;
+  int* d_col_ptr = nullptr;
+  int* d_count = nullptr;
+  int* d_cell_of = nullptr;
+  int* d_wrap = nullptr;
+  int* d_sorted = nullptr;
+  int* d_atom_struct = nullptr;
+  double* d_Eatom = nullptr;
+  double* d_F = nullptr;
+  double* d_Wat = nullptr;
+  // per-edge arrays
+  int* d_ej = nullptr;
+  int* d_ei = nullptr;
+  int* d_eS = nullptr;
+  double* d_ed = nullptr;
+  int* d_col_edge = nullptr;
+  float* d_Ee = nullptr;
+  float* d_g = nullptr;
+  // cells
+  int* d_cell_count = nullptr;
+  int* d_cell_start = nullptr;
+  int* d_cell_cursor = nullptr;
+  int64_t cell_cap = 0;
+  // structures
+  int64_t* d_offs = nullptr;
+  double* d_cells = nullptr;
+  int* d_pbc = nullptr;
+  int* d_nimg = nullptr;
+  double* d_Eout = nullptr;
+  double* d_Wout = nullptr;
+  int64_t struct_cap = 0;
+  // scratch
+  void* d_scan_tmp = nullptr;
+  size_t scan_tmp_cap = 0;
+  int* d_err = nullptr;
+  int* d_total = nullptr;
+  double* d_minmax = nullptr;
+  Caps caps;
+  Profiler prof;
+  int64_t launches = 0;                    // kernel launches issued by this context
+
+  // chunk workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int64_t ws_edges = 0, ws_atoms = 0;
+};
+
+namespace {
+
+allegro_status fail(allegro_ctx* c, allegro_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                        \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      cudaGetLastError();                                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? ALLEGRO_E_OOM : ALLEGRO_E_CUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                                  \
+    }                                                                                              \
+  } while (0)
+
+template <typename T>
+cudaError_t regrow(T*& p, int64_t& cap, int64_t need, double headroom = 1.05) {
+  if (need <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  int64_t n = std::max<int64_t>((int64_t)(need * headroom) + 16, 16);
+  cudaError_t e = cudaMalloc(&p, (size_t)n * sizeof(T));
+  cap = (e == cudaSuccess) ? n : 0;
+  return e;
+}
+
+template <typename T>
+cudaError_t grow(T*& p, Cap& cap, int64_t need) {
+  return regrow(p, cap.v, need);
+}
+
+inline Caps& caps_of(allegro_ctx* c) { return c->caps; }
+
+int prof_begin(allegro_ctx* c, const char* name, double flops, double bytes, int launches) {
+  c->launches += launches;
+  if (!c->prof.on) return -1;
+  Profiler& P = c->prof;
+  int k = (int)P.recs.size();
+  while ((int)P.ev.size() < 2 * (k + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    P.ev.push_back(e);
+  }
+  P.recs.push_back({name, k, flops, bytes, launches});
+  cudaEventRecord(P.ev[2 * k], c->stream);
+  return k;
+}
+
+void prof_end(allegro_ctx* c, int k) {
+  if (k >= 0) cudaEventRecord(c->prof.ev[2 * k + 1], c->stream);
+}
+
+struct ProfScope {
+  allegro_ctx* c;
+  int k;
+  ProfScope(allegro_ctx* c_, const char* name, double flops, double bytes, int launches = 1)
+      : c(c_), k(prof_begin(c_, name, flops, bytes, launches)) {}
+  ~ProfScope() { prof_end(c, k); }
+};
+
+// ------------------------------------------------------------------------
+// weights
+// ------------------------------------------------------------------------
+struct Reader {
+  const uint8_t* p;
+  size_t n, off = 0;
+  bool ok = true;
+  template <typename T>
+  T get() {
+    T v{};
+    if (off + sizeof(T) > n) { ok = false; return v; }
+    memcpy(&v, p + off, sizeof(T));
+    off += sizeof(T);
+    return v;
+  }
+  bool arr_f32(std::vector<float>& out, size_t count) {
+    if (off + count * 4 > n) { ok = false; return false; }
+    out.resize(count);
+    memcpy(out.data(), p + off, count * 4);
+    off += count * 4;
+    return true;
+  }
+  bool arr_f64(std::vector<double>& out, size_t count) {
+    if (off + count * 8 > n) { ok = false; return false; }
+    out.resize(count);
+    memcpy(out.data(), p + off, count * 8);
+    off += count * 8;
+    return true;
+  }
+};
+
+allegro_status upload_lin(allegro_ctx* c, const std::vector<float>& W, int N, int K, Lin& L) {
+  L.N = N; L.K = K;
+  L.ld = pad8(K);
+  L.ldT = pad8(N);
+  std::vector<float> f((size_t)N * L.ld, 0.0f), fT((size_t)K * L.ldT, 0.0f);
+  std::vector<bf16> b((size_t)N * L.ld), bT((size_t)K * L.ldT);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      f[(size_t)n * L.ld + k] = W[(size_t)n * K + k];
+      fT[(size_t)k * L.ldT + n] = W[(size_t)n * K + k];
+    }
+  for (size_t q = 0; q < f.size(); ++q) b[q] = __float2bfloat16_rn(f[q]);
+  for (size_t q = 0; q < fT.size(); ++q) bT[q] = __float2bfloat16_rn(fT[q]);
+  CUDA_TRY(c, cudaMalloc(&L.f32, f.size() * 4));
+  c->weight_allocs.push_back(L.f32);
+  CUDA_TRY(c, cudaMalloc(&L.f32T, fT.size() * 4));
+  c->weight_allocs.push_back(L.f32T);
+  CUDA_TRY(c, cudaMalloc(&L.b16, b.size() * 2));
+  c->weight_allocs.push_back(L.b16);
+  CUDA_TRY(c, cudaMalloc(&L.b16T, bT.size() * 2));
+  c->weight_allocs.push_back(L.b16T);
+  CUDA_TRY(c, cudaMemcpy(L.f32, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(L.f32T, fT.data(), fT.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(L.b16, b.data(), b.size() * 2, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(L.b16T, bT.data(), bT.size() * 2, cudaMemcpyHostToDevice));
+  return ALLEGRO_OK;
+}
+
+allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
+  Reader r{reinterpret_cast<const uint8_t*>(blob), bytes};
+  if (bytes < 8 || memcmp(blob, "ALGW", 4) != 0) return fail(c, ALLEGRO_E_INVALID, "weights: bad magic");
+  r.off = 4;
+  uint32_t ver = r.get<uint32_t>();
+  if (ver != 1) return fail(c, ALLEGRO_E_INVALID, "weights: unsupported version %u", ver);
+  Arch& a = c->arch;
+  a.rc = r.get<double>();
+  a.ann = r.get<double>();
+  a.ns = r.get<int32_t>(); a.nb = r.get<int32_t>(); a.p = r.get<int32_t>(); a.lmax = r.get<int32_t>();
+  a.nl = r.get<int32_t>(); a.C = r.get<int32_t>();
+  int n2 = r.get<int32_t>(), nlat = r.get<int32_t>(), ned = r.get<int32_t>();
+  if (!r.ok || n2 < 1 || n2 > 16 || nlat < 1 || nlat > 16 || ned < 0 || ned > 16)
+    return fail(c, ALLEGRO_E_INVALID, "weights: bad header");
+  for (int k = 0; k < n2; ++k) a.tb.push_back(r.get<int32_t>());
+  for (int k = 0; k < nlat; ++k) a.lat.push_back(r.get<int32_t>());
+  for (int k = 0; k < ned; ++k) a.edge.push_back(r.get<int32_t>());
+  if (!r.ok) return fail(c, ALLEGRO_E_INVALID, "weights: truncated header");
+  if (a.nl < 1 || a.nl > 2) return fail(c, ALLEGRO_E_INVALID, "weights: %d layers (supported: 1 or 2)", a.nl);
+  if (a.lmax < 1 || a.lmax > kMaxLmax) return fail(c, ALLEGRO_E_INVALID, "weights: l_max %d (supported: 1, 2)", a.lmax);
+  if (a.C < 8 || a.C > kMaxChannels || (a.C & (a.C - 1)))
+    return fail(c, ALLEGRO_E_INVALID, "weights: %d channels (supported: powers of two 8..128)", a.C);
+  if (a.ns < 1 || a.ns > kMaxSpecies || a.nb < 1 || a.nb > kMaxBessel || a.p < 2 || a.p > 16 || !(a.rc > 0) ||
+      !(a.ann > 0))
+    return fail(c, ALLEGRO_E_INVALID, "weights: bad species/basis/cutoff fields");
+  for (int w : a.tb) if (w < 1 || w > kMaxWidth) return fail(c, ALLEGRO_E_INVALID, "weights: bad two-body width");
+  for (int w : a.lat) if (w < 1 || w > kMaxWidth) return fail(c, ALLEGRO_E_INVALID, "weights: bad latent width");
+  for (int w : a.edge) if (w < 1 || w > 4096) return fail(c, ALLEGRO_E_INVALID, "weights: bad edge width");
+
+  const int nw = a.n_w();
+  std::vector<std::vector<float>> Wtb(n2);
+  int fan = a.K0in();
+  for (int k = 0; k < n2; ++k) {
+    r.arr_f32(Wtb[k], (size_t)a.tb[k] * fan);
+    fan = a.tb[k];
+  }
+  std::vector<float> Wemb;
+  r.arr_f32(Wemb, (size_t)nw * a.tb.back());
+  const int lm = a.lmax + 1;
+  std::vector<std::vector<float>> Wenv(a.nl), theta(a.nl);
+  std::vector<std::vector<std::vector<float>>> Wlat(a.nl, std::vector<std::vector<float>>(nlat));
+  for (int L = 1; L <= a.nl; ++L) {
+    int kin = a.Klat(L - 1);
+    r.arr_f32(Wenv[L - 1], (size_t)nw * kin);
+    r.arr_f32(theta[L - 1], (size_t)lm * 2 * lm * 2 * lm);
+    fan = kin + a.C;
+    for (int k = 0; k < nlat; ++k) {
+      r.arr_f32(Wlat[L - 1][k], (size_t)a.lat[k] * fan);
+      fan = a.lat[k];
+    }
+  }
+  std::vector<std::vector<float>> Wedge(ned + 1);
+  fan = a.lat.back();
+  for (int k = 0; k <= ned; ++k) {
+    int w = (k < ned) ? a.edge[k] : 1;
+    r.arr_f32(Wedge[k], (size_t)w * fan);
+    fan = w;
+  }
+  std::vector<double> sigma, mu;
+  r.arr_f64(sigma, a.ns);
+  r.arr_f64(mu, a.ns);
+  if (!r.ok || r.off != bytes) return fail(c, ALLEGRO_E_INVALID, "weights: size mismatch (%zu of %zu bytes)", r.off, bytes);
+
+  // device copies of every linear map
+  allegro_status s;
+  c->tb.resize(n2);
+  fan = a.K0in();
+  for (int k = 0; k < n2; ++k) {
+    if ((s = upload_lin(c, Wtb[k], a.tb[k], fan, c->tb[k])) != ALLEGRO_OK) return s;
+    fan = a.tb[k];
+  }
+  std::vector<float> W01((size_t)2 * nw * a.tb.back());
+  memcpy(W01.data(), Wemb.data(), Wemb.size() * 4);
+  memcpy(W01.data() + Wemb.size(), Wenv[0].data(), Wenv[0].size() * 4);
+  if ((s = upload_lin(c, W01, 2 * nw, a.tb.back(), c->w01)) != ALLEGRO_OK) return s;
+  if (a.nl == 2 && (s = upload_lin(c, Wenv[1], nw, a.lat.back(), c->env2)) != ALLEGRO_OK) return s;
+  c->lat.assign(a.nl, std::vector<Lin>(nlat));
+  for (int L = 1; L <= a.nl; ++L) {
+    fan = a.Klat(L - 1) + a.C;
+    for (int k = 0; k < nlat; ++k) {
+      if ((s = upload_lin(c, Wlat[L - 1][k], a.lat[k], fan, c->lat[L - 1][k])) != ALLEGRO_OK) return s;
+      fan = a.lat[k];
+    }
+  }
+  // linear edge-energy MLP folded into one vector: E_ij = v . x  (float64 product)
+  std::vector<double> rvec(1, 1.0);
+  for (int k = ned; k >= 0; --k) {
+    int out = (k < ned) ? a.edge[k] : 1;
+    int in = (k > 0) ? a.edge[k - 1] : a.lat.back();
+    std::vector<double> nx(in, 0.0);
+    for (int o = 0; o < out; ++o)
+      for (int i = 0; i < in; ++i) nx[i] += rvec[o] * (double)Wedge[k][(size_t)o * in + i];
+    rvec.swap(nx);
+  }
+  std::vector<float> v(rvec.begin(), rvec.end());
+  CUDA_TRY(c, cudaMalloc(&c->d_v, v.size() * 4));
+  c->weight_allocs.push_back(c->d_v);
+  CUDA_TRY(c, cudaMemcpy(c->d_v, v.data(), v.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMalloc(&c->d_sigma, a.ns * 8));
+  c->weight_allocs.push_back(c->d_sigma);
+  CUDA_TRY(c, cudaMalloc(&c->d_mu, a.ns * 8));
+  c->weight_allocs.push_back(c->d_mu);
+  CUDA_TRY(c, cudaMemcpy(c->d_sigma, sigma.data(), a.ns * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_mu, mu.data(), a.ns * 8, cudaMemcpyHostToDevice));
+
+  // tensor-product constants
+  const int S = a.S();
+  memset(&c->tp, 0, sizeof(c->tp));
+  c->tp.nu = (float)(1.0 / sqrt(a.ann));
+  int nin, nout;
+  if (a.nl == 2) {
+    std::vector<double> W;
+    fused_layer_tensor(a.lmax, theta[0].data(), W, nin, nout, false);
+    for (int p = 0; p < S; ++p)
+      for (int b = 0; b < S; ++b)
+        for (int q = 0; q < S; ++q) c->tp.W1[(p * S + b) * S + q] = (float)W[((size_t)p * S + b) * S + q];
+  }
+  {
+    std::vector<double> W;
+    fused_layer_tensor(a.lmax, theta[a.nl - 1].data(), W, nin, nout, true);
+    for (int p = 0; p < S; ++p)
+      for (int b = 0; b < S; ++b) {
+        double w = W[(size_t)p * S + b];
+        if (p == b) c->tp.clast[p] = (float)w;
+        else if (fabs(w) > 1e-12) return fail(c, ALLEGRO_E_INVALID, "internal: last-layer tensor not diagonal");
+      }
+  }
+  return ALLEGRO_OK;
+}
+
+// ------------------------------------------------------------------------
+// chunk workspace
+// ------------------------------------------------------------------------
+struct WS {
+  // activations (act = float or bf16) and float32 buffers, per chunk edge
+  void* h0; int ld_h0;
+  std::vector<void*> Ztb; std::vector<int> ld_Ztb;
+  void* H[2]; int ld_H;
+  void* X[2]; int ld_X[2];
+  void* Xlast; int ld_Xlast;
+  std::vector<std::vector<void*>> Zlat; std::vector<int> ld_Zlat;
+  float* W01; int ld_W01;
+  float* w2; int ld_w2;
+  float* D[2]; int ld_D[2];
+  void* wbar01; int ld_wbar01;
+  void* wbar2; int ld_wbar2;
+  float* xbar; int ld_xbar;
+  float* inbar; int ld_inbar;
+  float* Y; float* Ybar; float* u; float* ubar;
+  float* G1; float* G2;
+};
+
+// Lays the workspace out over `base` (or only measures it when base is null).
+size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* base, WS* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const int ntb = (int)a.tb.size(), nlat = (int)a.lat.size();
+  int maxw = 0;
+  for (int x : a.tb) maxw = std::max(maxw, x);
+  for (int x : a.lat) maxw = std::max(maxw, x);
+  const int nw = a.n_w(), S = a.S();
+  w->ld_h0 = pad8(a.K0in());
+  w->h0 = take((size_t)Ec * w->ld_h0 * act_bytes);
+  w->Ztb.resize(ntb); w->ld_Ztb.resize(ntb);
+  for (int k = 0; k < ntb; ++k) {
+    w->ld_Ztb[k] = pad8(a.tb[k]);
+    w->Ztb[k] = take((size_t)Ec * w->ld_Ztb[k] * act_bytes);
+  }
+  w->ld_H = pad8(maxw);
+  w->H[0] = take((size_t)Ec * w->ld_H * act_bytes);
+  w->H[1] = take((size_t)Ec * w->ld_H * act_bytes);
+  for (int L = 0; L < a.nl; ++L) {
+    w->ld_X[L] = pad8(a.Klat(L) + a.C);
+    w->X[L] = take((size_t)Ec * w->ld_X[L] * act_bytes);
+    w->ld_D[L] = w->ld_X[L];
+    w->D[L] = (float*)take((size_t)Ec * w->ld_D[L] * 4);
+  }
+  w->ld_Xlast = pad8(a.lat.back());
+  w->Xlast = take((size_t)Ec * w->ld_Xlast * act_bytes);
+  w->Zlat.assign(a.nl, std::vector<void*>(nlat));
+  w->ld_Zlat.resize(nlat);
+  for (int k = 0; k < nlat; ++k) w->ld_Zlat[k] = pad8(a.lat[k]);
+  for (int L = 0; L < a.nl; ++L)
+    for (int k = 0; k < nlat; ++k) w->Zlat[L][k] = take((size_t)Ec * w->ld_Zlat[k] * act_bytes);
+  w->ld_W01 = pad8(2 * nw);
+  w->W01 = (float*)take((size_t)Ec * w->ld_W01 * 4);
+  w->ld_w2 = pad8(nw);
+  w->w2 = (a.nl == 2) ? (float*)take((size_t)Ec * w->ld_w2 * 4) : nullptr;
+  w->ld_wbar01 = pad8(2 * nw);
+  w->wbar01 = take((size_t)Ec * w->ld_wbar01 * act_bytes);
+  w->ld_wbar2 = pad8(nw);
+  w->wbar2 = (a.nl == 2) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
+  w->ld_xbar = pad8(std::max(a.tb.back(), a.lat.back()));
+  w->xbar = (float*)take((size_t)Ec * w->ld_xbar * 4);
+  w->ld_inbar = pad8(a.K0in());
+  w->inbar = (float*)take((size_t)Ec * w->ld_inbar * 4);
+  w->Y = (float*)take((size_t)Ec * S * 4);
+  w->Ybar = (float*)take((size_t)Ec * S * 4);
+  w->u = (float*)take((size_t)Ec * 4);
+  w->ubar = (float*)take((size_t)Ec * 4);
+  w->G1 = (float*)take((size_t)Ac * a.C * S * 4);
+  w->G2 = (float*)take((size_t)Ac * a.C * S * 4);
+  return off + 256;
+}
+
+allegro_status ensure_ws(allegro_ctx* c, int64_t Ec, int64_t Ac, WS* w) {
+  const int act_bytes = (c->prec == ALLEGRO_PREC_BF16) ? 2 : 4;
+  if (Ec > c->ws_edges || Ac > c->ws_atoms || !c->ws) {
+    int64_t E2 = std::max<int64_t>(Ec, c->ws_edges), A2 = std::max<int64_t>(Ac, c->ws_atoms);
+    E2 = std::max<int64_t>((int64_t)(E2 * 1.05) + 64, 256);
+    A2 = std::max<int64_t>((int64_t)(A2 * 1.05) + 16, 64);
+    size_t bytes = layout_ws(c->arch, act_bytes, E2, A2, nullptr, w);
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_edges = c->ws_atoms = 0;
+    CUDA_TRY(c, cudaMalloc(&c->ws, bytes));
+    CUDA_TRY(c, cudaMemset(c->ws, 0, bytes));
+    c->ws_bytes = bytes;
+    c->ws_edges = E2;
+    c->ws_atoms = A2;
+  }
+  layout_ws(c->arch, act_bytes, c->ws_edges, c->ws_atoms,
+            reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(c->ws) + 255) & ~uintptr_t(255)), w);
+  return ALLEGRO_OK;
+}
+
+int64_t ws_bytes_per_edge(const allegro_ctx* c) {
+  WS w;
+  const int act_bytes = (c->prec == ALLEGRO_PREC_BF16) ? 2 : 4;
+  size_t b1 = layout_ws(c->arch, act_bytes, 1 << 16, 1, nullptr, &w);
+  return (int64_t)(b1 / (1 << 16)) + 1;
+}
+
+// ------------------------------------------------------------------------
+// input staging
+// ------------------------------------------------------------------------
+allegro_status stage_atoms(allegro_ctx* c, int64_t n, const double* pos, const int32_t* types) {
+  Caps& k = caps_of(c);
+  const int64_t need = std::max<int64_t>(n, 1);
+  CUDA_TRY(c, grow(c->d_pos, k.pos, 3 * need));
+  CUDA_TRY(c, grow(c->d_types, k.types, need));
+  CUDA_TRY(c, grow(c->d_species, k.species, need));
+  CUDA_TRY(c, grow(c->d_row_ptr, k.row_ptr, need + 1));
+  CUDA_TRY(c, grow(c->d_col_ptr, k.col_ptr, need + 1));
+  CUDA_TRY(c, grow(c->d_count, k.count, need + 1));
+  CUDA_TRY(c, grow(c->d_cell_of, k.cell_of, need));
+  CUDA_TRY(c, grow(c->d_wrap, k.wrap, 3 * need));
+  CUDA_TRY(c, grow(c->d_sorted, k.sorted, need));
+  CUDA_TRY(c, grow(c->d_atom_struct, k.atom_struct, need));
+  CUDA_TRY(c, grow(c->d_Eatom, k.Eatom, need));
+  CUDA_TRY(c, grow(c->d_F, k.F, 3 * need));
+  CUDA_TRY(c, grow(c->d_Wat, k.Wat, 9 * need));
+  size_t st = scan_tmp_bytes((int)std::max<int64_t>(need, 4096)) + 4096;
+  if (st > c->scan_tmp_cap) {
+    if (c->d_scan_tmp) cudaFree(c->d_scan_tmp);
+    c->d_scan_tmp = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_scan_tmp, st * 2));
+    c->scan_tmp_cap = st * 2;
+  }
+  if (n > 0) {
+    cudaMemcpyKind kp = is_device_ptr(pos) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyKind kt = is_device_ptr(types) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_pos, pos, (size_t)n * 3 * 8, kp, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_types, types, (size_t)n * 4, kt, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    map_types_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->d_types, c->d_pos, (int)n, c->d_map,
+                                                                         c->nmap, c->d_species, c->d_err);
+    CUDA_TRY(c, cudaGetLastError());
+  } else {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  }
+  return ALLEGRO_OK;
+}
+
+allegro_status ensure_structs(allegro_ctx* c, int64_t nstruct) {
+  Caps& k = caps_of(c);
+  int64_t need = std::max<int64_t>(nstruct, 1);
+  CUDA_TRY(c, grow(c->d_offs, k.offs, need + 1));
+  CUDA_TRY(c, grow(c->d_cells, k.cells, 9 * need));
+  CUDA_TRY(c, grow(c->d_pbc, k.pbc, 3 * need));
+  CUDA_TRY(c, grow(c->d_nimg, k.nimg, 3 * need));
+  CUDA_TRY(c, grow(c->d_Eout, k.Eout, need));
+  CUDA_TRY(c, grow(c->d_Wout, k.Wout, 9 * need));
+  return ALLEGRO_OK;
+}
+
+allegro_status ensure_edges(allegro_ctx* c, int64_t E) {
+  if (c->fixed && c->edge_cap > 0 && E > c->edge_cap)
+    return fail(c, ALLEGRO_E_CAPACITY, "neighbour list needs %lld edges, capacity is %lld", (long long)E,
+                (long long)c->edge_cap);
+  if (E > 2000000000LL) return fail(c, ALLEGRO_E_CAPACITY, "%lld edges exceed the int32 edge index", (long long)E);
+  Caps& k = caps_of(c);
+  int64_t need = std::max<int64_t>(std::max<int64_t>(E, c->fixed ? c->edge_cap : 0), 1);
+  CUDA_TRY(c, grow(c->d_ej, k.ej, need));
+  CUDA_TRY(c, grow(c->d_ei, k.ei, need));
+  CUDA_TRY(c, grow(c->d_eS, k.eS, 3 * need));
+  CUDA_TRY(c, grow(c->d_ed, k.ed, 3 * need));
+  CUDA_TRY(c, grow(c->d_col_edge, k.col_edge, need));
+  CUDA_TRY(c, grow(c->d_Ee, k.Ee, need));
+  CUDA_TRY(c, grow(c->d_g, k.g, 3 * need));
+  return ALLEGRO_OK;
+}
+
+allegro_status read_err(allegro_ctx* c, int* out) {
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = h;
+  return ALLEGRO_OK;
+}
+
+// CSC index and host row_ptr copy, shared by both neighbour paths.
+allegro_status finish_neighbors(allegro_ctx* c, int n, int64_t E) {
+  cudaStream_t st = c->stream;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_count, 0, (size_t)(n + 1) * 4, st));
+  {
+    ProfScope ps(c, "nb_csc", 0.0, (double)E * 16 + (double)n * 16, 6);
+    nb_columns(c->d_ej, (int)E, n, c->d_count, st);
+    exclusive_scan_i32(c->d_count, c->d_col_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_count, 0, (size_t)(n + 1) * 4, st));
+    nb_fill_columns(c->d_ej, (int)E, c->d_col_ptr, c->d_count, c->d_col_edge, st);
+    nb_sort_columns(c->d_col_ptr, n, c->d_col_edge, st);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  c->h_row_ptr.resize((size_t)n + 1);
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_row_ptr.data(), c->d_row_ptr, (size_t)(n + 1) * 4, cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  allegro_status s = read_err(c, &err);
+  if (s != ALLEGRO_OK) return s;
+  if (err & kErrBadInput)
+    return fail(c, ALLEGRO_E_INVALID, "a type is outside the species map or a position is not finite");
+  if (err & kErrNeighbor) return fail(c, ALLEGRO_E_CUDA, "internal: neighbour fill pass disagreed with its count");
+  c->n_atoms = n;
+  c->n_edges = E;
+  c->have_nb = true;
+  return ALLEGRO_OK;
+}
+
+void widths_of(const double* cell, double w[3]) {
+  const double* a = cell;
+  const double* b = cell + 3;
+  const double* cc = cell + 6;
+  auto cross = [](const double* x, const double* y, double* o) {
+    o[0] = x[1] * y[2] - x[2] * y[1];
+    o[1] = x[2] * y[0] - x[0] * y[2];
+    o[2] = x[0] * y[1] - x[1] * y[0];
+  };
+  double bc[3], ca[3], ab[3];
+  cross(b, cc, bc); cross(cc, a, ca); cross(a, b, ab);
+  double vol = fabs(a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]);
+  auto nrm = [](const double* x) { return sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]); };
+  w[0] = vol / nrm(bc); w[1] = vol / nrm(ca); w[2] = vol / nrm(ab);
+}
+
+bool invert3(const double* m, double* inv) {
+  double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+               m[2] * (m[3] * m[7] - m[4] * m[6]);
+  if (!(fabs(det) > 0) || !std::isfinite(det)) return false;
+  double id = 1.0 / det;
+  inv[0] = (m[4] * m[8] - m[5] * m[7]) * id;
+  inv[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+  inv[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+  inv[3] = (m[5] * m[6] - m[3] * m[8]) * id;
+  inv[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+  inv[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+  inv[6] = (m[3] * m[7] - m[4] * m[6]) * id;
+  inv[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+  inv[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+  return true;
+}
+
+template <typename T>
+allegro_status gemm(allegro_ctx* c, GemmArgs g) {
+  if (c->prec == ALLEGRO_PREC_BF16) {
+    std::string why;
+    if (!gemm_tc_bf16(g, c->stream, c->d_err, &why)) return fail(c, ALLEGRO_E_CUDA, "tcgen05 GEMM: %s", why.c_str());
+  } else {
+    gemm_simt_f32(g, c->stream);
+  }
+  return ALLEGRO_OK;
+}
+
+// ------------------------------------------------------------------------
+// model evaluation of one chunk of whole rows
+// ------------------------------------------------------------------------
+template <typename T>
+allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, int e1, bool backward) {
+  const Arch& a = c->arch;
+  cudaStream_t st = c->stream;
+  const int Ec = e1 - e0, Ac = a1 - a0;
+  if (Ec <= 0) return ALLEGRO_OK;
+  const int ntb = (int)a.tb.size(), nlat = (int)a.lat.size(), nl = a.nl, nw = a.n_w();
+  allegro_status s;
+  const double act = sizeof(T);
+  auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
+               void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
+               int ld_add = 0) {
+    const double outb = (epi == EPI_F32) ? 4.0 : act;
+    const double bytes = (double)Ec * (K * act + N * outb + (pre ? N * act : 0.0) + (add ? N * 4.0 : 0.0) +
+                                       (rowscale ? 4.0 : 0.0)) + (double)N * K * act;
+    ProfScope ps(c, c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc" : "gemm_simt", 2.0 * Ec * (double)N * K, bytes);
+    GemmArgs g;
+    g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
+    g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
+    return gemm<T>(c, g);
+  };
+  RowIO io;
+  io.a0 = a0; io.na = Ac; io.e0 = e0; io.row_ptr = c->d_row_ptr; io.C = a.C;
+  io.Y = w.Y; io.W01 = w.W01; io.ld01 = w.ld_W01; io.w2 = w.w2; io.ld2 = w.ld_w2; io.G1 = w.G1; io.G2 = w.G2;
+
+  const int S = a.S(), C = a.C;
+  // algorithmic bytes of the row kernels (per edge, per atom), float32 features
+  auto row_scope = [&](const char* name, double per_edge, double per_atom) {
+    return ProfScope(c, name, 0.0, (double)Ec * per_edge + (double)Ac * per_atom);
+  };
+  // ---- forward ----
+  {
+    ProfScope ps(c, "geom_fwd", 0.0, (double)Ec * (24 + 8 + 8 + S * 4 + 4 + w.ld_h0 * act));
+    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, (T*)w.h0, w.ld_h0, st);
+  }
+  const void* in = w.h0;
+  int ld_in = w.ld_h0, K = a.K0in();
+  for (int k = 0; k < ntb; ++k) {
+    const bool last = (k == ntb - 1);
+    void* out = last ? w.X[0] : w.H[k & 1];
+    int ldo = last ? w.ld_X[0] : w.ld_H;
+    if ((s = G(in, ld_in, K, c->tb[k], false, EPI_FWD_SILU, out, ldo, a.tb[k], w.Ztb[k], w.ld_Ztb[k],
+               last ? w.u : nullptr)) != ALLEGRO_OK)
+      return s;
+    in = out; ld_in = ldo; K = a.tb[k];
+  }
+  if ((s = G(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_F32, w.W01, w.ld_W01, 2 * nw)) != ALLEGRO_OK)
+    return s;
+  for (int L = 1; L <= nl; ++L) {
+    io.xs = w.X[L - 1]; io.ldxs = w.ld_X[L - 1]; io.xs_off = a.Klat(L - 1);
+    {
+      const double pe = (L < nl) ? (2.0 * nw * 4 + S * 4 + C * act)
+                                 : ((L == 1 ? 2.0 : 3.0) * nw * 4 + S * 4 + C * act);
+      const double pa = (L < nl) ? C * S * 4.0 : (L == 1 ? 1.0 : 2.0) * C * S * 4.0;
+      auto ps = row_scope(L < nl ? "row_fwd_mid" : "row_fwd_last", pe, pa);
+      row_fwd<T>(L, nl, a.lmax, io, c->tp, st);
+    }
+    in = w.X[L - 1]; ld_in = w.ld_X[L - 1]; K = a.Klat(L - 1) + a.C;
+    for (int k = 0; k < nlat; ++k) {
+      const bool last = (k == nlat - 1);
+      void* out = last ? (L < nl ? w.X[L] : w.Xlast) : w.H[k & 1];
+      int ldo = last ? (L < nl ? w.ld_X[L] : w.ld_Xlast) : w.ld_H;
+      if ((s = G(in, ld_in, K, c->lat[L - 1][k], false, EPI_FWD_SILU, out, ldo, a.lat[k], w.Zlat[L - 1][k],
+                 w.ld_Zlat[k], last ? w.u : nullptr)) != ALLEGRO_OK)
+        return s;
+      in = out; ld_in = ldo; K = a.lat[k];
+    }
+    if (L < nl) {
+      if ((s = G(w.X[L], w.ld_X[L], a.lat.back(), c->env2, false, EPI_F32, w.w2, w.ld_w2, nw)) != ALLEGRO_OK)
+        return s;
+    }
+  }
+  {
+    ProfScope ps(c, "edge_energy", 0.0, (double)Ec * (a.lat.back() * act + 4));
+    edge_energy<T>(Ec, a.lat.back(), (const T*)w.Xlast, w.ld_Xlast, c->d_v, c->d_Ee + e0, st);
+  }
+  if (!backward) return ALLEGRO_OK;
+
+  // ---- adjoint ----
+  // latent MLP of the last layer: xbar = sigma_{Z_i} v
+  {
+    ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * 2 * act + 16));
+    mlp_head_bwd<T>(Ec, a.lat.back(), nullptr, 0, c->d_v, c->d_ei, c->d_species, c->d_sigma, e0,
+                    (const T*)w.Zlat[nl - 1][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, true, (T*)w.H[0], w.ld_H,
+                    st);
+  }
+  auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
+                      int nlay, float* dst, int ld_dst, int Kin) -> allegro_status {
+    int cur = 0;
+    for (int k = nlay - 1; k >= 0; --k) {
+      const Lin& W = layers[k];
+      allegro_status r;
+      if (k > 0) {
+        r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]);
+        cur ^= 1;
+      } else {
+        r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_F32, dst, ld_dst, Kin);
+      }
+      if (r != ALLEGRO_OK) return r;
+    }
+    return ALLEGRO_OK;
+  };
+  if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
+                    a.Klat(nl - 1) + a.C)) != ALLEGRO_OK)
+    return s;
+  io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2; io.Ybar = w.Ybar;
+  if (nl == 1) {
+    io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
+    auto ps = row_scope("row_bwd_last", 2.0 * nw * 4 + C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
+    row_bwd<T>(1, 1, a.lmax, io, c->tp, st);
+  } else {
+    io.sbar2 = w.D[1] + a.Klat(1); io.ld_sbar2 = w.ld_D[1];
+    {
+      auto ps = row_scope("row_bwd_last", 2.0 * nw * 4 + C * 4 + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
+      row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
+    }
+    // xbar^1 = wbar^2 . env2 + D[1][:, :K1]
+    if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_F32, w.xbar, w.ld_xbar, a.lat.back(), nullptr, 0,
+               nullptr, w.D[1], w.ld_D[1])) != ALLEGRO_OK)
+      return s;
+    {
+      ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * (4 + 2 * act) + 12));
+      mlp_head_bwd<T>(Ec, a.lat.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
+                      (const T*)w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H,
+                      st);
+    }
+    if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C)) != ALLEGRO_OK)
+      return s;
+    io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
+    auto ps = row_scope("row_bwd_mid", 2.0 * nw * 4 + 2.0 * C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4,
+                        2.0 * C * S * 4);
+    row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
+  }
+  // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0]
+  if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_F32, w.xbar, w.ld_xbar, a.tb.back(), nullptr, 0,
+             nullptr, w.D[0], w.ld_D[0])) != ALLEGRO_OK)
+    return s;
+  {
+    ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.tb.back() * (4 + 2 * act) + 12));
+    mlp_head_bwd<T>(Ec, a.tb.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
+                    (const T*)w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);
+  }
+  if ((s = back_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, w.inbar, w.ld_inbar, a.K0in())) != ALLEGRO_OK) return s;
+  {
+    ProfScope ps(c, "geom_bwd", 0.0, (double)Ec * (24 + a.nb * 4 + 4 + S * 4 + 12));
+    edge_geom_bwd(Ec, e0, c->d_ed, a, w.inbar, w.ld_inbar, w.ubar, w.Ybar, c->d_g, st);
+  }
+  return ALLEGRO_OK;
+}
+
+allegro_status evaluate(allegro_ctx* c, bool backward) {
+  const int n = (int)c->n_atoms;
+  const int64_t E = c->n_edges;
+  // chunks of whole rows
+  int64_t budget = c->chunk_edges_user;
+  if (budget <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    int64_t per = ws_bytes_per_edge(c);
+    int64_t cap_bytes = std::min<int64_t>((int64_t)(fr * 0.5) + (int64_t)c->ws_bytes, 48ll << 30);
+    budget = std::max<int64_t>(cap_bytes / std::max<int64_t>(per, 1), 1 << 16);
+  }
+  std::vector<int> bounds{0};
+  {
+    int a = 0;
+    while (a < n) {
+      int64_t start = c->h_row_ptr[a];
+      int b = a + 1;
+      // largest b with row_ptr[b] - start <= budget (at least one row)
+      int lo = a + 1, hi = n;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if ((int64_t)c->h_row_ptr[mid] - start <= budget) lo = mid;
+        else hi = mid - 1;
+      }
+      b = std::max(lo, a + 1);
+      bounds.push_back(b);
+      a = b;
+    }
+    if (n == 0) bounds.push_back(0);
+  }
+  int64_t maxE = 1, maxA = 1;
+  for (size_t q = 0; q + 1 < bounds.size(); ++q) {
+    maxE = std::max<int64_t>(maxE, (int64_t)c->h_row_ptr[bounds[q + 1]] - c->h_row_ptr[bounds[q]]);
+    maxA = std::max<int64_t>(maxA, bounds[q + 1] - bounds[q]);
+  }
+  WS w;
+  allegro_status s = ensure_ws(c, maxE, maxA, &w);
+  if (s != ALLEGRO_OK) return s;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  for (size_t q = 0; q + 1 < bounds.size(); ++q) {
+    int a0 = bounds[q], a1 = bounds[q + 1];
+    int e0 = c->h_row_ptr[a0], e1 = c->h_row_ptr[a1];
+    s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk<bf16>(c, w, a0, a1, e0, e1, backward)
+                                       : run_chunk<float>(c, w, a0, a1, e0, e1, backward);
+    if (s != ALLEGRO_OK) return s;
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  {
+    ProfScope ps(c, "atom_reduce", 0.0, (double)E * (backward ? 60.0 : 4.0) + (double)n * (backward ? 128.0 : 16.0));
+    atom_reduce(n, c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_Ee, c->d_g, c->d_ed, c->d_species, c->d_sigma,
+                c->d_mu, backward, c->d_Eatom, c->d_F, c->d_Wat, c->stream);
+  }
+  {
+    ProfScope ps(c, "struct_reduce", 0.0, (double)n * (backward ? 104.0 : 8.0));
+    struct_reduce(c->nstruct, c->d_offs, c->d_Eatom, c->d_Wat, c->d_F, backward, c->d_Eout, c->d_Wout, c->d_err,
+                  c->stream);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return ALLEGRO_OK;
+}
+
+allegro_status copy_out(allegro_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return ALLEGRO_OK;
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+  return ALLEGRO_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const int32_t* species_map,
+                              int32_t n_types, double r_c, int32_t precision, int32_t device, allegro_ctx** out) {
+  if (!out) return ALLEGRO_E_INVALID;
+  *out = nullptr;
+  if (!weights_blob || blob_bytes == 0) return ALLEGRO_E_INVALID;
+  if (precision != ALLEGRO_PREC_FP32 && precision != ALLEGRO_PREC_BF16) return ALLEGRO_E_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return ALLEGRO_E_CUDA;
+  }
+  allegro_ctx* c = new allegro_ctx();
+  c->device = device;
+  c->prec = precision;
+  auto bail = [&](allegro_status s) {
+    fprintf(stderr, "allegro_create: %s\n", c->err.c_str());
+    allegro_destroy(c);
+    return s;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(fail(c, ALLEGRO_E_CUDA, "cudaSetDevice failed"));
+  if (precision == ALLEGRO_PREC_BF16) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    if (prop.major != 10 || prop.minor != 3)
+      return bail(fail(c, ALLEGRO_E_INVALID, "BF16 path needs sm_103 (found sm_%d%d)", prop.major, prop.minor));
+    std::string why;
+    if (!gemm_tc_init(&why)) return bail(fail(c, ALLEGRO_E_CUDA, "%s", why.c_str()));
+  }
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(c, ALLEGRO_E_CUDA, "cudaStreamCreate failed"));
+  c->stream = c->own_stream;
+  allegro_status s = load_model(c, weights_blob, blob_bytes);
+  if (s != ALLEGRO_OK) return bail(s);
+  if (r_c > 0 && fabs(r_c - c->arch.rc) > 1e-12 * c->arch.rc)
+    return bail(fail(c, ALLEGRO_E_INVALID, "r_c %g differs from the model cutoff %g", r_c, c->arch.rc));
+  // species map
+  if (species_map) {
+    if (n_types <= 0) return bail(fail(c, ALLEGRO_E_INVALID, "n_types must be positive"));
+    for (int t = 0; t < n_types; ++t) {
+      if (species_map[t] < 0 || species_map[t] >= c->arch.ns)
+        return bail(fail(c, ALLEGRO_E_INVALID, "species_map[%d] = %d out of range", t, species_map[t]));
+      c->species_map.push_back(species_map[t]);
+    }
+  } else {
+    for (int t = 0; t < c->arch.ns; ++t) c->species_map.push_back(t);
+  }
+  c->nmap = (int)c->species_map.size();
+  if (cudaMalloc(&c->d_map, c->nmap * 4) != cudaSuccess ||
+      cudaMemcpy(c->d_map, c->species_map.data(), c->nmap * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(c, ALLEGRO_E_OOM, "species map upload failed"));
+  if (cudaMalloc(&c->d_err, 16) != cudaSuccess || cudaMalloc(&c->d_total, 16) != cudaSuccess ||
+      cudaMalloc(&c->d_minmax, 12 * 8) != cudaSuccess)
+    return bail(fail(c, ALLEGRO_E_OOM, "scratch allocation failed"));
+  cudaMemset(c->d_err, 0, 16);
+  *out = c;
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_set_stream(allegro_ctx* c, void* stream) {
+  if (!c) return ALLEGRO_E_INVALID;
+  c->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : c->own_stream;
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_reserve(allegro_ctx* c, int64_t atom_cap, int64_t edge_cap, int32_t fixed,
+                               int64_t chunk_edges) {
+  if (!c || atom_cap < 0 || edge_cap < 0 || chunk_edges < 0) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  c->fixed = fixed != 0;
+  c->atom_cap = atom_cap;
+  c->edge_cap = edge_cap;
+  c->chunk_edges_user = chunk_edges;
+  if (atom_cap > 0) {
+    allegro_status s = stage_atoms(c, 0, nullptr, nullptr);
+    if (s != ALLEGRO_OK) return s;
+    Caps& k = caps_of(c);
+    CUDA_TRY(c, grow(c->d_pos, k.pos, 3 * atom_cap));
+  }
+  if (edge_cap > 0) {
+    bool f = c->fixed;
+    c->fixed = false;
+    allegro_status s = ensure_edges(c, edge_cap);
+    c->fixed = f;
+    if (s != ALLEGRO_OK) return s;
+  }
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* pos, const int32_t* types,
+                                 const double* cell, const uint8_t* pbc, int64_t* n_edges_out) {
+  if (!c) return ALLEGRO_E_INVALID;
+  c->have_nb = false;
+  if (n_atoms < 0 || n_atoms > 1000000000LL) return fail(c, ALLEGRO_E_INVALID, "bad n_atoms");
+  if (n_atoms > 0 && (!pos || !types)) return fail(c, ALLEGRO_E_INVALID, "pos and types are required");
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  const int n = (int)n_atoms;
+  allegro_status s = stage_atoms(c, n, pos, types);
+  if (s != ALLEGRO_OK) return s;
+  if ((s = ensure_structs(c, 1)) != ALLEGRO_OK) return s;
+  int64_t hoffs[2] = {0, n};
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_offs, hoffs, sizeof hoffs, cudaMemcpyHostToDevice, st));
+  c->nstruct = 1;
+  c->batched = false;
+
+  // cell and periodicity (host copies)
+  double hcell[9] = {0};
+  uint8_t hpbc[3] = {0, 0, 0};
+  if (cell) {
+    if (is_device_ptr(cell)) CUDA_TRY(c, cudaMemcpy(hcell, cell, sizeof hcell, cudaMemcpyDeviceToHost));
+    else memcpy(hcell, cell, sizeof hcell);
+    for (double v : hcell)
+      if (!std::isfinite(v)) return fail(c, ALLEGRO_E_INVALID, "cell is not finite");
+  }
+  if (pbc) {
+    if (is_device_ptr(pbc)) CUDA_TRY(c, cudaMemcpy(hpbc, pbc, 3, cudaMemcpyDeviceToHost));
+    else memcpy(hpbc, pbc, 3);
+  } else if (cell) {
+    hpbc[0] = hpbc[1] = hpbc[2] = 1;
+  }
+  CellGrid g{};
+  const double rc = c->arch.rc, rcm = rc * (1.0 + 1e-6);
+  double width[3] = {1, 1, 1};
+  if (cell) {
+    if (!invert3(hcell, g.inv)) return fail(c, ALLEGRO_E_INVALID, "cell is singular");
+    widths_of(hcell, width);
+    memcpy(g.cell, hcell, sizeof hcell);
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      if (hpbc[k]) return fail(c, ALLEGRO_E_INVALID, "a periodic axis needs a cell");
+      g.inv[k * 3 + k] = 1.0;
+    }
+  }
+  bool any_np = false;
+  for (int k = 0; k < 3; ++k) {
+    g.pbc[k] = hpbc[k] ? 1 : 0;
+    any_np |= !g.pbc[k];
+  }
+  double hmm[6] = {0, 0, 0, 0, 0, 0};
+  if (any_np && n > 0) {
+    nb_minmax_frac(c->d_pos, n, g.inv, c->d_minmax, st);
+    CUDA_TRY(c, cudaMemcpyAsync(hmm, c->d_minmax, 6 * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+  }
+  int64_t ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    double ext;
+    if (g.pbc[k]) {
+      ext = width[k];
+      g.lo[k] = 0; g.span[k] = 1;
+    } else {
+      double lo = hmm[k], hi = hmm[3 + k];
+      if (!(hi >= lo)) { lo = 0; hi = 0; }
+      g.lo[k] = lo;
+      g.span[k] = (hi - lo) * (1.0 + 1e-9) + 1e-300;
+      ext = (hi - lo) * (cell ? width[k] : 1.0);
+    }
+    int64_t nk = (int64_t)floor(ext / rcm);
+    nk = std::max<int64_t>(1, std::min<int64_t>(nk, 4096));
+    g.n[k] = (int)nk;
+    g.R[k] = (g.pbc[k] && ext / nk < rcm) ? (int)ceil(rcm * nk / ext) : 1;
+    ncell *= nk;
+  }
+  // very sparse grids: coarsen (larger cells stay >= r_c wide, so the stencil still covers r_c)
+  const int64_t max_cells = std::max<int64_t>(4 * (int64_t)n, 64);
+  while (ncell > max_cells) {
+    int kmax = 0;
+    for (int k = 1; k < 3; ++k) if (g.n[k] > g.n[kmax]) kmax = k;
+    g.n[kmax] = std::max(1, g.n[kmax] / 2);
+    ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  }
+  Caps& k = caps_of(c);
+  CUDA_TRY(c, grow(c->d_cell_count, k.cc, ncell + 1));
+  CUDA_TRY(c, grow(c->d_cell_start, k.cs, ncell + 1));
+  CUDA_TRY(c, grow(c->d_cell_cursor, k.ccur, ncell + 1));
+  size_t need_tmp = scan_tmp_bytes((int)std::max<int64_t>(ncell, n)) + 4096;
+  if (need_tmp > c->scan_tmp_cap) {
+    if (c->d_scan_tmp) cudaFree(c->d_scan_tmp);
+    c->d_scan_tmp = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_scan_tmp, need_tmp * 2));
+    c->scan_tmp_cap = need_tmp * 2;
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->d_cell_count, 0, (size_t)(ncell + 1) * 4, st));
+  {
+    ProfScope ps(c, "nb_bin_sort", 0.0, (double)n * 80 + (double)ncell * 16, 7);
+    nb_bin(c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_count, st);
+    exclusive_scan_i32(c->d_cell_count, c->d_cell_start, (int)ncell, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cursor, 0, (size_t)(ncell + 1) * 4, st));
+    nb_place(c->d_cell_of, n, c->d_cell_start, c->d_cell_cursor, c->d_sorted, st);
+    nb_sort_cells(c->d_cell_start, (int)ncell, c->d_sorted, st);
+  }
+  const double rc2 = rc * rc;
+  {
+    ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
+    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, rc2, c->d_count,
+              nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
+    exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
+  }
+  int hE = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&hE, c->d_row_ptr + n, 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  CUDA_TRY(c, cudaGetLastError());
+  if (hE < 0) return fail(c, ALLEGRO_E_CAPACITY, "edge count overflows int32");
+  if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
+  {
+    ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
+    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, rc2, nullptr,
+              c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
+  }
+  if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
+  if (n_edges_out) *n_edges_out = hE;
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_neighbors_batched(allegro_ctx* c, int32_t n_struct, const int64_t* atom_offsets,
+                                         const double* pos, const int32_t* types, const double* cells,
+                                         const uint8_t* pbc, int64_t* n_edges_out) {
+  if (!c) return ALLEGRO_E_INVALID;
+  c->have_nb = false;
+  if (n_struct < 1 || !atom_offsets) return fail(c, ALLEGRO_E_INVALID, "n_struct >= 1 and atom_offsets required");
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  std::vector<int64_t> offs((size_t)n_struct + 1);
+  if (is_device_ptr(atom_offsets))
+    CUDA_TRY(c, cudaMemcpy(offs.data(), atom_offsets, offs.size() * 8, cudaMemcpyDeviceToHost));
+  else memcpy(offs.data(), atom_offsets, offs.size() * 8);
+  if (offs[0] != 0) return fail(c, ALLEGRO_E_INVALID, "atom_offsets[0] must be 0");
+  for (int b = 0; b < n_struct; ++b)
+    if (offs[b + 1] < offs[b]) return fail(c, ALLEGRO_E_INVALID, "atom_offsets must be non-decreasing");
+  const int64_t n64 = offs[n_struct];
+  if (n64 > 1000000000LL) return fail(c, ALLEGRO_E_INVALID, "too many atoms");
+  const int n = (int)n64;
+  if (n > 0 && (!pos || !types)) return fail(c, ALLEGRO_E_INVALID, "pos and types are required");
+  allegro_status s = stage_atoms(c, n, pos, types);
+  if (s != ALLEGRO_OK) return s;
+  if ((s = ensure_structs(c, n_struct)) != ALLEGRO_OK) return s;
+  std::vector<double> hc;
+  std::vector<int> hp((size_t)3 * n_struct, 0), hn((size_t)3 * n_struct, 0);
+  if (cells) {
+    hc.resize((size_t)9 * n_struct);
+    if (is_device_ptr(cells)) CUDA_TRY(c, cudaMemcpy(hc.data(), cells, hc.size() * 8, cudaMemcpyDeviceToHost));
+    else memcpy(hc.data(), cells, hc.size() * 8);
+  }
+  std::vector<uint8_t> hpb((size_t)3 * n_struct, cells ? 1 : 0);
+  if (pbc) {
+    if (is_device_ptr(pbc)) CUDA_TRY(c, cudaMemcpy(hpb.data(), pbc, hpb.size(), cudaMemcpyDeviceToHost));
+    else memcpy(hpb.data(), pbc, hpb.size());
+  }
+  const double rc = c->arch.rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_offs, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, st));
+  // image ranges: |S_k| <= ceil(r_c / w_k + span_k), span_k the spread of the
+  // structure's fractional coordinates (positions need not be wrapped)
+  std::vector<double> hinv((size_t)9 * n_struct, 0.0), hspan((size_t)3 * n_struct, 0.0);
+  if (cells) {
+    for (int b = 0; b < n_struct; ++b)
+      if (!invert3(&hc[9 * (size_t)b], &hinv[9 * (size_t)b])) return fail(c, ALLEGRO_E_INVALID, "cell %d is singular", b);
+    double* d_inv = nullptr;
+    double* d_span = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d_inv, hinv.size() * 8));
+    CUDA_TRY(c, cudaMalloc(&d_span, hspan.size() * 8));
+    cudaMemcpyAsync(d_inv, hinv.data(), hinv.size() * 8, cudaMemcpyHostToDevice, st);
+    nb_struct_span(c->d_pos, c->d_offs, d_inv, n_struct, d_span, st);
+    cudaMemcpyAsync(hspan.data(), d_span, hspan.size() * 8, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(d_inv);
+    cudaFree(d_span);
+    if (e != cudaSuccess) return fail(c, ALLEGRO_E_CUDA, "span: %s", cudaGetErrorString(e));
+  }
+  for (int b = 0; b < n_struct; ++b) {
+    double w[3] = {1, 1, 1};
+    if (cells) widths_of(&hc[9 * (size_t)b], w);
+    for (int k = 0; k < 3; ++k) {
+      hp[3 * b + k] = hpb[3 * b + k] ? 1 : 0;
+      if (hp[3 * b + k] && !cells) return fail(c, ALLEGRO_E_INVALID, "a periodic axis needs a cell");
+      hn[3 * b + k] = hp[3 * b + k] ? (int)ceil(rc / w[k] + hspan[3 * b + k]) : 0;
+    }
+  }
+  if (cells) CUDA_TRY(c, cudaMemcpyAsync(c->d_cells, hc.data(), hc.size() * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_pbc, hp.data(), hp.size() * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nimg, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice, st));
+  atom_struct_kernel<<<n_struct, 128, 0, st>>>(c->d_offs, n_struct, c->d_atom_struct);
+  const double rc2 = rc * rc;
+  nb_bruteforce_batched(false, c->d_pos, c->d_offs, n_struct, cells ? c->d_cells : nullptr, c->d_pbc, c->d_nimg, rc2,
+                        c->d_atom_struct, n, c->d_count, nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
+  exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
+  int hE = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&hE, c->d_row_ptr + n, 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  CUDA_TRY(c, cudaGetLastError());
+  if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
+  nb_bruteforce_batched(true, c->d_pos, c->d_offs, n_struct, cells ? c->d_cells : nullptr, c->d_pbc, c->d_nimg, rc2,
+                        c->d_atom_struct, n, nullptr, c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
+  if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
+  c->nstruct = n_struct;
+  c->batched = true;
+  if (n_edges_out) *n_edges_out = hE;
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_energy_forces(allegro_ctx* c, double* E_total, double* E_atom, double* F, double* virial) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (!E_total) return fail(c, ALLEGRO_E_INVALID, "E_total is required");
+  if (!c->have_nb) return fail(c, ALLEGRO_E_STATE, "allegro_neighbors must succeed before energy_forces");
+  cudaSetDevice(c->device);
+  const bool backward = (F != nullptr) || (virial != nullptr);
+  allegro_status s = evaluate(c, backward);
+  if (s != ALLEGRO_OK) return s;
+  const size_t n = (size_t)c->n_atoms, B = (size_t)c->nstruct;
+  if ((s = copy_out(c, E_total, c->d_Eout, B * 8)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, E_atom, c->d_Eatom, n * 8)) != ALLEGRO_OK) return s;
+  if (F && (s = copy_out(c, F, c->d_F, n * 3 * 8)) != ALLEGRO_OK) return s;
+  if (virial && (s = copy_out(c, virial, c->d_Wout, B * 9 * 8)) != ALLEGRO_OK) return s;
+  int err = 0;
+  if ((s = read_err(c, &err)) != ALLEGRO_OK) return s;
+  if (err & kErrTimeout) return fail(c, ALLEGRO_E_TIMEOUT, "a bounded device wait expired; results are invalid");
+  if (err & kErrNonFinite) return fail(c, ALLEGRO_E_NONFINITE, "non-finite energy or force");
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_get_neighbors(allegro_ctx* c, int32_t* i, int32_t* j, int32_t* shift, int64_t cap) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (!c->have_nb) return fail(c, ALLEGRO_E_STATE, "no neighbour list");
+  if (cap < c->n_edges) return fail(c, ALLEGRO_E_CAPACITY, "cap %lld < %lld edges", (long long)cap, (long long)c->n_edges);
+  cudaSetDevice(c->device);
+  const size_t E = (size_t)c->n_edges;
+  allegro_status s;
+  if ((s = copy_out(c, i, c->d_ei, E * 4)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, j, c->d_ej, E * 4)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, shift, c->d_eS, E * 12)) != ALLEGRO_OK) return s;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_profile(allegro_ctx* c, int32_t enable) {
+  if (!c) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->prof.on = enable != 0;
+  c->prof.recs.clear();
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_profile_report(allegro_ctx* c, char* buf, size_t cap, int64_t* launches) {
+  if (!c) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (launches) *launches = c->launches;
+  if (!buf || cap == 0) return ALLEGRO_OK;
+  struct Agg { int n = 0; double ms = 0, flops = 0, bytes = 0; };
+  std::vector<std::pair<std::string, Agg>> agg;
+  for (const ProfRec& r : c->prof.recs) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->prof.ev[2 * r.ev], c->prof.ev[2 * r.ev + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    Agg* a = nullptr;
+    for (auto& p : agg)
+      if (p.first == r.name) a = &p.second;
+    if (!a) {
+      agg.push_back({r.name, Agg()});
+      a = &agg.back().second;
+    }
+    a->n += r.launches;
+    a->ms += ms;
+    a->flops += r.flops;
+    a->bytes += r.bytes;
+  }
+  std::string out = "{";
+  for (size_t q = 0; q < agg.size(); ++q) {
+    char line[256];
+    snprintf(line, sizeof line, "%s\"%s\": {\"launches\": %d, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+             q ? ", " : "", agg[q].first.c_str(), agg[q].second.n, agg[q].second.ms, agg[q].second.flops,
+             agg[q].second.bytes);
+    out += line;
+  }
+  out += "}";
+  if (out.size() + 1 > cap) return fail(c, ALLEGRO_E_CAPACITY, "report needs %zu bytes", out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return ALLEGRO_OK;
+}
+
+const char* allegro_last_error(const allegro_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void allegro_destroy(allegro_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  for (void* p : c->weight_allocs) cudaFree(p);
+  void* bufs[] = {c->d_map, c->d_pos, c->d_types, c->d_species, c->d_row_ptr, c->d_col_ptr, c->d_count,
+                  c->d_cell_of, c->d_wrap, c->d_sorted, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
+                  c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_col_edge, c->d_Ee, c->d_g, c->d_cell_count,
+                  c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
+                  c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->ws};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+// Per-edge and per-atom kernels that are not GEMMs or environment sums:
+//   edge geometry and basis (forward and adjoint), the elementwise head of each
+//   MLP's adjoint, the edge energy, and the float64 atom/structure reductions.
+//
+// Basis (Sec. "Training details": 8 Bessel functions and a polynomial envelope,
+// details as in the Allegro paper; readings fixed by this library):
+//   B_n(r) = sqrt(2/r_c) sin(n pi r / r_c) / r,  n = 1..n_bessel
+//   u(x)   = 1 - (p+1)(p+2)/2 x^p + p(p+2) x^(p+1) - p(p+1)/2 x^(p+2),  x = r / r_c
+// Real spherical harmonics, component-normalised (sum_m Y_lm^2 = 2l+1), of the
+// unit vector (x, y, z) = r_hat:
+//   l=0: 1
+//   l=1: sqrt3 y, sqrt3 z, sqrt3 x
+//   l=2: sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2 - 1), sqrt15 xz, sqrt15/2 (x^2 - y^2)
+// Two-body input row: [onehot(Z_i) | onehot(Z_j) | B(r)].
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace alg {
+
+template <typename T> __device__ __forceinline__ T to_act(float v);
+template <> __device__ __forceinline__ float to_act<float>(float v) { return v; }
+template <> __device__ __forceinline__ bf16 to_act<bf16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from_act(float v) { return v; }
+__device__ __forceinline__ float from_act(bf16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+struct BasisConst {
+  int ns, nb, p, lmax, S;
+  float rc, inv_rc, pref;       // pref = sqrt(2/r_c)
+  float c0, c1, c2;             // envelope coefficients
+};
+
+static BasisConst make_basis(const Arch& a) {
+  BasisConst b;
+  b.ns = a.ns; b.nb = a.nb; b.p = a.p; b.lmax = a.lmax; b.S = a.S();
+  b.rc = (float)a.rc; b.inv_rc = (float)(1.0 / a.rc); b.pref = (float)sqrt(2.0 / a.rc);
+  b.c0 = (float)((a.p + 1.0) * (a.p + 2.0) / 2.0);
+  b.c1 = (float)(a.p * (a.p + 2.0));
+  b.c2 = (float)(a.p * (a.p + 1.0) / 2.0);
+  return b;
+}
+
+__device__ __forceinline__ float ipow(float x, int p) {
+  float r = 1.0f;
+  for (int k = 0; k < p; ++k) r *= x;
+  return r;
+}
+
+__device__ __forceinline__ void sh_eval(int lmax, float x, float y, float z, float* Y) {
+  const float s3 = 1.7320508075688772f, s15 = 3.8729833462074170f, s5h = 1.1180339887498949f;
+  Y[0] = 1.0f;
+  if (lmax >= 1) { Y[1] = s3 * y; Y[2] = s3 * z; Y[3] = s3 * x; }
+  if (lmax >= 2) {
+    Y[4] = s15 * x * y; Y[5] = s15 * y * z; Y[6] = s5h * (3.0f * z * z - 1.0f);
+    Y[7] = s15 * x * z; Y[8] = 0.5f * s15 * (x * x - y * y);
+  }
+}
+
+// sum_a Ybar_a grad Y_a (gradient of the polynomial forms above w.r.t. (x, y, z))
+__device__ __forceinline__ void sh_vjp(int lmax, float x, float y, float z, const float* Yb, float G[3]) {
+  const float s3 = 1.7320508075688772f, s15 = 3.8729833462074170f, s5 = 2.2360679774997897f;
+  G[0] = G[1] = G[2] = 0.0f;
+  if (lmax >= 1) { G[1] += s3 * Yb[1]; G[2] += s3 * Yb[2]; G[0] += s3 * Yb[3]; }
+  if (lmax >= 2) {
+    G[0] += s15 * (Yb[4] * y + Yb[7] * z + Yb[8] * x);
+    G[1] += s15 * (Yb[4] * x + Yb[5] * z - Yb[8] * y);
+    G[2] += s15 * (Yb[5] * y + Yb[7] * x) + 3.0f * s5 * Yb[6] * z;
+  }
+}
+
+template <typename T>
+__global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
+                                const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
+                                float* __restrict__ Yout, float* __restrict__ uout, T* __restrict__ h0,
+                                int ld_h0) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ec) return;
+  size_t eg = (size_t)e0 + e;
+  double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+  double r64 = sqrt(dx * dx + dy * dy + dz * dz);
+  double ir = 1.0 / r64;
+  float r = (float)r64;
+  float x = (float)(dx * ir), y = (float)(dy * ir), z = (float)(dz * ir);
+  float Y[kMaxS];
+  sh_eval(bc.lmax, x, y, z, Y);
+  for (int a = 0; a < bc.S; ++a) Yout[(size_t)e * bc.S + a] = Y[a];
+  float xr = r * bc.inv_rc;
+  float u = 0.0f;
+  if (xr < 1.0f) {
+    float xp = ipow(xr, bc.p);
+    u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
+  }
+  uout[e] = u;
+  T* row = h0 + (size_t)e * ld_h0;
+  const int zi = species[ei[eg]], zj = species[ej[eg]];
+  for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
+  row[zi] = to_act<T>(1.0f);
+  row[bc.ns + zj] = to_act<T>(1.0f);
+  float ir32 = 1.0f / r;
+  for (int n = 1; n <= bc.nb; ++n) {
+    float s = sinpif((float)n * xr);
+    row[2 * bc.ns + n - 1] = to_act<T>(bc.pref * s * ir32);
+  }
+}
+
+template <typename T>
+void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
+                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, cudaStream_t st) {
+  if (Ec <= 0) return;
+  geom_fwd_kernel<T><<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, h0,
+                                                       ld_h0);
+}
+template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
+                                   float*, float*, float*, int, cudaStream_t);
+template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int*, const int*, const Arch&,
+                                  float*, float*, bf16*, int, cudaStream_t);
+
+__global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc,
+                                const float* __restrict__ inbar, int ld_in, const float* __restrict__ ubar,
+                                const float* __restrict__ Ybar, float* __restrict__ g) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ec) return;
+  size_t eg = (size_t)e0 + e;
+  double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+  double r64 = sqrt(dx * dx + dy * dy + dz * dz);
+  double ir = 1.0 / r64;
+  float r = (float)r64;
+  float x = (float)(dx * ir), y = (float)(dy * ir), z = (float)(dz * ir);
+  float xr = r * bc.inv_rc;
+  // dE/dr from the Bessel basis and the envelope
+  float dEdr = 0.0f;
+  const float* Bb = inbar + (size_t)e * ld_in + 2 * bc.ns;
+  float ir32 = 1.0f / r;
+  for (int n = 1; n <= bc.nb; ++n) {
+    float s, c;
+    sincospif((float)n * xr, &s, &c);
+    float k = (float)n * 3.14159265358979323846f * bc.inv_rc;
+    float dB = bc.pref * (k * c * r - s) * ir32 * ir32;
+    dEdr += Bb[n - 1] * dB;
+  }
+  if (xr < 1.0f) {
+    float xp1 = ipow(xr, bc.p - 1);
+    float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
+    dEdr += ubar[e] * du * bc.inv_rc;
+  }
+  float Yb[kMaxS];
+  for (int a = 0; a < bc.S; ++a) Yb[a] = Ybar[(size_t)e * bc.S + a];
+  float G[3];
+  sh_vjp(bc.lmax, x, y, z, Yb, G);
+  float rg = x * G[0] + y * G[1] + z * G[2];
+  float gx = x * dEdr + (G[0] - x * rg) * ir32;
+  float gy = y * dEdr + (G[1] - y * rg) * ir32;
+  float gz = z * dEdr + (G[2] - z * rg) * ir32;
+  g[3 * eg] = gx; g[3 * eg + 1] = gy; g[3 * eg + 2] = gz;
+}
+
+void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
+                   const float* ubar, const float* Ybar, float* g, cudaStream_t st) {
+  if (Ec <= 0) return;
+  geom_bwd_kernel<<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, make_basis(a), inbar, ld_in, ubar, Ybar, g);
+}
+
+// Adjoint head of an MLP whose output is x = u * silu(z):  given xbar,
+//   ubar += sum_n xbar_n silu(z_n),   zbar_n = xbar_n u silu'(z_n).
+// xbar = sigma_{Z_i} v when `xbar` is null (the last layer: E_ij = v . x with
+// the linear edge-energy MLP folded into v, and dE/dE_ij = sigma_{Z_i}).
+template <typename T>
+__global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, int ld_x,
+                                const float* __restrict__ vconst, const int* __restrict__ ei,
+                                const int* __restrict__ species, const double* __restrict__ sigma, int e0,
+                                const T* __restrict__ pre, int ld_pre,
+                                const float* __restrict__ u, float* __restrict__ ubar, bool ubar_init,
+                                T* __restrict__ zbar, int ld_z) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= Ec) return;
+  const int e = warp;
+  float sc = 1.0f;
+  if (!xbar) sc = (float)sigma[species[ei[(size_t)e0 + e]]];
+  const float ue = u[e];
+  float dot = 0.0f;
+  for (int n = lane; n < K; n += 32) {
+    float xb = xbar ? xbar[(size_t)e * ld_x + n] : sc * vconst[n];
+    float z = from_act(pre[(size_t)e * ld_pre + n]);
+    float s = sigmoidf_(z);
+    dot += xb * z * s;
+    zbar[(size_t)e * ld_z + n] = to_act<T>(xb * ue * s * (1.0f + z * (1.0f - s)));
+  }
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if (lane == 0) ubar[e] = ubar_init ? dot : ubar[e] + dot;
+}
+
+template <typename T>
+void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
+                  const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,
+                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st) {
+  if (Ec <= 0) return;
+  long long threads = (long long)Ec * 32;
+  head_bwd_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      Ec, K, xbar, ld_x, vconst, ei, species, sigma, e0, pre, ld_pre, u, ubar, ubar_init, zbar, ld_z);
+}
+template void mlp_head_bwd<float>(int, int, const float*, int, const float*, const int*, const int*,
+                                  const double*, int, const float*, int, const float*, float*, bool, float*, int,
+                                  cudaStream_t);
+template void mlp_head_bwd<bf16>(int, int, const float*, int, const float*, const int*, const int*,
+                                 const double*, int, const bf16*, int, const float*, float*, bool, bf16*, int,
+                                 cudaStream_t);
+
+// E_ij = v . x (the linear edge-energy MLP folded into one vector v)
+template <typename T>
+__global__ void edge_energy_kernel(int Ec, int K, const T* __restrict__ x, int ldx, const float* __restrict__ v,
+                                   float* __restrict__ Ee) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= Ec) return;
+  float s = 0.0f;
+  for (int n = lane; n < K; n += 32) s += from_act(x[(size_t)warp * ldx + n]) * v[n];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Ee[warp] = s;
+}
+
+template <typename T>
+void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, cudaStream_t st) {
+  if (Ec <= 0) return;
+  long long threads = (long long)Ec * 32;
+  edge_energy_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(Ec, K, x, ldx, v, Ee);
+}
+template void edge_energy<float>(int, int, const float*, int, const float*, float*, cudaStream_t);
+template void edge_energy<bf16>(int, int, const bf16*, int, const float*, float*, cudaStream_t);
+
+// Per atom i (float64): Etilde_i = sigma_Z E_i + mu_Z with E_i = sum_{row i} E_ij;
+// F_i = sum_{e in row i} g_e - sum_{e with j_e = i} g_e  (g_e = dE/dd_e);
+// per-atom virial W_i = - sum_{e in row i} d_e (x) g_e.
+__global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_ptr,
+                                   const int* __restrict__ col_edge, const float* __restrict__ Ee,
+                                   const float* __restrict__ g, const double* __restrict__ ed,
+                                   const int* __restrict__ species, const double* __restrict__ sigma,
+                                   const double* __restrict__ mu, bool want_forces, double* __restrict__ E_atom,
+                                   double* __restrict__ F, double* __restrict__ Wat) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = row_ptr[i], e1 = row_ptr[i + 1];
+  double Ei = 0.0;
+  double f[3] = {0, 0, 0};
+  double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int e = b; e < e1; ++e) {
+    Ei += (double)Ee[e];
+    if (want_forces) {
+      double gx = g[3 * (size_t)e], gy = g[3 * (size_t)e + 1], gz = g[3 * (size_t)e + 2];
+      f[0] += gx; f[1] += gy; f[2] += gz;
+      double d0 = ed[3 * (size_t)e], d1 = ed[3 * (size_t)e + 1], d2 = ed[3 * (size_t)e + 2];
+      W[0] -= d0 * gx; W[1] -= d0 * gy; W[2] -= d0 * gz;
+      W[3] -= d1 * gx; W[4] -= d1 * gy; W[5] -= d1 * gz;
+      W[6] -= d2 * gx; W[7] -= d2 * gy; W[8] -= d2 * gz;
+    }
+  }
+  const int z = species[i];
+  E_atom[i] = sigma[z] * Ei + mu[z];
+  if (want_forces) {
+    for (int k = col_ptr[i]; k < col_ptr[i + 1]; ++k) {
+      size_t e = (size_t)col_edge[k];
+      f[0] -= g[3 * e]; f[1] -= g[3 * e + 1]; f[2] -= g[3 * e + 2];
+    }
+    F[3 * (size_t)i] = f[0]; F[3 * (size_t)i + 1] = f[1]; F[3 * (size_t)i + 2] = f[2];
+    for (int q = 0; q < 9; ++q) Wat[9 * (size_t)i + q] = W[q];
+  }
+}
+
+void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
+                 const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
+                 bool want_forces, double* E_atom, double* F, double* Wat, cudaStream_t st) {
+  if (n <= 0) return;
+  atom_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, col_ptr, col_edge, Ee, g, ed, species, sigma,
+                                                      mu, want_forces, E_atom, F, Wat);
+}
+
+// One block per structure: E_b = sum of its atoms' Etilde_i, W_b = sum of W_i
+// (fixed-order tree reduction, so results are bitwise reproducible).  Also
+// flags non-finite per-atom energies or forces.
+__global__ void struct_reduce_kernel(const int64_t* __restrict__ offs, const double* __restrict__ E_atom,
+                                     const double* __restrict__ Wat, const double* __restrict__ F, bool want_w,
+                                     double* __restrict__ E_out, double* __restrict__ W_out,
+                                     int* __restrict__ d_err) {
+  const int b = blockIdx.x;
+  const long long a0 = offs[b], a1 = offs[b + 1];
+  __shared__ double sh[10][256];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  bool bad = false;
+  for (long long i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    double e = E_atom[i];
+    acc[0] += e;
+    bad |= !isfinite(e);
+    if (want_w) {
+      for (int q = 0; q < 9; ++q) acc[1 + q] += Wat[9 * i + q];
+      bad |= !(isfinite(F[3 * i]) && isfinite(F[3 * i + 1]) && isfinite(F[3 * i + 2]));
+    }
+  }
+  if (bad) atomicOr(d_err, kErrNonFinite);
+  for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    E_out[b] = sh[0][0];
+    if (want_w)
+      for (int q = 0; q < 9; ++q) W_out[9 * b + q] = sh[1 + q][0];
+  }
+}
+
+void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const double* Wat, const double* F,
+                   bool want_w, double* E_out, double* W_out, int* d_err, cudaStream_t st) {
+  if (nstruct <= 0) return;
+  struct_reduce_kernel<<<nstruct, 256, 0, st>>>(offs, E_atom, Wat, F, want_w, E_out, W_out, d_err);
+}
+
+}  // namespace alg

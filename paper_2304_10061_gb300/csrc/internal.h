@@ -1,0 +1,164 @@
+// Internal declarations shared by the translation units of liballegro_gb300.
+// Host orchestration lives in context.cu; kernels in neighbors.cu,
+// edge_kernels.cu, row_kernels.cu, gemm_simt.cu and gemm_tc.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/allegro.h"
+
+namespace alg {
+
+typedef __nv_bfloat16 bf16;
+
+// Largest sizes the kernels are instantiated for.
+constexpr int kMaxLmax = 2;
+constexpr int kMaxS = (kMaxLmax + 1) * (kMaxLmax + 1);   // spherical-harmonic components
+constexpr int kMaxChannels = 128;
+constexpr int kMaxWidth = 512;
+constexpr int kMaxSpecies = 64;
+constexpr int kMaxBessel = 16;
+
+// Device error word bits (set by kernels, read by the host after each call).
+enum DevErr : int {
+  kErrTimeout = 1,      // a bounded mbarrier wait ran out
+  kErrNeighbor = 2,     // neighbour fill pass disagreed with its count pass
+  kErrBadInput = 4,     // non-finite coordinates or an unknown type
+  kErrNonFinite = 8,    // a per-atom energy or force is NaN / Inf
+};
+
+struct Arch {
+  int ns = 0, nb = 0, p = 0, lmax = 0, nl = 0, C = 0;
+  double rc = 0, ann = 0;
+  std::vector<int> tb, lat, edge;
+  int S() const { return (lmax + 1) * (lmax + 1); }
+  int n_w() const { return C * (lmax + 1); }
+  int K0in() const { return 2 * ns + nb; }
+  int Klat(int L) const { return L == 0 ? tb.back() : lat.back(); }
+};
+
+// A linear map W [N x K] (out x in) with the device copies the GEMMs use:
+// forward B = W ([N][ld] row-major), backward B = W^T ([K][ldT]).
+struct Lin {
+  int N = 0, K = 0, ld = 0, ldT = 0;
+  float* f32 = nullptr;
+  float* f32T = nullptr;
+  bf16* b16 = nullptr;
+  bf16* b16T = nullptr;
+};
+
+// Tensor-product constants of one model, passed to kernels by value.
+struct TPConst {
+  float W1[kMaxS * kMaxS * kMaxS];  // fused path tensor of layer 1 (when 2 layers): W[a][b][c]
+  float clast[kMaxS];               // last layer: s = sum_a clast[a] V_a Gamma_a (diagonal of W[a][b][0])
+  float nu;                         // environment normalisation 1/sqrt(avg_num_neighbors)
+};
+
+enum Epi : int {
+  EPI_FWD_SILU = 0,   // pre = acc (optional store); out = silu(acc) * (rowscale ? rowscale[m] : 1)
+  EPI_F32 = 1,        // out(f32) = acc + (add ? add[m][n] : 0)
+  EPI_BWD_SILU = 2,   // out = acc * silu'(pre[m][n])
+};
+
+struct GemmArgs {
+  int M = 0, N = 0, K = 0;
+  const void* A = nullptr; int lda = 0;     // [M][lda] activations (float or bf16)
+  const Lin* W = nullptr; bool trans = false;
+  int epi = EPI_F32;
+  void* out = nullptr; int ldo = 0;
+  void* pre = nullptr; int ldp = 0;
+  const float* rowscale = nullptr;
+  const float* add = nullptr; int ld_add = 0;
+};
+
+// ---- launchers -----------------------------------------------------------
+// GEMMs
+void gemm_simt_f32(const GemmArgs& g, cudaStream_t st);
+bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
+bool gemm_tc_init(std::string* why);
+
+// scan / utilities
+void exclusive_scan_i32(const int* in, int* out, int n, int* d_total, void* tmp, size_t tmp_bytes,
+                        cudaStream_t st);
+size_t scan_tmp_bytes(int n);
+
+// neighbours
+struct CellGrid {
+  double inv[9];      // inverse cell (row-major), frac = pos * inv (row vector times matrix)
+  double cell[9];
+  int pbc[3];
+  int n[3];           // cells per axis
+  int R[3];           // stencil radius per axis
+  double lo[3], span[3];   // non-periodic axes: frac range mapped onto the grid
+};
+void nb_bin(const double* pos, int n, const CellGrid& g, int* cell_of, int* wrap, int* cell_count,
+            cudaStream_t st);
+void nb_place(const int* cell_of, int n, const int* cell_start, int* cell_cursor, int* sorted,
+              cudaStream_t st);
+void nb_sort_cells(const int* cell_start, int n_cells, int* sorted, cudaStream_t st);
+void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
+               const int* wrap, const int* cell_start, const int* sorted, double rc2,
+               int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
+               cudaStream_t st);
+void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,
+                           const double* cells, const int* pbc, const int* nimg, double rc2,
+                           const int* atom_struct, int n, int* count, const int* row_ptr, int* ej,
+                           int* ei, int* eS, double* ed, int* d_err, cudaStream_t st);
+void nb_columns(const int* ej, int E, int n, int* col_count, cudaStream_t st);
+void nb_fill_columns(const int* ej, int E, const int* col_ptr, int* cursor, int* col_edge,
+                     cudaStream_t st);
+void nb_sort_columns(const int* col_ptr, int n, int* col_edge, cudaStream_t st);
+void nb_struct_span(const double* pos, const int64_t* offs, const double* inv, int nstruct, double* span,
+                    cudaStream_t st);
+void nb_minmax_frac(const double* pos, int n, const double* inv, double* d_minmax, cudaStream_t st);
+
+// edge kernels
+template <typename T>
+void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
+                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, cudaStream_t st);
+void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
+                   const float* ubar, const float* Ybar, float* g, cudaStream_t st);
+template <typename T>
+void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
+                  const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,
+                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st);
+template <typename T>
+void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, cudaStream_t st);
+void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
+                 const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
+                 bool want_forces, double* E_atom, double* F, double* Wat, cudaStream_t st);
+void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const double* Wat, const double* F,
+                   bool want_w, double* E_out, double* W_out, int* d_err, cudaStream_t st);
+
+// row (per-atom) kernels: environment sums and tensor products
+struct RowIO {
+  int a0 = 0, na = 0, e0 = 0;
+  const int* row_ptr = nullptr;
+  int C = 0;
+  const float* Y = nullptr;            // [Ec][S]
+  const float* W01 = nullptr; int ld01 = 0;   // w0 at column 0, w1 at column n_w
+  const float* w2 = nullptr; int ld2 = 0;
+  float* G1 = nullptr; float* G2 = nullptr;   // [na][C][S]
+  void* xs = nullptr; int ldxs = 0; int xs_off = 0;   // s output (T), column offset
+  const float* sbar1 = nullptr; const float* sbar2 = nullptr; int ld_sbar1 = 0, ld_sbar2 = 0;
+  void* wbar01 = nullptr; int ld_wbar01 = 0;  // T
+  void* wbar2 = nullptr; int ld_wbar2 = 0;    // T
+  float* Ybar = nullptr;
+};
+template <typename T>
+void row_fwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st);
+template <typename T>
+void row_bwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st);
+
+// host-side O(3) constants (independent implementation)
+double cg_racah(int j1, int m1, int j2, int m2, int j3, int m3);
+void coupling_real(int l1, int l2, int l3, std::vector<double>& out);   // [(2l1+1)(2l2+1)(2l3+1)]
+void fused_layer_tensor(int lmax, const float* theta_raw, std::vector<double>& W, int& n_in, int& n_out,
+                        bool last);
+
+}  // namespace alg

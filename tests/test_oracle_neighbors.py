@@ -73,3 +73,20 @@ def test_centers_subset_matches_full_rows():
     sub = neighbor_list(s.pos, s.cell, s.pbc, 4.0, centers=cs)
     m = np.isin(full[0], cs)
     assert _same(sub, tuple(x[m] for x in full))
+
+
+def test_unwrapped_positions_find_all_images():
+    """Atoms outside the cell: the edge set equals that of the wrapped positions
+    with the image shifts adjusted by the wrap counts."""
+    rng = np.random.default_rng(5)
+    cell = np.array([[6.0, 0.0, 0.0], [2.1, 5.5, 0.0], [-1.3, 1.7, 7.2]])
+    frac = rng.uniform(-0.2, 1.2, size=(40, 3))
+    w = np.floor(frac)
+    pos = frac @ cell
+    posw = (frac - w) @ cell
+    i, j, S = neighbor_list(pos, cell, [True] * 3, 4.0)
+    iw, jw, Sw = neighbor_list(posw, cell, [True] * 3, 4.0)
+    # d = pos_j + S cell - pos_i = posw_j + (S + w_j - w_i) cell - posw_i
+    a = set(zip(i.tolist(), j.tolist(), map(tuple, (S + w[j].astype(int) - w[i].astype(int)).tolist())))
+    b = set(zip(iw.tolist(), jw.tolist(), map(tuple, Sw.tolist())))
+    assert a == b

@@ -270,10 +270,14 @@ __global__ void __launch_bounds__(192, 1)
         float v[32];
         tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         if (m < M) {
+          if (ep.vec && n0 + c0 + 32 <= N) {
+            epi_apply_vec32_bf16(ep, m, n0 + c0, v);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < N) epi_apply<bf16>(ep, m, n, v[j]);
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < N) epi_apply<bf16>(ep, m, n, v[j]);
+            }
           }
         }
       }

@@ -106,7 +106,7 @@ def test_c4_sampled_rows(model):
     s, _, _ = make_config("c4")
     model.neighbors(s.pos, s.species % 2, s.cell)
     i, j, S = model.get_neighbors()
-    assert model.n_edges > 26 * s.n_atoms
+    assert model.n_edges > 24 * s.n_atoms
     cs = np.random.default_rng(0).choice(s.n_atoms, 48, replace=False)
     want = neighbor_list(s.pos, s.cell, s.pbc, 4.0, centers=np.sort(cs))
     m = np.isin(i, cs)

@@ -218,6 +218,8 @@ def run_ours(args):
     def make(prec):
         m = Allegro(blob, precision=prec, device=local)
         m.set_stream(stream.cuda_stream)
+        if args.chunk_edges:
+            m.reserve(0, 0, False, args.chunk_edges)
         return m
 
     def timed(m, K, W, out):
@@ -342,6 +344,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--chunk-edges", type=int, default=0, help="edges per model pass (0 = automatic)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

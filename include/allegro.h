@@ -152,6 +152,32 @@ allegro_status allegro_get_neighbors(allegro_ctx* ctx, int32_t* i, int32_t* j, i
 allegro_status allegro_profile(allegro_ctx* ctx, int32_t enable);
 allegro_status allegro_profile_report(allegro_ctx* ctx, char* buf, size_t cap, int64_t* launches);
 
+/*
+ * allegro_neighbors_noalloc -- the ordered neighbour list of one small
+ * structure, computed without allocating any device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory while they run (an MD engine whose memory pool owns the GPU, a
+ * region under CUDA stream capture, a loop that must keep a fixed footprint),
+ * and so cannot create a context.  Same pair rule as allegro_neighbors, by an
+ * all-pairs search (meant for small structures).
+ *   pos[n_atoms*3]: device float64; n_atoms <= 16384 (larger sizes return
+ *       ALLEGRO_E_CAPACITY: the scratch is a fixed 128 KiB device array).
+ *   cell[9] (rows a, b, c) and pbc[3]: HOST pointers or NULL (no cell: no
+ *       periodicity).  Along periodic axes positions must lie within
+ *       fractional coordinates [-0.5, 1.5).
+ *   r_c > 0.  i[cap], j[cap], shift[cap*3]: device int32 outputs, rows in
+ *       ascending i.  *n_edges (host): the edge count; ALLEGRO_E_CAPACITY if it
+ *       exceeds cap (outputs then untouched).
+ *   stream: cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ * Runs on the current device.  Its scratch array lives in the library on every
+ * device that loads it, until process exit.  The first call on a device looks
+ * up the array's address there; make it before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU race and corrupt results.
+ */
+allegro_status allegro_neighbors_noalloc(const double* pos, int64_t n_atoms, const double* cell,
+                                         const uint8_t* pbc, double r_c, int32_t* i, int32_t* j,
+                                         int32_t* shift, int64_t cap, int64_t* n_edges, void* stream);
+
 /* allegro_last_error -- description of the last failure on ctx (never NULL). */
 const char* allegro_last_error(const allegro_ctx* ctx);
 

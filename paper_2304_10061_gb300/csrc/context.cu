@@ -457,7 +457,7 @@ struct WS {
   void* wbar2; int ld_wbar2;
   float* xbar; int ld_xbar;
   float* inbar; int ld_inbar;
-  float* Y; float* Ybar; float* u; float* ubar;
+  float* Y; float* Ybar; float* u; float* ubar; float* sig;
   float* G1; float* G2;
 };
 
@@ -513,6 +513,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->Ybar = (float*)take((size_t)Ec * S * 4);
   w->u = (float*)take((size_t)Ec * 4);
   w->ubar = (float*)take((size_t)Ec * 4);
+  w->sig = (float*)take((size_t)Ec * 4);
   w->G1 = (float*)take((size_t)Ac * a.C * S * 4);
   w->G2 = (float*)take((size_t)Ac * a.C * S * 4);
   return off + 256;
@@ -709,7 +710,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   const double act = sizeof(T);
   auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
-               int ld_add = 0) {
+               int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
     const double outb = (epi == EPI_F32) ? 4.0 : act;
     const double bytes = (double)Ec * (K * act + N * outb + (pre ? N * act : 0.0) + (add ? N * 4.0 : 0.0) +
                                        (rowscale ? 4.0 : 0.0)) + (double)N * K * act;
@@ -717,6 +718,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     GemmArgs g;
     g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
     g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
+    g.ubar = ubar; g.Eout = Eout; g.v = c->d_v; g.rowsig = w.sig;
     return gemm<T>(c, g);
   };
   RowIO io;
@@ -724,6 +726,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   io.Y = w.Y; io.W01 = w.W01; io.ld01 = w.ld_W01; io.w2 = w.w2; io.ld2 = w.ld_w2; io.G1 = w.G1; io.G2 = w.G2;
 
   const int S = a.S(), C = a.C;
+  // BF16 path: adjoint heads and the edge energy live in the tcgen05 GEMM epilogues
+  const bool fused = (c->prec == ALLEGRO_PREC_BF16);
   // algorithmic bytes of the row kernels (per edge, per atom), float32 features
   auto row_scope = [&](const char* name, double per_edge, double per_atom) {
     return ProfScope(c, name, 0.0, (double)Ec * per_edge + (double)Ac * per_atom);
@@ -731,7 +735,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   // ---- forward ----
   {
     ProfScope ps(c, "geom_fwd", 0.0, (double)Ec * (24 + 8 + 8 + S * 4 + 4 + w.ld_h0 * act));
-    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, (T*)w.h0, w.ld_h0, st);
+    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, (T*)w.h0, w.ld_h0, c->d_sigma,
+                     w.sig, st);
   }
   const void* in = w.h0;
   int ld_in = w.ld_h0, K = a.K0in();
@@ -758,6 +763,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     in = w.X[L - 1]; ld_in = w.ld_X[L - 1]; K = a.Klat(L - 1) + a.C;
     for (int k = 0; k < nlat; ++k) {
       const bool last = (k == nlat - 1);
+      if (fused && last && L == nl) {
+        // last latent layer + folded edge-energy MLP + start of the adjoint in one epilogue
+        if ((s = G(in, ld_in, K, c->lat[L - 1][k], false, EPI_LAST, w.H[0], w.ld_H, a.lat[k], nullptr, 0, w.u,
+                   nullptr, 0, w.ubar, c->d_Ee + e0)) != ALLEGRO_OK)
+          return s;
+        break;
+      }
       void* out = last ? (L < nl ? w.X[L] : w.Xlast) : w.H[k & 1];
       int ldo = last ? (L < nl ? w.ld_X[L] : w.ld_Xlast) : w.ld_H;
       if ((s = G(in, ld_in, K, c->lat[L - 1][k], false, EPI_FWD_SILU, out, ldo, a.lat[k], w.Zlat[L - 1][k],
@@ -770,15 +782,15 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
         return s;
     }
   }
-  {
+  if (!fused) {
     ProfScope ps(c, "edge_energy", 0.0, (double)Ec * (a.lat.back() * act + 4));
     edge_energy<T>(Ec, a.lat.back(), (const T*)w.Xlast, w.ld_Xlast, c->d_v, c->d_Ee + e0, st);
   }
   if (!backward) return ALLEGRO_OK;
 
   // ---- adjoint ----
-  // latent MLP of the last layer: xbar = sigma_{Z_i} v
-  {
+  // latent MLP of the last layer: xbar = sigma_{Z_i} v (fused into EPI_LAST on the BF16 path)
+  if (!fused) {
     ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * 2 * act + 16));
     mlp_head_bwd<T>(Ec, a.lat.back(), nullptr, 0, c->d_v, c->d_ei, c->d_species, c->d_sigma, e0,
                     (const T*)w.Zlat[nl - 1][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, true, (T*)w.H[0], w.ld_H,
@@ -814,11 +826,16 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       auto ps = row_scope("row_bwd_last", 2.0 * nw * 4 + C * 4 + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
       row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
     }
-    // xbar^1 = wbar^2 . env2 + D[1][:, :K1]
-    if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_F32, w.xbar, w.ld_xbar, a.lat.back(), nullptr, 0,
-               nullptr, w.D[1], w.ld_D[1])) != ALLEGRO_OK)
+    // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
+    if (fused) {
+      if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
+                 w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.D[1], w.ld_D[1], w.ubar)) != ALLEGRO_OK)
+        return s;
+    } else if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_F32, w.xbar, w.ld_xbar, a.lat.back(), nullptr,
+                      0, nullptr, w.D[1], w.ld_D[1])) != ALLEGRO_OK) {
       return s;
-    {
+    }
+    if (!fused) {
       ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * (4 + 2 * act) + 12));
       mlp_head_bwd<T>(Ec, a.lat.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
                       (const T*)w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H,
@@ -831,11 +848,16 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                         2.0 * C * S * 4);
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }
-  // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0]
-  if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_F32, w.xbar, w.ld_xbar, a.tb.back(), nullptr, 0,
-             nullptr, w.D[0], w.ld_D[0])) != ALLEGRO_OK)
+  // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0], then the head of x^0 = u silu(z)
+  if (fused) {
+    if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
+               w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.D[0], w.ld_D[0], w.ubar)) != ALLEGRO_OK)
+      return s;
+  } else if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_F32, w.xbar, w.ld_xbar, a.tb.back(), nullptr,
+                    0, nullptr, w.D[0], w.ld_D[0])) != ALLEGRO_OK) {
     return s;
-  {
+  }
+  if (!fused) {
     ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.tb.back() * (4 + 2 * act) + 12));
     mlp_head_bwd<T>(Ec, a.tb.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
                     (const T*)w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);

@@ -25,7 +25,7 @@ template <> __device__ __forceinline__ bf16 to_act<bf16>(float v) { return __flo
 __device__ __forceinline__ float from_act(float v) { return v; }
 __device__ __forceinline__ float from_act(bf16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float sigmoidf_(float z) { return __fdividef(1.0f, 1.0f + expf(-z)); }
 
 struct BasisConst {
   int ns, nb, p, lmax, S;
@@ -75,7 +75,7 @@ template <typename T>
 __global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
                                 const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
                                 float* __restrict__ Yout, float* __restrict__ uout, T* __restrict__ h0,
-                                int ld_h0) {
+                                int ld_h0, const double* __restrict__ sigma, float* __restrict__ sig) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Ec) return;
   size_t eg = (size_t)e0 + e;
@@ -96,6 +96,7 @@ __global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, c
   uout[e] = u;
   T* row = h0 + (size_t)e * ld_h0;
   const int zi = species[ei[eg]], zj = species[ej[eg]];
+  if (sig) sig[e] = (float)sigma[zi];
   for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
   row[zi] = to_act<T>(1.0f);
   row[bc.ns + zj] = to_act<T>(1.0f);
@@ -108,15 +109,16 @@ __global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, c
 
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
-                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, cudaStream_t st) {
+                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
+                   cudaStream_t st) {
   if (Ec <= 0) return;
   geom_fwd_kernel<T><<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, h0,
-                                                       ld_h0);
+                                                       ld_h0, sigma, sig);
 }
 template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
-                                   float*, float*, float*, int, cudaStream_t);
+                                   float*, float*, float*, int, const double*, float*, cudaStream_t);
 template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int*, const int*, const Arch&,
-                                  float*, float*, bf16*, int, cudaStream_t);
+                                  float*, float*, bf16*, int, const double*, float*, cudaStream_t);
 
 __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc,
                                 const float* __restrict__ inbar, int ld_in, const float* __restrict__ ubar,

@@ -17,6 +17,10 @@ struct EpiParams {
   const float* rowscale;
   const float* add; int ld_add;
   int vec;   // 1: every row start of out/pre/add is 16-byte aligned (vector path allowed)
+  float* ubar;
+  const float* v;
+  const float* rowsig;
+  float* Eout;
 };
 
 __device__ __forceinline__ float act_ld(const float* p) { return *p; }
@@ -24,7 +28,7 @@ __device__ __forceinline__ float act_ld(const bf16* p) { return __bfloat162float
 __device__ __forceinline__ void act_st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void act_st(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-__device__ __forceinline__ float epi_sigmoid(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float epi_sigmoid(float z) { return __fdividef(1.0f, 1.0f + expf(-z)); }
 
 template <typename T>
 __device__ __forceinline__ void epi_apply(const EpiParams& ep, int m, int n, float acc) {
@@ -110,6 +114,7 @@ inline EpiParams make_epi(const GemmArgs& g) {
   EpiParams e;
   e.epi = g.epi; e.out = g.out; e.ldo = g.ldo; e.pre = g.pre; e.ldp = g.ldp;
   e.rowscale = g.rowscale; e.add = g.add; e.ld_add = g.ld_add;
+  e.ubar = g.ubar; e.v = g.v; e.rowsig = g.rowsig; e.Eout = g.Eout;
   auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   e.vec = al(g.out) && al(g.pre) && al(g.add) && (g.ldo % 8 == 0) && (g.ldp % 8 == 0) && (g.ld_add % 8 == 0);
   return e;

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "epilogue.cuh"
 #include "internal.h"
@@ -70,6 +71,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
@@ -167,56 +172,143 @@ __device__ __forceinline__ constexpr uint32_t idesc_bf16() {
 }
 
 constexpr int kTcBM = 128, kTcBK = 64;
+constexpr int kEpiWarps = 4;                 // warps 2..5
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Per epilogue warp: two input staging buffers (pre bf16 32x32 + add f32 32x32)
+// and two output staging buffers (two 32x32 boxes, bf16 or f32).
+constexpr int kInBox = 2048 + 4096;
+constexpr int kOutBox = 4096 + 4096;
+constexpr int kEpiSmem = kEpiWarps * 2 * (kInBox + kOutBox);
 
 template <int BN>
-__host__ __device__ constexpr int tc_stages() {
-  return (110 * 1024) / (kTcBM * kTcBK * 2 + BN * kTcBK * 2) < 2   ? 2
-         : (110 * 1024) / (kTcBM * kTcBK * 2 + BN * kTcBK * 2) > 4 ? 4
-                                                                    : (110 * 1024) / (kTcBM * kTcBK * 2 + BN * kTcBK * 2);
+__host__ __device__ constexpr int tc_stage_bytes() {
+  return kTcBM * kTcBK * 2 + BN * kTcBK * 2;
 }
 
 template <int BN>
-__host__ __device__ constexpr int tc_tmem_cols() {
+__host__ __device__ constexpr int tc_stages() {
+  return (100 * 1024) / tc_stage_bytes<BN>() > 6 ? 6
+         : (100 * 1024) / tc_stage_bytes<BN>() < 2 ? 2
+                                                    : (100 * 1024) / tc_stage_bytes<BN>();
+}
+
+template <int BN>
+__host__ __device__ constexpr int tc_tmem_cols() {   // one accumulator buffer
   return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 }
 
 template <int BN>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)tc_stages<BN>() * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 1024 + 256;
+  return (size_t)tc_stages<BN>() * tc_stage_bytes<BN>() + kEpiSmem + 1024 + 256;
 }
 
+// --- epilogue staging: 32 x 32 boxes moved by TMA --------------------------
+// bf16 box rows are 64 bytes (64-byte swizzle), float32 box rows 128 bytes
+// (128-byte swizzle); the 16-byte unit u of row r sits at unit u ^ f(r) so the
+// row-per-lane accesses spread over all banks.
+__device__ __forceinline__ uint32_t sw64(int r, int u) { return r * 64 + ((u ^ ((r >> 1) & 3)) << 4); }
+__device__ __forceinline__ uint32_t sw128(int r, int u) { return r * 128 + ((u ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void st_bf16_row(uint8_t* box, int r, const float (&v)[32]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint4 x = make_uint4(pack_bf16x2(v[8 * u + 0], v[8 * u + 1]), pack_bf16x2(v[8 * u + 2], v[8 * u + 3]),
+                         pack_bf16x2(v[8 * u + 4], v[8 * u + 5]), pack_bf16x2(v[8 * u + 6], v[8 * u + 7]));
+    *reinterpret_cast<uint4*>(box + sw64(r, u)) = x;
+  }
+}
+__device__ __forceinline__ void ld_bf16_row(const uint8_t* box, int r, float (&v)[32]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint4 x = *reinterpret_cast<const uint4*>(box + sw64(r, u));
+    uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float2 f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w[t]));
+      v[8 * u + 2 * t] = f.x;
+      v[8 * u + 2 * t + 1] = f.y;
+    }
+  }
+}
+__device__ __forceinline__ void st_f32_row(uint8_t* box, int r, const float (&v)[32]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    *reinterpret_cast<float4*>(box + sw128(r, u)) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+}
+__device__ __forceinline__ void ld_f32_row(const uint8_t* box, int r, float (&v)[32]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    float4 x = *reinterpret_cast<const float4*>(box + sw128(r, u));
+    v[4 * u] = x.x; v[4 * u + 1] = x.y; v[4 * u + 2] = x.z; v[4 * u + 3] = x.w;
+  }
+}
+
+__device__ __forceinline__ float fast_sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+
+struct EpiMaps {
+  CUtensorMap out, pre, add;
+};
+
+// Persistent kernel: CTA b handles tiles b, b + gridDim.x, ...  Two TMEM
+// accumulator buffers: the MMA warp fills buffer (t & 1) while the epilogue
+// warps drain the other, and the TMA producer runs ahead through the
+// shared-memory ring across tile boundaries.  Each epilogue warp owns 32
+// rows; per 32-column chunk it pulls its epilogue inputs (pre-activation,
+// addend) with TMA, computes in registers, stages the results in swizzled
+// shared memory and writes them back with TMA bulk stores.
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
-                   int M, int N, int K, int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ EpiMaps em, EpiParams ep, int M, int N, int K, int* __restrict__ err) {
   constexpr int STAGES = tc_stages<BN>();
   constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
   constexpr uint32_t B_BYTES = BN * kTcBK * 2;
-  constexpr uint32_t TMEM_COLS = tc_tmem_cols<BN>();
+  constexpr uint32_t COLS = tc_tmem_cols<BN>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint8_t* sE = sB + STAGES * B_BYTES;                       // epilogue staging (1024-aligned)
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE + kEpiSmem);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfull + 1);
+  uint64_t* tfull = empty + STAGES;     // [2]
+  uint64_t* tempty = tfull + 2;         // [2]
+  uint64_t* inbar = tempty + 2;         // [kEpiWarps][2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + 2 * kEpiWarps);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
   const int nk = (K + kTcBK - 1) / kTcBK;
+  const int tiles_m = (M + kTcBM - 1) / kTcBM, tiles_n = (N + BN - 1) / BN;
+  const int ntiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps);
+    }
+    for (int q = 0; q < 2 * kEpiWarps; ++q) mbar_init(&inbar[q], 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    tc_alloc(tslot, TMEM_COLS);
+    tc_alloc(tslot, 2 * COLS);
     tc_relinquish();
   }
   tc_fence_before();
@@ -226,69 +318,221 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty[s], (r - 1) & 1)) {
-          atomicOr(err, kErrTimeout);
-          break;
+      uint32_t g = 0;   // global k-block counter (ring position)
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        const int m0 = (t % tiles_m) * kTcBM, n0 = (t / tiles_m) * BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const uint32_t s = g % STAGES, r = g / STAGES;
+          if (g >= (uint32_t)STAGES && !mbar_wait(&empty[s], (r - 1) & 1)) {
+            atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+          tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kb * kTcBK, m0);
+          tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kb * kTcBK, n0);
         }
-        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kb * kTcBK, m0);
-        tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kb * kTcBK, n0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
-        if (!mbar_wait(&full[s], r & 1)) {
-          atomicOr(err, kErrTimeout);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a_addr = smem_u32(sA + s * A_BYTES), b_addr = smem_u32(sB + s * B_BYTES);
+      uint32_t g = 0;
+      int lt = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+        const int b = lt & 1, use = lt >> 1;
+        bool ok = !*abort_flag && mbar_wait(&tempty[b], (use & 1) ^ 1);
+        if (ok) {
+          tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(b * COLS);
+          for (int kb = 0; kb < nk; ++kb, ++g) {
+            const uint32_t s = g % STAGES, r = g / STAGES;
+            if (!mbar_wait(&full[s], r & 1)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(sA + s * A_BYTES), b_addr = smem_u32(sB + s * B_BYTES);
 #pragma unroll
-        for (int k = 0; k < kTcBK / 16; ++k) {
-          tc_mma(tmem, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32), idesc,
-                 (kb > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kTcBK / 16; ++k)
+              tc_mma(dt, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32), idesc,
+                     (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[s]);
+          }
         }
-        tc_commit(&empty[s]);
+        if (!ok) {
+          atomicOr(err, kErrTimeout);
+          *abort_flag = 1;
+        }
+        tc_commit(&tfull[b]);
+        if (!ok) break;
       }
-      tc_commit(tfull);
     }
     __syncwarp();
   } else {
-    const int q = warp & 3;   // TMEM lane quarter this warp may access
-    const bool ok = mbar_wait(tfull, 0);
-    if (!ok && lane == 0) atomicOr(err, kErrTimeout);
-    tc_fence_after();
-    if (ok) {
-      const int m = m0 + q * 32 + lane;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        if (n0 + c0 >= N) break;
+    const int q = warp & 3;            // TMEM lane quarter this warp may access
+    const int ew = warp - 2;           // epilogue warp index
+    uint8_t* my_in = sE + ew * 2 * (kInBox + kOutBox);
+    uint8_t* my_out = my_in + 2 * kInBox;
+    uint64_t* my_bar = inbar + 2 * ew;
+    const bool need_pre = (ep.epi == EPI_BWD_SILU || ep.epi == EPI_HEAD);
+    const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_F32 || ep.epi == EPI_HEAD);
+    const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? 4096u : 0u);
+    const bool out_f32 = (ep.epi == EPI_F32);
+    const bool store_pre = (ep.epi == EPI_FWD_SILU) && ep.pre;
+    uint32_t in_phase = 0;             // parity bit per input buffer
+    int oc = 0;                        // output chunks issued (buffer = oc & 1)
+    int ic = 0;                        // input chunks issued (buffer = ic & 1)
+    auto issue_in = [&](int m_box, int n_box) {
+      if (in_bytes == 0) return;
+      if (lane == 0) {
+        uint8_t* dst = my_in + (ic & 1) * kInBox;
+        mbar_expect_tx(&my_bar[ic & 1], in_bytes);
+        if (need_pre) tma_load_2d(dst, &em.pre, &my_bar[ic & 1], n_box, m_box);
+        if (need_add) tma_load_2d(dst + 2048, &em.add, &my_bar[ic & 1], n_box, m_box);
+      }
+      ++ic;
+    };
+    int lt = 0;
+    bool aborted = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int b = lt & 1, use = lt >> 1;
+      const bool ok = mbar_wait(&tfull[b], use & 1);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        *abort_flag = 1;
+        aborted = true;
+        break;
+      }
+      tc_fence_after();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      const int m0 = (t % tiles_m) * kTcBM, n0 = (t / tiles_m) * BN;
+      const int mrow = m0 + q * 32;     // first row of this warp's box
+      const int m = mrow + lane;
+      const bool live = m < M;
+      const float rs = (live && ep.rowscale) ? ep.rowscale[m] : 1.0f;
+      const float sg = (live && ep.rowsig) ? ep.rowsig[m] : 1.0f;
+      float acc1 = 0.0f;
+      const uint32_t base = tmem + (uint32_t)(b * COLS) + ((uint32_t)(q * 32) << 16);
+      const int nch = (min(BN, N - n0) + 31) / 32;
+      int cur_in = ic;                  // index of the input chunk for c = 0
+      issue_in(mrow, n0);
+      for (int c = 0; c < nch; ++c) {
+        const int n = n0 + 32 * c;
         float v[32];
-        tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (m < M) {
-          if (ep.vec && n0 + c0 + 32 <= N) {
-            epi_apply_vec32_bf16(ep, m, n0 + c0, v);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + c0 + j;
-              if (n < N) epi_apply<bf16>(ep, m, n, v[j]);
-            }
+        tc_ld32(base + (uint32_t)(32 * c), v);
+        if (c == nch - 1) {
+          // every TMEM read of this buffer is complete (tcgen05.wait::ld in tc_ld32)
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        float z[32], a[32];
+        if (in_bytes) {
+          const int ib = cur_in & 1;
+          const uint32_t par = (in_phase >> ib) & 1u;
+          if (!mbar_wait(&my_bar[ib], par)) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
           }
+          in_phase ^= (1u << ib);
+          const uint8_t* src = my_in + ib * kInBox;
+          if (need_pre) ld_bf16_row(src, lane, z);
+          if (need_add) ld_f32_row(src + 2048, lane, a);
+          __syncwarp();
+          ++cur_in;
+          if (c + 1 < nch) issue_in(mrow, n + 32);
+        }
+        // compute
+        float o2[32];
+        if (ep.epi == EPI_FWD_SILU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            o2[j] = v[j];
+            v[j] = v[j] * fast_sigmoid(v[j]) * rs;
+          }
+        } else if (ep.epi == EPI_F32) {
+          if (need_add) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += a[j];
+          }
+        } else if (ep.epi == EPI_BWD_SILU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float s = fast_sigmoid(z[j]);
+            v[j] = v[j] * s * (1.0f + z[j] * (1.0f - s));
+          }
+        } else if (ep.epi == EPI_HEAD) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float xb = v[j] + a[j];
+            const float s = fast_sigmoid(z[j]);
+            acc1 += xb * z[j] * s;
+            v[j] = xb * rs * s * (1.0f + z[j] * (1.0f - s));
+          }
+        } else {   // EPI_LAST
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float vn = (n + j < N) ? ep.v[n + j] : 0.0f;
+            const float s = fast_sigmoid(v[j]);
+            acc1 += vn * v[j] * s;
+            v[j] = sg * vn * rs * s * (1.0f + v[j] * (1.0f - s));
+          }
+        }
+        // stage and store
+        uint8_t* ob = my_out + (oc & 1) * kOutBox;
+        if (lane == 0) bulk_wait_read1();      // the store that used this buffer two chunks ago has read it
+        __syncwarp();
+        if (out_f32) st_f32_row(ob, lane, v);
+        else st_bf16_row(ob, lane, v);
+        if (store_pre) st_bf16_row(ob + 4096, lane, o2);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&em.out, ob, n, mrow);
+          if (store_pre) tma_store_2d(&em.pre, ob + 4096, n, mrow);
+          bulk_commit();
+        }
+        ++oc;
+      }
+      if (live) {
+        if (ep.epi == EPI_HEAD) {
+          ep.ubar[m] += acc1;
+        } else if (ep.epi == EPI_LAST) {
+          ep.Eout[m] = rs * acc1;
+          ep.ubar[m] = sg * acc1;
         }
       }
     }
+    (void)aborted;
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tc_dealloc(tmem, TMEM_COLS);
+    tc_dealloc(tmem, 2 * COLS);
   }
+}
+
+static int g_num_sms = 0;
+
+// 2-D tensor map over a row-major [rows][ld] array of `esize`-byte elements,
+// box 32 x 32, swizzle matched to the row width of the box.
+static bool make_box_map(CUtensorMap* tm, const void* base, int cols, int rows, int ld, int esize) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        esize == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 template <int BN>
@@ -303,14 +547,31 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
     }
     attr_set = true;
   }
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
   CUtensorMap ta, tb;
   if (!make_tmap(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)g.lda * 2, kTcBK, kTcBM) ||
       !make_tmap(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 2, kTcBK, BN)) {
     if (why) *why = "cuTensorMapEncodeTiled failed (alignment or extent)";
     return false;
   }
-  dim3 grid((g.M + kTcBM - 1) / kTcBM, (g.N + BN - 1) / BN);
-  gemm_tc_kernel<BN><<<grid, 192, tc_smem_bytes<BN>(), st>>>(ta, tb, make_epi(g), g.M, g.N, g.K, d_err);
+  EpiMaps em;
+  memset(&em, 0, sizeof em);
+  const bool f32out = (g.epi == EPI_F32);
+  bool ok = make_box_map(&em.out, g.out, g.N, g.M, g.ldo, f32out ? 4 : 2);
+  if (ok && g.pre) ok = make_box_map(&em.pre, g.pre, g.N, g.M, g.ldp, 2);
+  if (ok && g.add) ok = make_box_map(&em.add, g.add, g.N, g.M, g.ld_add, 4);
+  if (!ok) {
+    if (why) *why = "cuTensorMapEncodeTiled failed for an epilogue operand";
+    return false;
+  }
+  const int tiles = ((g.M + kTcBM - 1) / kTcBM) * ((g.N + BN - 1) / BN);
+  const int grid = tiles < g_num_sms ? tiles : g_num_sms;
+  gemm_tc_kernel<BN><<<grid, kThreads, tc_smem_bytes<BN>(), st>>>(ta, tb, em, make_epi(g), g.M, g.N, g.K, d_err);
   return true;
 }
 
@@ -325,6 +586,10 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
     return false;
   }
   const int tiles = (g.N + 255) / 256;
+  if ((g.epi == EPI_HEAD || g.epi == EPI_LAST) && tiles != 1) {
+    if (why) *why = "fused head epilogues need N <= 256";
+    return false;
+  }
   int bn = (g.N + tiles - 1) / tiles;
   bn = (bn + 31) / 32 * 32;
   switch (bn) {

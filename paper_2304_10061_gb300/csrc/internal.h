@@ -63,6 +63,15 @@ enum Epi : int {
   EPI_FWD_SILU = 0,   // pre = acc (optional store); out = silu(acc) * (rowscale ? rowscale[m] : 1)
   EPI_F32 = 1,        // out(f32) = acc + (add ? add[m][n] : 0)
   EPI_BWD_SILU = 2,   // out = acc * silu'(pre[m][n])
+  // Adjoint head of x = u * silu(z) fused into the GEMM producing xbar
+  // (BF16 path, whole rows per CTA): xbar = acc + add; out = xbar u silu'(z);
+  // ubar[m] += sum_n xbar_n silu(z_n).
+  EPI_HEAD = 3,
+  // Last latent layer fused with the folded edge-energy MLP and the start of
+  // the adjoint (BF16 path, whole rows per CTA): z = acc, h = silu(z);
+  // E[m] = u sum_n v_n h_n;  ubar[m] = sigma_m sum_n v_n h_n;
+  // out = sigma_m v u silu'(z)  (the gradient w.r.t. z, input of the adjoint GEMMs).
+  EPI_LAST = 4,
 };
 
 struct GemmArgs {
@@ -74,6 +83,10 @@ struct GemmArgs {
   void* pre = nullptr; int ldp = 0;
   const float* rowscale = nullptr;
   const float* add = nullptr; int ld_add = 0;
+  float* ubar = nullptr;           // EPI_HEAD / EPI_LAST
+  const float* v = nullptr;        // EPI_LAST: folded edge-energy vector [N]
+  const float* rowsig = nullptr;   // EPI_LAST: sigma_{Z_i} per row
+  float* Eout = nullptr;           // EPI_LAST: E_ij per row
 };
 
 // ---- launchers -----------------------------------------------------------
@@ -120,7 +133,8 @@ void nb_minmax_frac(const double* pos, int n, const double* inv, double* d_minma
 // edge kernels
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
-                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, cudaStream_t st);
+                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
+                   cudaStream_t st);
 void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
                    const float* ubar, const float* Ybar, float* g, cudaStream_t st);
 template <typename T>

@@ -105,10 +105,23 @@ def _peaks():
         return None
 
 
+def _by_kernel(report: dict) -> dict:
+    """Per-launch records are labelled '<kernel>/<which map>'; sum them per kernel."""
+    out = {}
+    for k, v in report.items():
+        base = k.split("/")[0]
+        a = out.setdefault(base, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+        for f in a:
+            a[f] += v[f]
+    return out
+
+
 def _roofline(report: dict, step_ms_total: float):
     """Dominant kernel (largest total time) of the timed region against its roofline."""
     if not report:
         return None
+    detail = report
+    report = _by_kernel(report)
     name, r = max(report.items(), key=lambda kv: kv[1]["ms"])
     peaks = _peaks()
     tensor = name.startswith("gemm_tc")
@@ -125,7 +138,12 @@ def _roofline(report: dict, step_ms_total: float):
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
             "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
             "traffic": None, "launches": r["launches"], "ms_per_launch": round(r["ms"] / max(r["launches"], 1), 5),
-            "share_of_timed_region": share}
+            "share_of_timed_region": share,
+            "gemm_detail": {k.split("/", 1)[1]: {
+                                                 "share": round(v["ms"] / max(step_ms_total, 1e-9), 4),
+                                                 "TFLOP/s": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 1),
+                                                 "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
+                            for k, v in sorted(detail.items(), key=lambda kv: -kv[1]["ms"]) if "/" in k}}
 
 
 def _cpu_baseline(arch, w, blob, precision_models: dict):

@@ -87,7 +87,7 @@ struct Cap {
   int64_t v = 0;
 };
 struct Caps {
-  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat;
+  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat, pos4;
   Cap ej, ei, eS, ed, col_edge, Ee, g;
   Cap cc, cs, ccur;
   Cap offs, cells, pbc, nimg, Eout, Wout;
@@ -142,6 +142,7 @@ struct allegro_ctx {
   int* d_cell_of = nullptr;
   int* d_wrap = nullptr;
   int* d_sorted = nullptr;
+  float4* d_pos4 = nullptr;                // wrapped float32 positions in cell order
   int* d_atom_struct = nullptr;
   double* d_Eatom = nullptr;
   double* d_F = nullptr;
@@ -173,6 +174,7 @@ struct allegro_ctx {
   int* d_err = nullptr;
   int* d_total = nullptr;
   double* d_minmax = nullptr;
+  double* d_red_scratch = nullptr;         // partial sums of the per-structure reduction
   Caps caps;
   Profiler prof;
   int64_t launches = 0;                    // kernel launches issued by this context
@@ -562,6 +564,7 @@ allegro_status stage_atoms(allegro_ctx* c, int64_t n, const double* pos, const i
   CUDA_TRY(c, grow(c->d_cell_of, k.cell_of, need));
   CUDA_TRY(c, grow(c->d_wrap, k.wrap, 3 * need));
   CUDA_TRY(c, grow(c->d_sorted, k.sorted, need));
+  CUDA_TRY(c, grow(c->d_pos4, k.pos4, need));
   CUDA_TRY(c, grow(c->d_atom_struct, k.atom_struct, need));
   CUDA_TRY(c, grow(c->d_Eatom, k.Eatom, need));
   CUDA_TRY(c, grow(c->d_F, k.F, 3 * need));
@@ -685,6 +688,26 @@ bool invert3(const double* m, double* inv) {
   return true;
 }
 
+// Stable profiling label of a GEMM: which linear map, forward or transposed.
+const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
+  static std::vector<std::string> names;
+  std::string n;
+  for (size_t k = 0; k < c->tb.size(); ++k)
+    if (W == &c->tb[k]) n = "two_body." + std::to_string(k);
+  if (W == &c->w01) n = "embed_env1";
+  if (W == &c->env2) n = "env2";
+  for (size_t L = 0; L < c->lat.size(); ++L)
+    for (size_t k = 0; k < c->lat[L].size(); ++k)
+      if (W == &c->lat[L][k]) n = "latent." + std::to_string(L + 1) + "." + std::to_string(k);
+  const char* en[] = {"silu", "f32", "dsilu", "head", "last"};
+  n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : "gemm_simt/") + n + (trans ? "^T" : "") + ":" +
+      en[epi];
+  for (auto& x : names)
+    if (x == n) return x.c_str();
+  names.push_back(n);
+  return names.back().c_str();
+}
+
 template <typename T>
 allegro_status gemm(allegro_ctx* c, GemmArgs g) {
   if (c->prec == ALLEGRO_PREC_BF16) {
@@ -714,7 +737,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     const double outb = (epi == EPI_F32) ? 4.0 : act;
     const double bytes = (double)Ec * (K * act + N * outb + (pre ? N * act : 0.0) + (add ? N * 4.0 : 0.0) +
                                        (rowscale ? 4.0 : 0.0)) + (double)N * K * act;
-    ProfScope ps(c, c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc" : "gemm_simt", 2.0 * Ec * (double)N * K, bytes);
+    ProfScope ps(c, gemm_label(c, &W, trans, epi), 2.0 * Ec * (double)N * K, bytes);
     GemmArgs g;
     g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
     g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
@@ -926,7 +949,7 @@ allegro_status evaluate(allegro_ctx* c, bool backward) {
   {
     ProfScope ps(c, "struct_reduce", 0.0, (double)n * (backward ? 104.0 : 8.0));
     struct_reduce(c->nstruct, c->d_offs, c->d_Eatom, c->d_Wat, c->d_F, backward, c->d_Eout, c->d_Wout, c->d_err,
-                  c->stream);
+                  c->d_red_scratch, n, c->stream);
   }
   CUDA_TRY(c, cudaGetLastError());
   return ALLEGRO_OK;
@@ -997,7 +1020,7 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
       cudaMemcpy(c->d_map, c->species_map.data(), c->nmap * 4, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(c, ALLEGRO_E_OOM, "species map upload failed"));
   if (cudaMalloc(&c->d_err, 16) != cudaSuccess || cudaMalloc(&c->d_total, 16) != cudaSuccess ||
-      cudaMalloc(&c->d_minmax, 12 * 8) != cudaSuccess)
+      cudaMalloc(&c->d_minmax, 12 * 8) != cudaSuccess || cudaMalloc(&c->d_red_scratch, 12 * 1024 * 8) != cudaSuccess)
     return bail(fail(c, ALLEGRO_E_OOM, "scratch allocation failed"));
   cudaMemset(c->d_err, 0, 16);
   *out = c;
@@ -1136,11 +1159,32 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
     CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cursor, 0, (size_t)(ncell + 1) * 4, st));
     nb_place(c->d_cell_of, n, c->d_cell_start, c->d_cell_cursor, c->d_sorted, st);
     nb_sort_cells(c->d_cell_start, (int)ncell, c->d_sorted, st);
+    nb_pos4(c->d_pos, n, g, c->d_wrap, c->d_sorted, c->d_pos4, st);
+  }
+  // Error band of the float32 prefilter: bound X on |wrapped coordinate| and
+  // |image offset|, per-component error <= 8 ulp(X), squared-distance error
+  // <= 2 sqrt3 r_c delta + 3 delta^2 + rounding of the sum; safety factor 4.
+  float band;
+  {
+    double X = 0.0, Xoff = 0.0;
+    for (int k3 = 0; k3 < 3; ++k3) {
+      double Fk = g.pbc[k3] ? 1.0 : std::max(fabs(hmm[k3]), fabs(hmm[3 + k3])) + 1.0;
+      double rowlen = cell ? sqrt(hcell[3 * k3] * hcell[3 * k3] + hcell[3 * k3 + 1] * hcell[3 * k3 + 1] +
+                                  hcell[3 * k3 + 2] * hcell[3 * k3 + 2])
+                           : 1.0;
+      X += Fk * rowlen;
+      Xoff += (g.pbc[k3] ? g.R[k3] : 0) * rowlen;
+    }
+    const double delta = 8.0 * (X + Xoff) * std::ldexp(1.0, -23);
+    const double bd = 4.0 * (2.0 * sqrt(3.0) * rc * delta + 3.0 * delta * delta + 1e-6 * rc * rc);
+    band = (float)bd;
+    if (!(band > 0) || !std::isfinite(band) || band > 0.25 * rc * rc) band = 1e30f;   // prefilter off
   }
   const double rc2 = rc * rc;
   {
     ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
-    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, rc2, c->d_count,
+    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, rc2, band,
+              c->d_count,
               nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
     exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
   }
@@ -1152,7 +1196,8 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
   {
     ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
-    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, rc2, nullptr,
+    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, rc2, band,
+              nullptr,
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
@@ -1340,10 +1385,10 @@ void allegro_destroy(allegro_ctx* c) {
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->weight_allocs) cudaFree(p);
   void* bufs[] = {c->d_map, c->d_pos, c->d_types, c->d_species, c->d_row_ptr, c->d_col_ptr, c->d_count,
-                  c->d_cell_of, c->d_wrap, c->d_sorted, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
+                  c->d_cell_of, c->d_wrap, c->d_sorted, c->d_pos4, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
                   c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_col_edge, c->d_Ee, c->d_g, c->d_cell_count,
                   c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
-                  c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->ws};
+                  c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

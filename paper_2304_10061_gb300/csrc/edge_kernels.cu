@@ -80,10 +80,12 @@ __global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, c
   if (e >= Ec) return;
   size_t eg = (size_t)e0 + e;
   double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
-  double r64 = sqrt(dx * dx + dy * dy + dz * dz);
-  double ir = 1.0 / r64;
-  float r = (float)r64;
-  float x = (float)(dx * ir), y = (float)(dy * ir), z = (float)(dz * ir);
+  // float32 geometry from the exact float64 displacement
+  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+  const float r2 = fx * fx + fy * fy + fz * fz;
+  const float ir32 = rsqrtf(r2);
+  const float r = r2 * ir32;
+  const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
   float Y[kMaxS];
   sh_eval(bc.lmax, x, y, z, Y);
   for (int a = 0; a < bc.S; ++a) Yout[(size_t)e * bc.S + a] = Y[a];
@@ -100,7 +102,6 @@ __global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, c
   for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
   row[zi] = to_act<T>(1.0f);
   row[bc.ns + zj] = to_act<T>(1.0f);
-  float ir32 = 1.0f / r;
   for (int n = 1; n <= bc.nb; ++n) {
     float s = sinpif((float)n * xr);
     row[2 * bc.ns + n - 1] = to_act<T>(bc.pref * s * ir32);
@@ -127,15 +128,16 @@ __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, B
   if (e >= Ec) return;
   size_t eg = (size_t)e0 + e;
   double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
-  double r64 = sqrt(dx * dx + dy * dy + dz * dz);
-  double ir = 1.0 / r64;
-  float r = (float)r64;
-  float x = (float)(dx * ir), y = (float)(dy * ir), z = (float)(dz * ir);
+  // float32 geometry from the exact float64 displacement
+  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+  const float r2 = fx * fx + fy * fy + fz * fz;
+  const float ir32 = rsqrtf(r2);
+  const float r = r2 * ir32;
+  const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
   float xr = r * bc.inv_rc;
   // dE/dr from the Bessel basis and the envelope
   float dEdr = 0.0f;
   const float* Bb = inbar + (size_t)e * ld_in + 2 * bc.ns;
-  float ir32 = 1.0f / r;
   for (int n = 1; n <= bc.nb; ++n) {
     float s, c;
     sincospif((float)n * xr, &s, &c);
@@ -315,9 +317,51 @@ __global__ void struct_reduce_kernel(const int64_t* __restrict__ offs, const dou
   }
 }
 
+// Large single structures: first a fixed grid of blocks reduces contiguous
+// atom ranges into partials (offsets describe the ranges), then one block
+// reduces the partials; both in fixed order.
+__global__ void partial_offsets_kernel(const int64_t* __restrict__ offs, int parts, int64_t* __restrict__ po) {
+  const long long n = offs[1];
+  for (int p = threadIdx.x; p <= parts; p += blockDim.x) po[p] = (n * p) / parts;
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partE, const double* __restrict__ partW, int parts,
+                                    bool want_w, double* __restrict__ E_out, double* __restrict__ W_out) {
+  __shared__ double sh[10][256];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int p = threadIdx.x; p < parts; p += blockDim.x) {
+    acc[0] += partE[p];
+    if (want_w)
+      for (int q = 0; q < 9; ++q) acc[1 + q] += partW[9 * (size_t)p + q];
+  }
+  for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    E_out[0] = sh[0][0];
+    if (want_w)
+      for (int q = 0; q < 9; ++q) W_out[q] = sh[1 + q][0];
+  }
+}
+
 void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const double* Wat, const double* F,
-                   bool want_w, double* E_out, double* W_out, int* d_err, cudaStream_t st) {
+                   bool want_w, double* E_out, double* W_out, int* d_err, double* scratch, int64_t n_atoms,
+                   cudaStream_t st) {
   if (nstruct <= 0) return;
+  const int parts = 1024;
+  if (nstruct == 1 && n_atoms > 16 * parts && scratch) {
+    int64_t* po = reinterpret_cast<int64_t*>(scratch);
+    double* pE = scratch + (parts + 2);
+    double* pW = pE + parts;
+    partial_offsets_kernel<<<1, 256, 0, st>>>(offs, parts, po);
+    struct_reduce_kernel<<<parts, 256, 0, st>>>(po, E_atom, Wat, F, want_w, pE, pW, d_err);
+    sum_partials_kernel<<<1, 256, 0, st>>>(pE, pW, parts, want_w, E_out, W_out);
+    return;
+  }
   struct_reduce_kernel<<<nstruct, 256, 0, st>>>(offs, E_atom, Wat, F, want_w, E_out, W_out, d_err);
 }
 

@@ -75,6 +75,7 @@ enum Epi : int {
 };
 
 struct GemmArgs {
+  const char* label = "gemm";      // profiling label
   int M = 0, N = 0, K = 0;
   const void* A = nullptr; int lda = 0;     // [M][lda] activations (float or bf16)
   const Lin* W = nullptr; bool trans = false;
@@ -114,9 +115,11 @@ void nb_bin(const double* pos, int n, const CellGrid& g, int* cell_of, int* wrap
 void nb_place(const int* cell_of, int n, const int* cell_start, int* cell_cursor, int* sorted,
               cudaStream_t st);
 void nb_sort_cells(const int* cell_start, int n_cells, int* sorted, cudaStream_t st);
+void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
+             cudaStream_t st);
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, double rc2,
-               int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
+               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, double rc2,
+               float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
                cudaStream_t st);
 void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,
                            const double* cells, const int* pbc, const int* nimg, double rc2,
@@ -147,7 +150,8 @@ void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_e
                  const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
                  bool want_forces, double* E_atom, double* F, double* Wat, cudaStream_t st);
 void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const double* Wat, const double* F,
-                   bool want_w, double* E_out, double* W_out, int* d_err, cudaStream_t st);
+                   bool want_w, double* E_out, double* W_out, int* d_err, double* scratch, int64_t n_atoms,
+                   cudaStream_t st);
 
 // row (per-atom) kernels: environment sums and tensor products
 struct RowIO {

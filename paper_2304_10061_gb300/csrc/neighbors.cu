@@ -273,10 +273,34 @@ __device__ __forceinline__ bool pair_test(const double* __restrict__ pi, const d
   return r2 < rc2;
 }
 
+// Wrapped positions pw = pos - wrap . cell in float32, stored in cell-sorted
+// order (pos4[s] belongs to atom sorted[s]).
+__global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, const int* __restrict__ wrap,
+                            const int* __restrict__ sorted, float4* __restrict__ pos4) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int j = sorted[s];
+  double p[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    p[x] = pos[3 * (size_t)j + x];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[x] -= (double)wrap[3 * (size_t)j + k] * g.cell[k * 3 + x];
+  }
+  pos4[s] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.0f);
+}
+
+// Neighbour search.  A float32 prefilter on the wrapped positions decides
+// every candidate whose squared distance is farther than `band` from r_c^2;
+// candidates inside the band take the exact float64 test.  `band` is computed
+// on the host from a bound on the float32 rounding of the wrapped coordinates
+// and image offsets (with a safety factor), so the prefilter never changes a
+// decision.  Accepted edges get their float64 displacement for later stages.
 __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, CellGrid g,
                               const int* __restrict__ cell_of, const int* __restrict__ wrap,
                               const int* __restrict__ cell_start, const int* __restrict__ sorted,
-                              double rc2, int* __restrict__ count, const int* __restrict__ row_ptr,
+                              const float4* __restrict__ pos4, double rc2, float band,
+                              int* __restrict__ count, const int* __restrict__ row_ptr,
                               int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS,
                               double* __restrict__ ed, int* __restrict__ d_err) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,7 +312,13 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
   c[1] = (ci / g.n[2]) % g.n[1];
   c[0] = ci / (g.n[2] * g.n[1]);
   const int wi0 = wrap[3 * (size_t)i], wi1 = wrap[3 * (size_t)i + 1], wi2 = wrap[3 * (size_t)i + 2];
-  double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+  const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+  const float4 pi4 = pos4[t];
+  const float rc2f = (float)rc2;
+  const float lo2 = rc2f - band, hi2 = rc2f + band;
+  float cf[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) cf[k] = (float)g.cell[k];
   int k = 0;
   const int base = fill ? row_ptr[i] : 0;
   const int cap = fill ? (row_ptr[i + 1] - base) : 0;
@@ -306,14 +336,28 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
         else if (cc2 < 0 || cc2 >= g.n[2]) continue;
         const int cell = (cc0 * g.n[1] + cc1) * g.n[2] + cc2;
         const int b = cell_start[cell], e = cell_start[cell + 1];
+        // image offset of this stencil cell (float32), relative to i
+        const float ox = (float)q0 * cf[0] + (float)q1 * cf[3] + (float)q2 * cf[6] - pi4.x;
+        const float oy = (float)q0 * cf[1] + (float)q1 * cf[4] + (float)q2 * cf[7] - pi4.y;
+        const float oz = (float)q0 * cf[2] + (float)q1 * cf[5] + (float)q2 * cf[8] - pi4.z;
         for (int s = b; s < e; ++s) {
+          const float4 pj = pos4[s];
+          const float dx = pj.x + ox, dy = pj.y + oy, dz = pj.z + oz;
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          if (r2f > hi2) continue;
           const int j = sorted[s];
           int S0 = g.pbc[0] ? q0 - wrap[3 * (size_t)j] + wi0 : 0;
           int S1 = g.pbc[1] ? q1 - wrap[3 * (size_t)j + 1] + wi1 : 0;
           int S2 = g.pbc[2] ? q2 - wrap[3 * (size_t)j + 2] + wi2 : 0;
           if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
           double d[3];
-          if (!pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2, d)) continue;
+          if (r2f >= lo2 || fill) {
+            const bool in = pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2, d);
+            if (!in) {
+              if (r2f < lo2) atomicOr(d_err, kErrNeighbor);   // the prefilter bound was violated
+              continue;
+            }
+          }
           if (fill) {
             if (k < cap) {
               size_t o = (size_t)base + k;
@@ -335,12 +379,19 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
   }
 }
 
-void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, double rc2, int* count,
-               const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err, cudaStream_t st) {
+void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
+             cudaStream_t st) {
   if (n <= 0) return;
-  search_kernel<<<(n + 127) / 128, 128, 0, st>>>(fill, pos, n, g, cell_of, wrap, cell_start, sorted,
-                                                 rc2, count, row_ptr, ej, ei, eS, ed, d_err);
+  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, n, g, wrap, sorted, pos4);
+}
+
+void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
+               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, double rc2,
+               float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
+               cudaStream_t st) {
+  if (n <= 0) return;
+  search_kernel<<<(n + 127) / 128, 128, 0, st>>>(fill, pos, n, g, cell_of, wrap, cell_start, sorted, pos4,
+                                                 rc2, band, count, row_ptr, ej, ei, eS, ed, d_err);
 }
 
 // ---------------------------------------------------------------------------

@@ -153,6 +153,21 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 16 consecutive 32-bit TMEM columns -> 16 registers per thread.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor: K-major operand tile written by TMA with
 // the 128-byte swizzle (rows of 128 bytes, 8-row groups 1024 bytes apart).
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -172,13 +187,15 @@ __device__ __forceinline__ constexpr uint32_t idesc_bf16() {
 }
 
 constexpr int kTcBM = 128, kTcBK = 64;
-constexpr int kEpiWarps = 4;                 // warps 2..5
+constexpr int kEpiWarps = 8;                 // warps 2..9: two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-// Per epilogue warp: two input staging buffers (pre bf16 32x32 + add f32 32x32)
-// and two output staging buffers (two 32x32 boxes, bf16 or f32).
-constexpr int kInBox = 2048 + 4096;
-constexpr int kOutBox = 4096 + 4096;
-constexpr int kEpiSmem = kEpiWarps * 2 * (kInBox + kOutBox);
+// Per epilogue warp: two output staging buffers, each one float32 32x32 box
+// or two bf16 32x32 boxes (activation and pre-activation).
+constexpr int kOutBox = 4096;
+// One input slot per epilogue warp: the pre-activation (bf16 32x32) and/or the
+// float32 addend (32x32) of the warp's next chunk, fetched by TMA.
+constexpr int kInSlot = 2048 + 4096;
+constexpr int kEpiSmem = kEpiWarps * (2 * kOutBox + kInSlot);
 
 template <int BN>
 __host__ __device__ constexpr int tc_stage_bytes() {
@@ -187,9 +204,9 @@ __host__ __device__ constexpr int tc_stage_bytes() {
 
 template <int BN>
 __host__ __device__ constexpr int tc_stages() {
-  return (100 * 1024) / tc_stage_bytes<BN>() > 6 ? 6
-         : (100 * 1024) / tc_stage_bytes<BN>() < 2 ? 2
-                                                    : (100 * 1024) / tc_stage_bytes<BN>();
+  return (110 * 1024) / tc_stage_bytes<BN>() > 6 ? 6
+         : (110 * 1024) / tc_stage_bytes<BN>() < 2 ? 2
+                                                    : (110 * 1024) / tc_stage_bytes<BN>();
 }
 
 template <int BN>
@@ -199,7 +216,7 @@ __host__ __device__ constexpr int tc_tmem_cols() {   // one accumulator buffer
 
 template <int BN>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)tc_stages<BN>() * tc_stage_bytes<BN>() + kEpiSmem + 1024 + 256;
+  return (size_t)tc_stages<BN>() * tc_stage_bytes<BN>() + kEpiSmem + 1024 + 3072;
 }
 
 // --- epilogue staging: 32 x 32 boxes moved by TMA --------------------------
@@ -254,6 +271,35 @@ __device__ __forceinline__ void ld_f32_row(const uint8_t* box, int r, float (&v)
   }
 }
 
+// 16 columns (half hh of a 32-column box row) into the swizzled staging boxes.
+__device__ __forceinline__ void st_bf16_half(uint8_t* box, int r, int hh, const float (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    uint4 x = make_uint4(pack_bf16x2(v[8 * u + 0], v[8 * u + 1]), pack_bf16x2(v[8 * u + 2], v[8 * u + 3]),
+                         pack_bf16x2(v[8 * u + 4], v[8 * u + 5]), pack_bf16x2(v[8 * u + 6], v[8 * u + 7]));
+    *reinterpret_cast<uint4*>(box + sw64(r, 2 * hh + u)) = x;
+  }
+}
+__device__ __forceinline__ void st_f32_half(uint8_t* box, int r, int hh, const float (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<float4*>(box + sw128(r, 4 * hh + u)) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+}
+__device__ __forceinline__ void load_bf16x16(const bf16* p, float (&v)[16]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    uint4 x = q[k];
+    uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float2 f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w[t]));
+      v[8 * k + 2 * t] = f.x;
+      v[8 * k + 2 * t + 1] = f.y;
+    }
+  }
+}
+
 __device__ __forceinline__ float fast_sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 struct EpiMaps {
@@ -284,8 +330,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;     // [2]
   uint64_t* tempty = tfull + 2;         // [2]
-  uint64_t* inbar = tempty + 2;         // [kEpiWarps][2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + 2 * kEpiWarps);
+  uint64_t* rsbar = tempty + 2;         // [4 quarters][2 buffers]: partial row sums ready
+  uint64_t* inbar = rsbar + 8;          // [kEpiWarps]: input slot filled
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kEpiWarps);
+  float* rowsum = reinterpret_cast<float*>(tslot + 4);                 // [4][2][32] partial row sums
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,7 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
     }
-    for (int q = 0; q < 2 * kEpiWarps; ++q) mbar_init(&inbar[q], 1);
+    for (int q = 0; q < 8; ++q) mbar_init(&rsbar[q], 1);
+    for (int q = 0; q < kEpiWarps; ++q) mbar_init(&inbar[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -370,45 +419,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
+    // Epilogue: warp pair (h = 0, 1) per TMEM lane quarter q; warp h takes
+    // the 32-column chunks c = h, h + 2, ... of each tile, in 16-column halves.
     const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int ew = warp - 2;           // epilogue warp index
-    uint8_t* my_in = sE + ew * 2 * (kInBox + kOutBox);
-    uint8_t* my_out = my_in + 2 * kInBox;
-    uint64_t* my_bar = inbar + 2 * ew;
+    const int ew = warp - 2;           // epilogue warp index 0..7
+    const int h = ew >> 2;
+    uint8_t* my_out = sE + ew * (2 * kOutBox + kInSlot);
+    uint8_t* my_in = my_out + 2 * kOutBox;
     const bool need_pre = (ep.epi == EPI_BWD_SILU || ep.epi == EPI_HEAD);
     const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_F32 || ep.epi == EPI_HEAD);
     const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? 4096u : 0u);
     const bool out_f32 = (ep.epi == EPI_F32);
     const bool store_pre = (ep.epi == EPI_FWD_SILU) && ep.pre;
-    uint32_t in_phase = 0;             // parity bit per input buffer
-    int oc = 0;                        // output chunks issued (buffer = oc & 1)
-    int ic = 0;                        // input chunks issued (buffer = ic & 1)
-    auto issue_in = [&](int m_box, int n_box) {
-      if (in_bytes == 0) return;
+    const bool rowsums = (ep.epi == EPI_HEAD || ep.epi == EPI_LAST);
+    uint32_t in_par = 0;
+    // fetch the inputs of chunk c of tile t into the slot (lane 0 issues)
+    auto fetch = [&](int tt, int cc) {
+      if (in_bytes == 0 || tt >= ntiles) return;
       if (lane == 0) {
-        uint8_t* dst = my_in + (ic & 1) * kInBox;
-        mbar_expect_tx(&my_bar[ic & 1], in_bytes);
-        if (need_pre) tma_load_2d(dst, &em.pre, &my_bar[ic & 1], n_box, m_box);
-        if (need_add) tma_load_2d(dst + 2048, &em.add, &my_bar[ic & 1], n_box, m_box);
+        const int mb = (tt % tiles_m) * kTcBM + q * 32, nb = (tt / tiles_m) * BN + 32 * cc;
+        mbar_expect_tx(&inbar[ew], in_bytes);
+        if (need_pre) tma_load_2d(my_in, &em.pre, &inbar[ew], nb, mb);
+        if (need_add) tma_load_2d(my_in + 2048, &em.add, &inbar[ew], nb, mb);
       }
-      ++ic;
     };
+    auto nch_of = [&](int tt) { return (min(BN, N - (tt / tiles_m) * BN) + 31) / 32; };
+    int oc = 0;                        // output chunks issued (buffer = oc & 1)
     int lt = 0;
-    bool aborted = false;
+    if (h < nch_of(blockIdx.x)) fetch(blockIdx.x, h);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int b = lt & 1, use = lt >> 1;
       const bool ok = mbar_wait(&tfull[b], use & 1);
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         *abort_flag = 1;
-        aborted = true;
         break;
       }
       tc_fence_after();
-      if (*abort_flag) {
-        aborted = true;
-        break;
-      }
+      if (*abort_flag) break;
       const int m0 = (t % tiles_m) * kTcBM, n0 = (t / tiles_m) * BN;
       const int mrow = m0 + q * 32;     // first row of this warp's box
       const int m = mrow + lane;
@@ -417,97 +465,116 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float sg = (live && ep.rowsig) ? ep.rowsig[m] : 1.0f;
       float acc1 = 0.0f;
       const uint32_t base = tmem + (uint32_t)(b * COLS) + ((uint32_t)(q * 32) << 16);
-      const int nch = (min(BN, N - n0) + 31) / 32;
-      int cur_in = ic;                  // index of the input chunk for c = 0
-      issue_in(mrow, n0);
-      for (int c = 0; c < nch; ++c) {
-        const int n = n0 + 32 * c;
-        float v[32];
-        tc_ld32(base + (uint32_t)(32 * c), v);
-        if (c == nch - 1) {
-          // every TMEM read of this buffer is complete (tcgen05.wait::ld in tc_ld32)
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[b]);
-        }
-        float z[32], a[32];
-        if (in_bytes) {
-          const int ib = cur_in & 1;
-          const uint32_t par = (in_phase >> ib) & 1u;
-          if (!mbar_wait(&my_bar[ib], par)) {
-            if (lane == 0) atomicOr(err, kErrTimeout);
-            *abort_flag = 1;
-          }
-          in_phase ^= (1u << ib);
-          const uint8_t* src = my_in + ib * kInBox;
-          if (need_pre) ld_bf16_row(src, lane, z);
-          if (need_add) ld_f32_row(src + 2048, lane, a);
-          __syncwarp();
-          ++cur_in;
-          if (c + 1 < nch) issue_in(mrow, n + 32);
-        }
-        // compute
-        float o2[32];
-        if (ep.epi == EPI_FWD_SILU) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            o2[j] = v[j];
-            v[j] = v[j] * fast_sigmoid(v[j]) * rs;
-          }
-        } else if (ep.epi == EPI_F32) {
-          if (need_add) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += a[j];
-          }
-        } else if (ep.epi == EPI_BWD_SILU) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float s = fast_sigmoid(z[j]);
-            v[j] = v[j] * s * (1.0f + z[j] * (1.0f - s));
-          }
-        } else if (ep.epi == EPI_HEAD) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float xb = v[j] + a[j];
-            const float s = fast_sigmoid(z[j]);
-            acc1 += xb * z[j] * s;
-            v[j] = xb * rs * s * (1.0f + z[j] * (1.0f - s));
-          }
-        } else {   // EPI_LAST
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float vn = (n + j < N) ? ep.v[n + j] : 0.0f;
-            const float s = fast_sigmoid(v[j]);
-            acc1 += vn * v[j] * s;
-            v[j] = sg * vn * rs * s * (1.0f + v[j] * (1.0f - s));
-          }
-        }
-        // stage and store
+      const int nch = nch_of(t);
+      for (int c = h; c < nch; c += 2) {
         uint8_t* ob = my_out + (oc & 1) * kOutBox;
         if (lane == 0) bulk_wait_read1();      // the store that used this buffer two chunks ago has read it
         __syncwarp();
-        if (out_f32) st_f32_row(ob, lane, v);
-        else st_bf16_row(ob, lane, v);
-        if (store_pre) st_bf16_row(ob + 4096, lane, o2);
+        float zc[32], ac[32];
+        if (in_bytes) {
+          if (!mbar_wait(&inbar[ew], in_par)) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+          }
+          in_par ^= 1u;
+          if (need_pre) ld_bf16_row(my_in, lane, zc);
+          if (need_add) ld_f32_row(my_in + 2048, lane, ac);
+          __syncwarp();
+          // prefetch this warp's next chunk (possibly in its next tile)
+          if (c + 2 < nch) fetch(t, c + 2);
+          else if (t + (int)gridDim.x < ntiles && h < nch_of(t + gridDim.x)) fetch(t + gridDim.x, h);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int n = n0 + 32 * c + 16 * hh;
+          float v[16];
+          tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
+          float z[16], a[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            z[j] = need_pre ? zc[16 * hh + j] : 0.0f;
+            a[j] = need_add ? ac[16 * hh + j] : 0.0f;
+          }
+          float o2[16];
+          if (ep.epi == EPI_FWD_SILU) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              o2[j] = v[j];
+              v[j] = v[j] * fast_sigmoid(v[j]) * rs;
+            }
+          } else if (ep.epi == EPI_F32) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += a[j];
+          } else if (ep.epi == EPI_BWD_SILU) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float sgm = fast_sigmoid(z[j]);
+              v[j] = v[j] * sgm * (1.0f + z[j] * (1.0f - sgm));
+            }
+          } else if (ep.epi == EPI_HEAD) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float xb = v[j] + a[j];
+              const float sgm = fast_sigmoid(z[j]);
+              acc1 += xb * z[j] * sgm;
+              v[j] = xb * rs * sgm * (1.0f + z[j] * (1.0f - sgm));
+            }
+          } else {   // EPI_LAST
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float vn = (n + j < N) ? ep.v[n + j] : 0.0f;
+              const float sgm = fast_sigmoid(v[j]);
+              acc1 += vn * v[j] * sgm;
+              v[j] = sg * vn * rs * sgm * (1.0f + v[j] * (1.0f - sgm));
+            }
+          }
+          if (out_f32) st_f32_half(ob, lane, hh, v);
+          else st_bf16_half(ob, lane, hh, v);
+          if (store_pre) st_bf16_half(ob + 2048, lane, hh, o2);
+        }
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          tma_store_2d(&em.out, ob, n, mrow);
-          if (store_pre) tma_store_2d(&em.pre, ob + 4096, n, mrow);
+          tma_store_2d(&em.out, ob, n0 + 32 * c, mrow);
+          if (store_pre) tma_store_2d(&em.pre, ob + 2048, n0 + 32 * c, mrow);
           bulk_commit();
         }
         ++oc;
       }
-      if (live) {
-        if (ep.epi == EPI_HEAD) {
-          ep.ubar[m] += acc1;
-        } else if (ep.epi == EPI_LAST) {
-          ep.Eout[m] = rs * acc1;
-          ep.ubar[m] = sg * acc1;
+      // every TMEM read of this buffer by this warp is complete (tcgen05.wait::ld)
+      tc_fence_before();
+      __syncwarp();
+      if (!rowsums || h == 1) {
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (rowsums) {
+        // combine the two warps' partial row sums in a fixed order (h = 0 + h = 1);
+        // warp h = 0 releases the TMEM buffer only after reading the partials, so
+        // warp h = 1 cannot overwrite them before they are read
+        float* rsum = rowsum + (q * 2 + b) * 32;
+        if (h == 1) {
+          rsum[lane] = acc1;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&rsbar[q * 2 + b]);
+        } else {
+          if (!mbar_wait(&rsbar[q * 2 + b], use & 1)) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+          }
+          const float tot = acc1 + rsum[lane];
+          if (live) {
+            if (ep.epi == EPI_HEAD) {
+              ep.ubar[m] += tot;
+            } else {
+              ep.Eout[m] = rs * tot;
+              ep.ubar[m] = sg * tot;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
         }
       }
     }
-    (void)aborted;
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   }

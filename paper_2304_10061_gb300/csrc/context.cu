@@ -452,8 +452,8 @@ struct WS {
   void* X[2]; int ld_X[2];
   void* Xlast; int ld_Xlast;
   std::vector<std::vector<void*>> Zlat; std::vector<int> ld_Zlat;
-  float* W01; int ld_W01;
-  float* w2; int ld_w2;
+  void* W01; int ld_W01;     // [w0 | w1] (activation type)
+  void* w2; int ld_w2;       // (activation type)
   float* D[2]; int ld_D[2];
   void* wbar01; int ld_wbar01;
   void* wbar2; int ld_wbar2;
@@ -500,9 +500,9 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   for (int L = 0; L < a.nl; ++L)
     for (int k = 0; k < nlat; ++k) w->Zlat[L][k] = take((size_t)Ec * w->ld_Zlat[k] * act_bytes);
   w->ld_W01 = pad8(2 * nw);
-  w->W01 = (float*)take((size_t)Ec * w->ld_W01 * 4);
+  w->W01 = take((size_t)Ec * w->ld_W01 * act_bytes);
   w->ld_w2 = pad8(nw);
-  w->w2 = (a.nl == 2) ? (float*)take((size_t)Ec * w->ld_w2 * 4) : nullptr;
+  w->w2 = (a.nl == 2) ? take((size_t)Ec * w->ld_w2 * act_bytes) : nullptr;
   w->ld_wbar01 = pad8(2 * nw);
   w->wbar01 = take((size_t)Ec * w->ld_wbar01 * act_bytes);
   w->ld_wbar2 = pad8(nw);
@@ -699,7 +699,7 @@ const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
   for (size_t L = 0; L < c->lat.size(); ++L)
     for (size_t k = 0; k < c->lat[L].size(); ++k)
       if (W == &c->lat[L][k]) n = "latent." + std::to_string(L + 1) + "." + std::to_string(k);
-  const char* en[] = {"silu", "f32", "dsilu", "head", "last"};
+  const char* en[] = {"silu", "f32", "dsilu", "head", "last", "linear"};
   n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : "gemm_simt/") + n + (trans ? "^T" : "") + ":" +
       en[epi];
   for (auto& x : names)
@@ -734,7 +734,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
                int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
-    const double outb = (epi == EPI_F32) ? 4.0 : act;
+    const double outb = (epi == EPI_F32) ? 4.0 : act;   // EPI_LINEAR / SiLU modes: activation type
     const double bytes = (double)Ec * (K * act + N * outb + (pre ? N * act : 0.0) + (add ? N * 4.0 : 0.0) +
                                        (rowscale ? 4.0 : 0.0)) + (double)N * K * act;
     ProfScope ps(c, gemm_label(c, &W, trans, epi), 2.0 * Ec * (double)N * K, bytes);
@@ -772,13 +772,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       return s;
     in = out; ld_in = ldo; K = a.tb[k];
   }
-  if ((s = G(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_F32, w.W01, w.ld_W01, 2 * nw)) != ALLEGRO_OK)
+  if ((s = G(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_LINEAR, w.W01, w.ld_W01, 2 * nw)) != ALLEGRO_OK)
     return s;
   for (int L = 1; L <= nl; ++L) {
     io.xs = w.X[L - 1]; io.ldxs = w.ld_X[L - 1]; io.xs_off = a.Klat(L - 1);
     {
-      const double pe = (L < nl) ? (2.0 * nw * 4 + S * 4 + C * act)
-                                 : ((L == 1 ? 2.0 : 3.0) * nw * 4 + S * 4 + C * act);
+      const double pe = (L < nl) ? (2.0 * nw * act + S * 4 + C * act)
+                                 : ((L == 1 ? 2.0 : 3.0) * nw * act + S * 4 + C * act);
       const double pa = (L < nl) ? C * S * 4.0 : (L == 1 ? 1.0 : 2.0) * C * S * 4.0;
       auto ps = row_scope(L < nl ? "row_fwd_mid" : "row_fwd_last", pe, pa);
       row_fwd<T>(L, nl, a.lmax, io, c->tp, st);
@@ -801,7 +801,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       in = out; ld_in = ldo; K = a.lat[k];
     }
     if (L < nl) {
-      if ((s = G(w.X[L], w.ld_X[L], a.lat.back(), c->env2, false, EPI_F32, w.w2, w.ld_w2, nw)) != ALLEGRO_OK)
+      if ((s = G(w.X[L], w.ld_X[L], a.lat.back(), c->env2, false, EPI_LINEAR, w.w2, w.ld_w2, nw)) != ALLEGRO_OK)
         return s;
     }
   }
@@ -841,12 +841,12 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2; io.Ybar = w.Ybar;
   if (nl == 1) {
     io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
-    auto ps = row_scope("row_bwd_last", 2.0 * nw * 4 + C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
+    auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
     row_bwd<T>(1, 1, a.lmax, io, c->tp, st);
   } else {
     io.sbar2 = w.D[1] + a.Klat(1); io.ld_sbar2 = w.ld_D[1];
     {
-      auto ps = row_scope("row_bwd_last", 2.0 * nw * 4 + C * 4 + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
+      auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * 4 + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
       row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
     }
     // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
@@ -867,7 +867,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C)) != ALLEGRO_OK)
       return s;
     io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
-    auto ps = row_scope("row_bwd_mid", 2.0 * nw * 4 + 2.0 * C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4,
+    auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4,
                         2.0 * C * S * 4);
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }

@@ -41,6 +41,8 @@ __device__ __forceinline__ void epi_apply(const EpiParams& ep, int m, int n, flo
     float v = acc;
     if (ep.add) v += ep.add[(size_t)m * ep.ld_add + n];
     reinterpret_cast<float*>(ep.out)[(size_t)m * ep.ldo + n] = v;
+  } else if (ep.epi == EPI_LINEAR) {
+    act_st(reinterpret_cast<T*>(ep.out) + (size_t)m * ep.ldo + n, acc);
   } else {
     float z = act_ld(reinterpret_cast<const T*>(ep.pre) + (size_t)m * ep.ldp + n);
     float s = epi_sigmoid(z);

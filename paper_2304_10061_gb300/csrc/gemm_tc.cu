@@ -505,6 +505,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else if (ep.epi == EPI_F32) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += a[j];
+          } else if (ep.epi == EPI_LINEAR) {
+            // activation-type copy of the accumulator
           } else if (ep.epi == EPI_BWD_SILU) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {

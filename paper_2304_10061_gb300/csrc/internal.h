@@ -72,6 +72,7 @@ enum Epi : int {
   // E[m] = u sum_n v_n h_n;  ubar[m] = sigma_m sum_n v_n h_n;
   // out = sigma_m v u silu'(z)  (the gradient w.r.t. z, input of the adjoint GEMMs).
   EPI_LAST = 4,
+  EPI_LINEAR = 5,     // out = acc in the activation type (bf16 on the BF16 path)
 };
 
 struct GemmArgs {
@@ -159,8 +160,8 @@ struct RowIO {
   const int* row_ptr = nullptr;
   int C = 0;
   const float* Y = nullptr;            // [Ec][S]
-  const float* W01 = nullptr; int ld01 = 0;   // w0 at column 0, w1 at column n_w
-  const float* w2 = nullptr; int ld2 = 0;
+  const void* W01 = nullptr; int ld01 = 0;    // w0 at column 0, w1 at column n_w (activation type)
+  const void* w2 = nullptr; int ld2 = 0;      // (activation type)
   float* G1 = nullptr; float* G2 = nullptr;   // [na][C][S]
   void* xs = nullptr; int ldxs = 0; int xs_off = 0;   // s output (T), column offset
   const float* sbar1 = nullptr; const float* sbar2 = nullptr; int ld_sbar1 = 0, ld_sbar2 = 0;

@@ -26,6 +26,9 @@
 
 namespace alg {
 
+__device__ __forceinline__ float ld_act(const float* p) { return *p; }
+__device__ __forceinline__ float ld_act(const bf16* p) { return __bfloat162float(*p); }
+
 template <typename T> __device__ __forceinline__ T to_act2(float v);
 template <> __device__ __forceinline__ float to_act2<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 to_act2<bf16>(float v) { return __float2bfloat16_rn(v); }
@@ -48,12 +51,13 @@ __global__ void row_fwd_mid_kernel(RowIO io, TPConst tp) {
   float G[S];
 #pragma unroll
   for (int b = 0; b < S; ++b) G[b] = 0.0f;
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w1 = io.W01 + (size_t)e * io.ld01 + nw + u * LM;
+    const T* w1 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + nw + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     float wl[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = w1[l];
+    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w1 + l);
 #pragma unroll
     for (int b = 0; b < S; ++b) G[b] += wl[LOf<LMAX>::l(b)] * Y[b];
   }
@@ -72,12 +76,13 @@ __global__ void row_fwd_mid_kernel(RowIO io, TPConst tp) {
     M0[p] = s;
   }
   T* xs = reinterpret_cast<T*>(io.xs);
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
+    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     float wl[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = w0[l];
+    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w0 + l);
     float s = 0.0f;
 #pragma unroll
     for (int p = 0; p < S; ++p) s += wl[LOf<LMAX>::l(p)] * Y[p] * M0[p];
@@ -157,17 +162,18 @@ __global__ void row_fwd_last_kernel(RowIO io, TPConst tp) {
   const int a = blockIdx.x, u = threadIdx.x, C = io.C;
   const int rb = io.row_ptr[io.a0 + a] - io.e0, re = io.row_ptr[io.a0 + a + 1] - io.e0;
   const int nw = C * LM;
-  const float* wsrc = (NL == 1) ? io.W01 + nw : io.w2;
+  const T* wsrc = (NL == 1) ? reinterpret_cast<const T*>(io.W01) + nw : reinterpret_cast<const T*>(io.w2);
   const int ldw = (NL == 1) ? io.ld01 : io.ld2;
   float G[S];
 #pragma unroll
   for (int b = 0; b < S; ++b) G[b] = 0.0f;
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w = wsrc + (size_t)e * ldw + u * LM;
+    const T* w = wsrc + (size_t)e * ldw + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     float wl[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = w[l];
+    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w + l);
 #pragma unroll
     for (int b = 0; b < S; ++b) G[b] += wl[LOf<LMAX>::l(b)] * Y[b];
   }
@@ -190,12 +196,13 @@ __global__ void row_fwd_last_kernel(RowIO io, TPConst tp) {
     for (int b = 0; b < S; ++b) Tv[b] = cg[b];
   }
   T* xs = reinterpret_cast<T*>(io.xs);
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
+    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     float wl[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = w0[l];
+    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w0 + l);
     float s = 0.0f;
 #pragma unroll
     for (int p = 0; p < S; ++p) s += wl[LOf<LMAX>::l(p)] * Y[p] * Tv[p];
@@ -228,13 +235,14 @@ __global__ void row_bwd_last_kernel(RowIO io, TPConst tp) {
   float Q[S];
 #pragma unroll
   for (int b = 0; b < S; ++b) Q[b] = 0.0f;
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
+    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     const float sb = sbar[(size_t)e * lds + u];
     float w0l[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) w0l[l] = w0[l];
+    for (int l = 0; l < LM; ++l) w0l[l] = ld_act(w0 + l);
 #pragma unroll
     for (int b = 0; b < S; ++b) Q[b] += sb * w0l[LOf<LMAX>::l(b)] * Y[b];
   }
@@ -264,17 +272,17 @@ __global__ void row_bwd_last_kernel(RowIO io, TPConst tp) {
   T* wb01 = reinterpret_cast<T*>(io.wbar01);
   T* wbL = (NL == 1) ? wb01 + nw : reinterpret_cast<T*>(io.wbar2);
   const int ldwb = (NL == 1) ? io.ld_wbar01 : io.ld_wbar2;
-  const float* wsrc = (NL == 1) ? io.W01 + nw : io.w2;
+  const T* wsrc = (NL == 1) ? reinterpret_cast<const T*>(io.W01) + nw : reinterpret_cast<const T*>(io.w2);
   const int ldw = (NL == 1) ? io.ld01 : io.ld2;
   for (int eg = rb; eg < re; eg += kEB) {
     const int nk = min(kEB, re - eg);
     for (int k = 0; k < nk; ++k) {
       const int e = eg + k;
       const float* Y = io.Y + (size_t)e * S;
-      const float* w = wsrc + (size_t)e * ldw + u * LM;
+      const T* w = wsrc + (size_t)e * ldw + u * LM;
       float wl[LM], gl[LM];
 #pragma unroll
-      for (int l = 0; l < LM; ++l) { wl[l] = w[l]; gl[l] = 0.0f; }
+      for (int l = 0; l < LM; ++l) { wl[l] = ld_act(w + l); gl[l] = 0.0f; }
 #pragma unroll
       for (int b = 0; b < S; ++b) gl[LOf<LMAX>::l(b)] += Gb[b] * Y[b];
 #pragma unroll
@@ -284,10 +292,10 @@ __global__ void row_bwd_last_kernel(RowIO io, TPConst tp) {
       for (int b = 0; b < S; ++b) yc[b] = tp.nu * wl[LOf<LMAX>::l(b)] * Gb[b];
       if constexpr (NL == 1) {
         const float sb = sbar[(size_t)e * lds + u];
-        const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
+        const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
         float w0l[LM], g0[LM];
 #pragma unroll
-        for (int l = 0; l < LM; ++l) { w0l[l] = w0[l]; g0[l] = 0.0f; }
+        for (int l = 0; l < LM; ++l) { w0l[l] = ld_act(w0 + l); g0[l] = 0.0f; }
 #pragma unroll
         for (int b = 0; b < S; ++b) {
           const float v0b = sb * tp.clast[b] * G[b];
@@ -322,14 +330,15 @@ __global__ void row_bwd_mid_kernel(RowIO io, TPConst tp) {
   float Q1[S], Q2[S];
 #pragma unroll
   for (int b = 0; b < S; ++b) { Q1[b] = 0.0f; Q2[b] = 0.0f; }
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
-    const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
+    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
     const float* Y = io.Y + (size_t)e * S;
     const float sb1 = io.sbar1[(size_t)e * io.ld_sbar1 + u];
     const float sb2 = io.sbar2[(size_t)e * io.ld_sbar2 + u];
     float w0l[LM];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) w0l[l] = w0[l];
+    for (int l = 0; l < LM; ++l) w0l[l] = ld_act(w0 + l);
 #pragma unroll
     for (int p = 0; p < S; ++p) {
       const float v0 = w0l[LOf<LMAX>::l(p)] * Y[p];
@@ -361,14 +370,14 @@ __global__ void row_bwd_mid_kernel(RowIO io, TPConst tp) {
     const int nk = min(kEB, re - eg);
     for (int k = 0; k < nk; ++k) {
       const int e = eg + k;
-      const float* w0 = io.W01 + (size_t)e * io.ld01 + u * LM;
-      const float* w1 = w0 + nw;
+      const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
+      const T* w1 = w0 + nw;
       const float* Y = io.Y + (size_t)e * S;
       const float sb1 = io.sbar1[(size_t)e * io.ld_sbar1 + u];
       const float sb2 = io.sbar2[(size_t)e * io.ld_sbar2 + u];
       float w0l[LM], w1l[LM], g0[LM], g1[LM];
 #pragma unroll
-      for (int l = 0; l < LM; ++l) { w0l[l] = w0[l]; w1l[l] = w1[l]; g0[l] = 0.0f; g1[l] = 0.0f; }
+      for (int l = 0; l < LM; ++l) { w0l[l] = ld_act(w0 + l); w1l[l] = ld_act(w1 + l); g0[l] = 0.0f; g1[l] = 0.0f; }
       float yc[S];
 #pragma unroll
       for (int b = 0; b < S; ++b) {

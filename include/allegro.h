@@ -130,6 +130,24 @@ allegro_status allegro_energy_forces(allegro_ctx* ctx, double* E_total, double* 
                                      double* F, double* virial);
 
 /*
+ * allegro_md_verlet -- velocity-Verlet molecular dynamics of one structure
+ * (Sec. "Problem Overview": MD integrates Newton's equations with femtosecond
+ * time steps): per step v += dt/2 F/m, x += dt v, neighbour rebuild, forces,
+ * v += dt/2 F/m, all on the GPU.
+ *   pos[n_atoms*3] (A) and vel[n_atoms*3] (A/fs): in/out, host or device.
+ *   types[n_atoms]: caller types (mapped as in allegro_neighbors);
+ *   masses[n_types]: amu per caller type (host or device), all > 0.
+ *   cell, pbc: as allegro_neighbors (positions are not wrapped).
+ *   dt: fs; n_steps >= 0.  E_pot, E_kin: [n_steps+1] (eV) or NULL, the
+ *   potential (sum sigma_Z E_i + mu_Z) and kinetic energy at steps 0..n_steps.
+ * Forces and the neighbour list of the final positions stay in the context.
+ */
+allegro_status allegro_md_verlet(allegro_ctx* ctx, int64_t n_atoms, double* pos, double* vel,
+                                 const int32_t* types, const double* masses, int32_t n_types,
+                                 const double* cell, const uint8_t* pbc, double dt, int64_t n_steps,
+                                 double* E_pot, double* E_kin);
+
+/*
  * allegro_get_neighbors -- copy the last neighbour list out, sorted by centre
  * atom i (rows in ascending i; order inside a row is deterministic but
  * unspecified).  i[cap], j[cap], shift[cap*3] int32 (any may be NULL);

@@ -146,6 +146,22 @@ class Allegro:
                                                   _ptr(out.get("F")), _ptr(out.get("virial"))))
         return out
 
+    def md_verlet(self, pos, vel, types, masses, dt: float, n_steps: int, cell=None, pbc=None):
+        """Velocity-Verlet MD on the GPU.  pos/vel are updated in place (numpy or torch,
+        host or device).  Returns (E_pot [n_steps+1], E_kin [n_steps+1]) as numpy arrays."""
+        types = _as(types, np.int32)
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        cell = _as(cell, np.float64)
+        pbc = _as(pbc, np.uint8)
+        n = int(pos.shape[0])
+        Ep = np.zeros(n_steps + 1)
+        Ek = np.zeros(n_steps + 1)
+        self._check(self._L.allegro_md_verlet(self._ctx, n, _ptr(pos), _ptr(vel), _ptr(types), masses.ctypes.data,
+                                              masses.size, _ptr(cell), _ptr(pbc), float(dt), int(n_steps),
+                                              Ep.ctypes.data, Ek.ctypes.data))
+        self.n_atoms, self.n_struct = n, 1
+        return Ep, Ek
+
     def profile(self, enable: bool = True):
         self._check(self._L.allegro_profile(self._ctx, int(bool(enable))))
 

@@ -20,7 +20,7 @@ PREC = {"fp32": 0, "bf16": 1}
 
 EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
-           "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_last_error",
+           "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_last_error",
            "allegro_destroy")
 
 _lib = None
@@ -46,6 +46,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_profile_report.argtypes = [vp, ctypes.c_char_p, sz, ctypes.POINTER(i64)]
     L.allegro_neighbors_noalloc.argtypes = [dp, i64, dp, dp, ctypes.c_double, dp, dp, dp, i64,
                                             ctypes.POINTER(i64), vp]
+    L.allegro_md_verlet.argtypes = [vp, i64, dp, dp, dp, dp, i32, dp, dp, ctypes.c_double, i64, dp, dp]
     L.allegro_last_error.argtypes = [vp]
     L.allegro_last_error.restype = ctypes.c_char_p
     L.allegro_destroy.argtypes = [vp]

@@ -177,6 +177,16 @@ struct allegro_ctx {
   double* d_red_scratch = nullptr;         // partial sums of the per-structure reduction
   Caps caps;
   Profiler prof;
+  // velocity-Verlet state
+  double* d_md_pos = nullptr;
+  double* d_md_vel = nullptr;
+  double* d_md_invm = nullptr;
+  int* d_md_types = nullptr;
+  double* d_md_masses = nullptr;
+  double* d_md_E = nullptr;
+  double* d_md_K = nullptr;
+  double* d_md_part = nullptr;
+  int64_t md_atoms = 0, md_steps = 0;
   int64_t launches = 0;                    // kernel launches issued by this context
 
   // chunk workspace
@@ -1310,6 +1320,73 @@ allegro_status allegro_energy_forces(allegro_ctx* c, double* E_total, double* E_
   return ALLEGRO_OK;
 }
 
+allegro_status allegro_md_verlet(allegro_ctx* c, int64_t n_atoms, double* pos, double* vel, const int32_t* types,
+                                 const double* masses, int32_t n_types, const double* cell, const uint8_t* pbc,
+                                 double dt, int64_t n_steps, double* E_pot, double* E_kin) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (n_atoms < 1 || n_atoms > 1000000000LL || !pos || !vel || !types || !masses || n_types < 1 || n_steps < 0 ||
+      !(dt > 0) || !std::isfinite(dt))
+    return fail(c, ALLEGRO_E_INVALID, "md_verlet: bad arguments");
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  const int n = (int)n_atoms;
+  if (n_atoms > c->md_atoms) {
+    cudaFree(c->d_md_pos); cudaFree(c->d_md_vel); cudaFree(c->d_md_invm); cudaFree(c->d_md_types);
+    c->d_md_pos = c->d_md_vel = c->d_md_invm = nullptr;
+    c->d_md_types = nullptr;
+    c->md_atoms = 0;
+    CUDA_TRY(c, cudaMalloc(&c->d_md_pos, (size_t)n * 24));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_vel, (size_t)n * 24));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_invm, (size_t)n * 8));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_types, (size_t)n * 4));
+    c->md_atoms = n_atoms;
+  }
+  if (n_steps + 1 > c->md_steps || !c->d_md_part) {
+    cudaFree(c->d_md_E); cudaFree(c->d_md_K); cudaFree(c->d_md_part); cudaFree(c->d_md_masses);
+    c->d_md_E = c->d_md_K = c->d_md_part = c->d_md_masses = nullptr;
+    c->md_steps = 0;
+    CUDA_TRY(c, cudaMalloc(&c->d_md_E, (size_t)(n_steps + 1) * 8));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_K, (size_t)(n_steps + 1) * 8));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_part, 256 * 8));
+    CUDA_TRY(c, cudaMalloc(&c->d_md_masses, 4096 * 8));
+    c->md_steps = n_steps + 1;
+  }
+  if (n_types > 4096) return fail(c, ALLEGRO_E_INVALID, "md_verlet: too many types");
+  auto kind = [](const void* p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_md_pos, pos, (size_t)n * 24, kind(pos), st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_md_vel, vel, (size_t)n * 24, kind(vel), st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_md_types, types, (size_t)n * 4, kind(types), st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_md_masses, masses, (size_t)n_types * 8, kind(masses), st));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  md_inv_mass(n, c->d_md_types, c->d_md_masses, n_types, c->d_md_invm, c->d_err, st);
+  int err = 0;
+  allegro_status s = read_err(c, &err);
+  if (s != ALLEGRO_OK) return s;
+  if (err) return fail(c, ALLEGRO_E_INVALID, "md_verlet: a type has no positive mass");
+  // forces at the initial positions
+  if ((s = allegro_neighbors(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, nullptr)) != ALLEGRO_OK) return s;
+  if ((s = evaluate(c, true)) != ALLEGRO_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_md_E, c->d_Eout, 8, cudaMemcpyDeviceToDevice, st));
+  md_kinetic(n, c->d_md_vel, c->d_md_invm, c->d_md_part, c->d_md_K, st);
+  for (int64_t k = 1; k <= n_steps; ++k) {
+    md_kick(n, c->d_md_pos, c->d_md_vel, c->d_F, c->d_md_invm, dt, true, st);
+    if ((s = allegro_neighbors(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, nullptr)) != ALLEGRO_OK) return s;
+    if ((s = evaluate(c, true)) != ALLEGRO_OK) return s;
+    md_kick(n, c->d_md_pos, c->d_md_vel, c->d_F, c->d_md_invm, dt, false, st);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_md_E + k, c->d_Eout, 8, cudaMemcpyDeviceToDevice, st));
+    md_kinetic(n, c->d_md_vel, c->d_md_invm, c->d_md_part, c->d_md_K + k, st);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  if ((s = copy_out(c, pos, c->d_md_pos, (size_t)n * 24)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, vel, c->d_md_vel, (size_t)n * 24)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, E_pot, c->d_md_E, (size_t)(n_steps + 1) * 8)) != ALLEGRO_OK) return s;
+  if ((s = copy_out(c, E_kin, c->d_md_K, (size_t)(n_steps + 1) * 8)) != ALLEGRO_OK) return s;
+  if ((s = read_err(c, &err)) != ALLEGRO_OK) return s;
+  if (err & kErrTimeout) return fail(c, ALLEGRO_E_TIMEOUT, "a bounded device wait expired; results are invalid");
+  if (err & kErrNonFinite) return fail(c, ALLEGRO_E_NONFINITE, "non-finite energy or force");
+  return ALLEGRO_OK;
+}
+
 allegro_status allegro_get_neighbors(allegro_ctx* c, int32_t* i, int32_t* j, int32_t* shift, int64_t cap) {
   if (!c) return ALLEGRO_E_INVALID;
   if (!c->have_nb) return fail(c, ALLEGRO_E_STATE, "no neighbour list");
@@ -1388,7 +1465,9 @@ void allegro_destroy(allegro_ctx* c) {
                   c->d_cell_of, c->d_wrap, c->d_sorted, c->d_pos4, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
                   c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_col_edge, c->d_Ee, c->d_g, c->d_cell_count,
                   c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
-                  c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws};
+                  c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,
+                  c->d_md_pos, c->d_md_vel, c->d_md_invm, c->d_md_types, c->d_md_masses, c->d_md_E, c->d_md_K,
+                  c->d_md_part};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

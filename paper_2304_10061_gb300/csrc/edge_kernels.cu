@@ -366,3 +366,85 @@ void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const
 }
 
 }  // namespace alg
+
+namespace alg {
+
+// ---------------------------------------------------------------------------
+// Velocity Verlet (Sec. "Problem Overview": MD integrates Newton's equations
+// with femtosecond steps).  Units: A, A/fs, amu, eV/A; kACC converts
+// eV/(A amu) to A/fs^2.
+// ---------------------------------------------------------------------------
+constexpr double kACC = 9.648533212e-3;
+
+__global__ void inv_mass_kernel(int n, const int* __restrict__ types, const double* __restrict__ masses, int nm,
+                                double* __restrict__ inv_m, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = types[i];
+  const double m = (t >= 0 && t < nm) ? masses[t] : 0.0;
+  if (!(m > 0)) atomicOr(err, kErrBadInput);
+  inv_m[i] = (m > 0) ? 1.0 / m : 0.0;
+}
+
+// v += dt/2 a;  and, when drift, x += dt v
+__global__ void kick_drift_kernel(int n, double* __restrict__ pos, double* __restrict__ vel,
+                                  const double* __restrict__ F, const double* __restrict__ inv_m, double dt,
+                                  bool drift) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double h = 0.5 * dt * kACC * inv_m[i];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    double v = vel[3 * (size_t)i + x] + h * F[3 * (size_t)i + x];
+    vel[3 * (size_t)i + x] = v;
+    if (drift) pos[3 * (size_t)i + x] += dt * v;
+  }
+}
+
+// Kinetic energy 0.5 sum m v^2 / kACC in float64, two fixed-order levels.
+__global__ void kinetic_partial_kernel(int n, const double* __restrict__ vel, const double* __restrict__ inv_m,
+                                       double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double vx = vel[3 * (size_t)i], vy = vel[3 * (size_t)i + 1], vz = vel[3 * (size_t)i + 2];
+    acc += (vx * vx + vy * vy + vz * vz) / inv_m[i];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void kinetic_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) acc += part[p];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 0.5 * sh[0] / kACC;
+}
+
+void md_inv_mass(int n, const int* types, const double* masses, int nm, double* inv_m, int* err, cudaStream_t st) {
+  if (n > 0) inv_mass_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, types, masses, nm, inv_m, err);
+}
+
+void md_kick(int n, double* pos, double* vel, const double* F, const double* inv_m, double dt, bool drift,
+             cudaStream_t st) {
+  if (n > 0) kick_drift_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, vel, F, inv_m, dt, drift);
+}
+
+void md_kinetic(int n, const double* vel, const double* inv_m, double* part, double* out, cudaStream_t st) {
+  const int parts = 256;
+  kinetic_partial_kernel<<<parts, 256, 0, st>>>(n, vel, inv_m, part);
+  kinetic_final_kernel<<<1, 256, 0, st>>>(part, parts, out);
+}
+
+}  // namespace alg

@@ -154,6 +154,12 @@ void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const
                    bool want_w, double* E_out, double* W_out, int* d_err, double* scratch, int64_t n_atoms,
                    cudaStream_t st);
 
+// velocity Verlet
+void md_inv_mass(int n, const int* types, const double* masses, int nm, double* inv_m, int* err, cudaStream_t st);
+void md_kick(int n, double* pos, double* vel, const double* F, const double* inv_m, double dt, bool drift,
+             cudaStream_t st);
+void md_kinetic(int n, const double* vel, const double* inv_m, double* part, double* out, cudaStream_t st);
+
 // row (per-atom) kernels: environment sums and tensor products
 struct RowIO {
   int a0 = 0, na = 0, e0 = 0;

@@ -1,0 +1,80 @@
+"""Velocity-Verlet MD on the GPU (allegro_md_verlet) against the oracle's
+Verlet with oracle forces, and energy conservation."""
+import numpy as np
+import pytest
+
+from gpu_util import lib_model
+from oracle.allegro import AllegroOracle
+from oracle.neighbors import neighbor_list
+from oracle.verlet import verlet_step, kinetic_energy
+from synth import make_config, weights_to_blob, lattice_box, ARCHS, make_weights, SPECIES_MASSES
+
+pytestmark = pytest.mark.gpu
+
+
+def _velocities(n, masses, T_K, seed):
+    rng = np.random.default_rng(seed)
+    kT = 8.617333e-5 * T_K                       # eV
+    return rng.normal(size=(n, 3)) * np.sqrt(kT * 9.648533212e-3 / masses[:, None])
+
+
+def test_md_matches_oracle_verlet_c1():
+    s, arch, w = make_config("c1")
+    type_masses = np.array(SPECIES_MASSES[:2])
+    masses = type_masses[s.species]
+    vel0 = _velocities(s.n_atoms, masses, 300.0, 1)
+    m = lib_model(weights_to_blob(arch, w))
+    pos = s.pos.copy(); vel = vel0.copy()
+    Ep, Ek = m.md_verlet(pos, vel, s.species, type_masses, dt=0.5, n_steps=20, cell=s.cell)
+    m.close()
+    orc = AllegroOracle(arch, w)
+
+    def force_fn(p):
+        i, j, S = neighbor_list(p, s.cell, s.pbc, 4.0)
+        E, _, F, _ = orc.energy_forces(p, s.species, s.cell, i, j, S)
+        return E, F
+
+    p, v = s.pos.copy(), vel0.copy()
+    E0, F = force_fn(p)
+    assert abs(Ep[0] - E0) < 1e-5 * abs(E0)
+    assert abs(Ek[0] - kinetic_energy(v, masses)) < 1e-12
+    for k in range(20):
+        p, v, F, E = verlet_step(p, v, F, masses, 0.5, force_fn)
+        assert abs(Ep[k + 1] - E) < 1e-5 * max(1.0, abs(E))
+    # bounds from the float32 force gate |dF| <= 1e-4 rms|F| accumulated over the run:
+    # |dv| <= n dt a_conv |dF| / m_min,  |dx| <= n dt |dv|
+    rms = np.sqrt((F ** 2).mean())
+    dv = 20 * 0.5 * 9.648533212e-3 * 1e-4 * rms / masses.min()
+    np.testing.assert_allclose(vel, v, rtol=0, atol=dv)
+    np.testing.assert_allclose(pos, p, rtol=0, atol=20 * 0.5 * dv)
+    assert abs(Ek[-1] - kinetic_energy(v, masses)) < 1e-4 * Ek[-1]
+
+
+def test_md_energy_conservation_fp32():
+    arch = ARCHS["c2"]
+    w = make_weights(arch, 1)
+    s = lattice_box(1000, (1000 / 0.1) ** (1 / 3), seed=12)
+    masses = np.array(SPECIES_MASSES)
+    vel = _velocities(s.n_atoms, masses[s.species], 300.0, 2)
+    m = lib_model(weights_to_blob(arch, w))
+    pos = s.pos.copy()
+    Ep, Ek = m.md_verlet(pos, vel, s.species, masses, dt=0.25, n_steps=200, cell=s.cell)
+    m.close()
+    Et = Ep + Ek
+    assert np.all(np.isfinite(Et))
+    assert np.abs(Et - Et[0]).max() / s.n_atoms < 1e-4
+    assert np.abs(Ek - Ek[0]).max() > 1e-3            # the system actually moves
+
+
+def test_md_bf16_runs_and_device_buffers():
+    import torch
+    s, arch, w = make_config("c1")
+    type_masses = np.array(SPECIES_MASSES[:2])
+    vel0 = _velocities(s.n_atoms, type_masses[s.species], 300.0, 3)
+    m = lib_model(weights_to_blob(arch, w), precision="bf16")
+    pos = torch.tensor(s.pos, device="cuda"); vel = torch.tensor(vel0, device="cuda")
+    Ep, Ek = m.md_verlet(pos, vel, torch.tensor(s.species, dtype=torch.int32, device="cuda"), type_masses,
+                         dt=0.5, n_steps=10, cell=s.cell)
+    m.close()
+    assert np.all(np.isfinite(Ep + Ek)) and torch.isfinite(pos).all()
+    assert not torch.equal(pos.cpu(), torch.tensor(s.pos))

@@ -188,6 +188,7 @@ struct allegro_ctx {
   double* d_md_part = nullptr;
   int64_t md_atoms = 0, md_steps = 0;
   int64_t launches = 0;                    // kernel launches issued by this context
+  bool chain = true;                       // fuse consecutive MLP layers (BF16 path)
 
   // chunk workspace
   void* ws = nullptr;
@@ -741,18 +742,58 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   const int ntb = (int)a.tb.size(), nlat = (int)a.lat.size(), nl = a.nl, nw = a.n_w();
   allegro_status s;
   const double act = sizeof(T);
-  auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
-               void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
-               int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
-    const double outb = (epi == EPI_F32) ? 4.0 : act;   // EPI_LINEAR / SiLU modes: activation type
-    const double bytes = (double)Ec * (K * act + N * outb + (pre ? N * act : 0.0) + (add ? N * 4.0 : 0.0) +
-                                       (rowscale ? 4.0 : 0.0)) + (double)N * K * act;
-    ProfScope ps(c, gemm_label(c, &W, trans, epi), 2.0 * Ec * (double)N * K, bytes);
+  auto mk = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
+                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
+                int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
     GemmArgs g;
     g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
     g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
     g.ubar = ubar; g.Eout = Eout; g.v = c->d_v; g.rowsig = w.sig;
+    return g;
+  };
+  auto gbytes = [&](const GemmArgs& g, bool count_in, bool count_out) {
+    const double outb = (g.epi == EPI_F32) ? 4.0 : act;   // EPI_LINEAR / SiLU modes: activation type
+    return (double)Ec * ((count_in ? g.K * act : 0.0) + (count_out ? g.N * outb : 0.0) + (g.pre ? g.N * act : 0.0) +
+                         (g.add ? g.N * 4.0 : 0.0) + (g.rowscale ? 4.0 : 0.0)) +
+           (double)g.N * g.K * act;
+  };
+  auto run1 = [&](const GemmArgs& g) {
+    ProfScope ps(c, gemm_label(c, g.W, g.trans, g.epi), 2.0 * Ec * (double)g.N * g.K, gbytes(g, true, true));
     return gemm<T>(c, g);
+  };
+  // Two consecutive layers: one fused kernel when the shapes allow (BF16 path), else two GEMMs.
+  auto run2 = [&](const GemmArgs& g1, const GemmArgs& g2) -> allegro_status {
+    // Fused pairs measured faster only for SiLU -> SiLU forward layers; the
+    // others are bound by epilogue throughput and run as separate kernels.
+    const bool want_chain = g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU;
+    if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
+      std::string why;
+      static std::vector<std::string> names;
+      std::string nm = std::string(gemm_label(c, g1.W, g1.trans, g1.epi)) + "+" +
+                       std::string(gemm_label(c, g2.W, g2.trans, g2.epi)).substr(8);
+      const char* label = nullptr;
+      for (auto& x : names) if (x == nm) label = x.c_str();
+      if (!label) { names.push_back(nm); label = names.back().c_str(); }
+      bool launched;
+      {
+        ProfScope ps(c, label, 2.0 * Ec * ((double)g1.N * g1.K + (double)g2.N * g2.K),
+                     gbytes(g1, true, false) + gbytes(g2, false, true));
+        launched = gemm_chain_bf16(g1, g2, c->stream, c->d_err, &why);
+      }
+      if (launched) return ALLEGRO_OK;
+      if (!why.empty()) return fail(c, ALLEGRO_E_CUDA, "tcgen05 chain GEMM: %s", why.c_str());
+    }
+    allegro_status r = run1(g1);
+    if (r != ALLEGRO_OK) return r;
+    GemmArgs g2b = g2;              // separate kernels: layer 2 reads layer 1's output from HBM
+    g2b.A = g1.out;
+    g2b.lda = g1.ldo;
+    return run1(g2b);
+  };
+  auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
+               void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
+               int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
+    return run1(mk(A, lda, K, W, trans, epi, out, ldo, N, pre, ldp, rowscale, add, ld_add, ubar, Eout));
   };
   RowIO io;
   io.a0 = a0; io.na = Ac; io.e0 = e0; io.row_ptr = c->d_row_ptr; io.C = a.C;
@@ -773,15 +814,35 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   }
   const void* in = w.h0;
   int ld_in = w.ld_h0, K = a.K0in();
-  for (int k = 0; k < ntb; ++k) {
-    const bool last = (k == ntb - 1);
-    void* out = last ? w.X[0] : w.H[k & 1];
-    int ldo = last ? w.ld_X[0] : w.ld_H;
-    if ((s = G(in, ld_in, K, c->tb[k], false, EPI_FWD_SILU, out, ldo, a.tb[k], w.Ztb[k], w.ld_Ztb[k],
-               last ? w.u : nullptr)) != ALLEGRO_OK)
-      return s;
-    in = out; ld_in = ldo; K = a.tb[k];
-  }
+  // forward MLP layers [k0, k1) of `layers`: layer k writes pre Z[k], activation to H (or to `last_out`)
+  auto fwd_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
+                     int nlay, const void*& src, int& ld_src, int& Kin, void* last_out, int ld_last) -> allegro_status {
+    int k = 0;
+    while (k < nlay) {
+      const bool last = (k == nlay - 1);
+      void* out = last ? last_out : w.H[k & 1];
+      int ldo = last ? ld_last : w.ld_H;
+      GemmArgs g1 = mk(src, ld_src, Kin, layers[k], false, EPI_FWD_SILU, out, ldo, layers[k].N, Z[k], ldZ[k],
+                       last ? w.u : nullptr);
+      if (k + 1 < nlay && k + 1 == nlay - 1 && k >= 0) {
+        // chain the last two layers (the intermediate activation stays on chip)
+        GemmArgs g2 = mk(nullptr, 0, layers[k].N, layers[k + 1], false, EPI_FWD_SILU, last_out, ld_last,
+                         layers[k + 1].N, Z[k + 1], ldZ[k + 1], w.u);
+        g1.rowscale = nullptr;
+        g1.out = w.H[k & 1]; g1.ldo = w.ld_H;
+        allegro_status r = run2(g1, g2);
+        if (r != ALLEGRO_OK) return r;
+        src = last_out; ld_src = ld_last; Kin = layers[k + 1].N;
+        return ALLEGRO_OK;
+      }
+      allegro_status r = run1(g1);
+      if (r != ALLEGRO_OK) return r;
+      src = out; ld_src = ldo; Kin = layers[k].N;
+      ++k;
+    }
+    return ALLEGRO_OK;
+  };
+  if ((s = fwd_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, in, ld_in, K, w.X[0], w.ld_X[0])) != ALLEGRO_OK) return s;
   if ((s = G(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_LINEAR, w.W01, w.ld_W01, 2 * nw)) != ALLEGRO_OK)
     return s;
   for (int L = 1; L <= nl; ++L) {
@@ -794,21 +855,26 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       row_fwd<T>(L, nl, a.lmax, io, c->tp, st);
     }
     in = w.X[L - 1]; ld_in = w.ld_X[L - 1]; K = a.Klat(L - 1) + a.C;
-    for (int k = 0; k < nlat; ++k) {
-      const bool last = (k == nlat - 1);
-      if (fused && last && L == nl) {
-        // last latent layer + folded edge-energy MLP + start of the adjoint in one epilogue
-        if ((s = G(in, ld_in, K, c->lat[L - 1][k], false, EPI_LAST, w.H[0], w.ld_H, a.lat[k], nullptr, 0, w.u,
-                   nullptr, 0, w.ubar, c->d_Ee + e0)) != ALLEGRO_OK)
+    if (fused && L == nl) {
+      // last latent MLP; its final layer carries the folded edge energy and the start of the adjoint
+      if (nlat >= 2) {
+        if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, nlat - 2, in, ld_in, K, nullptr, 0)) !=
+            ALLEGRO_OK)
           return s;
-        break;
-      }
-      void* out = last ? (L < nl ? w.X[L] : w.Xlast) : w.H[k & 1];
-      int ldo = last ? (L < nl ? w.ld_X[L] : w.ld_Xlast) : w.ld_H;
-      if ((s = G(in, ld_in, K, c->lat[L - 1][k], false, EPI_FWD_SILU, out, ldo, a.lat[k], w.Zlat[L - 1][k],
-                 w.ld_Zlat[k], last ? w.u : nullptr)) != ALLEGRO_OK)
+        GemmArgs g1 = mk(in, ld_in, K, c->lat[L - 1][nlat - 2], false, EPI_FWD_SILU, w.H[1], w.ld_H,
+                         a.lat[nlat - 2], w.Zlat[L - 1][nlat - 2], w.ld_Zlat[nlat - 2]);
+        GemmArgs g2 = mk(nullptr, 0, a.lat[nlat - 2], c->lat[L - 1][nlat - 1], false, EPI_LAST, w.H[0], w.ld_H,
+                         a.lat[nlat - 1], nullptr, 0, w.u, nullptr, 0, w.ubar, c->d_Ee + e0);
+        if ((s = run2(g1, g2)) != ALLEGRO_OK) return s;
+      } else if ((s = G(in, ld_in, K, c->lat[L - 1][0], false, EPI_LAST, w.H[0], w.ld_H, a.lat[0], nullptr, 0, w.u,
+                        nullptr, 0, w.ubar, c->d_Ee + e0)) != ALLEGRO_OK) {
         return s;
-      in = out; ld_in = ldo; K = a.lat[k];
+      }
+    } else {
+      void* dst = (L < nl) ? w.X[L] : w.Xlast;
+      const int ld_dst = (L < nl) ? w.ld_X[L] : w.ld_Xlast;
+      if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, nlat, in, ld_in, K, dst, ld_dst)) != ALLEGRO_OK)
+        return s;
     }
     if (L < nl) {
       if ((s = G(w.X[L], w.ld_X[L], a.lat.back(), c->env2, false, EPI_LINEAR, w.w2, w.ld_w2, nw)) != ALLEGRO_OK)
@@ -832,16 +898,27 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
                       int nlay, float* dst, int ld_dst, int Kin) -> allegro_status {
     int cur = 0;
-    for (int k = nlay - 1; k >= 0; --k) {
+    int k = nlay - 1;
+    while (k >= 0) {
       const Lin& W = layers[k];
       allegro_status r;
-      if (k > 0) {
-        r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]);
-        cur ^= 1;
-      } else {
-        r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_F32, dst, ld_dst, Kin);
+      if (k >= 1) {
+        GemmArgs g1 = mk(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]);
+        if (k - 1 >= 0) {
+          const Lin& W2 = layers[k - 1];
+          const bool to_dst = (k - 1 == 0);
+          GemmArgs g2 = to_dst ? mk(nullptr, 0, W2.N, W2, true, EPI_F32, dst, ld_dst, Kin)
+                               : mk(nullptr, 0, W2.N, W2, true, EPI_BWD_SILU, w.H[cur], w.ld_H, W2.K, Z[k - 2],
+                                    ldZ[k - 2]);
+          r = run2(g1, g2);
+          if (r != ALLEGRO_OK) return r;
+          k -= 2;
+          continue;
+        }
       }
+      r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_F32, dst, ld_dst, Kin);
       if (r != ALLEGRO_OK) return r;
+      --k;
     }
     return ALLEGRO_OK;
   };

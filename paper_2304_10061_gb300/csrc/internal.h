@@ -96,6 +96,7 @@ struct GemmArgs {
 void gemm_simt_f32(const GemmArgs& g, cudaStream_t st);
 bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
 bool gemm_tc_init(std::string* why);
+bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why);
 
 // scan / utilities
 void exclusive_scan_i32(const int* in, int* out, int n, int* d_total, void* tmp, size_t tmp_bytes,

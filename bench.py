@@ -98,6 +98,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_max(x: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(atoms_per_rank: int, ms_per_step_local: float, world: int, dist=None, device=None):
+    """Whole-job throughput: every rank evaluates its own replica, so the job
+    processes world x atoms per step in the slowest rank's step time."""
+    ms = reduce_max(ms_per_step_local, dist, device)
+    return ms, atoms_per_rank * world / (ms * 1e-3)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -116,7 +133,19 @@ def _by_kernel(report: dict) -> dict:
     return out
 
 
-def _roofline(report: dict, step_ms_total: float):
+def _traffic_per_launch(detail: dict, steps: int, n_edges: int):
+    """DRAM traffic per GEMM launch from the committed ncu capture (bytes per edge per
+    launch), scaled to this run's edges per launch (= edges / chunks per step)."""
+    try:
+        ref = json.load(open(os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")))
+        gem = [v for k, v in detail.items() if k.startswith("gemm_tc/")]
+        chunks = gem[0]["launches"] / steps
+        return ref["dram_bytes_per_edge_per_gemm_launch"] * n_edges / chunks
+    except Exception:
+        return None
+
+
+def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int = 0):
     """Dominant kernel (largest total time) of the timed region against its roofline."""
     if not report:
         return None
@@ -137,7 +166,10 @@ def _roofline(report: dict, step_ms_total: float):
              sorted(report.items(), key=lambda kv: -kv[1]["ms"])}
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
             "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
-            "traffic": None, "launches": r["launches"], "ms_per_launch": round(r["ms"] / max(r["launches"], 1), 5),
+            "traffic": _traffic_per_launch(detail, steps, n_edges) if tensor else None,
+            "traffic_unit": "bytes per launch (DRAM read + write)",
+            "algorithmic_bytes_per_launch": r["bytes"] / max(r["launches"], 1),
+            "launches": r["launches"], "ms_per_launch": round(r["ms"] / max(r["launches"], 1), 5),
             "share_of_timed_region": share,
             "gemm_detail": {k.split("/", 1)[1]: {
                                                  "share": round(v["ms"] / max(step_ms_total, 1e-9), 4),
@@ -280,11 +312,7 @@ def run_ours(args):
     m.profile(False)
     clk = clocks.stop()
     n_edges = m.n_edges
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = N * ws / (ms_max * 1e-3)
+    ms_max, value = aggregate(N, ms, ws, dist, dev)
 
     # ---- end to end: pinned host inputs, host outputs, every step ----
     hpos = torch.tensor(s.pos).pin_memory()
@@ -304,9 +332,7 @@ def run_ours(args):
         m.energy_forces(out=hout)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ke
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_max = reduce_max(e2e_s, dist, dev)
     h2d = N * 3 * 8 + N * 4 + 9 * 8
     d2h = 8 + N * 8 + N * 3 * 8 + 9 * 8
 
@@ -320,6 +346,51 @@ def run_ours(args):
     else:
         m32 = None
 
+    # ---- context workloads: batched uneven molecules, and an MD run with 1 fs steps ----
+    extra = {}
+    if not args.skip_extra:
+        from synth import molecule_batch, lattice_box
+        from synth.structures import pack
+        import numpy as np
+        mols = molecule_batch(2048, seed=2)
+        mpos, mspec, moffs = pack(mols)
+        bt = {}
+        for prec in (args.precision, "fp32"):
+            mb = make(prec)
+            mb.neighbors_batched(moffs, mpos, mspec)
+            mb.energy_forces()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                mb.neighbors_batched(moffs, mpos, mspec)
+                mb.energy_forces()
+            torch.cuda.synchronize()
+            bt[prec] = len(mpos) * 3 / (time.perf_counter() - t0)
+            ne = mb.n_edges
+            mb.close()
+        extra["batched_2048_molecules"] = {
+            "atoms": int(len(mpos)), "edges": int(ne), "unit": UNIT, args.precision: bt[args.precision],
+            "fp32": bt["fp32"], "note": "2048 gas-phase molecules of 8-64 atoms in one packed edge list, "
+                                        "per-molecule E/F/virial; host inputs each step"}
+        s2, _, _ = make_config("c2")
+        masses = np.array([1.008, 15.999, 12.011, 14.007, 32.06])
+        rng = np.random.default_rng(0)
+        vel = rng.normal(size=(s2.n_atoms, 3)) * np.sqrt(0.0257 * 9.648533212e-3 / masses[s2.species][:, None])
+        mm = make(args.precision)
+        p2 = s2.pos.copy()
+        mm.md_verlet(p2, vel, s2.species, masses, 1.0, 2, cell=s2.cell)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nmd = 10
+        Ep, Ek = mm.md_verlet(p2, vel, s2.species, masses, 1.0, nmd, cell=s2.cell)
+        torch.cuda.synchronize()
+        dt_md = time.perf_counter() - t0
+        mm.close()
+        extra["md_23552_atoms"] = {"dt_fs": 1.0, "steps": nmd, "timesteps_per_s": nmd / dt_md,
+                                   "atom_steps_per_s": s2.n_atoms * nmd / dt_md,
+                                   "energy_drift_eV_per_atom": float(abs((Ep[-1] + Ek[-1]) - (Ep[0] + Ek[0])) / s2.n_atoms),
+                                   "note": "velocity Verlet on the GPU, neighbour rebuild every step"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
@@ -328,12 +399,13 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (edge arrays of several GB per step)",
                        "parallelism": f"replicas x{ws}"},
             "clocks": clk,
-            "e2e": {"value": N * ws / float(e2e_t.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": N * ws / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches1 - launches0),
-            "roofline": _roofline(report, ms * args.steps)}
+            "roofline": _roofline(report, ms * args.steps, args.steps, n_edges)}
     if fp32:
         line["fp32"] = fp32
+    line.update(extra)
     if rank == 0 and ws == 1 and not args.skip_cpu:
         models = {args.precision: m}
         if m32 is not None:
@@ -363,6 +435,7 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--chunk-edges", type=int, default=0, help="edges per model pass (0 = automatic)")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the batched-molecule and MD context runs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -435,9 +435,17 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   if (a.nl == 2) {
     std::vector<double> W;
     fused_layer_tensor(a.lmax, theta[0].data(), W, nin, nout, false);
+    double wmax = 0.0;
+    for (double x : W) wmax = std::max(wmax, fabs(x));
     for (int p = 0; p < S; ++p)
       for (int b = 0; b < S; ++b)
-        for (int q = 0; q < S; ++q) c->tp.W1[(p * S + b) * S + q] = (float)W[((size_t)p * S + b) * S + q];
+        for (int q = 0; q < S; ++q) {
+          const double w = W[((size_t)p * S + b) * S + q];
+          if (tp_nonzero(p, b, q)) c->tp.W1[(p * S + b) * S + q] = (float)w;
+          else if (fabs(w) > 1e-9 * wmax)   // the kernels skip these entries
+            return fail(c, ALLEGRO_E_INVALID, "internal: layer-1 tensor entry (%d,%d,%d) outside the coupling pattern",
+                        p, b, q);
+        }
   }
   {
     std::vector<double> W;
@@ -470,7 +478,7 @@ struct WS {
   void* wbar2; int ld_wbar2;
   float* xbar; int ld_xbar;
   float* inbar; int ld_inbar;
-  float* Y; float* Ybar; float* u; float* ubar; float* sig;
+  float* Y; float* Ybar[3]; float* u; float* ubar; float* sig;
   float* G1; float* G2;
 };
 
@@ -523,7 +531,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->ld_inbar = pad8(a.K0in());
   w->inbar = (float*)take((size_t)Ec * w->ld_inbar * 4);
   w->Y = (float*)take((size_t)Ec * S * 4);
-  w->Ybar = (float*)take((size_t)Ec * S * 4);
+  for (int k = 0; k < 3; ++k) w->Ybar[k] = (float*)take((size_t)Ec * S * 4);
   w->u = (float*)take((size_t)Ec * 4);
   w->ubar = (float*)take((size_t)Ec * 4);
   w->sig = (float*)take((size_t)Ec * 4);
@@ -925,7 +933,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
                     a.Klat(nl - 1) + a.C)) != ALLEGRO_OK)
     return s;
-  io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2; io.Ybar = w.Ybar;
+  io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2;
+  for (int k = 0; k < 3; ++k) io.Ybar[k] = w.Ybar[k];
   if (nl == 1) {
     io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
     auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
@@ -974,8 +983,9 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   }
   if ((s = back_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, w.inbar, w.ld_inbar, a.K0in())) != ALLEGRO_OK) return s;
   {
-    ProfScope ps(c, "geom_bwd", 0.0, (double)Ec * (24 + a.nb * 4 + 4 + S * 4 + 12));
-    edge_geom_bwd(Ec, e0, c->d_ed, a, w.inbar, w.ld_inbar, w.ubar, w.Ybar, c->d_g, st);
+    ProfScope ps(c, "geom_bwd", 0.0, (double)Ec * (24 + a.nb * 4 + 4 + (nl == 2 ? 3 : 2) * S * 4 + 12));
+    YbarParts yb{{w.Ybar[0], w.Ybar[1], nl == 2 ? w.Ybar[2] : nullptr}};
+    edge_geom_bwd(Ec, e0, c->d_ed, a, w.inbar, w.ld_inbar, w.ubar, yb, c->d_g, st);
   }
   return ALLEGRO_OK;
 }

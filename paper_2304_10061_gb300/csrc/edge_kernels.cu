@@ -123,7 +123,7 @@ template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int
 
 __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc,
                                 const float* __restrict__ inbar, int ld_in, const float* __restrict__ ubar,
-                                const float* __restrict__ Ybar, float* __restrict__ g) {
+                                YbarParts yb, float* __restrict__ g) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Ec) return;
   size_t eg = (size_t)e0 + e;
@@ -150,8 +150,13 @@ __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, B
     float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
     dEdr += ubar[e] * du * bc.inv_rc;
   }
+  // Ybar arrives in up to three partial arrays (one per row-kernel pass), summed in a fixed order
   float Yb[kMaxS];
-  for (int a = 0; a < bc.S; ++a) Yb[a] = Ybar[(size_t)e * bc.S + a];
+  for (int a = 0; a < bc.S; ++a) {
+    float t = yb.p[0][(size_t)e * bc.S + a] + yb.p[1][(size_t)e * bc.S + a];
+    if (yb.p[2]) t += yb.p[2][(size_t)e * bc.S + a];
+    Yb[a] = t;
+  }
   float G[3];
   sh_vjp(bc.lmax, x, y, z, Yb, G);
   float rg = x * G[0] + y * G[1] + z * G[2];
@@ -162,9 +167,9 @@ __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, B
 }
 
 void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
-                   const float* ubar, const float* Ybar, float* g, cudaStream_t st) {
+                   const float* ubar, const YbarParts& yb, float* g, cudaStream_t st) {
   if (Ec <= 0) return;
-  geom_bwd_kernel<<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, make_basis(a), inbar, ld_in, ubar, Ybar, g);
+  geom_bwd_kernel<<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, make_basis(a), inbar, ld_in, ubar, yb, g);
 }
 
 // Adjoint head of an MLP whose output is x = u * silu(z):  given xbar,

@@ -59,6 +59,31 @@ struct TPConst {
   float nu;                         // environment normalisation 1/sqrt(avg_num_neighbors)
 };
 
+// Nonzero pattern of the fused path tensor W[a][b][c] of a layer whose inputs
+// and outputs are natural-parity irreps, l_max <= 2, real spherical harmonics
+// ordered m = -l..l within each l (index a = l^2 + l + m).  W[a][b][c] can be
+// nonzero only if (l_a, l_b, l_c) satisfies the triangle rule with l_a + l_b +
+// l_c even (parity), |m_c| = |m_a| + |m_b| or ||m_a| - |m_b|| (the product of
+// two real harmonics carries only those |m|), and the sine/cosine type of m_c
+// (m < 0: sine) is the product of the types of m_a and m_b (sin sin and cos cos
+// give cos, sin cos gives sin).  The host checks every loaded tensor against it.
+__host__ __device__ constexpr int sh_l(int a) { return a < 1 ? 0 : (a < 4 ? 1 : 2); }
+__host__ __device__ constexpr int sh_m(int a) { return a - sh_l(a) * sh_l(a) - sh_l(a); }
+__host__ __device__ constexpr int iabs_c(int x) { return x < 0 ? -x : x; }
+__host__ __device__ constexpr bool tp_nonzero(int a, int b, int c) {
+  return iabs_c(sh_l(a) - sh_l(b)) <= sh_l(c) && sh_l(c) <= sh_l(a) + sh_l(b) &&
+         ((sh_l(a) + sh_l(b) + sh_l(c)) & 1) == 0 &&
+         (iabs_c(sh_m(c)) == iabs_c(sh_m(a)) + iabs_c(sh_m(b)) ||
+          iabs_c(sh_m(c)) == iabs_c(iabs_c(sh_m(a)) - iabs_c(sh_m(b)))) &&
+         ((sh_m(c) < 0) == ((sh_m(a) < 0) != (sh_m(b) < 0)));
+}
+// some c with W[a][b][c] possibly nonzero
+__host__ __device__ constexpr bool tp_any_c(int a, int b, int S) {
+  bool r = false;
+  for (int c = 0; c < S; ++c) r = r || tp_nonzero(a, b, c);
+  return r;
+}
+
 enum Epi : int {
   EPI_FWD_SILU = 0,   // pre = acc (optional store); out = silu(acc) * (rowscale ? rowscale[m] : 1)
   EPI_F32 = 1,        // out(f32) = acc + (add ? add[m][n] : 0)
@@ -140,8 +165,12 @@ template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
                    const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
                    cudaStream_t st);
+// Partial adjoints of Y [Ec][S] written by the row-kernel passes (p[2] may be null)
+struct YbarParts {
+  const float* p[3];
+};
 void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
-                   const float* ubar, const float* Ybar, float* g, cudaStream_t st);
+                   const float* ubar, const YbarParts& yb, float* g, cudaStream_t st);
 template <typename T>
 void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
                   const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,
@@ -174,7 +203,10 @@ struct RowIO {
   const float* sbar1 = nullptr; const float* sbar2 = nullptr; int ld_sbar1 = 0, ld_sbar2 = 0;
   void* wbar01 = nullptr; int ld_wbar01 = 0;  // T
   void* wbar2 = nullptr; int ld_wbar2 = 0;    // T
-  float* Ybar = nullptr;
+  // partial adjoints of Y, [Ec][S] each, written (not accumulated) by one pass each:
+  //   one layer:  row_bwd_last pass 1 -> Ybar[0], pass 2 -> Ybar[1]
+  //   two layers: row_bwd_last -> Ybar[0], row_bwd_mid pass 1 -> Ybar[1], pass 2 -> Ybar[2]
+  float* Ybar[3] = {nullptr, nullptr, nullptr};
 };
 template <typename T>
 void row_fwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st);

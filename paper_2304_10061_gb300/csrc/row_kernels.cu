@@ -3,22 +3,27 @@
 //
 // Eq. 1 (bilinearity): V^{ij,L} = V^{ij,L-1} (x) Gamma^{i,L},
 //   Gamma^{i,L}_{u,(l,m)} = nu * sum_{k in N(i)} w^{ik,L}_{u,l} Y_{lm}(r_ik),
-// so each product needs one environment per centre atom i.  A block owns one
-// centre atom and its whole CSR row (all edges (i, j)); thread u owns
-// channel u (the tensor product is channel-wise: the u index is shared).  The
-// per-atom sums over the row are register accumulations -- deterministic, no
-// atomics -- and per-edge results are written in the same kernel.
+// so each product needs one environment per centre atom i.  One warp owns one
+// centre atom and its whole CSR row (all edges (i, j)); lane t owns the CPL
+// consecutive channels [CPL t, CPL t + CPL) (the tensor product is
+// channel-wise: the u index is shared).  The per-atom sums over the row are
+// register accumulations -- deterministic, no atomics -- and per-edge results
+// are written in the same kernel.  A lane's per-edge weights (CPL (l_max+1)
+// values) are one vector load; the row's Y values are staged once per segment
+// in shared memory and read back as 16-byte vectors by every lane.
 //
 // Tensor product with the strided layout and fused path weights (Sec.
 // "Optimized tensor product"): V^L_c = sum_{a,b} W[a][b][c] V^{L-1}_a Gamma_b.
-// Per atom the kernel first contracts W with Gamma (M[a][c] = sum_b W[a][b][c]
-// Gamma_b, the cheap order: once per atom), then each edge costs S x S FMAs.
-// The last layer keeps only the scalar output; its W[a][b][0] is diagonal
-// (w3j(l,l,0) pairs m1 = m2), so s = sum_a clast[a] V_a Gamma_a (the paper's
-// removal of the redundant dimension).
+// Per atom the kernel contracts W with Gamma once (M[a][c] = sum_b W[a][b][c]
+// Gamma_b, the cheap order), then each edge costs O(S) per channel.  The
+// per-atom contractions visit only the entries the coupling pattern allows
+// (83 of 729 for l_max = 2; `tp_nonzero`), resolved at compile time.  The last
+// layer keeps only the scalar output; its W[a][b][0] is diagonal (w3j(l,l,0)
+// pairs m1 = m2), so s = sum_a clast[a] V_a Gamma_a (the paper's removal of the
+// redundant dimension).
 //
-// Channel sums (the adjoint of Y, which is shared by all channels) go through
-// shared memory a few edges at a time, in a fixed order: bitwise reproducible.
+// Channel sums (the adjoint of Y, which is shared by all channels) are warp
+// reductions with a fixed shuffle pattern: bitwise reproducible.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -26,68 +31,362 @@
 
 namespace alg {
 
-__device__ __forceinline__ float ld_act(const float* p) { return *p; }
-__device__ __forceinline__ float ld_act(const bf16* p) { return __bfloat162float(*p); }
+namespace {
+
+constexpr int kRowWarps = 4;   // atoms (warps) per block
+constexpr int kYSeg = 64;      // edges per staged segment of Y
+
+template <int LMAX>
+__device__ __forceinline__ constexpr int lof(int a) { return a < 1 ? 0 : (a < 4 ? 1 : (a < 9 ? 2 : 3)); }
+
+// ---- vector access to a lane's span of N consecutive elements ------------
+// The span starts at a multiple of its own byte size inside a 16-byte aligned
+// row, so it is aligned to the largest power of two (<= 16) dividing that size.
+template <int NB>
+struct SpanAlign {
+  static constexpr int v = (NB % 16 == 0) ? 16 : (NB % 8 == 0) ? 8 : 4;
+  static_assert(NB % 4 == 0, "a lane span must be a whole number of 32-bit words");
+};
+
+template <int NB>
+__device__ __forceinline__ void ld_words(const void* p, uint32_t (&w)[NB / 4]) {
+  constexpr int AL = SpanAlign<NB>::v;
+  if constexpr (AL == 16) {
+#pragma unroll
+    for (int i = 0; i < NB / 16; ++i) {
+      const uint4 x = reinterpret_cast<const uint4*>(p)[i];
+      w[4 * i] = x.x; w[4 * i + 1] = x.y; w[4 * i + 2] = x.z; w[4 * i + 3] = x.w;
+    }
+  } else if constexpr (AL == 8) {
+#pragma unroll
+    for (int i = 0; i < NB / 8; ++i) {
+      const uint2 x = reinterpret_cast<const uint2*>(p)[i];
+      w[2 * i] = x.x; w[2 * i + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB / 4; ++i) w[i] = reinterpret_cast<const uint32_t*>(p)[i];
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void st_words(void* p, const uint32_t (&w)[NB / 4]) {
+  constexpr int AL = SpanAlign<NB>::v;
+  if constexpr (AL == 16) {
+#pragma unroll
+    for (int i = 0; i < NB / 16; ++i)
+      reinterpret_cast<uint4*>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else if constexpr (AL == 8) {
+#pragma unroll
+    for (int i = 0; i < NB / 8; ++i) reinterpret_cast<uint2*>(p)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB / 4; ++i) reinterpret_cast<uint32_t*>(p)[i] = w[i];
+  }
+}
+
+// bf16 -> float is exact: the bf16 bits are the upper half of the float.
+template <typename T, int N>
+__device__ __forceinline__ void unpack_span(const uint32_t (&w)[N * sizeof(T) / 4], float (&o)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) o[k] = __uint_as_float(w[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void ld_span(const T* p, float (&o)[N]) {
+  constexpr int NB = N * (int)sizeof(T);
+  uint32_t w[NB / 4];
+  ld_words<NB>(p, w);
+  unpack_span<T, N>(w, o);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void st_span(T* p, const float (&v)[N]) {
+  constexpr int NB = N * (int)sizeof(T);
+  uint32_t w[NB / 4];
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = __float_as_uint(v[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      w[k] = *reinterpret_cast<uint32_t*>(&h);
+    }
+  }
+  st_words<NB>(p, w);
+}
 
 template <typename T> __device__ __forceinline__ T to_act2(float v);
 template <> __device__ __forceinline__ float to_act2<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 to_act2<bf16>(float v) { return __float2bfloat16_rn(v); }
 
-template <int LMAX>
-struct LOf {
-  static __device__ __forceinline__ constexpr int l(int a) { return a < 1 ? 0 : (a < 4 ? 1 : (a < 9 ? 2 : 3)); }
+// ---- Y staging: the row segment's Y values, padded to 16-byte records -----
+template <int S>
+struct YStage {
+  static constexpr int P = (S + 3) & ~3;
+  float* ys;   // this warp's [kYSeg][P]
+  __device__ __forceinline__ void load(const float* Y, int e0, int cnt, int lane) const {
+    __syncwarp();
+    const float* src = Y + (size_t)e0 * S;
+    for (int t = lane; t < cnt * S; t += 32) {
+      const int k = t / S, b = t - k * S;
+      ys[k * P + b] = src[t];
+    }
+    __syncwarp();
+  }
+  __device__ __forceinline__ void get(int k, float (&y)[S]) const {
+    float v[P];
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+      const float4 x = reinterpret_cast<const float4*>(ys + k * P)[q];
+      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+#pragma unroll
+    for (int b = 0; b < S; ++b) y[b] = v[b];
+  }
 };
+
+// ---- channel sums of an S-vector over the warp (fixed pattern) ------------
+// Reduce-scatter: after the exchanges at distance 16, 8 (and 4 for eight
+// values) each lane holds the sum of one value index over the lanes that
+// differ in those bits; the remaining distances complete the sum.  Writes
+// the S sums into ybar[0..S).
+__device__ __forceinline__ float rs_step(float lo, float hi, bool upper, int dist) {
+  const float send = upper ? lo : hi;
+  const float keep = upper ? hi : lo;
+  return keep + __shfl_xor_sync(0xffffffffu, send, dist);
+}
+
+template <int S>
+__device__ __forceinline__ void warp_channel_sum(const float (&v)[S], int lane, float* ybar) {
+  if constexpr (S == 9) {
+    float a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = rs_step(v[i], v[i + 4], lane & 16, 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) b[i] = rs_step(a[i], a[i + 2], lane & 8, 8);
+    float c = rs_step(b[0], b[1], lane & 4, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    float t = v[8];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+    if ((lane & 3) == 0) ybar[(lane >> 2) & 7] = c;
+    if (lane == 1) ybar[8] = t;
+  } else {
+    static_assert(S == 4, "l_max 1 or 2");
+    float a[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) a[i] = rs_step(v[i], v[i + 2], lane & 16, 16);
+    float c = rs_step(a[0], a[1], lane & 8, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    if ((lane & 7) == 0) ybar[(lane >> 3) & 3] = c;
+  }
+}
+
+struct RowCtx {
+  int a, lane, u0, rb, re;
+  bool act;
+};
+
+template <int CPL>
+__device__ __forceinline__ bool row_ctx(const RowIO& io, RowCtx& r) {
+  const int warp = threadIdx.x >> 5;
+  r.lane = threadIdx.x & 31;
+  r.a = blockIdx.x * kRowWarps + warp;
+  if (r.a >= io.na) return false;
+  r.u0 = CPL * r.lane;
+  r.act = r.u0 < io.C;
+  r.rb = io.row_ptr[io.a0 + r.a] - io.e0;
+  r.re = io.row_ptr[io.a0 + r.a + 1] - io.e0;
+  return true;
+}
+
+// per-atom [C][S] float arrays: lane's CPL x S block
+template <int CPL, int S>
+__device__ __forceinline__ void ld_atom(const float* base, const RowIO& io, const RowCtx& r, float (&o)[CPL][S]) {
+  float t[CPL * S];
+  if (r.act) ld_span<float, CPL * S>(base + ((size_t)r.a * io.C + r.u0) * S, t);
+  else {
+#pragma unroll
+    for (int q = 0; q < CPL * S; ++q) t[q] = 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int b = 0; b < S; ++b) o[j][b] = t[j * S + b];
+}
+
+template <int CPL, int S>
+__device__ __forceinline__ void st_atom(float* base, const RowIO& io, const RowCtx& r, const float (&v)[CPL][S]) {
+  if (!r.act) return;
+  float t[CPL * S];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int b = 0; b < S; ++b) t[j * S + b] = v[j][b];
+  st_span<float, CPL * S>(base + ((size_t)r.a * io.C + r.u0) * S, t);
+}
+
+// lane's weights w[e][u0 .. u0+CPL)[0..LM) of one per-edge weight array, as raw 32-bit words
+template <typename T, int CPL, int LM>
+struct WSpan {
+  static constexpr int N = CPL * LM;
+  static constexpr int NB = N * (int)sizeof(T);
+  static constexpr int NW = NB / 4;
+};
+
+template <typename T, int CPL, int LM>
+__device__ __forceinline__ void ld_w_raw(const T* arr, int ld, int col0, int e, const RowCtx& r,
+                                         uint32_t (&w)[WSpan<T, CPL, LM>::NW]) {
+  if (r.act) ld_words<WSpan<T, CPL, LM>::NB>(arr + (size_t)e * ld + col0 + r.u0 * LM, w);
+  else {
+#pragma unroll
+    for (int q = 0; q < WSpan<T, CPL, LM>::NW; ++q) w[q] = 0u;
+  }
+}
+
+template <typename T, int CPL, int LM>
+__device__ __forceinline__ void st_w(T* arr, int ld, int col0, int e, const RowCtx& r, const float (&w)[CPL * LM]) {
+  if (r.act) st_span<T, CPL * LM>(arr + (size_t)e * ld + col0 + r.u0 * LM, w);
+}
+
+template <int CPL>
+__device__ __forceinline__ void ld_sbar(const float* sbar, int ld, int e, const RowCtx& r, float (&s)[CPL]) {
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) s[j] = r.act ? sbar[(size_t)e * ld + r.u0 + j] : 0.0f;
+}
+
+// Edges of a segment in batches of D: the loads of a whole batch are issued
+// before any of its arithmetic, so each warp keeps D edges of loads in flight.
+template <int D, typename Load, typename Comp>
+__device__ __forceinline__ void edge_batches(int cnt, Load&& load, Comp&& comp) {
+  for (int k0 = 0; k0 < cnt; k0 += D) {
+    const int nb = min(D, cnt - k0);
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+      if (u < nb) load(u, k0 + u);
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+      if (u < nb) comp(u, k0 + u);
+  }
+}
+
+constexpr int kBatchLight = 8;   // edges per batch in passes with one weight array
+constexpr int kBatchHeavy = 4;   // in the first adjoint passes (weights + sbar, more live state)
+
+// Gamma-type environment sum over the row: G[j][b] = sum_e w[e][j][l(b)] Y[e][b]
+template <typename T, int LMAX, int CPL>
+__device__ __forceinline__ void env_sum(const RowIO& io, const RowCtx& r, const YStage<(LMAX + 1) * (LMAX + 1)>& ys,
+                                        const T* warr, int ldw, int col0, float (&G)[CPL][(LMAX + 1) * (LMAX + 1)],
+                                        int& staged) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  using WS = WSpan<T, CPL, LM>;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int b = 0; b < S; ++b) G[j][b] = 0.0f;
+  for (int sb = r.rb; sb < r.re; sb += kYSeg) {
+    const int cnt = min(kYSeg, r.re - sb);
+    ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchLight][WS::NW];
+    edge_batches<kBatchLight>(
+        cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(warr, ldw, col0, sb + k, r, raw[u]); },
+        [&](int u, int k) {
+          float y[S], w[WS::N];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w);
+#pragma unroll
+          for (int j = 0; j < CPL; ++j)
+#pragma unroll
+            for (int b = 0; b < S; ++b) G[j][b] += w[j * LM + lof<LMAX>(b)] * y[b];
+        });
+  }
+}
+
+// s[e][u] = sum_p w0[e][u][l(p)] Y[e][p] M[u][p]  (scalar output of a product), written at column xs_off + u
+template <typename T, int LMAX, int CPL>
+__device__ __forceinline__ void scalar_out(const RowIO& io, const RowCtx& r, const YStage<(LMAX + 1) * (LMAX + 1)>& ys,
+                                           const float (&M)[CPL][(LMAX + 1) * (LMAX + 1)], int staged) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  using WS = WSpan<T, CPL, LM>;
+  const T* W01 = reinterpret_cast<const T*>(io.W01);
+  T* xs = reinterpret_cast<T*>(io.xs);
+  const int nseg = (r.re - r.rb + kYSeg - 1) / kYSeg;
+  for (int q = nseg - 1; q >= 0; --q) {   // last segment first: it is still staged
+    const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
+    if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchLight][WS::NW];
+    edge_batches<kBatchLight>(
+        cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]); },
+        [&](int u, int k) {
+          const int e = sb + k;
+          float y[S], w[WS::N];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w);
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            float t[LM];
+#pragma unroll
+            for (int l = 0; l < LM; ++l) t[l] = 0.0f;
+#pragma unroll
+            for (int p = 0; p < S; ++p) t[lof<LMAX>(p)] += y[p] * M[j][p];
+            float sv = 0.0f;
+#pragma unroll
+            for (int l = 0; l < LM; ++l) sv += w[j * LM + l] * t[l];
+            if (r.act) xs[(size_t)e * io.ldxs + io.xs_off + r.u0 + j] = to_act2<T>(sv);
+          }
+        });
+  }
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // forward, layer 1 of a two-layer model: Gamma^1 and s^1 = V^1_{0e}
 // ---------------------------------------------------------------------------
-template <typename T, int LMAX>
-__global__ void row_fwd_mid_kernel(RowIO io, TPConst tp) {
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kRowWarps) row_fwd_mid_kernel(RowIO io, TPConst tp) {
   constexpr int S = (LMAX + 1) * (LMAX + 1);
-  constexpr int LM = LMAX + 1;
-  const int a = blockIdx.x, u = threadIdx.x, C = io.C;
-  const int rb = io.row_ptr[io.a0 + a] - io.e0, re = io.row_ptr[io.a0 + a + 1] - io.e0;
-  const int nw = C * LM;
-  float G[S];
+  __shared__ __align__(16) float ysm[kRowWarps * kYSeg * YStage<S>::P];
+  RowCtx r;
+  if (!row_ctx<CPL>(io, r)) return;
+  const YStage<S> ys{ysm + (threadIdx.x >> 5) * kYSeg * YStage<S>::P};
+  const int nw = io.C * (LMAX + 1);
+  int staged = -1;
+  float G[CPL][S];
+  env_sum<T, LMAX, CPL>(io, r, ys, reinterpret_cast<const T*>(io.W01), io.ld01, nw, G, staged);
 #pragma unroll
-  for (int b = 0; b < S; ++b) G[b] = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w1 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + nw + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    float wl[LM];
+  for (int j = 0; j < CPL; ++j)
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w1 + l);
+    for (int b = 0; b < S; ++b) G[j][b] *= tp.nu;
+  st_atom<CPL, S>(io.G1, io, r, G);
+  // only the scalar output c = 0 is needed here: M0[p] = sum_b W[p][b][0] G_b
+  float M0[CPL][S];
 #pragma unroll
-    for (int b = 0; b < S; ++b) G[b] += wl[LOf<LMAX>::l(b)] * Y[b];
-  }
+  for (int j = 0; j < CPL; ++j)
 #pragma unroll
-  for (int b = 0; b < S; ++b) {
-    G[b] *= tp.nu;
-    io.G1[((size_t)a * C + u) * S + b] = G[b];
-  }
-  // only the scalar output c = 0 is needed here: M0[a'] = sum_b W[a'][b][0] G_b
-  float M0[S];
+    for (int p = 0; p < S; ++p) {
+      float s = 0.0f;
 #pragma unroll
-  for (int p = 0; p < S; ++p) {
-    float s = 0.0f;
-#pragma unroll
-    for (int b = 0; b < S; ++b) s += tp.W1[(p * S + b) * S + 0] * G[b];
-    M0[p] = s;
-  }
-  T* xs = reinterpret_cast<T*>(io.xs);
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    float wl[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w0 + l);
-    float s = 0.0f;
-#pragma unroll
-    for (int p = 0; p < S; ++p) s += wl[LOf<LMAX>::l(p)] * Y[p] * M0[p];
-    xs[(size_t)e * io.ldxs + io.xs_off + u] = to_act2<T>(s);
-  }
+      for (int b = 0; b < S; ++b)
+        if (tp_nonzero(p, b, 0)) s += tp.W1[(p * S + b) * S + 0] * G[j][b];
+      M0[j][p] = s;
+    }
+  scalar_out<T, LMAX, CPL>(io, r, ys, M0, staged);
 }
 
 // ---------------------------------------------------------------------------
@@ -111,324 +410,392 @@ __device__ __forceinline__ void make_T2(const TPConst& tp, const float (&G1)[S],
     float t = 0.0f;
 #pragma unroll
     for (int b = 0; b < S; ++b) {
-      float r = 0.0f;
+      if (!tp_any_c(p, b, S)) continue;
+      float q = 0.0f;
 #pragma unroll
-      for (int c = 0; c < S; ++c) r += tp.W1[(p * S + b) * S + c] * cg[c];
-      t += G1[b] * r;
+      for (int c = 0; c < S; ++c)
+        if (tp_nonzero(p, b, c)) q += tp.W1[(p * S + b) * S + c] * cg[c];
+      t += G1[b] * q;
     }
     T2[p] = t;
   }
 }
 
-// Channel sums of per-edge S-vectors, EB edges at a time, through shared
-// memory laid out [EB][S][C+1] (conflict-free), fixed summation order.
-template <int S>
-struct YSum {
-  float* red;
-  int C;
-  __device__ __forceinline__ void put(int k, const float (&v)[S]) const {
-#pragma unroll
-    for (int b = 0; b < S; ++b) red[(k * S + b) * (C + 1) + threadIdx.x] = v[b];
-  }
-  // writes (accumulate = false) or adds the sums into Ybar rows e0 .. e0+nk-1
-  __device__ __forceinline__ void flush(float* Ybar, int e0, int nk, bool accumulate) const {
-    __syncthreads();
-    for (int t = threadIdx.x; t < nk * S; t += C) {
-      const float* row = red + t * (C + 1);
-      float s = 0.0f;
-      for (int q = 0; q < C; ++q) s += row[q];
-      const int k = t / S, b = t - k * S;
-      float* y = Ybar + (size_t)(e0 + k) * S + b;
-      *y = accumulate ? *y + s : s;
-    }
-    __syncthreads();
-  }
-};
-
-constexpr int kEB = 4;   // edges per channel-sum batch
-
-template <int S>
-__host__ __device__ constexpr size_t ysum_smem(int C) {
-  return (size_t)kEB * S * (C + 1) * sizeof(float);
-}
-
 // ---------------------------------------------------------------------------
 // forward, last layer NL: Gamma^NL and s^NL
 // ---------------------------------------------------------------------------
-template <typename T, int LMAX, int NL>
-__global__ void row_fwd_last_kernel(RowIO io, TPConst tp) {
+template <typename T, int LMAX, int NL, int CPL>
+__global__ void __launch_bounds__(32 * kRowWarps) row_fwd_last_kernel(RowIO io, TPConst tp) {
   constexpr int S = (LMAX + 1) * (LMAX + 1);
-  constexpr int LM = LMAX + 1;
-  const int a = blockIdx.x, u = threadIdx.x, C = io.C;
-  const int rb = io.row_ptr[io.a0 + a] - io.e0, re = io.row_ptr[io.a0 + a + 1] - io.e0;
-  const int nw = C * LM;
-  const T* wsrc = (NL == 1) ? reinterpret_cast<const T*>(io.W01) + nw : reinterpret_cast<const T*>(io.w2);
+  __shared__ __align__(16) float ysm[kRowWarps * kYSeg * YStage<S>::P];
+  RowCtx r;
+  if (!row_ctx<CPL>(io, r)) return;
+  const YStage<S> ys{ysm + (threadIdx.x >> 5) * kYSeg * YStage<S>::P};
+  const int nw = io.C * (LMAX + 1);
+  const T* wsrc = (NL == 1) ? reinterpret_cast<const T*>(io.W01) : reinterpret_cast<const T*>(io.w2);
   const int ldw = (NL == 1) ? io.ld01 : io.ld2;
-  float G[S];
+  const int col0 = (NL == 1) ? nw : 0;
+  int staged = -1;
+  float G[CPL][S];
+  env_sum<T, LMAX, CPL>(io, r, ys, wsrc, ldw, col0, G, staged);
+  float Tv[CPL][S];
+  float G1[CPL][S];
+  if constexpr (NL == 2) ld_atom<CPL, S>(io.G1, io, r, G1);
 #pragma unroll
-  for (int b = 0; b < S; ++b) G[b] = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w = wsrc + (size_t)e * ldw + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    float wl[LM];
+  for (int j = 0; j < CPL; ++j) {
+    float cg[S];
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w + l);
+    for (int b = 0; b < S; ++b) {
+      G[j][b] *= tp.nu;
+      cg[b] = tp.clast[b] * G[j][b];
+    }
+    if constexpr (NL == 2) {
+      make_T2<S>(tp, G1[j], cg, Tv[j]);
+    } else {
 #pragma unroll
-    for (int b = 0; b < S; ++b) G[b] += wl[LOf<LMAX>::l(b)] * Y[b];
+      for (int b = 0; b < S; ++b) Tv[j][b] = cg[b];
+    }
   }
-  float* Gout = (NL == 1) ? io.G1 : io.G2;
-  float cg[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) {
-    G[b] *= tp.nu;
-    Gout[((size_t)a * C + u) * S + b] = G[b];
-    cg[b] = tp.clast[b] * G[b];
-  }
-  float Tv[S];
-  if constexpr (NL == 2) {
-    float G1[S];
-#pragma unroll
-    for (int b = 0; b < S; ++b) G1[b] = io.G1[((size_t)a * C + u) * S + b];
-    make_T2<S>(tp, G1, cg, Tv);
-  } else {
-#pragma unroll
-    for (int b = 0; b < S; ++b) Tv[b] = cg[b];
-  }
-  T* xs = reinterpret_cast<T*>(io.xs);
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    float wl[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = ld_act(w0 + l);
-    float s = 0.0f;
-#pragma unroll
-    for (int p = 0; p < S; ++p) s += wl[LOf<LMAX>::l(p)] * Y[p] * Tv[p];
-    xs[(size_t)e * io.ldxs + io.xs_off + u] = to_act2<T>(s);
-  }
+  st_atom<CPL, S>((NL == 1) ? io.G1 : io.G2, io, r, G);
+  scalar_out<T, LMAX, CPL>(io, r, ys, Tv, staged);
 }
 
 // ---------------------------------------------------------------------------
 // adjoint, last layer NL.  Given sbar^NL[e][u]:
 //   NL = 2:  Gamma^2bar = clast . (M^1^T Q2);  wbar^2 and Ybar (=) from Gamma^2bar
 //   NL = 1:  Gamma^1bar_b = clast_b sum_e sbar_e V^0_{e,b};  V^0bar = sbar clast Gamma^1;
-//            wbar^0, wbar^1 and Ybar (=) in one pass
+//            wbar^0 and its Ybar part (=) in the first pass, wbar^1 and its Ybar part (+=) in the second
 // ---------------------------------------------------------------------------
-template <typename T, int LMAX, int NL>
-__global__ void row_bwd_last_kernel(RowIO io, TPConst tp) {
+template <typename T, int LMAX, int NL, int CPL>
+__global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, TPConst tp) {
   constexpr int S = (LMAX + 1) * (LMAX + 1);
   constexpr int LM = LMAX + 1;
-  extern __shared__ float red_dyn[];
-  const YSum<S> ys{red_dyn, io.C};
-  const int a = blockIdx.x, u = threadIdx.x, C = io.C;
-  const int rb = io.row_ptr[io.a0 + a] - io.e0, re = io.row_ptr[io.a0 + a + 1] - io.e0;
-  const int nw = C * LM;
-  const float* Gl = (NL == 1) ? io.G1 : io.G2;
+  __shared__ __align__(16) float ysm[kRowWarps * kYSeg * YStage<S>::P];
+  RowCtx r;
+  if (!row_ctx<CPL>(io, r)) return;
+  const YStage<S> ys{ysm + (threadIdx.x >> 5) * kYSeg * YStage<S>::P};
+  const int nw = io.C * LM;
+  const T* W01 = reinterpret_cast<const T*>(io.W01);
   const float* sbar = (NL == 1) ? io.sbar1 : io.sbar2;
   const int lds = (NL == 1) ? io.ld_sbar1 : io.ld_sbar2;
-  float G[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) G[b] = Gl[((size_t)a * C + u) * S + b];
-  // pass 1: Q[a] = sum_e sbar_e V^0_{e,a}
-  float Q[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) Q[b] = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    const float sb = sbar[(size_t)e * lds + u];
-    float w0l[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) w0l[l] = ld_act(w0 + l);
-#pragma unroll
-    for (int b = 0; b < S; ++b) Q[b] += sb * w0l[LOf<LMAX>::l(b)] * Y[b];
-  }
-  float Gb[S];
-  if constexpr (NL == 2) {
-    float G1[S];
-#pragma unroll
-    for (int b = 0; b < S; ++b) {
-      G1[b] = io.G1[((size_t)a * C + u) * S + b];
-      Gb[b] = 0.0f;
-    }
-#pragma unroll
-    for (int p = 0; p < S; ++p)
-#pragma unroll
-      for (int bp = 0; bp < S; ++bp) {
-        const float gq = G1[bp] * Q[p];
-#pragma unroll
-        for (int b = 0; b < S; ++b) Gb[b] += tp.W1[(p * S + bp) * S + b] * gq;
-      }
-#pragma unroll
-    for (int b = 0; b < S; ++b) Gb[b] *= tp.clast[b];
-  } else {
-#pragma unroll
-    for (int b = 0; b < S; ++b) Gb[b] = tp.clast[b] * Q[b];
-  }
-  // pass 2
   T* wb01 = reinterpret_cast<T*>(io.wbar01);
-  T* wbL = (NL == 1) ? wb01 + nw : reinterpret_cast<T*>(io.wbar2);
-  const int ldwb = (NL == 1) ? io.ld_wbar01 : io.ld_wbar2;
-  const T* wsrc = (NL == 1) ? reinterpret_cast<const T*>(io.W01) + nw : reinterpret_cast<const T*>(io.w2);
-  const int ldw = (NL == 1) ? io.ld01 : io.ld2;
-  for (int eg = rb; eg < re; eg += kEB) {
-    const int nk = min(kEB, re - eg);
-    for (int k = 0; k < nk; ++k) {
-      const int e = eg + k;
-      const float* Y = io.Y + (size_t)e * S;
-      const T* w = wsrc + (size_t)e * ldw + u * LM;
-      float wl[LM], gl[LM];
+  // NL = 1: V^0bar_{e,a} = sbar_e cG_a with cG = clast Gamma^1 (known before the pass)
+  float cG[CPL][S];
+  if constexpr (NL == 1) {
+    ld_atom<CPL, S>(io.G1, io, r, cG);
 #pragma unroll
-      for (int l = 0; l < LM; ++l) { wl[l] = ld_act(w + l); gl[l] = 0.0f; }
+    for (int j = 0; j < CPL; ++j)
 #pragma unroll
-      for (int b = 0; b < S; ++b) gl[LOf<LMAX>::l(b)] += Gb[b] * Y[b];
+      for (int b = 0; b < S; ++b) cG[j][b] *= tp.clast[b];
+  }
+  // pass 1: Q[a] = sum_e sbar_e V^0_{e,a}  (+ NL = 1: wbar^0, Ybar from w^0)
+  float Q[CPL][S];
 #pragma unroll
-      for (int l = 0; l < LM; ++l) wbL[(size_t)e * ldwb + u * LM + l] = to_act2<T>(tp.nu * gl[l]);
-      float yc[S];
+  for (int j = 0; j < CPL; ++j)
 #pragma unroll
-      for (int b = 0; b < S; ++b) yc[b] = tp.nu * wl[LOf<LMAX>::l(b)] * Gb[b];
-      if constexpr (NL == 1) {
-        const float sb = sbar[(size_t)e * lds + u];
-        const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-        float w0l[LM], g0[LM];
+    for (int b = 0; b < S; ++b) Q[j][b] = 0.0f;
+  int staged = -1;
+  using WS = WSpan<T, CPL, LM>;
+  for (int sb = r.rb; sb < r.re; sb += kYSeg) {
+    const int cnt = min(kYSeg, r.re - sb);
+    ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchHeavy][WS::NW];
+    float sraw[kBatchHeavy][CPL];
+    edge_batches<kBatchHeavy>(
+        cnt,
+        [&](int u, int k) {
+          ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
+          ld_sbar<CPL>(sbar, lds, sb + k, r, sraw[u]);
+        },
+        [&](int u, int k) {
+          const int e = sb + k;
+          float y[S], w0[WS::N], yc[S], g0[WS::N];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w0);
 #pragma unroll
-        for (int l = 0; l < LM; ++l) { w0l[l] = ld_act(w0 + l); g0[l] = 0.0f; }
+          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
 #pragma unroll
-        for (int b = 0; b < S; ++b) {
-          const float v0b = sb * tp.clast[b] * G[b];
-          g0[LOf<LMAX>::l(b)] += v0b * Y[b];
-          yc[b] += w0l[LOf<LMAX>::l(b)] * v0b;
+          for (int j = 0; j < CPL; ++j) {
+            const float sj = sraw[u][j];
+            float t[LM];
+#pragma unroll
+            for (int l = 0; l < LM; ++l) { t[l] = sj * w0[j * LM + l]; g0[j * LM + l] = 0.0f; }
+#pragma unroll
+            for (int b = 0; b < S; ++b) Q[j][b] += t[lof<LMAX>(b)] * y[b];
+            if constexpr (NL == 1) {
+#pragma unroll
+              for (int b = 0; b < S; ++b) {
+                const float v0b = sj * cG[j][b];
+                g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
+                yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b;
+              }
+            }
+          }
+          if constexpr (NL == 1) {
+            st_w<T, CPL, LM>(wb01, io.ld_wbar01, 0, e, r, g0);
+            warp_channel_sum<S>(yc, r.lane, io.Ybar[0] + (size_t)e * S);
+          }
+        });
+  }
+  // Gamma^NL bar, pre-scaled by nu
+  float Gb[CPL][S];
+  float G1[CPL][S];
+  if constexpr (NL == 2) ld_atom<CPL, S>(io.G1, io, r, G1);
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    if constexpr (NL == 2) {
+#pragma unroll
+      for (int b = 0; b < S; ++b) Gb[j][b] = 0.0f;
+#pragma unroll
+      for (int p = 0; p < S; ++p)
+#pragma unroll
+        for (int bp = 0; bp < S; ++bp) {
+          if (!tp_any_c(p, bp, S)) continue;
+          const float gq = G1[j][bp] * Q[j][p];
+#pragma unroll
+          for (int b = 0; b < S; ++b)
+            if (tp_nonzero(p, bp, b)) Gb[j][b] += tp.W1[(p * S + bp) * S + b] * gq;
         }
 #pragma unroll
-        for (int l = 0; l < LM; ++l) wb01[(size_t)e * io.ld_wbar01 + u * LM + l] = to_act2<T>(g0[l]);
-      }
-      ys.put(k, yc);
+      for (int b = 0; b < S; ++b) Gb[j][b] *= tp.clast[b] * tp.nu;
+    } else {
+#pragma unroll
+      for (int b = 0; b < S; ++b) Gb[j][b] = tp.clast[b] * Q[j][b] * tp.nu;
     }
-    ys.flush(io.Ybar, eg, nk, false);
+  }
+  // pass 2: wbar^NL_l = nu sum_{b in l} Gamma^NL bar_b Y_b;  Ybar += sum_u nu w^NL Gamma^NL bar
+  T* wbL = (NL == 1) ? wb01 : reinterpret_cast<T*>(io.wbar2);
+  const int ldwb = (NL == 1) ? io.ld_wbar01 : io.ld_wbar2;
+  const T* wsrc = (NL == 1) ? W01 : reinterpret_cast<const T*>(io.w2);
+  const int ldw = (NL == 1) ? io.ld01 : io.ld2;
+  const int col0 = (NL == 1) ? nw : 0;
+  const int nseg = (r.re - r.rb + kYSeg - 1) / kYSeg;
+  float* ybar_out = io.Ybar[NL == 1 ? 1 : 0];
+  for (int q = nseg - 1; q >= 0; --q) {
+    const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
+    if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchLight][WS::NW];
+    edge_batches<kBatchLight>(
+        cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(wsrc, ldw, col0, sb + k, r, raw[u]); },
+        [&](int u, int k) {
+          const int e = sb + k;
+          float y[S], w[WS::N], g[WS::N], yc[S];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w);
+#pragma unroll
+          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+            for (int l = 0; l < LM; ++l) g[j * LM + l] = 0.0f;
+#pragma unroll
+            for (int b = 0; b < S; ++b) {
+              g[j * LM + lof<LMAX>(b)] += Gb[j][b] * y[b];
+              yc[b] += w[j * LM + lof<LMAX>(b)] * Gb[j][b];
+            }
+          }
+          st_w<T, CPL, LM>(wbL, ldwb, col0, e, r, g);
+          warp_channel_sum<S>(yc, r.lane, ybar_out + (size_t)e * S);
+        });
   }
 }
 
 // ---------------------------------------------------------------------------
 // adjoint, layer 1 of a two-layer model (factorised, see above):
-//   pass 1: Q1 = sum_e sbar^1 V^0, Q2 = sum_e sbar^2 V^0
-//   per atom: T1, T2, Gamma^1bar
-//   pass 2: V^0bar = sbar^2 T2 + sbar^1 T1;  wbar^0_l = sum_m V^0bar Y;
-//           wbar^1_l = nu sum_m Gamma^1bar Y;  Ybar += sum_u (w^0 V^0bar + nu w^1 Gamma^1bar)
+//   per atom first: T1, T2 (from Gamma^1, Gamma^2)
+//   pass 1: Q1 = sum_e sbar^1 V^0, Q2 = sum_e sbar^2 V^0;
+//           V^0bar = sbar^2 T2 + sbar^1 T1;  wbar^0_l = sum_m V^0bar Y;  Ybar += sum_u w^0 V^0bar
+//   per atom: Gamma^1bar (pre-scaled by nu)
+//   pass 2: wbar^1_l = nu sum_m Gamma^1bar Y;  Ybar += sum_u nu w^1 Gamma^1bar
 // ---------------------------------------------------------------------------
-template <typename T, int LMAX>
-__global__ void row_bwd_mid_kernel(RowIO io, TPConst tp) {
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, TPConst tp) {
   constexpr int S = (LMAX + 1) * (LMAX + 1);
   constexpr int LM = LMAX + 1;
-  extern __shared__ float red_dyn[];
-  const YSum<S> ys{red_dyn, io.C};
-  const int a = blockIdx.x, u = threadIdx.x, C = io.C;
-  const int rb = io.row_ptr[io.a0 + a] - io.e0, re = io.row_ptr[io.a0 + a + 1] - io.e0;
-  const int nw = C * LM;
-  float Q1[S], Q2[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) { Q1[b] = 0.0f; Q2[b] = 0.0f; }
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-    const float* Y = io.Y + (size_t)e * S;
-    const float sb1 = io.sbar1[(size_t)e * io.ld_sbar1 + u];
-    const float sb2 = io.sbar2[(size_t)e * io.ld_sbar2 + u];
-    float w0l[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) w0l[l] = ld_act(w0 + l);
-#pragma unroll
-    for (int p = 0; p < S; ++p) {
-      const float v0 = w0l[LOf<LMAX>::l(p)] * Y[p];
-      Q1[p] += sb1 * v0;
-      Q2[p] += sb2 * v0;
-    }
-  }
-  float G1[S], cg2[S], T1[S], T2[S], G1b[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) {
-    G1[b] = io.G1[((size_t)a * C + u) * S + b];
-    cg2[b] = tp.clast[b] * io.G2[((size_t)a * C + u) * S + b];
-    T1[b] = 0.0f; T2[b] = 0.0f; G1b[b] = 0.0f;
-  }
-#pragma unroll
-  for (int p = 0; p < S; ++p)
-#pragma unroll
-    for (int b = 0; b < S; ++b) {
-      float r = 0.0f;
-#pragma unroll
-      for (int c = 0; c < S; ++c) r += tp.W1[(p * S + b) * S + c] * cg2[c];
-      const float w0c = tp.W1[(p * S + b) * S + 0];
-      T2[p] += G1[b] * r;
-      T1[p] += w0c * G1[b];
-      G1b[b] += Q2[p] * r + Q1[p] * w0c;
-    }
+  __shared__ __align__(16) float ysm[kRowWarps * kYSeg * YStage<S>::P];
+  RowCtx r;
+  if (!row_ctx<CPL>(io, r)) return;
+  const YStage<S> ys{ysm + (threadIdx.x >> 5) * kYSeg * YStage<S>::P};
+  const int nw = io.C * LM;
+  const T* W01 = reinterpret_cast<const T*>(io.W01);
   T* wb = reinterpret_cast<T*>(io.wbar01);
-  for (int eg = rb; eg < re; eg += kEB) {
-    const int nk = min(kEB, re - eg);
-    for (int k = 0; k < nk; ++k) {
-      const int e = eg + k;
-      const T* w0 = reinterpret_cast<const T*>(io.W01) + (size_t)e * io.ld01 + u * LM;
-      const T* w1 = w0 + nw;
-      const float* Y = io.Y + (size_t)e * S;
-      const float sb1 = io.sbar1[(size_t)e * io.ld_sbar1 + u];
-      const float sb2 = io.sbar2[(size_t)e * io.ld_sbar2 + u];
-      float w0l[LM], w1l[LM], g0[LM], g1[LM];
+  float T1[CPL][S], T2[CPL][S];
+  {
+    float G1[CPL][S], cg2[CPL][S];
+    ld_atom<CPL, S>(io.G1, io, r, G1);
+    ld_atom<CPL, S>(io.G2, io, r, cg2);
 #pragma unroll
-      for (int l = 0; l < LM; ++l) { w0l[l] = ld_act(w0 + l); w1l[l] = ld_act(w1 + l); g0[l] = 0.0f; g1[l] = 0.0f; }
-      float yc[S];
+    for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+      for (int b = 0; b < S; ++b) cg2[j][b] *= tp.clast[b];
+      make_T2<S>(tp, G1[j], cg2[j], T2[j]);
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
+        float t = 0.0f;
+#pragma unroll
+        for (int b = 0; b < S; ++b)
+          if (tp_nonzero(p, b, 0)) t += tp.W1[(p * S + b) * S + 0] * G1[j][b];
+        T1[j][p] = t;
+      }
+    }
+  }
+  float Q1[CPL][S], Q2[CPL][S];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int b = 0; b < S; ++b) { Q1[j][b] = 0.0f; Q2[j][b] = 0.0f; }
+  int staged = -1;
+  using WS = WSpan<T, CPL, LM>;
+  for (int sb = r.rb; sb < r.re; sb += kYSeg) {
+    const int cnt = min(kYSeg, r.re - sb);
+    ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchHeavy][WS::NW];
+    float s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
+    edge_batches<kBatchHeavy>(
+        cnt,
+        [&](int u, int k) {
+          ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
+          ld_sbar<CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
+          ld_sbar<CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
+        },
+        [&](int u, int k) {
+          const int e = sb + k;
+          float y[S], w0[WS::N], g0[WS::N], yc[S];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w0);
+#pragma unroll
+          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const float s1 = s1r[u][j], s2 = s2r[u][j];
+            float t1[LM], t2[LM];
+#pragma unroll
+            for (int l = 0; l < LM; ++l) {
+              t1[l] = s1 * w0[j * LM + l];
+              t2[l] = s2 * w0[j * LM + l];
+              g0[j * LM + l] = 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < S; ++b) {
+              Q1[j][b] += t1[lof<LMAX>(b)] * y[b];
+              Q2[j][b] += t2[lof<LMAX>(b)] * y[b];
+              const float v0b = s2 * T2[j][b] + s1 * T1[j][b];
+              g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
+              yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b;
+            }
+          }
+          st_w<T, CPL, LM>(wb, io.ld_wbar01, 0, e, r, g0);
+          warp_channel_sum<S>(yc, r.lane, io.Ybar[1] + (size_t)e * S);
+        });
+  }
+  // Gamma^1bar_b = nu sum_{a,c} W1[a][b][c] (cg2_c Q2_a + [c = 0] Q1_a)
+  float G1b[CPL][S];
+  {
+    float cg2[CPL][S];
+    ld_atom<CPL, S>(io.G2, io, r, cg2);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+      for (int b = 0; b < S; ++b) cg2[j][b] *= tp.clast[b];
+      // gather order (one output at a time) keeps few values live
 #pragma unroll
       for (int b = 0; b < S; ++b) {
-        const float v0b = sb2 * T2[b] + sb1 * T1[b];
-        g0[LOf<LMAX>::l(b)] += v0b * Y[b];
-        g1[LOf<LMAX>::l(b)] += G1b[b] * Y[b];
-        yc[b] = w0l[LOf<LMAX>::l(b)] * v0b + tp.nu * w1l[LOf<LMAX>::l(b)] * G1b[b];
-      }
+        float acc = 0.0f;
 #pragma unroll
-      for (int l = 0; l < LM; ++l) {
-        wb[(size_t)e * io.ld_wbar01 + u * LM + l] = to_act2<T>(g0[l]);
-        wb[(size_t)e * io.ld_wbar01 + nw + u * LM + l] = to_act2<T>(tp.nu * g1[l]);
+        for (int p = 0; p < S; ++p) {
+          if (tp_any_c(p, b, S)) {
+            float q = 0.0f;
+#pragma unroll
+            for (int c = 0; c < S; ++c)
+              if (tp_nonzero(p, b, c)) q += tp.W1[(p * S + b) * S + c] * cg2[j][c];
+            acc += Q2[j][p] * q;
+          }
+          if (tp_nonzero(p, b, 0)) acc += Q1[j][p] * tp.W1[(p * S + b) * S + 0];
+        }
+        G1b[j][b] = acc * tp.nu;
       }
-      ys.put(k, yc);
     }
-    ys.flush(io.Ybar, eg, nk, true);
+  }
+  const int nseg = (r.re - r.rb + kYSeg - 1) / kYSeg;
+  for (int q = nseg - 1; q >= 0; --q) {
+    const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
+    if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchLight][WS::NW];
+    edge_batches<kBatchLight>(
+        cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(W01, io.ld01, nw, sb + k, r, raw[u]); },
+        [&](int u, int k) {
+          const int e = sb + k;
+          float y[S], w1[WS::N], g1[WS::N], yc[S];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w1);
+#pragma unroll
+          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+            for (int l = 0; l < LM; ++l) g1[j * LM + l] = 0.0f;
+#pragma unroll
+            for (int b = 0; b < S; ++b) {
+              g1[j * LM + lof<LMAX>(b)] += G1b[j][b] * y[b];
+              yc[b] += w1[j * LM + lof<LMAX>(b)] * G1b[j][b];
+            }
+          }
+          st_w<T, CPL, LM>(wb, io.ld_wbar01, nw, e, r, g1);
+          warp_channel_sum<S>(yc, r.lane, io.Ybar[2] + (size_t)e * S);
+        });
   }
 }
 
 // ---------------------------------------------------------------------------
+namespace {
+template <typename T, int CPL>
+void row_fwd_cpl(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st) {
+  dim3 grid((io.na + kRowWarps - 1) / kRowWarps), block(32 * kRowWarps);
+  if (layer < nl) {
+    if (lmax == 1) row_fwd_mid_kernel<T, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_fwd_mid_kernel<T, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+  } else if (nl == 1) {
+    if (lmax == 1) row_fwd_last_kernel<T, 1, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_fwd_last_kernel<T, 2, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+  } else {
+    if (lmax == 1) row_fwd_last_kernel<T, 1, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_fwd_last_kernel<T, 2, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+  }
+}
+
+template <typename T, int CPL>
+void row_bwd_cpl(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st) {
+  dim3 grid((io.na + kRowWarps - 1) / kRowWarps), block(32 * kRowWarps);
+  if (layer < nl) {
+    if (lmax == 1) row_bwd_mid_kernel<T, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_bwd_mid_kernel<T, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+  } else if (nl == 1) {
+    if (lmax == 1) row_bwd_last_kernel<T, 1, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_bwd_last_kernel<T, 2, 1, CPL><<<grid, block, 0, st>>>(io, tp);
+  } else {
+    if (lmax == 1) row_bwd_last_kernel<T, 1, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+    else row_bwd_last_kernel<T, 2, 2, CPL><<<grid, block, 0, st>>>(io, tp);
+  }
+}
+}  // namespace
+
+// Channels per lane: 2 up to 64 channels (lanes >= C/2 idle below 64), 4 for 128.
 template <typename T>
 void row_fwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st) {
   if (io.na <= 0) return;
-  dim3 grid(io.na), block(io.C);
-  if (layer < nl) {
-    if (lmax == 1) row_fwd_mid_kernel<T, 1><<<grid, block, 0, st>>>(io, tp);
-    else row_fwd_mid_kernel<T, 2><<<grid, block, 0, st>>>(io, tp);
-  } else if (nl == 1) {
-    if (lmax == 1) row_fwd_last_kernel<T, 1, 1><<<grid, block, 0, st>>>(io, tp);
-    else row_fwd_last_kernel<T, 2, 1><<<grid, block, 0, st>>>(io, tp);
-  } else {
-    if (lmax == 1) row_fwd_last_kernel<T, 1, 2><<<grid, block, 0, st>>>(io, tp);
-    else row_fwd_last_kernel<T, 2, 2><<<grid, block, 0, st>>>(io, tp);
-  }
+  if (io.C > 64) row_fwd_cpl<T, 4>(layer, nl, lmax, io, tp, st);
+  else row_fwd_cpl<T, 2>(layer, nl, lmax, io, tp, st);
 }
 
 template <typename T>
 void row_bwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st) {
   if (io.na <= 0) return;
-  dim3 grid(io.na), block(io.C);
-  const size_t sm1 = ysum_smem<4>(io.C), sm2 = ysum_smem<9>(io.C);
-  if (layer < nl) {
-    if (lmax == 1) row_bwd_mid_kernel<T, 1><<<grid, block, sm1, st>>>(io, tp);
-    else row_bwd_mid_kernel<T, 2><<<grid, block, sm2, st>>>(io, tp);
-  } else if (nl == 1) {
-    if (lmax == 1) row_bwd_last_kernel<T, 1, 1><<<grid, block, sm1, st>>>(io, tp);
-    else row_bwd_last_kernel<T, 2, 1><<<grid, block, sm2, st>>>(io, tp);
-  } else {
-    if (lmax == 1) row_bwd_last_kernel<T, 1, 2><<<grid, block, sm1, st>>>(io, tp);
-    else row_bwd_last_kernel<T, 2, 2><<<grid, block, sm2, st>>>(io, tp);
-  }
+  if (io.C > 64) row_bwd_cpl<T, 4>(layer, nl, lmax, io, tp, st);
+  else row_bwd_cpl<T, 2>(layer, nl, lmax, io, tp, st);
 }
 
 template void row_fwd<float>(int, int, int, const RowIO&, const TPConst&, cudaStream_t);

@@ -19,6 +19,10 @@ pytestmark = pytest.mark.gpu
 TINY2 = Arch(n_species=3, lmax=2, n_layers=2, channels=8, two_body=(16, 32), latent=(32, 32), edge=(8,))
 TINY1 = Arch(n_species=3, lmax=2, n_layers=1, channels=16, two_body=(24,), latent=(40,), edge=())
 L1X2 = Arch(n_species=2, lmax=1, n_layers=2, channels=32, two_body=(64,), latent=(64, 96), edge=(16, 8))
+# 128 channels: four channels per lane in the row kernels
+C128 = Arch(n_species=2, lmax=2, n_layers=2, channels=128, two_body=(64, 128), latent=(128,), edge=())
+# dense rows (~85 neighbours): rows longer than one staged segment of the row kernels
+DENSE = Arch(n_species=3, lmax=2, n_layers=2, channels=16, two_body=(32,), latent=(32,), edge=())
 
 
 def _cases():
@@ -28,12 +32,18 @@ def _cases():
     s2 = lattice_box(2000, (2000 / 0.1) ** (1 / 3), seed=5)
     sl = lattice_box(700, (700 / 0.1) ** (1 / 3), seed=8)
     sl.species = sl.species % 2
+    s128 = lattice_box(256, (256 / 0.1) ** (1 / 3), seed=9)
+    s128.species = s128.species % 2
+    sd = lattice_box(400, (400 / 0.32) ** (1 / 3), seed=10)
+    sd.species = sd.species % 3
     return {
         "c1": (a1, w1, s1),
         "tiny2_lmax2_C8": (TINY2, make_weights(TINY2, 3), st),
         "tiny1_lmax2_C16": (TINY1, make_weights(TINY1, 4), st),
         "lmax1_two_layers": (L1X2, make_weights(L1X2, 6), sl),
         "c2arch_2000": (ARCHS["c2"], make_weights(ARCHS["c2"], 1), s2),
+        "C128_lmax2": (C128, make_weights(C128, 7), s128),
+        "dense_rows_85": (DENSE, make_weights(DENSE, 8), sd),
     }
 
 

@@ -473,7 +473,7 @@ struct WS {
   std::vector<std::vector<void*>> Zlat; std::vector<int> ld_Zlat;
   void* W01; int ld_W01;     // [w0 | w1] (activation type)
   void* w2; int ld_w2;       // (activation type)
-  float* D[2]; int ld_D[2];
+  void* D[2]; int ld_D[2];   // adjoint of the latent MLP input [x | s], activation type
   void* wbar01; int ld_wbar01;
   void* wbar2; int ld_wbar2;
   float* xbar; int ld_xbar;
@@ -509,7 +509,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
     w->ld_X[L] = pad8(a.Klat(L) + a.C);
     w->X[L] = take((size_t)Ec * w->ld_X[L] * act_bytes);
     w->ld_D[L] = w->ld_X[L];
-    w->D[L] = (float*)take((size_t)Ec * w->ld_D[L] * 4);
+    w->D[L] = take((size_t)Ec * w->ld_D[L] * act_bytes);
   }
   w->ld_Xlast = pad8(a.lat.back());
   w->Xlast = take((size_t)Ec * w->ld_Xlast * act_bytes);
@@ -751,7 +751,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   allegro_status s;
   const double act = sizeof(T);
   auto mk = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
-                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
+                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const void* add = nullptr,
                 int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
     GemmArgs g;
     g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
@@ -762,7 +762,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   auto gbytes = [&](const GemmArgs& g, bool count_in, bool count_out) {
     const double outb = (g.epi == EPI_F32) ? 4.0 : act;   // EPI_LINEAR / SiLU modes: activation type
     return (double)Ec * ((count_in ? g.K * act : 0.0) + (count_out ? g.N * outb : 0.0) + (g.pre ? g.N * act : 0.0) +
-                         (g.add ? g.N * 4.0 : 0.0) + (g.rowscale ? 4.0 : 0.0)) +
+                         (g.add ? g.N * (g.epi == EPI_HEAD ? act : 4.0) : 0.0) + (g.rowscale ? 4.0 : 0.0)) +
            (double)g.N * g.K * act;
   };
   auto run1 = [&](const GemmArgs& g) {
@@ -799,7 +799,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     return run1(g2b);
   };
   auto G = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
-               void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const float* add = nullptr,
+               void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const void* add = nullptr,
                int ld_add = 0, float* ubar = nullptr, float* Eout = nullptr) {
     return run1(mk(A, lda, K, W, trans, epi, out, ldo, N, pre, ldp, rowscale, add, ld_add, ubar, Eout));
   };
@@ -904,7 +904,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                     st);
   }
   auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
-                      int nlay, float* dst, int ld_dst, int Kin) -> allegro_status {
+                      int nlay, void* dst, int ld_dst, int Kin, int epi_dst) -> allegro_status {
     int cur = 0;
     int k = nlay - 1;
     while (k >= 0) {
@@ -915,7 +915,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
         if (k - 1 >= 0) {
           const Lin& W2 = layers[k - 1];
           const bool to_dst = (k - 1 == 0);
-          GemmArgs g2 = to_dst ? mk(nullptr, 0, W2.N, W2, true, EPI_F32, dst, ld_dst, Kin)
+          GemmArgs g2 = to_dst ? mk(nullptr, 0, W2.N, W2, true, epi_dst, dst, ld_dst, Kin)
                                : mk(nullptr, 0, W2.N, W2, true, EPI_BWD_SILU, w.H[cur], w.ld_H, W2.K, Z[k - 2],
                                     ldZ[k - 2]);
           r = run2(g1, g2);
@@ -924,25 +924,26 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
           continue;
         }
       }
-      r = G(w.H[cur], w.ld_H, W.N, W, true, EPI_F32, dst, ld_dst, Kin);
+      r = G(w.H[cur], w.ld_H, W.N, W, true, epi_dst, dst, ld_dst, Kin);
       if (r != ALLEGRO_OK) return r;
       --k;
     }
     return ALLEGRO_OK;
   };
+  // D (the latent inputs' adjoint) is stored in the activation type: EPI_LINEAR
   if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
-                    a.Klat(nl - 1) + a.C)) != ALLEGRO_OK)
+                    a.Klat(nl - 1) + a.C, EPI_LINEAR)) != ALLEGRO_OK)
     return s;
   io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2;
   for (int k = 0; k < 3; ++k) io.Ybar[k] = w.Ybar[k];
   if (nl == 1) {
-    io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
-    auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
+    io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
+    auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * act + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
     row_bwd<T>(1, 1, a.lmax, io, c->tp, st);
   } else {
-    io.sbar2 = w.D[1] + a.Klat(1); io.ld_sbar2 = w.ld_D[1];
+    io.sbar2 = (const T*)w.D[1] + a.Klat(1); io.ld_sbar2 = w.ld_D[1];
     {
-      auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * 4 + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
+      auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * act + S * 4 + nw * act + S * 4, 2.0 * C * S * 4);
       row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
     }
     // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
@@ -960,10 +961,11 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                       (const T*)w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H,
                       st);
     }
-    if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C)) != ALLEGRO_OK)
+    if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C, EPI_LINEAR)) !=
+        ALLEGRO_OK)
       return s;
-    io.sbar1 = w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
-    auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * 4 + S * 4 + 2.0 * nw * act + 2 * S * 4,
+    io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
+    auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * act + S * 4 + 2.0 * nw * act + 2 * S * 4,
                         2.0 * C * S * 4);
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }
@@ -981,7 +983,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     mlp_head_bwd<T>(Ec, a.tb.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
                     (const T*)w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);
   }
-  if ((s = back_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, w.inbar, w.ld_inbar, a.K0in())) != ALLEGRO_OK) return s;
+  if ((s = back_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, w.inbar, w.ld_inbar, a.K0in(), EPI_F32)) != ALLEGRO_OK) return s;
   {
     ProfScope ps(c, "geom_bwd", 0.0, (double)Ec * (24 + a.nb * 4 + 4 + (nl == 2 ? 3 : 2) * S * 4 + 12));
     YbarParts yb{{w.Ybar[0], w.Ybar[1], nl == 2 ? w.Ybar[2] : nullptr}};

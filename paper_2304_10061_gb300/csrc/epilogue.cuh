@@ -15,7 +15,7 @@ struct EpiParams {
   void* out; int ldo;
   void* pre; int ldp;
   const float* rowscale;
-  const float* add; int ld_add;
+  const void* add; int ld_add;   // float (EPI_F32), bf16 (EPI_HEAD, tcgen05 path)
   int vec;   // 1: every row start of out/pre/add is 16-byte aligned (vector path allowed)
   float* ubar;
   const float* v;
@@ -39,7 +39,7 @@ __device__ __forceinline__ void epi_apply(const EpiParams& ep, int m, int n, flo
     act_st(reinterpret_cast<T*>(ep.out) + (size_t)m * ep.ldo + n, h);
   } else if (ep.epi == EPI_F32) {
     float v = acc;
-    if (ep.add) v += ep.add[(size_t)m * ep.ld_add + n];
+    if (ep.add) v += reinterpret_cast<const float*>(ep.add)[(size_t)m * ep.ld_add + n];
     reinterpret_cast<float*>(ep.out)[(size_t)m * ep.ldo + n] = v;
   } else if (ep.epi == EPI_LINEAR) {
     act_st(reinterpret_cast<T*>(ep.out) + (size_t)m * ep.ldo + n, acc);
@@ -90,7 +90,7 @@ __device__ __forceinline__ void epi_apply_vec32_bf16(const EpiParams& ep, int m,
   } else if (ep.epi == EPI_F32) {
     float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(ep.out) + (size_t)m * ep.ldo + n);
     if (ep.add) {
-      const float4* a = reinterpret_cast<const float4*>(ep.add + (size_t)m * ep.ld_add + n);
+      const float4* a = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(ep.add) + (size_t)m * ep.ld_add + n);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         float4 x = a[k];

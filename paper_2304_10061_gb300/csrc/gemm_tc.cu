@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* my_in = my_out + 2 * kOutBox;
     const bool need_pre = (ep.epi == EPI_BWD_SILU || ep.epi == EPI_HEAD);
     const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_F32 || ep.epi == EPI_HEAD);
-    const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? 4096u : 0u);
+    const bool add16 = (ep.epi == EPI_HEAD);      // the HEAD addend is bf16, the F32 one float
+    const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? (add16 ? 2048u : 4096u) : 0u);
     const bool out_f32 = (ep.epi == EPI_F32);
     const bool store_pre = (ep.epi == EPI_FWD_SILU) && ep.pre;
     const bool rowsums = (ep.epi == EPI_HEAD || ep.epi == EPI_LAST);
@@ -491,7 +492,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           in_par ^= 1u;
           if (need_pre) ld_bf16_row(my_in, lane, zc);
-          if (need_add) ld_f32_row(my_in + 2048, lane, ac);
+          if (need_add) {
+            if (add16) ld_bf16_row(my_in + 2048, lane, ac);
+            else ld_f32_row(my_in + 2048, lane, ac);
+          }
           __syncwarp();
           // prefetch this warp's next chunk (possibly in its next tile)
           if (c + 2 < nch) fetch(t, c + 2);
@@ -1015,7 +1019,7 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
   const bool f32out = (g.epi == EPI_F32);
   bool ok = make_box_map(&em.out, g.out, g.N, g.M, g.ldo, f32out ? 4 : 2);
   if (ok && g.pre) ok = make_box_map(&em.pre, g.pre, g.N, g.M, g.ldp, 2);
-  if (ok && g.add) ok = make_box_map(&em.add, g.add, g.N, g.M, g.ld_add, 4);
+  if (ok && g.add) ok = make_box_map(&em.add, g.add, g.N, g.M, g.ld_add, g.epi == EPI_HEAD ? 2 : 4);
   if (!ok) {
     if (why) *why = "cuTensorMapEncodeTiled failed for an epilogue operand";
     return false;

@@ -109,7 +109,8 @@ struct GemmArgs {
   void* out = nullptr; int ldo = 0;
   void* pre = nullptr; int ldp = 0;
   const float* rowscale = nullptr;
-  const float* add = nullptr; int ld_add = 0;
+  // addend [M][ld_add]: float for EPI_F32, the activation type (bf16) for EPI_HEAD on the BF16 path
+  const void* add = nullptr; int ld_add = 0;
   float* ubar = nullptr;           // EPI_HEAD / EPI_LAST
   const float* v = nullptr;        // EPI_LAST: folded edge-energy vector [N]
   const float* rowsig = nullptr;   // EPI_LAST: sigma_{Z_i} per row
@@ -200,7 +201,7 @@ struct RowIO {
   const void* w2 = nullptr; int ld2 = 0;      // (activation type)
   float* G1 = nullptr; float* G2 = nullptr;   // [na][C][S]
   void* xs = nullptr; int ldxs = 0; int xs_off = 0;   // s output (T), column offset
-  const float* sbar1 = nullptr; const float* sbar2 = nullptr; int ld_sbar1 = 0, ld_sbar2 = 0;
+  const void* sbar1 = nullptr; const void* sbar2 = nullptr; int ld_sbar1 = 0, ld_sbar2 = 0;   // T
   void* wbar01 = nullptr; int ld_wbar01 = 0;  // T
   void* wbar2 = nullptr; int ld_wbar2 = 0;    // T
   // partial adjoints of Y, [Ec][S] each, written (not accumulated) by one pass each:

@@ -262,10 +262,20 @@ __device__ __forceinline__ void st_w(T* arr, int ld, int col0, int e, const RowC
   if (r.act) st_span<T, CPL * LM>(arr + (size_t)e * ld + col0 + r.u0 * LM, w);
 }
 
-template <int CPL>
-__device__ __forceinline__ void ld_sbar(const float* sbar, int ld, int e, const RowCtx& r, float (&s)[CPL]) {
+// lane's CPL values of a per-edge adjoint row (activation type, any column
+// offset), kept as raw bits until the arithmetic so that a batch's loads are
+// not serialised behind conversions
+template <typename T> struct RawOf { typedef uint32_t type; };
+template <> struct RawOf<bf16> { typedef unsigned short type; };
+__device__ __forceinline__ float raw_f(uint32_t v) { return __uint_as_float(v); }
+__device__ __forceinline__ float raw_f(unsigned short v) { return __uint_as_float((uint32_t)v << 16); }
+
+template <typename T, int CPL>
+__device__ __forceinline__ void ld_sbar(const void* sbar, int ld, int e, const RowCtx& r,
+                                        typename RawOf<T>::type (&s)[CPL]) {
+  const typename RawOf<T>::type* p = reinterpret_cast<const typename RawOf<T>::type*>(sbar) + (size_t)e * ld + r.u0;
 #pragma unroll
-  for (int j = 0; j < CPL; ++j) s[j] = r.act ? sbar[(size_t)e * ld + r.u0 + j] : 0.0f;
+  for (int j = 0; j < CPL; ++j) s[j] = r.act ? p[j] : 0;
 }
 
 // Edges of a segment in batches of D: the loads of a whole batch are issued
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
   const YStage<S> ys{ysm + (threadIdx.x >> 5) * kYSeg * YStage<S>::P};
   const int nw = io.C * LM;
   const T* W01 = reinterpret_cast<const T*>(io.W01);
-  const float* sbar = (NL == 1) ? io.sbar1 : io.sbar2;
+  const void* sbar = (NL == 1) ? io.sbar1 : io.sbar2;
   const int lds = (NL == 1) ? io.ld_sbar1 : io.ld_sbar2;
   T* wb01 = reinterpret_cast<T*>(io.wbar01);
   // NL = 1: V^0bar_{e,a} = sbar_e cG_a with cG = clast Gamma^1 (known before the pass)
@@ -501,12 +511,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
     uint32_t raw[kBatchHeavy][WS::NW];
-    float sraw[kBatchHeavy][CPL];
+    typename RawOf<T>::type sraw[kBatchHeavy][CPL];
     edge_batches<kBatchHeavy>(
         cnt,
         [&](int u, int k) {
           ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
-          ld_sbar<CPL>(sbar, lds, sb + k, r, sraw[u]);
+          ld_sbar<T, CPL>(sbar, lds, sb + k, r, sraw[u]);
         },
         [&](int u, int k) {
           const int e = sb + k;
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
           for (int b = 0; b < S; ++b) yc[b] = 0.0f;
 #pragma unroll
           for (int j = 0; j < CPL; ++j) {
-            const float sj = sraw[u][j];
+            const float sj = raw_f(sraw[u][j]);
             float t[LM];
 #pragma unroll
             for (int l = 0; l < LM; ++l) { t[l] = sj * w0[j * LM + l]; g0[j * LM + l] = 0.0f; }
@@ -653,13 +663,13 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
     uint32_t raw[kBatchHeavy][WS::NW];
-    float s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
+    typename RawOf<T>::type s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
     edge_batches<kBatchHeavy>(
         cnt,
         [&](int u, int k) {
           ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
-          ld_sbar<CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
-          ld_sbar<CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
+          ld_sbar<T, CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
+          ld_sbar<T, CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
         },
         [&](int u, int k) {
           const int e = sb + k;
@@ -670,7 +680,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
           for (int b = 0; b < S; ++b) yc[b] = 0.0f;
 #pragma unroll
           for (int j = 0; j < CPL; ++j) {
-            const float s1 = s1r[u][j], s2 = s2r[u][j];
+            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
             float t1[LM], t2[LM];
 #pragma unroll
             for (int l = 0; l < LM; ++l) {

@@ -313,7 +313,14 @@ __device__ __forceinline__ void load_bf16x16(const bf16* p, float (&v)[16]) {
   }
 }
 
-__device__ __forceinline__ float fast_sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+// sigma(z) = (1 + tanh(z / 2)) / 2 with the hardware tanh approximation (one
+// transcendental-unit op instead of an exponential and a reciprocal; its
+// relative error, about 2^-11, is below the bf16 rounding of the outputs)
+__device__ __forceinline__ float fast_sigmoid(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return fmaf(0.5f, t, 0.5f);
+}
 
 struct EpiMaps {
   CUtensorMap out, pre, add;
@@ -353,6 +360,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nk = (K + kTcBK - 1) / kTcBK;
   const int tiles_m = (M + kTcBM - 1) / kTcBM, tiles_n = (N + BN - 1) / BN;
   const int ntiles = tiles_m * tiles_n;
+  // tile t -> (row block t / tiles_n, column block t % tiles_n): the column
+  // blocks of one row block run on neighbouring CTAs at the same time, so the
+  // A rows they share come from L2 after the first read
+  auto tm0 = [&](int tt) { return (tt / tiles_n) * kTcBM; };
+  auto tn0 = [&](int tt) { return (tt % tiles_n) * BN; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t g = 0;   // global k-block counter (ring position)
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-        const int m0 = (t % tiles_m) * kTcBM, n0 = (t / tiles_m) * BN;
+        const int m0 = tm0(t), n0 = tn0(t);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const uint32_t s = g % STAGES, r = g / STAGES;
           if (g >= (uint32_t)STAGES && !mbar_wait(&empty[s], (r - 1) & 1)) {
@@ -451,13 +463,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto fetch = [&](int tt, int cc) {
       if (in_bytes == 0 || tt >= ntiles) return;
       if (lane == 0) {
-        const int mb = (tt % tiles_m) * kTcBM + q * 32, nb = (tt / tiles_m) * BN + 32 * cc;
+        const int mb = tm0(tt) + q * 32, nb = tn0(tt) + 32 * cc;
         mbar_expect_tx(&inbar[ew], in_bytes);
         if (need_pre) tma_load_2d(my_in, &em.pre, &inbar[ew], nb, mb);
         if (need_add) tma_load_2d(my_in + 2048, &em.add, &inbar[ew], nb, mb);
       }
     };
-    auto nch_of = [&](int tt) { return (min(BN, N - (tt / tiles_m) * BN) + 31) / 32; };
+    auto nch_of = [&](int tt) { return (min(BN, N - tn0(tt)) + 31) / 32; };
     int oc = 0;                        // output chunks issued (buffer = oc & 1)
     int lt = 0;
     if (h < nch_of(blockIdx.x)) fetch(blockIdx.x, h);
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       if (*abort_flag) break;
-      const int m0 = (t % tiles_m) * kTcBM, n0 = (t / tiles_m) * BN;
+      const int m0 = tm0(t), n0 = tn0(t);
       const int mrow = m0 + q * 32;     // first row of this warp's box
       const int m = mrow + lane;
       const bool live = m < M;

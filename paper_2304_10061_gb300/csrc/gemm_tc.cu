@@ -199,26 +199,36 @@ __device__ __forceinline__ constexpr uint32_t idesc_bf16() {
 }
 
 constexpr int kTcBM = 128, kTcBK = 64;
-constexpr int kEpiWarps = 8;                 // warps 2..9: two per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
-// Per epilogue warp: two output staging buffers, each one float32 32x32 box
-// or two bf16 32x32 boxes (activation and pre-activation).
+// Epilogue warps: EPQ per 32-lane TMEM quarter (2 or 4), warps 2 .. 2 + 4 EPQ - 1.
+// Four per quarter for the arithmetic-heavy epilogues (more warps hide the
+// latency of the TMEM loads and transcendental ops), two for the plain copies
+// (which rather want the deeper operand ring and the double-buffered output
+// staging that the smaller epilogue footprint leaves room for).
+template <int EPQ> __host__ __device__ constexpr int tc_threads() { return 64 + 32 * 4 * EPQ; }
+// Per epilogue warp: output staging (each buffer a float32 32x32 box, or two
+// bf16 32x32 boxes: activation and pre-activation; double-buffered with two
+// warps per quarter) and one input slot (the bf16 pre-activation and the
+// bf16 addend of the warp's next chunk, fetched by TMA).  In the row-sum modes
+// (no pre-activation store) the upper half of the first output buffer carries
+// the warp's partial row sums, one 128-byte slot per TMEM buffer.
 constexpr int kOutBox = 4096;
-// One input slot per epilogue warp: the pre-activation (bf16 32x32) and/or the
-// float32 addend (32x32) of the warp's next chunk, fetched by TMA.
-constexpr int kInSlot = 2048 + 4096;
-constexpr int kEpiSmem = kEpiWarps * (2 * kOutBox + kInSlot);
+constexpr int kInSlot = 4096;
+template <int EPQ> __host__ __device__ constexpr int tc_out_bufs() { return EPQ == 2 ? 2 : 1; }
+template <int EPQ> __host__ __device__ constexpr int tc_epi_slot() { return tc_out_bufs<EPQ>() * kOutBox + kInSlot; }
+template <int EPQ> __host__ __device__ constexpr int tc_epi_smem() { return 4 * EPQ * tc_epi_slot<EPQ>(); }
+constexpr int kTcSmemMax = 232448;           // dynamic shared memory per block (227 KB)
+constexpr int kTcMisc = 1024;                // mbarriers, TMEM slot, flags
 
 template <int BN>
 __host__ __device__ constexpr int tc_stage_bytes() {
   return kTcBM * kTcBK * 2 + BN * kTcBK * 2;
 }
 
-template <int BN>
+template <int BN, int EPQ>
 __host__ __device__ constexpr int tc_stages() {
-  return (110 * 1024) / tc_stage_bytes<BN>() > 6 ? 6
-         : (110 * 1024) / tc_stage_bytes<BN>() < 2 ? 2
-                                                    : (110 * 1024) / tc_stage_bytes<BN>();
+  return (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - kTcMisc) / tc_stage_bytes<BN>() > 6
+             ? 6
+             : (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - kTcMisc) / tc_stage_bytes<BN>();
 }
 
 template <int BN>
@@ -226,10 +236,12 @@ __host__ __device__ constexpr int tc_tmem_cols() {   // one accumulator buffer
   return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 }
 
-template <int BN>
+template <int BN, int EPQ>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)tc_stages<BN>() * tc_stage_bytes<BN>() + kEpiSmem + 1024 + 3072;
+  return (size_t)tc_stages<BN, EPQ>() * tc_stage_bytes<BN>() + tc_epi_smem<EPQ>() + 1024 + kTcMisc;
 }
+static_assert(tc_stages<256, 4>() >= 2 && tc_smem_bytes<256, 4>() <= (size_t)kTcSmemMax, "shared-memory budget");
+static_assert(tc_stages<256, 2>() >= 2 && tc_smem_bytes<256, 2>() <= (size_t)kTcSmemMax, "shared-memory budget");
 
 // --- epilogue staging: 32 x 32 boxes moved by TMA --------------------------
 // bf16 box rows are 64 bytes (64-byte swizzle), float32 box rows 128 bytes
@@ -326,18 +338,38 @@ struct EpiMaps {
   CUtensorMap out, pre, add;
 };
 
+// Raw bf16 words of one 32-column row of a swizzled bf16 32x32 box (16 words).
+__device__ __forceinline__ void ld_bf16_row_raw(const uint8_t* box, int r, uint32_t (&w)[16]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const uint4 x = *reinterpret_cast<const uint4*>(box + sw64(r, u));
+    w[4 * u] = x.x; w[4 * u + 1] = x.y; w[4 * u + 2] = x.z; w[4 * u + 3] = x.w;
+  }
+}
+// element j (0..31) of such a row
+__device__ __forceinline__ float bf16_word_elem(const uint32_t (&w)[16], int j) {
+  const uint32_t x = w[j >> 1];
+  return __uint_as_float((j & 1) ? (x & 0xffff0000u) : (x << 16));
+}
+
 // Persistent kernel: CTA b handles tiles b, b + gridDim.x, ...  Two TMEM
 // accumulator buffers: the MMA warp fills buffer (t & 1) while the epilogue
 // warps drain the other, and the TMA producer runs ahead through the
-// shared-memory ring across tile boundaries.  Each epilogue warp owns 32
-// rows; per 32-column chunk it pulls its epilogue inputs (pre-activation,
-// addend) with TMA, computes in registers, stages the results in swizzled
-// shared memory and writes them back with TMA bulk stores.
-template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+// shared-memory ring across tile boundaries.  Four epilogue warps share each
+// 32-lane quarter of TMEM (warp h takes the 32-column chunks h, h + 4, ...);
+// per chunk a warp takes its epilogue inputs (pre-activation, addend; fetched
+// by TMA one chunk ahead), computes in registers 16 columns at a time, stages
+// the results in swizzled shared memory and writes them back with TMA bulk
+// stores.
+// With 18 warps five share one SM sub-partition's 16K registers: at most 96 per thread.
+template <int BN, int EPQ>
+__global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ EpiMaps em, EpiParams ep, int M, int N, int K, int* __restrict__ err) {
-  constexpr int STAGES = tc_stages<BN>();
+  constexpr int STAGES = tc_stages<BN, EPQ>();
+  constexpr int kEpiWarps = 4 * EPQ;
+  constexpr int kEpiSlot = tc_epi_slot<EPQ>();
+  constexpr int kNOut = tc_out_bufs<EPQ>();
   constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
   constexpr uint32_t B_BYTES = BN * kTcBK * 2;
   constexpr uint32_t COLS = tc_tmem_cols<BN>();
@@ -346,14 +378,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint8_t* sE = sB + STAGES * B_BYTES;                       // epilogue staging (1024-aligned)
-  uint64_t* full = reinterpret_cast<uint64_t*>(sE + kEpiSmem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE + tc_epi_smem<EPQ>());
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;     // [2]
   uint64_t* tempty = tfull + 2;         // [2]
   uint64_t* rsbar = tempty + 2;         // [4 quarters][2 buffers]: partial row sums ready
   uint64_t* inbar = rsbar + 8;          // [kEpiWarps]: input slot filled
   uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kEpiWarps);
-  float* rowsum = reinterpret_cast<float*>(tslot + 4);                 // [4][2][32] partial row sums
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -375,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
     }
-    for (int q = 0; q < 8; ++q) mbar_init(&rsbar[q], 1);
+    for (int q = 0; q < 8; ++q) mbar_init(&rsbar[q], EPQ - 1);
     for (int q = 0; q < kEpiWarps; ++q) mbar_init(&inbar[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -444,17 +475,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // Epilogue: warp pair (h = 0, 1) per TMEM lane quarter q; warp h takes
-    // the 32-column chunks c = h, h + 2, ... of each tile, in 16-column halves.
     const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int ew = warp - 2;           // epilogue warp index 0..7
-    const int h = ew >> 2;
-    uint8_t* my_out = sE + ew * (2 * kOutBox + kInSlot);
-    uint8_t* my_in = my_out + 2 * kOutBox;
+    const int ew = warp - 2;           // epilogue warp index 0..kEpiWarps-1
+    const int h = ew >> 2;             // 0..EPQ-1 within the quarter
+    uint8_t* my_out = sE + ew * kEpiSlot;
+    uint8_t* my_in = my_out + kNOut * kOutBox;
     const bool need_pre = (ep.epi == EPI_BWD_SILU || ep.epi == EPI_HEAD);
-    const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_F32 || ep.epi == EPI_HEAD);
-    const bool add16 = (ep.epi == EPI_HEAD);      // the HEAD addend is bf16, the F32 one float
-    const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? (add16 ? 2048u : 4096u) : 0u);
+    const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_HEAD);
+    const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? 2048u : 0u);
     const bool out_f32 = (ep.epi == EPI_F32);
     const bool store_pre = (ep.epi == EPI_FWD_SILU) && ep.pre;
     const bool rowsums = (ep.epi == EPI_HEAD || ep.epi == EPI_LAST);
@@ -470,8 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     auto nch_of = [&](int tt) { return (min(BN, N - tn0(tt)) + 31) / 32; };
-    int oc = 0;                        // output chunks issued (buffer = oc & 1)
     int lt = 0;
+    int oc = 0;                        // output chunks issued (buffer = oc % kNOut)
     if (h < nch_of(blockIdx.x)) fetch(blockIdx.x, h);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int b = lt & 1, use = lt >> 1;
@@ -492,43 +520,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       float acc1 = 0.0f;
       const uint32_t base = tmem + (uint32_t)(b * COLS) + ((uint32_t)(q * 32) << 16);
       const int nch = nch_of(t);
-      for (int c = h; c < nch; c += 2) {
-        uint8_t* ob = my_out + (oc & 1) * kOutBox;
-        if (lane == 0) bulk_wait_read1();      // the store that used this buffer two chunks ago has read it
-        __syncwarp();
-        float zc[32], ac[32];
+      for (int c = h; c < nch; c += EPQ) {
+        uint8_t* ob = my_out + (oc % kNOut) * kOutBox;
+        // inputs of this chunk, kept as packed bf16 words
+        uint32_t zw[16], aw[16];
         if (in_bytes) {
           if (!mbar_wait(&inbar[ew], in_par)) {
             if (lane == 0) atomicOr(err, kErrTimeout);
             *abort_flag = 1;
           }
           in_par ^= 1u;
-          if (need_pre) ld_bf16_row(my_in, lane, zc);
-          if (need_add) {
-            if (add16) ld_bf16_row(my_in + 2048, lane, ac);
-            else ld_f32_row(my_in + 2048, lane, ac);
-          }
+          if (need_pre) ld_bf16_row_raw(my_in, lane, zw);
+          if (need_add) ld_bf16_row_raw(my_in + 2048, lane, aw);
           __syncwarp();
           // prefetch this warp's next chunk (possibly in its next tile)
-          if (c + 2 < nch) fetch(t, c + 2);
+          if (c + EPQ < nch) fetch(t, c + EPQ);
           else if (t + (int)gridDim.x < ntiles && h < nch_of(t + gridDim.x)) fetch(t + gridDim.x, h);
         }
-        uint32_t raw[2][16];
-        tc_ld16_nw(base + (uint32_t)(32 * c), raw[0]);
-        tc_ld16_nw(base + (uint32_t)(32 * c + 16), raw[1]);
-        tc_wait_ld();
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int n = n0 + 32 * c + 16 * hh;
           float v[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(raw[hh][j]);
-          float z[16], a[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            z[j] = need_pre ? zc[16 * hh + j] : 0.0f;
-            a[j] = need_add ? ac[16 * hh + j] : 0.0f;
-          }
+          tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
           float o2[16];
           if (ep.epi == EPI_FWD_SILU) {
 #pragma unroll
@@ -536,24 +549,23 @@ __global__ void __launch_bounds__(kThreads, 1)
               o2[j] = v[j];
               v[j] = v[j] * fast_sigmoid(v[j]) * rs;
             }
-          } else if (ep.epi == EPI_F32) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += a[j];
-          } else if (ep.epi == EPI_LINEAR) {
-            // activation-type copy of the accumulator
+          } else if (ep.epi == EPI_F32 || ep.epi == EPI_LINEAR) {
+            // the accumulator as it is (float32 or activation type)
           } else if (ep.epi == EPI_BWD_SILU) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float sgm = fast_sigmoid(z[j]);
-              v[j] = v[j] * sgm * (1.0f + z[j] * (1.0f - sgm));
+              const float z = bf16_word_elem(zw, 16 * hh + j);
+              const float sgm = fast_sigmoid(z);
+              v[j] = v[j] * sgm * (1.0f + z * (1.0f - sgm));
             }
           } else if (ep.epi == EPI_HEAD) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float xb = v[j] + a[j];
-              const float sgm = fast_sigmoid(z[j]);
-              acc1 += xb * z[j] * sgm;
-              v[j] = xb * rs * sgm * (1.0f + z[j] * (1.0f - sgm));
+              const float z = bf16_word_elem(zw, 16 * hh + j);
+              const float xb = v[j] + (need_add ? bf16_word_elem(aw, 16 * hh + j) : 0.0f);
+              const float sgm = fast_sigmoid(z);
+              acc1 += xb * z * sgm;
+              v[j] = xb * rs * sgm * (1.0f + z * (1.0f - sgm));
             }
           } else {   // EPI_LAST
 #pragma unroll
@@ -563,6 +575,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               acc1 += vn * v[j] * sgm;
               v[j] = sg * vn * rs * sgm * (1.0f + v[j] * (1.0f - sgm));
             }
+          }
+          if (hh == 0) {
+            // the staging buffer is free once the store that used it has read it
+            if (lane == 0) {
+              if (kNOut == 1) bulk_wait_read0();
+              else bulk_wait_read1();
+            }
+            __syncwarp();
           }
           if (out_f32) st_f32_half(ob, lane, hh, v);
           else st_bf16_half(ob, lane, hh, v);
@@ -577,27 +597,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++oc;
       }
-      // every TMEM read of this buffer by this warp is complete (tcgen05.wait::ld)
+      // every TMEM read of this buffer by this warp is complete (tcgen05.ld waits)
       tc_fence_before();
       __syncwarp();
-      if (!rowsums || h == 1) {
+      if (!rowsums) {
         if (lane == 0) mbar_arrive(&tempty[b]);
-      }
-      if (rowsums) {
-        // combine the two warps' partial row sums in a fixed order (h = 0 + h = 1);
-        // warp h = 0 releases the TMEM buffer only after reading the partials, so
-        // warp h = 1 cannot overwrite them before they are read
-        float* rsum = rowsum + (q * 2 + b) * 32;
-        if (h == 1) {
-          rsum[lane] = acc1;
+      } else {
+        // combine the quarter's partial row sums in a fixed order (h = 0, 1, 2, 3).
+        // Warp h = 0 releases the TMEM buffer only after reading the partials,
+        // so no warp can overwrite a partial slot (indexed by the buffer)
+        // before it is read.
+        float* part = reinterpret_cast<float*>(my_out + 2048 + b * 128);
+        if (h != 0) {
+          part[lane] = acc1;
           __syncwarp();
-          if (lane == 0) mbar_arrive(&rsbar[q * 2 + b]);
+          if (lane == 0) {
+            mbar_arrive(&rsbar[q * 2 + b]);
+            mbar_arrive(&tempty[b]);
+          }
         } else {
           if (!mbar_wait(&rsbar[q * 2 + b], use & 1)) {
             if (lane == 0) atomicOr(err, kErrTimeout);
             *abort_flag = 1;
           }
-          const float tot = acc1 + rsum[lane];
+          float tot = acc1;
+#pragma unroll
+          for (int hp = 1; hp < EPQ; ++hp)
+            tot += reinterpret_cast<const float*>(sE + (ew + 4 * hp) * kEpiSlot + 2048 + b * 128)[lane];
           if (live) {
             if (ep.epi == EPI_HEAD) {
               ep.ubar[m] += tot;
@@ -634,7 +660,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // or float32.  Used for consecutive MLP layers (Sec. "Mixed-precision
 // calculations": the MLP GEMMs are the dominant cost).
 // ===========================================================================
-constexpr int kChainEpiSmem = kEpiWarps * (4096 + 2048);   // per warp: one out box + one 2 KB input slot
+constexpr int kChainEpiWarps = 8;            // warps 2..9: two per TMEM lane quarter
+constexpr int kChainThreads = 64 + 32 * kChainEpiWarps;
+constexpr int kChainEpiSmem = kChainEpiWarps * (4096 + 2048);   // per warp: one out box + one 2 KB input slot
 
 __host__ __device__ constexpr int chain_stage_bytes(int n1, int n2rows) {
   return kTcBM * kTcBK * 2 + (n1 > n2rows ? n1 : n2rows) * kTcBK * 2;
@@ -675,7 +703,7 @@ __device__ __forceinline__ void epi2_half(const EpiParams& ep, int n, int N, flo
 }
 
 template <int N1, int BN2>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kChainThreads, 1)
     gemm_chain_kernel(const __grid_constant__ ChainMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1, int N2,
                       int* __restrict__ err) {
   constexpr int B2ROWS = BN2;                        // rows of B2 per stage (<= 320)
@@ -697,8 +725,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* t2full = a2full + 1;
   uint64_t* t2empty = t2full + 1;
   uint64_t* rsbar = t2empty + 1;        // [4]
-  uint64_t* inbar = rsbar + 4;          // [kEpiWarps]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kEpiWarps);
+  uint64_t* inbar = rsbar + 4;          // [kChainEpiWarps]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kChainEpiWarps);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   float* rowsum = reinterpret_cast<float*>(tslot + 4);   // [4][32]
 
@@ -712,12 +740,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&empty[s2], 1);
     }
     mbar_init(t1full, 1);
-    mbar_init(t1empty, kEpiWarps);
-    mbar_init(a2full, kEpiWarps);
+    mbar_init(t1empty, kChainEpiWarps);
+    mbar_init(a2full, kChainEpiWarps);
     mbar_init(t2full, 1);
-    mbar_init(t2empty, kEpiWarps);
+    mbar_init(t2empty, kChainEpiWarps);
     for (int q = 0; q < 4; ++q) mbar_init(&rsbar[q], 1);
-    for (int q = 0; q < kEpiWarps; ++q) mbar_init(&inbar[q], 1);
+    for (int q = 0; q < kChainEpiWarps; ++q) mbar_init(&inbar[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1002,12 +1030,12 @@ static bool make_box_map(CUtensorMap* tm, const void* base, int cols, int rows, 
   return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int EPQ>
 static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st, int* d_err, std::string* why) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes<BN>());
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, EPQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes<BN, EPQ>());
     if (e != cudaSuccess) {
       if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
       return false;
@@ -1031,14 +1059,15 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
   const bool f32out = (g.epi == EPI_F32);
   bool ok = make_box_map(&em.out, g.out, g.N, g.M, g.ldo, f32out ? 4 : 2);
   if (ok && g.pre) ok = make_box_map(&em.pre, g.pre, g.N, g.M, g.ldp, 2);
-  if (ok && g.add) ok = make_box_map(&em.add, g.add, g.N, g.M, g.ld_add, g.epi == EPI_HEAD ? 2 : 4);
+  if (ok && g.add) ok = make_box_map(&em.add, g.add, g.N, g.M, g.ld_add, 2);
   if (!ok) {
     if (why) *why = "cuTensorMapEncodeTiled failed for an epilogue operand";
     return false;
   }
   const int tiles = ((g.M + kTcBM - 1) / kTcBM) * ((g.N + BN - 1) / BN);
   const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_tc_kernel<BN><<<grid, kThreads, tc_smem_bytes<BN>(), st>>>(ta, tb, em, make_epi(g), g.M, g.N, g.K, d_err);
+  gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), tc_smem_bytes<BN, EPQ>(), st>>>(ta, tb, em, make_epi(g), g.M,
+                                                                                    g.N, g.K, d_err);
   return true;
 }
 
@@ -1052,6 +1081,10 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
     if (why) *why = "tcgen05 GEMM operands must be 16-byte aligned with pitches a multiple of 8 elements";
     return false;
   }
+  if (g.add && g.epi != EPI_HEAD) {
+    if (why) *why = "the tcgen05 GEMM takes an addend only in the HEAD epilogue (bf16)";
+    return false;
+  }
   const int tiles = (g.N + 255) / 256;
   if ((g.epi == EPI_HEAD || g.epi == EPI_LAST) && tiles != 1) {
     if (why) *why = "fused head epilogues need N <= 256";
@@ -1059,15 +1092,20 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
   }
   int bn = (g.N + tiles - 1) / tiles;
   bn = (bn + 31) / 32 * 32;
+  // four epilogue warps per quarter for the arithmetic epilogues (instantiated
+  // for the tile widths the MLP adjoints use), two for plain copies
+  const bool wide = !(g.epi == EPI_LINEAR || g.epi == EPI_F32);
   switch (bn) {
-    case 32: return launch_bn<32>(g, B, ldb, st, d_err, why);
-    case 64: return launch_bn<64>(g, B, ldb, st, d_err, why);
-    case 96: return launch_bn<96>(g, B, ldb, st, d_err, why);
-    case 128: return launch_bn<128>(g, B, ldb, st, d_err, why);
-    case 160: return launch_bn<160>(g, B, ldb, st, d_err, why);
-    case 192: return launch_bn<192>(g, B, ldb, st, d_err, why);
-    case 224: return launch_bn<224>(g, B, ldb, st, d_err, why);
-    default: return launch_bn<256>(g, B, ldb, st, d_err, why);
+    case 32: return launch_bn<32, 2>(g, B, ldb, st, d_err, why);
+    case 64: return wide ? launch_bn<64, 4>(g, B, ldb, st, d_err, why) : launch_bn<64, 2>(g, B, ldb, st, d_err, why);
+    case 96: return launch_bn<96, 2>(g, B, ldb, st, d_err, why);
+    case 128:
+      return wide ? launch_bn<128, 4>(g, B, ldb, st, d_err, why) : launch_bn<128, 2>(g, B, ldb, st, d_err, why);
+    case 160: return launch_bn<160, 2>(g, B, ldb, st, d_err, why);
+    case 192: return launch_bn<192, 2>(g, B, ldb, st, d_err, why);
+    case 224: return launch_bn<224, 2>(g, B, ldb, st, d_err, why);
+    default:
+      return wide ? launch_bn<256, 4>(g, B, ldb, st, d_err, why) : launch_bn<256, 2>(g, B, ldb, st, d_err, why);
   }
 }
 
@@ -1111,7 +1149,7 @@ static bool launch_chain(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st
   }
   const int tiles = (g1.M + kTcBM - 1) / kTcBM;
   const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_chain_kernel<N1, BN2><<<grid, kThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M, g1.K, g2.N, d_err);
+  gemm_chain_kernel<N1, BN2><<<grid, kChainThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M, g1.K, g2.N, d_err);
   return true;
 }
 

@@ -773,7 +773,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   auto run2 = [&](const GemmArgs& g1, const GemmArgs& g2) -> allegro_status {
     // Fused pairs measured faster only for SiLU -> SiLU forward layers; the
     // others are bound by epilogue throughput and run as separate kernels.
-    const bool want_chain = g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_LAST);
+    const bool want_chain = g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU;
     if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
       std::string why;
       static std::vector<std::string> names;

@@ -1097,7 +1097,7 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
   const bool wide = !(g.epi == EPI_LINEAR || g.epi == EPI_F32);
   switch (bn) {
     case 32: return launch_bn<32, 2>(g, B, ldb, st, d_err, why);
-    case 64: return wide ? launch_bn<64, 4>(g, B, ldb, st, d_err, why) : launch_bn<64, 2>(g, B, ldb, st, d_err, why);
+    case 64: return launch_bn<64, 2>(g, B, ldb, st, d_err, why);
     case 96: return launch_bn<96, 2>(g, B, ldb, st, d_err, why);
     case 128:
       return wide ? launch_bn<128, 4>(g, B, ldb, st, d_err, why) : launch_bn<128, 2>(g, B, ldb, st, d_err, why);

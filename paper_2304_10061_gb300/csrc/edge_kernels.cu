@@ -71,40 +71,69 @@ __device__ __forceinline__ void sh_vjp(int lmax, float x, float y, float z, cons
   }
 }
 
+// One block of kGeomBlock edges: each thread builds its edge's Y and two-body
+// input row in shared memory; the block then writes both arrays back as
+// contiguous 16-byte vectors (the per-edge records are 36 and 2 ld_h0 bytes,
+// so per-thread stores would scatter over many partial sectors).
+constexpr int kGeomBlock = 128;
+
 template <typename T>
-__global__ void geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
-                                const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
-                                float* __restrict__ Yout, float* __restrict__ uout, T* __restrict__ h0,
-                                int ld_h0, const double* __restrict__ sigma, float* __restrict__ sig) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Ec) return;
-  size_t eg = (size_t)e0 + e;
-  double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
-  // float32 geometry from the exact float64 displacement
-  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-  const float r2 = fx * fx + fy * fy + fz * fz;
-  const float ir32 = rsqrtf(r2);
-  const float r = r2 * ir32;
-  const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
-  float Y[kMaxS];
-  sh_eval(bc.lmax, x, y, z, Y);
-  for (int a = 0; a < bc.S; ++a) Yout[(size_t)e * bc.S + a] = Y[a];
-  float xr = r * bc.inv_rc;
-  float u = 0.0f;
-  if (xr < 1.0f) {
-    float xp = ipow(xr, bc.p);
-    u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
+__global__ void __launch_bounds__(kGeomBlock) geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed,
+                                                             const int* __restrict__ ei, const int* __restrict__ ej,
+                                                             const int* __restrict__ species, BasisConst bc,
+                                                             float* __restrict__ Yout, float* __restrict__ uout,
+                                                             T* __restrict__ h0, int ld_h0,
+                                                             const double* __restrict__ sigma,
+                                                             float* __restrict__ sig) {
+  extern __shared__ __align__(16) uint8_t geom_sm[];
+  float* sY = reinterpret_cast<float*>(geom_sm);                          // [kGeomBlock][S]
+  T* sH = reinterpret_cast<T*>(geom_sm + kGeomBlock * kMaxS * 4);         // [kGeomBlock][ld_h0]
+  const int eb = blockIdx.x * kGeomBlock;
+  const int nloc = min(kGeomBlock, Ec - eb);
+  const int tl = threadIdx.x;
+  const int e = eb + tl;
+  if (tl < nloc) {
+    const size_t eg = (size_t)e0 + e;
+    const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+    // float32 geometry from the exact float64 displacement
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float r2 = fx * fx + fy * fy + fz * fz;
+    const float ir32 = rsqrtf(r2);
+    const float r = r2 * ir32;
+    const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
+    float Y[kMaxS];
+    sh_eval(bc.lmax, x, y, z, Y);
+    for (int a = 0; a < bc.S; ++a) sY[tl * bc.S + a] = Y[a];
+    const float xr = r * bc.inv_rc;
+    float u = 0.0f;
+    if (xr < 1.0f) {
+      const float xp = ipow(xr, bc.p);
+      u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
+    }
+    uout[e] = u;
+    T* row = sH + (size_t)tl * ld_h0;
+    const int zi = species[ei[eg]], zj = species[ej[eg]];
+    if (sig) sig[e] = (float)sigma[zi];
+    for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
+    row[zi] = to_act<T>(1.0f);
+    row[bc.ns + zj] = to_act<T>(1.0f);
+    for (int n = 1; n <= bc.nb; ++n) {
+      const float sn = sinpif((float)n * xr);
+      row[2 * bc.ns + n - 1] = to_act<T>(bc.pref * sn * ir32);
+    }
   }
-  uout[e] = u;
-  T* row = h0 + (size_t)e * ld_h0;
-  const int zi = species[ei[eg]], zj = species[ej[eg]];
-  if (sig) sig[e] = (float)sigma[zi];
-  for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
-  row[zi] = to_act<T>(1.0f);
-  row[bc.ns + zj] = to_act<T>(1.0f);
-  for (int n = 1; n <= bc.nb; ++n) {
-    float s = sinpif((float)n * xr);
-    row[2 * bc.ns + n - 1] = to_act<T>(bc.pref * s * ir32);
+  __syncthreads();
+  // Y: nloc * S floats starting at float eb * S (4-byte aligned only): scalar, coalesced
+  {
+    float* dst = Yout + (size_t)eb * bc.S;
+    for (int q = tl; q < nloc * bc.S; q += kGeomBlock) dst[q] = sY[q];
+  }
+  // h0: rows of ld_h0 elements, 16-byte aligned and a multiple of 16 bytes (ld_h0 % 8 == 0)
+  {
+    const int n16 = nloc * ld_h0 * (int)sizeof(T) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(sH);
+    uint4* dst = reinterpret_cast<uint4*>(h0 + (size_t)eb * ld_h0);
+    for (int q = tl; q < n16; q += kGeomBlock) dst[q] = src[q];
   }
 }
 
@@ -113,8 +142,11 @@ void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* e
                    const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
                    cudaStream_t st) {
   if (Ec <= 0) return;
-  geom_fwd_kernel<T><<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, h0,
-                                                       ld_h0, sigma, sig);
+  const size_t smem = (size_t)kGeomBlock * kMaxS * 4 + (size_t)kGeomBlock * ld_h0 * sizeof(T);
+  if (smem > 48 * 1024)   // many species: opt in to more than the default dynamic shared memory
+    cudaFuncSetAttribute(geom_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  geom_fwd_kernel<T><<<(Ec + kGeomBlock - 1) / kGeomBlock, kGeomBlock, smem, st>>>(
+      Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, h0, ld_h0, sigma, sig);
 }
 template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
                                    float*, float*, float*, int, const double*, float*, cudaStream_t);

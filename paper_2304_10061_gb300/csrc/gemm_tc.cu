@@ -217,7 +217,9 @@ template <int EPQ> __host__ __device__ constexpr int tc_out_bufs() { return EPQ 
 template <int EPQ> __host__ __device__ constexpr int tc_epi_slot() { return tc_out_bufs<EPQ>() * kOutBox + kInSlot; }
 template <int EPQ> __host__ __device__ constexpr int tc_epi_smem() { return 4 * EPQ * tc_epi_slot<EPQ>(); }
 constexpr int kTcSmemMax = 232448;           // dynamic shared memory per block (227 KB)
-constexpr int kTcMisc = 1024;                // mbarriers, TMEM slot, flags
+// mbarriers, TMEM slot, flags; with two epilogue warps per quarter also the
+// partial row sums ([4 quarters][2 TMEM buffers][32] floats)
+template <int EPQ> __host__ __device__ constexpr int tc_misc() { return EPQ == 2 ? 2048 : 1024; }
 
 template <int BN>
 __host__ __device__ constexpr int tc_stage_bytes() {
@@ -226,9 +228,9 @@ __host__ __device__ constexpr int tc_stage_bytes() {
 
 template <int BN, int EPQ>
 __host__ __device__ constexpr int tc_stages() {
-  return (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - kTcMisc) / tc_stage_bytes<BN>() > 6
+  return (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - tc_misc<EPQ>()) / tc_stage_bytes<BN>() > 6
              ? 6
-             : (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - kTcMisc) / tc_stage_bytes<BN>();
+             : (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - tc_misc<EPQ>()) / tc_stage_bytes<BN>();
 }
 
 template <int BN>
@@ -238,7 +240,7 @@ __host__ __device__ constexpr int tc_tmem_cols() {   // one accumulator buffer
 
 template <int BN, int EPQ>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)tc_stages<BN, EPQ>() * tc_stage_bytes<BN>() + tc_epi_smem<EPQ>() + 1024 + kTcMisc;
+  return (size_t)tc_stages<BN, EPQ>() * tc_stage_bytes<BN>() + tc_epi_smem<EPQ>() + 1024 + tc_misc<EPQ>();
 }
 static_assert(tc_stages<256, 4>() >= 2 && tc_smem_bytes<256, 4>() <= (size_t)kTcSmemMax, "shared-memory budget");
 static_assert(tc_stages<256, 2>() >= 2 && tc_smem_bytes<256, 2>() <= (size_t)kTcSmemMax, "shared-memory budget");
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
   uint64_t* inbar = rsbar + 8;          // [kEpiWarps]: input slot filled
   uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kEpiWarps);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  float* rowpart = reinterpret_cast<float*>(tslot + 4);   // EPQ == 2: [4][2][32] partial row sums
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (K + kTcBK - 1) / kTcBK;
@@ -532,6 +535,8 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
           in_par ^= 1u;
           if (need_pre) ld_bf16_row_raw(my_in, lane, zw);
           if (need_add) ld_bf16_row_raw(my_in + 2048, lane, aw);
+          // the slot's generic reads are ordered before the next TMA write into it
+          fence_async_smem();
           __syncwarp();
           // prefetch this warp's next chunk (possibly in its next tile)
           if (c + EPQ < nch) fetch(t, c + EPQ);
@@ -607,7 +612,12 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
         // Warp h = 0 releases the TMEM buffer only after reading the partials,
         // so no warp can overwrite a partial slot (indexed by the buffer)
         // before it is read.
-        float* part = reinterpret_cast<float*>(my_out + 2048 + b * 128);
+        // EPQ == 4: in the unused upper half of the warp's staging buffer; EPQ == 2: a dedicated slot
+        auto part_of = [&](int ewp) -> float* {
+          return EPQ == 2 ? rowpart + ((q * 2 + b) * 32)
+                          : reinterpret_cast<float*>(sE + ewp * kEpiSlot + 2048 + b * 128);
+        };
+        float* part = part_of(ew);
         if (h != 0) {
           part[lane] = acc1;
           __syncwarp();
@@ -623,7 +633,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
           float tot = acc1;
 #pragma unroll
           for (int hp = 1; hp < EPQ; ++hp)
-            tot += reinterpret_cast<const float*>(sE + (ew + 4 * hp) * kEpiSlot + 2048 + b * 128)[lane];
+            tot += part_of(ew + 4 * hp)[lane];
           if (live) {
             if (ep.epi == EPI_HEAD) {
               ep.ubar[m] += tot;
@@ -864,6 +874,7 @@ __global__ void __launch_bounds__(kChainThreads, 1)
       }
       in_par ^= 1u;
       ld_bf16_row(ib, lane, zc);
+      fence_async_smem();      // the slot's generic reads are ordered before the next TMA write into it
       __syncwarp();
     };
     auto out_wait = [&]() {

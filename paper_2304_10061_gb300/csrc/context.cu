@@ -87,7 +87,7 @@ struct Cap {
   int64_t v = 0;
 };
 struct Caps {
-  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat, pos4;
+  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat, pos4, pw;
   Cap ej, ei, eS, ed, col_edge, Ee, g;
   Cap cc, cs, ccur;
   Cap offs, cells, pbc, nimg, Eout, Wout;
@@ -143,6 +143,7 @@ struct allegro_ctx {
   int* d_wrap = nullptr;
   int* d_sorted = nullptr;
   float4* d_pos4 = nullptr;                // wrapped float32 positions in cell order
+  double* d_pw = nullptr;                  // wrapped float64 positions in cell order [3 n]
   int* d_atom_struct = nullptr;
   double* d_Eatom = nullptr;
   double* d_F = nullptr;
@@ -584,6 +585,7 @@ allegro_status stage_atoms(allegro_ctx* c, int64_t n, const double* pos, const i
   CUDA_TRY(c, grow(c->d_wrap, k.wrap, 3 * need));
   CUDA_TRY(c, grow(c->d_sorted, k.sorted, need));
   CUDA_TRY(c, grow(c->d_pos4, k.pos4, need));
+  CUDA_TRY(c, grow(c->d_pw, k.pw, 3 * need));
   CUDA_TRY(c, grow(c->d_atom_struct, k.atom_struct, need));
   CUDA_TRY(c, grow(c->d_Eatom, k.Eatom, need));
   CUDA_TRY(c, grow(c->d_F, k.F, 3 * need));
@@ -1258,7 +1260,7 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
     CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cursor, 0, (size_t)(ncell + 1) * 4, st));
     nb_place(c->d_cell_of, n, c->d_cell_start, c->d_cell_cursor, c->d_sorted, st);
     nb_sort_cells(c->d_cell_start, (int)ncell, c->d_sorted, st);
-    nb_pos4(c->d_pos, n, g, c->d_wrap, c->d_sorted, c->d_pos4, st);
+    nb_pos4(c->d_pos, n, g, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, st);
   }
   // Error band of the float32 prefilter: bound X on |wrapped coordinate| and
   // |image offset|, per-component error <= 8 ulp(X), squared-distance error
@@ -1282,8 +1284,8 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   const double rc2 = rc * rc;
   {
     ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
-    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, rc2, band,
-              c->d_count,
+    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
+              band, c->d_count,
               nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
     exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
   }
@@ -1295,8 +1297,8 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
   {
     ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
-    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, rc2, band,
-              nullptr,
+    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
+              band, nullptr,
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
@@ -1551,7 +1553,7 @@ void allegro_destroy(allegro_ctx* c) {
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->weight_allocs) cudaFree(p);
   void* bufs[] = {c->d_map, c->d_pos, c->d_types, c->d_species, c->d_row_ptr, c->d_col_ptr, c->d_count,
-                  c->d_cell_of, c->d_wrap, c->d_sorted, c->d_pos4, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
+                  c->d_cell_of, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, c->d_atom_struct, c->d_Eatom, c->d_F, c->d_Wat,
                   c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_col_edge, c->d_Ee, c->d_g, c->d_cell_count,
                   c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
                   c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,

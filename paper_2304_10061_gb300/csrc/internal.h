@@ -144,11 +144,11 @@ void nb_place(const int* cell_of, int n, const int* cell_start, int* cell_cursor
               cudaStream_t st);
 void nb_sort_cells(const int* cell_start, int n_cells, int* sorted, cudaStream_t st);
 void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
-             cudaStream_t st);
+             double* pw, cudaStream_t st);
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, double rc2,
-               float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
-               cudaStream_t st);
+               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
+               double rc2, float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed,
+               int* d_err, cudaStream_t st);
 void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,
                            const double* cells, const int* pbc, const int* nimg, double rc2,
                            const int* atom_struct, int n, int* count, const int* row_ptr, int* ej,

@@ -273,10 +273,11 @@ __device__ __forceinline__ bool pair_test(const double* __restrict__ pi, const d
   return r2 < rc2;
 }
 
-// Wrapped positions pw = pos - wrap . cell in float32, stored in cell-sorted
-// order (pos4[s] belongs to atom sorted[s]).
+// Wrapped positions pw = pos - wrap . cell in cell-sorted order (pos4[s] and
+// pw[3 s ..] belong to atom sorted[s]): float32 for the prefilter, float64 for
+// the displacements of accepted edges.
 __global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, const int* __restrict__ wrap,
-                            const int* __restrict__ sorted, float4* __restrict__ pos4) {
+                            const int* __restrict__ sorted, float4* __restrict__ pos4, double* __restrict__ pw) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int j = sorted[s];
@@ -288,6 +289,9 @@ __global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, c
     for (int k = 0; k < 3; ++k) p[x] -= (double)wrap[3 * (size_t)j + k] * g.cell[k * 3 + x];
   }
   pos4[s] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.0f);
+  pw[3 * (size_t)s] = p[0];
+  pw[3 * (size_t)s + 1] = p[1];
+  pw[3 * (size_t)s + 2] = p[2];
 }
 
 // Neighbour search.  A float32 prefilter on the wrapped positions decides
@@ -295,11 +299,15 @@ __global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, c
 // candidates inside the band take the exact float64 test.  `band` is computed
 // on the host from a bound on the float32 rounding of the wrapped coordinates
 // and image offsets (with a safety factor), so the prefilter never changes a
-// decision.  Accepted edges get their float64 displacement for later stages.
-__global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, CellGrid g,
+// decision.  Accepted edges get their float64 displacement for later stages:
+// from the exact test inside the band, else (pw_j + q . cell) - pw_i from the
+// float64 wrapped positions (the same vector up to float64 rounding; the
+// edge's image shift is S = q - w_j + w_i).
+template <bool fill>
+__global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g,
                               const int* __restrict__ cell_of, const int* __restrict__ wrap,
                               const int* __restrict__ cell_start, const int* __restrict__ sorted,
-                              const float4* __restrict__ pos4, double rc2, float band,
+                              const float4* __restrict__ pos4, const double* __restrict__ pw, double rc2, float band,
                               int* __restrict__ count, const int* __restrict__ row_ptr,
                               int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS,
                               double* __restrict__ ed, int* __restrict__ d_err) {
@@ -314,6 +322,7 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
   const int wi0 = wrap[3 * (size_t)i], wi1 = wrap[3 * (size_t)i + 1], wi2 = wrap[3 * (size_t)i + 2];
   const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
   const float4 pi4 = pos4[t];
+  const double pwi[3] = {pw[3 * (size_t)t], pw[3 * (size_t)t + 1], pw[3 * (size_t)t + 2]};
   const float rc2f = (float)rc2;
   const float lo2 = rc2f - band, hi2 = rc2f + band;
   float cf[9];
@@ -340,6 +349,13 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
         const float ox = (float)q0 * cf[0] + (float)q1 * cf[3] + (float)q2 * cf[6] - pi4.x;
         const float oy = (float)q0 * cf[1] + (float)q1 * cf[4] + (float)q2 * cf[7] - pi4.y;
         const float oz = (float)q0 * cf[2] + (float)q1 * cf[5] + (float)q2 * cf[8] - pi4.z;
+        // float64 image offset (fill pass only; zero away from the box faces)
+        double qoff[3] = {0.0, 0.0, 0.0};
+        if (fill && (q0 | q1 | q2)) {
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            qoff[x] = (double)q0 * g.cell[x] + (double)q1 * g.cell[3 + x] + (double)q2 * g.cell[6 + x];
+        }
         for (int s = b; s < e; ++s) {
           const float4 pj = pos4[s];
           const float dx = pj.x + ox, dy = pj.y + oy, dz = pj.z + oz;
@@ -351,12 +367,11 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
           int S2 = g.pbc[2] ? q2 - wrap[3 * (size_t)j + 2] + wi2 : 0;
           if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
           double d[3];
-          if (r2f >= lo2 || fill) {
-            const bool in = pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2, d);
-            if (!in) {
-              if (r2f < lo2) atomicOr(d_err, kErrNeighbor);   // the prefilter bound was violated
-              continue;
-            }
+          if (r2f >= lo2) {
+            if (!pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2, d)) continue;
+          } else if constexpr (fill) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) d[x] = (pw[3 * (size_t)s + x] + qoff[x]) - pwi[x];
           }
           if (fill) {
             if (k < cap) {
@@ -380,18 +395,22 @@ __global__ void search_kernel(bool fill, const double* __restrict__ pos, int n, 
 }
 
 void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
-             cudaStream_t st) {
+             double* pw, cudaStream_t st) {
   if (n <= 0) return;
-  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, n, g, wrap, sorted, pos4);
+  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, n, g, wrap, sorted, pos4, pw);
 }
 
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, double rc2,
-               float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed, int* d_err,
-               cudaStream_t st) {
+               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
+               double rc2, float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed,
+               int* d_err, cudaStream_t st) {
   if (n <= 0) return;
-  search_kernel<<<(n + 127) / 128, 128, 0, st>>>(fill, pos, n, g, cell_of, wrap, cell_start, sorted, pos4,
-                                                 rc2, band, count, row_ptr, ej, ei, eS, ed, d_err);
+  if (fill)
+    search_kernel<true><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
+                                                         band, count, row_ptr, ej, ei, eS, ed, d_err);
+  else
+    search_kernel<false><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
+                                                          band, count, row_ptr, ej, ei, eS, ed, d_err);
 }
 
 // ---------------------------------------------------------------------------

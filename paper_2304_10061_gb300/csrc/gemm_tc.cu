@@ -1172,7 +1172,8 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
   if (g1.M <= 0) return true;
   if (g2.K != g1.N || g2.M != g1.M) return false;
   if (!(g1.epi == EPI_FWD_SILU || g1.epi == EPI_BWD_SILU)) return false;
-  if (!(g2.epi == EPI_FWD_SILU || g2.epi == EPI_BWD_SILU || g2.epi == EPI_LAST || (g2.epi == EPI_F32 && !g2.add)))
+  if (!(g2.epi == EPI_FWD_SILU || g2.epi == EPI_BWD_SILU || g2.epi == EPI_LAST || g2.epi == EPI_LINEAR ||
+        (g2.epi == EPI_F32 && !g2.add)))
     return false;
   if (g1.epi == EPI_BWD_SILU && !g1.pre) return false;
   if (g2.epi == EPI_BWD_SILU && !g2.pre) return false;

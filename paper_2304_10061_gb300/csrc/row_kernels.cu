@@ -294,7 +294,8 @@ __device__ __forceinline__ void edge_batches(int cnt, Load&& load, Comp&& comp) 
 }
 
 constexpr int kBatchLight = 8;   // edges per batch in passes with one weight array
-constexpr int kBatchHeavy = 4;   // in the first adjoint passes (weights + sbar, more live state)
+constexpr int kBatchHeavy = 4;   // first pass of the layer-1 adjoint (weights + two sbar, most live state)
+constexpr int kBatchLastP1 = 8;  // first pass of the last-layer adjoint (weights + one sbar)
 
 // Gamma-type environment sum over the row: G[j][b] = sum_e w[e][j][l(b)] Y[e][b]
 template <typename T, int LMAX, int CPL>
@@ -510,9 +511,9 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
     const int cnt = min(kYSeg, r.re - sb);
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
-    uint32_t raw[kBatchHeavy][WS::NW];
-    typename RawOf<T>::type sraw[kBatchHeavy][CPL];
-    edge_batches<kBatchHeavy>(
+    uint32_t raw[kBatchLastP1][WS::NW];
+    typename RawOf<T>::type sraw[kBatchLastP1][CPL];
+    edge_batches<kBatchLastP1>(
         cnt,
         [&](int u, int k) {
           ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);

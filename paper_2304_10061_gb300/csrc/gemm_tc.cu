@@ -205,32 +205,29 @@ constexpr int kTcBM = 128, kTcBK = 64;
 // (which rather want the deeper operand ring and the double-buffered output
 // staging that the smaller epilogue footprint leaves room for).
 template <int EPQ> __host__ __device__ constexpr int tc_threads() { return 64 + 32 * 4 * EPQ; }
-// Per epilogue warp: output staging (each buffer a float32 32x32 box, or two
-// bf16 32x32 boxes: activation and pre-activation; double-buffered with two
-// warps per quarter) and one input slot (the bf16 pre-activation and the
-// bf16 addend of the warp's next chunk, fetched by TMA).  In the row-sum modes
-// (no pre-activation store) the upper half of the first output buffer carries
-// the warp's partial row sums, one 128-byte slot per TMEM buffer.
-constexpr int kOutBox = 4096;
-constexpr int kInSlot = 4096;
-template <int EPQ> __host__ __device__ constexpr int tc_out_bufs() { return EPQ == 2 ? 2 : 1; }
-template <int EPQ> __host__ __device__ constexpr int tc_epi_slot() { return tc_out_bufs<EPQ>() * kOutBox + kInSlot; }
-template <int EPQ> __host__ __device__ constexpr int tc_epi_smem() { return 4 * EPQ * tc_epi_slot<EPQ>(); }
+// Shared memory of one CTA: the operand ring (A and B k-blocks), then per
+// epilogue warp its output staging buffers and its input slot, then the
+// mbarriers, flags and partial row sums.  The epilogue part depends on the
+// mode (TcLayout, chosen on the host): a bf16 32x32 output box is 2 KB, a
+// float32 box or an activation + pre-activation pair 4 KB; two output buffers
+// (double-buffered TMA stores) with two warps per quarter, one with four; an
+// input slot of 2 KB per bf16 input (pre-activation, addend).  The ring takes
+// the rest, up to kTcMaxStages k-blocks.
 constexpr int kTcSmemMax = 232448;           // dynamic shared memory per block (227 KB)
-// mbarriers, TMEM slot, flags; with two epilogue warps per quarter also the
-// partial row sums ([4 quarters][2 TMEM buffers][32] floats)
-template <int EPQ> __host__ __device__ constexpr int tc_misc() { return EPQ == 2 ? 2048 : 1024; }
+constexpr int kTcMisc = 4096;                // mbarriers, TMEM slot, flags, partial row sums
+constexpr int kTcMaxStages = 8;
+
+struct TcLayout {
+  int stages;      // operand ring depth
+  int out_box;     // bytes per output buffer
+  int n_out;       // output buffers per warp
+  int in_slot;     // bytes of the input slot
+  int epi_slot;    // n_out * out_box + in_slot
+};
 
 template <int BN>
 __host__ __device__ constexpr int tc_stage_bytes() {
   return kTcBM * kTcBK * 2 + BN * kTcBK * 2;
-}
-
-template <int BN, int EPQ>
-__host__ __device__ constexpr int tc_stages() {
-  return (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - tc_misc<EPQ>()) / tc_stage_bytes<BN>() > 6
-             ? 6
-             : (kTcSmemMax - tc_epi_smem<EPQ>() - 1024 - tc_misc<EPQ>()) / tc_stage_bytes<BN>();
 }
 
 template <int BN>
@@ -239,11 +236,22 @@ __host__ __device__ constexpr int tc_tmem_cols() {   // one accumulator buffer
 }
 
 template <int BN, int EPQ>
-__host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)tc_stages<BN, EPQ>() * tc_stage_bytes<BN>() + tc_epi_smem<EPQ>() + 1024 + tc_misc<EPQ>();
+static TcLayout tc_layout(int epi, bool pre) {
+  TcLayout L;
+  const bool wide_out = (epi == EPI_F32) || (epi == EPI_FWD_SILU && pre);
+  L.out_box = wide_out ? 4096 : 2048;
+  L.n_out = (EPQ == 2) ? 2 : 1;
+  L.in_slot = (epi == EPI_BWD_SILU) ? 2048 : (epi == EPI_HEAD ? 4096 : 0);
+  L.epi_slot = L.n_out * L.out_box + L.in_slot;
+  const int epi_smem = 4 * EPQ * L.epi_slot;
+  const int st = (kTcSmemMax - 1024 - kTcMisc - epi_smem) / tc_stage_bytes<BN>();
+  L.stages = st > kTcMaxStages ? kTcMaxStages : st;
+  return L;
 }
-static_assert(tc_stages<256, 4>() >= 2 && tc_smem_bytes<256, 4>() <= (size_t)kTcSmemMax, "shared-memory budget");
-static_assert(tc_stages<256, 2>() >= 2 && tc_smem_bytes<256, 2>() <= (size_t)kTcSmemMax, "shared-memory budget");
+template <int BN, int EPQ>
+static size_t tc_smem_bytes(const TcLayout& L) {
+  return (size_t)L.stages * tc_stage_bytes<BN>() + (size_t)4 * EPQ * L.epi_slot + 1024 + kTcMisc;
+}
 
 // --- epilogue staging: 32 x 32 boxes moved by TMA --------------------------
 // bf16 box rows are 64 bytes (64-byte swizzle), float32 box rows 128 bytes
@@ -367,11 +375,12 @@ __device__ __forceinline__ float bf16_word_elem(const uint32_t (&w)[16], int j) 
 template <int BN, int EPQ>
 __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ EpiMaps em, EpiParams ep, int M, int N, int K, int* __restrict__ err) {
-  constexpr int STAGES = tc_stages<BN, EPQ>();
+                   const __grid_constant__ EpiMaps em, EpiParams ep, TcLayout lay, int M, int N, int K,
+                   int* __restrict__ err) {
+  const int STAGES = lay.stages;
   constexpr int kEpiWarps = 4 * EPQ;
-  constexpr int kEpiSlot = tc_epi_slot<EPQ>();
-  constexpr int kNOut = tc_out_bufs<EPQ>();
+  const int kEpiSlot = lay.epi_slot;
+  const int kNOut = lay.n_out;
   constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
   constexpr uint32_t B_BYTES = BN * kTcBK * 2;
   constexpr uint32_t COLS = tc_tmem_cols<BN>();
@@ -380,7 +389,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint8_t* sE = sB + STAGES * B_BYTES;                       // epilogue staging (1024-aligned)
-  uint64_t* full = reinterpret_cast<uint64_t*>(sE + tc_epi_smem<EPQ>());
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE + 4 * EPQ * kEpiSlot);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;     // [2]
   uint64_t* tempty = tfull + 2;         // [2]
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
   uint64_t* inbar = rsbar + 8;          // [kEpiWarps]: input slot filled
   uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kEpiWarps);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-  float* rowpart = reinterpret_cast<float*>(tslot + 4);   // EPQ == 2: [4][2][32] partial row sums
+  float* rowpart = reinterpret_cast<float*>(tslot + 4);   // [4 quarters][2 buffers][EPQ - 1][32] partial row sums
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (K + kTcBK - 1) / kTcBK;
@@ -482,7 +491,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
     const int ew = warp - 2;           // epilogue warp index 0..kEpiWarps-1
     const int h = ew >> 2;             // 0..EPQ-1 within the quarter
     uint8_t* my_out = sE + ew * kEpiSlot;
-    uint8_t* my_in = my_out + kNOut * kOutBox;
+    uint8_t* my_in = my_out + kNOut * lay.out_box;
     const bool need_pre = (ep.epi == EPI_BWD_SILU || ep.epi == EPI_HEAD);
     const bool need_add = (ep.add != nullptr) && (ep.epi == EPI_HEAD);
     const uint32_t in_bytes = (need_pre ? 2048u : 0u) + (need_add ? 2048u : 0u);
@@ -524,7 +533,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
       const uint32_t base = tmem + (uint32_t)(b * COLS) + ((uint32_t)(q * 32) << 16);
       const int nch = nch_of(t);
       for (int c = h; c < nch; c += EPQ) {
-        uint8_t* ob = my_out + (oc % kNOut) * kOutBox;
+        uint8_t* ob = my_out + (oc % kNOut) * lay.out_box;
         // inputs of this chunk, kept as packed bf16 words
         uint32_t zw[16], aw[16];
         if (in_bytes) {
@@ -612,12 +621,8 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
         // Warp h = 0 releases the TMEM buffer only after reading the partials,
         // so no warp can overwrite a partial slot (indexed by the buffer)
         // before it is read.
-        // EPQ == 4: in the unused upper half of the warp's staging buffer; EPQ == 2: a dedicated slot
-        auto part_of = [&](int ewp) -> float* {
-          return EPQ == 2 ? rowpart + ((q * 2 + b) * 32)
-                          : reinterpret_cast<float*>(sE + ewp * kEpiSlot + 2048 + b * 128);
-        };
-        float* part = part_of(ew);
+        auto part_of = [&](int hp) -> float* { return rowpart + (((q * 2 + b) * (EPQ - 1) + (hp - 1)) * 32); };
+        float* part = h != 0 ? part_of(h) : nullptr;
         if (h != 0) {
           part[lane] = acc1;
           __syncwarp();
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
           float tot = acc1;
 #pragma unroll
           for (int hp = 1; hp < EPQ; ++hp)
-            tot += part_of(ew + 4 * hp)[lane];
+            tot += part_of(hp)[lane];
           if (live) {
             if (ep.epi == EPI_HEAD) {
               ep.ubar[m] += tot;
@@ -1046,7 +1051,7 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, EPQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes<BN, EPQ>());
+                                         kTcSmemMax);
     if (e != cudaSuccess) {
       if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
       return false;
@@ -1075,10 +1080,15 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
     if (why) *why = "cuTensorMapEncodeTiled failed for an epilogue operand";
     return false;
   }
+  const TcLayout lay = tc_layout<BN, EPQ>(g.epi, g.pre != nullptr);
+  if (lay.stages < 2) {
+    if (why) *why = "tcgen05 GEMM: shared memory too small for two operand stages";
+    return false;
+  }
+  const size_t smem = tc_smem_bytes<BN, EPQ>(lay);
   const int tiles = ((g.M + kTcBM - 1) / kTcBM) * ((g.N + BN - 1) / BN);
   const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), tc_smem_bytes<BN, EPQ>(), st>>>(ta, tb, em, make_epi(g), g.M,
-                                                                                    g.N, g.K, d_err);
+  gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), smem, st>>>(ta, tb, em, make_epi(g), lay, g.M, g.N, g.K, d_err);
   return true;
 }
 

@@ -154,14 +154,24 @@ def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int =
     name, r = max(report.items(), key=lambda kv: kv[1]["ms"])
     peaks = _peaks()
     tensor = name.startswith("gemm_tc")
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    tc_peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+    tc_ctx = None
+    bound = "hbm"
     if tensor:
-        peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-        achieved = r["flops"] / (r["ms"] * 1e-3) / 1e12
-        unit, bound = "TFLOP/s", "tensor"
+        # the MLP GEMMs' arithmetic intensity (algorithmic FLOPs per algorithmic byte)
+        # decides which roof binds them: below the ridge point it is HBM
+        intensity = r["flops"] / max(r["bytes"], 1.0)
+        ridge = tc_peak * 1e12 / (hbm_peak * 1e9)
+        tflops = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        tc_ctx = {"achieved_tflops": round(tflops, 2), "peak_tflops": tc_peak, "frac": round(tflops / tc_peak, 4),
+                  "arithmetic_intensity_flop_per_byte": round(intensity, 1),
+                  "ridge_flop_per_byte": round(ridge, 1)}
+        bound = "tensor" if intensity >= ridge else "hbm"
+    if bound == "tensor":
+        peak, achieved, unit = tc_peak, r["flops"] / (r["ms"] * 1e-3) / 1e12, "TFLOP/s"
     else:
-        peak = peaks["hbm_gbs"] if peaks else 6800.0
-        achieved = r["bytes"] / (r["ms"] * 1e-3) / 1e9
-        unit, bound = "GB/s", "hbm"
+        peak, achieved, unit = hbm_peak, r["bytes"] / (r["ms"] * 1e-3) / 1e9, "GB/s"
     share = {k: round(v["ms"] / max(step_ms_total, 1e-9), 4) for k, v in
              sorted(report.items(), key=lambda kv: -kv[1]["ms"])}
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
@@ -170,6 +180,7 @@ def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int =
             "traffic_unit": "bytes per launch (DRAM read + write)",
             "algorithmic_bytes_per_launch": r["bytes"] / max(r["launches"], 1),
             "launches": r["launches"], "ms_per_launch": round(r["ms"] / max(r["launches"], 1), 5),
+            "tensor": tc_ctx,
             "share_of_timed_region": share,
             "gemm_detail": {k.split("/", 1)[1]: {
                                                  "share": round(v["ms"] / max(step_ms_total, 1e-9), 4),

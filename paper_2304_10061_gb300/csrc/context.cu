@@ -466,7 +466,6 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
 // ------------------------------------------------------------------------
 struct WS {
   // activations (act = float or bf16) and float32 buffers, per chunk edge
-  void* h0; int ld_h0;
   std::vector<void*> Ztb; std::vector<int> ld_Ztb;
   void* H[2]; int ld_H;
   void* X[2]; int ld_X[2];
@@ -478,7 +477,6 @@ struct WS {
   void* wbar01; int ld_wbar01;
   void* wbar2; int ld_wbar2;
   float* xbar; int ld_xbar;
-  float* inbar; int ld_inbar;
   float* Y; float* Ybar[3]; float* u; float* ubar; float* sig;
   float* G1; float* G2;
 };
@@ -496,8 +494,6 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   for (int x : a.tb) maxw = std::max(maxw, x);
   for (int x : a.lat) maxw = std::max(maxw, x);
   const int nw = a.n_w(), S = a.S();
-  w->ld_h0 = pad8(a.K0in());
-  w->h0 = take((size_t)Ec * w->ld_h0 * act_bytes);
   w->Ztb.resize(ntb); w->ld_Ztb.resize(ntb);
   for (int k = 0; k < ntb; ++k) {
     w->ld_Ztb[k] = pad8(a.tb[k]);
@@ -529,8 +525,6 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->wbar2 = (a.nl == 2) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
   w->ld_xbar = pad8(std::max(a.tb.back(), a.lat.back()));
   w->xbar = (float*)take((size_t)Ec * w->ld_xbar * 4);
-  w->ld_inbar = pad8(a.K0in());
-  w->inbar = (float*)take((size_t)Ec * w->ld_inbar * 4);
   w->Y = (float*)take((size_t)Ec * S * 4);
   for (int k = 0; k < 3; ++k) w->Ybar[k] = (float*)take((size_t)Ec * S * 4);
   w->u = (float*)take((size_t)Ec * 4);
@@ -818,20 +812,27 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     return ProfScope(c, name, 0.0, (double)Ec * per_edge + (double)Ac * per_atom);
   };
   // ---- forward ----
+  // geometry, basis and the first two-body layer in one kernel (its output in H[1], or in X[0]
+  // scaled by u when it is the two-body MLP's only layer)
+  const bool tb_single = (ntb == 1);
   {
-    ProfScope ps(c, "geom_fwd", 0.0, (double)Ec * (24 + 8 + 8 + S * 4 + 4 + w.ld_h0 * act));
-    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, (T*)w.h0, w.ld_h0, c->d_sigma,
-                     w.sig, st);
+    ProfScope ps(c, "geom_fwd", 2.0 * Ec * a.tb[0] * (a.nb + 2),
+                 (double)Ec * (24 + 8 + 8 + S * 4 + 4 + 4 + 2.0 * a.tb[0] * act));
+    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, c->d_sigma, w.sig,
+                     c->tb[0].f32T, c->tb[0].ldT, (T*)w.Ztb[0], w.ld_Ztb[0],
+                     (T*)(tb_single ? w.X[0] : w.H[1]), tb_single ? w.ld_X[0] : w.ld_H, tb_single, st);
   }
-  const void* in = w.h0;
-  int ld_in = w.ld_h0, K = a.K0in();
+  const void* in = w.H[1];
+  int ld_in = w.ld_H, K = a.tb[0];
   // forward MLP layers [k0, k1) of `layers`: layer k writes pre Z[k], activation to H (or to `last_out`)
+  // layers [k0, nlay) of `layers`; layer k writes its activation to H[(k - k0) & 1] (or to `last_out`)
   auto fwd_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
-                     int nlay, const void*& src, int& ld_src, int& Kin, void* last_out, int ld_last) -> allegro_status {
-    int k = 0;
+                     int k0, int nlay, const void*& src, int& ld_src, int& Kin, void* last_out,
+                     int ld_last) -> allegro_status {
+    int k = k0;
     while (k < nlay) {
       const bool last = (k == nlay - 1);
-      void* out = last ? last_out : w.H[k & 1];
+      void* out = last ? last_out : w.H[(k - k0) & 1];
       int ldo = last ? ld_last : w.ld_H;
       GemmArgs g1 = mk(src, ld_src, Kin, layers[k], false, EPI_FWD_SILU, out, ldo, layers[k].N, Z[k], ldZ[k],
                        last ? w.u : nullptr);
@@ -840,7 +841,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
         GemmArgs g2 = mk(nullptr, 0, layers[k].N, layers[k + 1], false, EPI_FWD_SILU, last_out, ld_last,
                          layers[k + 1].N, Z[k + 1], ldZ[k + 1], w.u);
         g1.rowscale = nullptr;
-        g1.out = w.H[k & 1]; g1.ldo = w.ld_H;
+        g1.out = w.H[(k - k0) & 1]; g1.ldo = w.ld_H;
         allegro_status r = run2(g1, g2);
         if (r != ALLEGRO_OK) return r;
         src = last_out; ld_src = ld_last; Kin = layers[k + 1].N;
@@ -853,7 +854,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     }
     return ALLEGRO_OK;
   };
-  if ((s = fwd_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, in, ld_in, K, w.X[0], w.ld_X[0])) != ALLEGRO_OK) return s;
+  if (ntb > 1 && (s = fwd_mlp(c->tb, w.Ztb, w.ld_Ztb, 1, ntb, in, ld_in, K, w.X[0], w.ld_X[0])) != ALLEGRO_OK)
+    return s;
   if ((s = G(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_LINEAR, w.W01, w.ld_W01, 2 * nw)) != ALLEGRO_OK)
     return s;
   for (int L = 1; L <= nl; ++L) {
@@ -869,7 +871,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     if (fused && L == nl) {
       // last latent MLP; its final layer carries the folded edge energy and the start of the adjoint
       if (nlat >= 2) {
-        if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, nlat - 2, in, ld_in, K, nullptr, 0)) !=
+        if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, 0, nlat - 2, in, ld_in, K, nullptr, 0)) !=
             ALLEGRO_OK)
           return s;
         GemmArgs g1 = mk(in, ld_in, K, c->lat[L - 1][nlat - 2], false, EPI_FWD_SILU, w.H[1], w.ld_H,
@@ -884,7 +886,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     } else {
       void* dst = (L < nl) ? w.X[L] : w.Xlast;
       const int ld_dst = (L < nl) ? w.ld_X[L] : w.ld_Xlast;
-      if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, nlat, in, ld_in, K, dst, ld_dst)) != ALLEGRO_OK)
+      if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, 0, nlat, in, ld_in, K, dst, ld_dst)) != ALLEGRO_OK)
         return s;
     }
     if (L < nl) {
@@ -986,11 +988,21 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     mlp_head_bwd<T>(Ec, a.tb.back(), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
                     (const T*)w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);
   }
-  if ((s = back_mlp(c->tb, w.Ztb, w.ld_Ztb, ntb, w.inbar, w.ld_inbar, a.K0in(), EPI_F32)) != ALLEGRO_OK) return s;
+  // two-body MLP adjoint down to zbar0; the first layer's transposed product is folded into geom_bwd
+  int cur0 = 0;
+  for (int k = ntb - 1; k >= 1; --k) {
+    const Lin& W = c->tb[k];
+    if ((s = G(w.H[cur0], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur0 ^ 1], w.ld_H, W.K, w.Ztb[k - 1],
+               w.ld_Ztb[k - 1])) != ALLEGRO_OK)
+      return s;
+    cur0 ^= 1;
+  }
   {
-    ProfScope ps(c, "geom_bwd", 0.0, (double)Ec * (24 + a.nb * 4 + 4 + (nl == 2 ? 3 : 2) * S * 4 + 12));
+    ProfScope ps(c, "geom_bwd", 2.0 * Ec * a.tb[0] * a.nb,
+                 (double)Ec * (24 + a.tb[0] * act + 4 + (nl == 2 ? 3 : 2) * S * 4 + 12));
     YbarParts yb{{w.Ybar[0], w.Ybar[1], nl == 2 ? w.Ybar[2] : nullptr}};
-    edge_geom_bwd(Ec, e0, c->d_ed, a, w.inbar, w.ld_inbar, w.ubar, yb, c->d_g, st);
+    edge_geom_bwd<T>(Ec, e0, c->d_ed, a, (const T*)w.H[cur0], w.ld_H, c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb,
+                     c->d_g, st);
   }
   return ALLEGRO_OK;
 }

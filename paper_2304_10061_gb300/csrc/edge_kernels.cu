@@ -13,6 +13,8 @@
 //   l=2: sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2 - 1), sqrt15 xz, sqrt15/2 (x^2 - y^2)
 // Two-body input row: [onehot(Z_i) | onehot(Z_j) | B(r)].
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -24,6 +26,8 @@ template <> __device__ __forceinline__ float to_act<float>(float v) { return v; 
 template <> __device__ __forceinline__ bf16 to_act<bf16>(float v) { return __float2bfloat16_rn(v); }
 __device__ __forceinline__ float from_act(float v) { return v; }
 __device__ __forceinline__ float from_act(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(bf16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return __fdividef(1.0f, 1.0f + expf(-z)); }
 
@@ -71,115 +75,258 @@ __device__ __forceinline__ void sh_vjp(int lmax, float x, float y, float z, cons
   }
 }
 
-// One block of kGeomBlock edges: each thread builds its edge's Y and two-body
-// input row in shared memory; the block then writes both arrays back as
-// contiguous 16-byte vectors (the per-edge records are 36 and 2 ld_h0 bytes,
-// so per-thread stores would scatter over many partial sectors).
+// Sigmoid of the path's MLP epilogues: the BF16 path's GEMMs use the hardware
+// tanh approximation, sigma(z) = (1 + tanh(z/2)) / 2, the float32 path the
+// exponential form; the fused first layer uses the same one as its adjoint.
+template <typename T> __device__ __forceinline__ float path_sigmoid(float z);
+template <> __device__ __forceinline__ float path_sigmoid<float>(float z) { return sigmoidf_(z); }
+template <> __device__ __forceinline__ float path_sigmoid<bf16>(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return fmaf(0.5f, t, 0.5f);
+}
+
+// Edge geometry, basis and the first two-body layer, one block of kGeomBlock
+// edges.  The layer's input row [onehot(Z_i) | onehot(Z_j) | B(r)] is never
+// formed: z_k = W0[k][Z_i] + W0[k][ns + Z_j] + sum_n W0[k][2 ns + n] B_n(r),
+// with W0 read as its transpose W0t[input][output] from shared memory, 32
+// output columns at a time.  Outputs: Y, u, sigma_{Z_i}, the pre-activation
+// z and the activation silu(z) (times u when the layer is the MLP's last), all
+// staged in shared memory and written back as contiguous runs (per-thread
+// records would scatter over partial sectors).
 constexpr int kGeomBlock = 128;
+constexpr int kGeomCols = 32;                   // output columns per pass
+constexpr int kGeomWPad = kGeomCols + 4;        // padded shared row of W0t (float4-aligned, bank-spread)
 
 template <typename T>
-__global__ void __launch_bounds__(kGeomBlock) geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed,
-                                                             const int* __restrict__ ei, const int* __restrict__ ej,
-                                                             const int* __restrict__ species, BasisConst bc,
-                                                             float* __restrict__ Yout, float* __restrict__ uout,
-                                                             T* __restrict__ h0, int ld_h0,
-                                                             const double* __restrict__ sigma,
-                                                             float* __restrict__ sig) {
-  extern __shared__ __align__(16) uint8_t geom_sm[];
-  float* sY = reinterpret_cast<float*>(geom_sm);                          // [kGeomBlock][S]
-  T* sH = reinterpret_cast<T*>(geom_sm + kGeomBlock * kMaxS * 4);         // [kGeomBlock][ld_h0]
-  const int eb = blockIdx.x * kGeomBlock;
-  const int nloc = min(kGeomBlock, Ec - eb);
-  const int tl = threadIdx.x;
-  const int e = eb + tl;
-  if (tl < nloc) {
-    const size_t eg = (size_t)e0 + e;
-    const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
-    // float32 geometry from the exact float64 displacement
-    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-    const float r2 = fx * fx + fy * fy + fz * fz;
-    const float ir32 = rsqrtf(r2);
-    const float r = r2 * ir32;
-    const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
-    float Y[kMaxS];
-    sh_eval(bc.lmax, x, y, z, Y);
-    for (int a = 0; a < bc.S; ++a) sY[tl * bc.S + a] = Y[a];
-    const float xr = r * bc.inv_rc;
-    float u = 0.0f;
-    if (xr < 1.0f) {
-      const float xp = ipow(xr, bc.p);
-      u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
+__host__ __device__ constexpr int geom_stage_ld() { return kGeomCols + 16 / (int)sizeof(T); }   // padded row, 16-byte multiple
+
+// four consecutive activation-type values from floats (8- or 16-byte aligned)
+__device__ __forceinline__ void st4_act(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4_act(bf16* p, const float (&v)[4]) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_rows_out(const T* src, int lds, T* dst, int ldd, int c0, int nrows, int nc) {
+  // rows of nc elements from shared (row pitch lds) to global (row pitch ldd, column offset c0)
+  const bool vec = ((nc * (int)sizeof(T)) % 16 == 0) && ((c0 * (int)sizeof(T)) % 16 == 0) &&
+                   ((ldd * (int)sizeof(T)) % 16 == 0);
+  if (vec) {
+    const int per = nc * (int)sizeof(T) / 16;
+    for (int q = threadIdx.x; q < nrows * per; q += blockDim.x) {
+      const int rr = q / per, cc = q - rr * per;
+      reinterpret_cast<uint4*>(dst + (size_t)rr * ldd + c0)[cc] = reinterpret_cast<const uint4*>(src + rr * lds)[cc];
     }
-    uout[e] = u;
-    T* row = sH + (size_t)tl * ld_h0;
-    const int zi = species[ei[eg]], zj = species[ej[eg]];
-    if (sig) sig[e] = (float)sigma[zi];
-    for (int k = 0; k < ld_h0; ++k) row[k] = to_act<T>(0.0f);
-    row[zi] = to_act<T>(1.0f);
-    row[bc.ns + zj] = to_act<T>(1.0f);
-    for (int n = 1; n <= bc.nb; ++n) {
-      const float sn = sinpif((float)n * xr);
-      row[2 * bc.ns + n - 1] = to_act<T>(bc.pref * sn * ir32);
+  } else {
+    for (int q = threadIdx.x; q < nrows * nc; q += blockDim.x) {
+      const int rr = q / nc, cc = q - rr * nc;
+      dst[(size_t)rr * ldd + c0 + cc] = src[rr * lds + cc];
     }
   }
-  __syncthreads();
-  // Y: nloc * S floats starting at float eb * S (4-byte aligned only): scalar, coalesced
-  {
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGeomBlock)
+    geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
+                    const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
+                    float* __restrict__ Yout, float* __restrict__ uout, const double* __restrict__ sigma,
+                    float* __restrict__ sig, const float* __restrict__ W0t, int ldW, int N0, T* __restrict__ Zout,
+                    int ldZ, T* __restrict__ Hout, int ldH, int scale_u) {
+  constexpr int LDS = geom_stage_ld<T>();
+  extern __shared__ __align__(16) uint8_t geom_sm[];
+  const int K0 = 2 * bc.ns + bc.nb;
+  const int WP = kGeomWPad;   // shared row pitch of W0t (floats)
+  float* sY = reinterpret_cast<float*>(geom_sm);                                  // [kGeomBlock][kMaxS]
+  float* sW = sY + kGeomBlock * kMaxS;                                            // [K0][WP]
+  T* sZ = reinterpret_cast<T*>(sW + K0 * WP);                                     // [kGeomBlock][LDS]
+  T* sH = sZ + kGeomBlock * LDS;                                                  // [kGeomBlock][LDS]
+  const int tl = threadIdx.x;
+  const int ntiles = (Ec + kGeomBlock - 1) / kGeomBlock;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int eb = tile * kGeomBlock;
+    const int nloc = min(kGeomBlock, Ec - eb);
+    const int e = eb + tl;
+    float B[kMaxBessel];
+    float u = 0.0f;
+    int zi = 0, zj = 0;
+    __syncthreads();   // the previous tile's Y staging has been copied out
+    if (tl < nloc) {
+      const size_t eg = (size_t)e0 + e;
+      const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+      // float32 geometry from the exact float64 displacement
+      const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+      const float r2 = fx * fx + fy * fy + fz * fz;
+      const float ir32 = rsqrtf(r2);
+      const float r = r2 * ir32;
+      const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
+      float Y[kMaxS];
+      sh_eval(bc.lmax, x, y, z, Y);
+#pragma unroll
+      for (int a = 0; a < kMaxS; ++a)
+        if (a < bc.S) sY[tl * bc.S + a] = Y[a];
+      const float xr = r * bc.inv_rc;
+      if (xr < 1.0f) {
+        const float xp = ipow(xr, bc.p);
+        u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
+      }
+      uout[e] = u;
+      zi = species[ei[eg]];
+      zj = species[ej[eg]];
+      if (sig) sig[e] = (float)sigma[zi];
+#pragma unroll
+      for (int n = 0; n < kMaxBessel; ++n)
+        B[n] = (n < bc.nb) ? bc.pref * sinpif((float)(n + 1) * xr) * ir32 : 0.0f;
+    }
+    const float rsc = scale_u ? u : 1.0f;
+    for (int c0 = 0; c0 < N0; c0 += kGeomCols) {
+      const int nc = min(kGeomCols, N0 - c0);
+      __syncthreads();   // the previous pass's staging has been copied out
+      for (int q = tl; q < K0 * kGeomCols; q += kGeomBlock) {
+        const int rr = q / kGeomCols, cc = q - rr * kGeomCols;
+        sW[rr * kGeomWPad + cc] = (cc < nc) ? W0t[(size_t)rr * ldW + c0 + cc] : 0.0f;
+      }
+      __syncthreads();
+      if (tl < nloc) {
+        const float* wi = sW + zi * WP;
+        const float* wj = sW + (bc.ns + zj) * WP;
+        const float* wb = sW + 2 * bc.ns * WP;
+#pragma unroll 2
+        for (int c4 = 0; c4 < kGeomCols; c4 += 4) {
+          const float4 a = *reinterpret_cast<const float4*>(wi + c4);
+          const float4 b = *reinterpret_cast<const float4*>(wj + c4);
+          float acc[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+#pragma unroll
+          for (int n = 0; n < kMaxBessel; ++n) {
+            if (n < bc.nb) {
+              const float4 w = *reinterpret_cast<const float4*>(wb + n * WP + c4);
+              acc[0] += B[n] * w.x; acc[1] += B[n] * w.y; acc[2] += B[n] * w.z; acc[3] += B[n] * w.w;
+            }
+          }
+          float hv[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) hv[k] = acc[k] * path_sigmoid<T>(acc[k]) * rsc;
+          st4_act(sZ + tl * LDS + c4, acc);
+          st4_act(sH + tl * LDS + c4, hv);
+        }
+      }
+      __syncthreads();
+      copy_rows_out<T>(sZ, LDS, Zout + (size_t)eb * ldZ, ldZ, c0, nloc, nc);
+      copy_rows_out<T>(sH, LDS, Hout + (size_t)eb * ldH, ldH, c0, nloc, nc);
+    }
+    // Y: nloc * S floats starting at float eb * S (4-byte aligned only): scalar, coalesced
     float* dst = Yout + (size_t)eb * bc.S;
     for (int q = tl; q < nloc * bc.S; q += kGeomBlock) dst[q] = sY[q];
-  }
-  // h0: rows of ld_h0 elements, 16-byte aligned and a multiple of 16 bytes (ld_h0 % 8 == 0)
-  {
-    const int n16 = nloc * ld_h0 * (int)sizeof(T) / 16;
-    const uint4* src = reinterpret_cast<const uint4*>(sH);
-    uint4* dst = reinterpret_cast<uint4*>(h0 + (size_t)eb * ld_h0);
-    for (int q = tl; q < n16; q += kGeomBlock) dst[q] = src[q];
   }
 }
 
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
-                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
-                   cudaStream_t st) {
+                   const Arch& a, float* Y, float* u, const double* sigma, float* sig, const float* W0t, int ldW,
+                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st) {
   if (Ec <= 0) return;
-  const size_t smem = (size_t)kGeomBlock * kMaxS * 4 + (size_t)kGeomBlock * ld_h0 * sizeof(T);
+  const int N0 = a.tb[0], K0 = a.K0in();
+  const size_t stage = (size_t)kGeomBlock * kMaxS * 4 + 2 * (size_t)kGeomBlock * geom_stage_ld<T>() * sizeof(T);
+  const int tiles = (Ec + kGeomBlock - 1) / kGeomBlock;
+  // one tile per block, 32 weight columns staged per pass (measured faster than persistent
+  // blocks holding all of W0t)
+  const size_t smem = stage + (size_t)K0 * kGeomWPad * 4;
   if (smem > 48 * 1024)   // many species: opt in to more than the default dynamic shared memory
     cudaFuncSetAttribute(geom_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  geom_fwd_kernel<T><<<(Ec + kGeomBlock - 1) / kGeomBlock, kGeomBlock, smem, st>>>(
-      Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, h0, ld_h0, sigma, sig);
+  geom_fwd_kernel<T><<<tiles, kGeomBlock, smem, st>>>(
+      Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, sigma, sig, W0t, ldW, N0, Z0, ldZ, H0, ldH,
+      scale_u ? 1 : 0);
 }
 template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
-                                   float*, float*, float*, int, const double*, float*, cudaStream_t);
+                                   float*, float*, const double*, float*, const float*, int, float*, int, float*,
+                                   int, bool, cudaStream_t);
 template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int*, const int*, const Arch&,
-                                  float*, float*, bf16*, int, const double*, float*, cudaStream_t);
+                                  float*, float*, const double*, float*, const float*, int, bf16*, int, bf16*, int,
+                                  bool, cudaStream_t);
 
-__global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc,
-                                const float* __restrict__ inbar, int ld_in, const float* __restrict__ ubar,
-                                YbarParts yb, float* __restrict__ g) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
+// Adjoint of the geometry.  The first two-body layer's input adjoint is only
+// needed for its Bessel part: Bbar_n = sum_k zbar0_k W0[k][2 ns + n] (the
+// one-hot species inputs carry no geometry), formed here from zbar0 and the
+// Bessel rows of W0t held in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kGeomBlock)
+    geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc, const T* __restrict__ zbar0,
+                    int ldz, const float* __restrict__ W0t, int ldW, int N0, const float* __restrict__ ubar,
+                    YbarParts yb, float* __restrict__ g) {
+  extern __shared__ __align__(16) float wb_sm[];   // [nb][N0]: Bessel rows of W0t
+  for (int q = threadIdx.x; q < bc.nb * N0; q += blockDim.x) {
+    const int n = q / N0, k = q - n * N0;
+    wb_sm[q] = W0t[(size_t)(2 * bc.ns + n) * ldW + k];
+  }
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Ec) return;
-  size_t eg = (size_t)e0 + e;
-  double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+  const size_t eg = (size_t)e0 + e;
+  const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
   // float32 geometry from the exact float64 displacement
   const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
   const float r2 = fx * fx + fy * fy + fz * fz;
   const float ir32 = rsqrtf(r2);
   const float r = r2 * ir32;
   const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
-  float xr = r * bc.inv_rc;
+  const float xr = r * bc.inv_rc;
+  // Bbar = zbar0 . W0[:, 2 ns:]
+  float Bb[kMaxBessel];
+#pragma unroll
+  for (int n = 0; n < kMaxBessel; ++n) Bb[n] = 0.0f;
+  const T* zr = zbar0 + (size_t)e * ldz;
+  constexpr int V = 16 / (int)sizeof(T);   // elements per 16-byte vector
+  int k0 = 0;
+  if ((ldz * (int)sizeof(T)) % 16 == 0 && N0 % 4 == 0) {   // 16-byte aligned rows: vector loads
+    for (; k0 + V <= N0; k0 += V) {
+      const uint4 q = *reinterpret_cast<const uint4*>(zr + k0);
+      const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+      float zk[V];
+      if constexpr (sizeof(T) == 2) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          zk[2 * t] = __uint_as_float(wv[t] << 16);
+          zk[2 * t + 1] = __uint_as_float(wv[t] & 0xffff0000u);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) zk[t] = __uint_as_float(wv[t]);
+      }
+#pragma unroll
+      for (int n = 0; n < kMaxBessel; ++n) {
+        if (n < bc.nb) {
+#pragma unroll
+          for (int v4 = 0; v4 < V; v4 += 4) {   // weight rows are float4-aligned (N0 % 4 == 0 on this path)
+            const float4 wv4 = *reinterpret_cast<const float4*>(wb_sm + n * N0 + k0 + v4);
+            Bb[n] += zk[v4] * wv4.x + zk[v4 + 1] * wv4.y + zk[v4 + 2] * wv4.z + zk[v4 + 3] * wv4.w;
+          }
+        }
+      }
+    }
+  }
+  for (int k = k0; k < N0; ++k) {
+    const float zk = to_f32(zr[k]);
+#pragma unroll
+    for (int n = 0; n < kMaxBessel; ++n)
+      if (n < bc.nb) Bb[n] += zk * wb_sm[n * N0 + k];
+  }
   // dE/dr from the Bessel basis and the envelope
   float dEdr = 0.0f;
-  const float* Bb = inbar + (size_t)e * ld_in + 2 * bc.ns;
-  for (int n = 1; n <= bc.nb; ++n) {
-    float s, c;
-    sincospif((float)n * xr, &s, &c);
-    float k = (float)n * 3.14159265358979323846f * bc.inv_rc;
-    float dB = bc.pref * (k * c * r - s) * ir32 * ir32;
+#pragma unroll
+  for (int n = 1; n <= kMaxBessel; ++n) {
+    if (n > bc.nb) break;
+    float sn, cn;
+    sincospif((float)n * xr, &sn, &cn);
+    const float kk = (float)n * 3.14159265358979323846f * bc.inv_rc;
+    const float dB = bc.pref * (kk * cn * r - sn) * ir32 * ir32;
     dEdr += Bb[n - 1] * dB;
   }
   if (xr < 1.0f) {
-    float xp1 = ipow(xr, bc.p - 1);
-    float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
+    const float xp1 = ipow(xr, bc.p - 1);
+    const float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
     dEdr += ubar[e] * du * bc.inv_rc;
   }
   // Ybar arrives in up to three partial arrays (one per row-kernel pass), summed in a fixed order
@@ -191,18 +338,26 @@ __global__ void geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, B
   }
   float G[3];
   sh_vjp(bc.lmax, x, y, z, Yb, G);
-  float rg = x * G[0] + y * G[1] + z * G[2];
-  float gx = x * dEdr + (G[0] - x * rg) * ir32;
-  float gy = y * dEdr + (G[1] - y * rg) * ir32;
-  float gz = z * dEdr + (G[2] - z * rg) * ir32;
-  g[3 * eg] = gx; g[3 * eg + 1] = gy; g[3 * eg + 2] = gz;
+  const float rg = x * G[0] + y * G[1] + z * G[2];
+  g[3 * eg] = x * dEdr + (G[0] - x * rg) * ir32;
+  g[3 * eg + 1] = y * dEdr + (G[1] - y * rg) * ir32;
+  g[3 * eg + 2] = z * dEdr + (G[2] - z * rg) * ir32;
 }
 
-void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
-                   const float* ubar, const YbarParts& yb, float* g, cudaStream_t st) {
+template <typename T>
+void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const T* zbar0, int ldz, const float* W0t,
+                   int ldW, const float* ubar, const YbarParts& yb, float* g, cudaStream_t st) {
   if (Ec <= 0) return;
-  geom_bwd_kernel<<<(Ec + 127) / 128, 128, 0, st>>>(Ec, e0, ed, make_basis(a), inbar, ld_in, ubar, yb, g);
+  const size_t smem = (size_t)a.nb * a.tb[0] * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(geom_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  geom_bwd_kernel<T><<<(Ec + kGeomBlock - 1) / kGeomBlock, kGeomBlock, smem, st>>>(
+      Ec, e0, ed, make_basis(a), zbar0, ldz, W0t, ldW, a.tb[0], ubar, yb, g);
 }
+template void edge_geom_bwd<float>(int, int, const double*, const Arch&, const float*, int, const float*, int,
+                                   const float*, const YbarParts&, float*, cudaStream_t);
+template void edge_geom_bwd<bf16>(int, int, const double*, const Arch&, const bf16*, int, const float*, int,
+                                  const float*, const YbarParts&, float*, cudaStream_t);
 
 // Adjoint head of an MLP whose output is x = u * silu(z):  given xbar,
 //   ubar += sum_n xbar_n silu(z_n),   zbar_n = xbar_n u silu'(z_n).

@@ -582,12 +582,24 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
               v[j] = xb * rs * sgm * (1.0f + z * (1.0f - sgm));
             }
           } else {   // EPI_LAST
+            // the 16 entries of v for these columns (one vector load each for 4 when all are inside N)
+            float vv[16];
+            if (n + 16 <= N) {
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(ep.v + n) + k4);
+                vv[4 * k4] = x.x; vv[4 * k4 + 1] = x.y; vv[4 * k4 + 2] = x.z; vv[4 * k4 + 3] = x.w;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) vv[j] = (n + j < N) ? ep.v[n + j] : 0.0f;
+            }
+            const float srs = sg * rs;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float vn = (n + j < N) ? ep.v[n + j] : 0.0f;
               const float sgm = fast_sigmoid(v[j]);
-              acc1 += vn * v[j] * sgm;
-              v[j] = sg * vn * rs * sgm * (1.0f + v[j] * (1.0f - sgm));
+              acc1 += vv[j] * v[j] * sgm;
+              v[j] = srs * vv[j] * sgm * (1.0f + v[j] * (1.0f - sgm));
             }
           }
           if (hh == 0) {

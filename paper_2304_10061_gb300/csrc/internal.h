@@ -162,16 +162,20 @@ void nb_struct_span(const double* pos, const int64_t* offs, const double* inv, i
 void nb_minmax_frac(const double* pos, int n, const double* inv, double* d_minmax, cudaStream_t st);
 
 // edge kernels
+// geometry, basis (Y, u, sigma_{Z_i}) and the first two-body layer (pre-activation Z0, activation H0,
+// times u when that layer is the two-body MLP's last); W0t = W0 transposed, [K0in][ldW] float32
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
-                   const Arch& a, float* Y, float* u, T* h0, int ld_h0, const double* sigma, float* sig,
-                   cudaStream_t st);
+                   const Arch& a, float* Y, float* u, const double* sigma, float* sig, const float* W0t, int ldW,
+                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st);
 // Partial adjoints of Y [Ec][S] written by the row-kernel passes (p[2] may be null)
 struct YbarParts {
   const float* p[3];
 };
-void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const float* inbar, int ld_in,
-                   const float* ubar, const YbarParts& yb, float* g, cudaStream_t st);
+// edge forces g_ij from zbar0 (adjoint of the first two-body pre-activation), ubar and Ybar
+template <typename T>
+void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const T* zbar0, int ldz, const float* W0t,
+                   int ldW, const float* ubar, const YbarParts& yb, float* g, cudaStream_t st);
 template <typename T>
 void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
                   const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,

@@ -34,6 +34,15 @@ WORKLOAD = ("1,048,576-atom periodic water-density box (218.9 A cube, jittered l
             "latent 2x256, edge 256->128->1, r_c 4 A, seeded random weights")
 
 
+def _workload(args, s) -> str:
+    """The workload string: the headline box, or what --config / --atoms selected."""
+    if args.config == "c4" and not args.atoms:
+        return WORKLOAD
+    L = float(abs(s.cell[0][0])) if s.cell is not None else 0.0
+    return (f"{s.n_atoms:,}-atom periodic box ({L:.1f} A cube, config {args.config}), same model family and "
+            "seeded random weights")
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -268,7 +277,12 @@ def run_ours(args):
 
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    s, arch, w = make_config(args.config)
+    over = {}
+    if args.atoms:   # same density as the configuration, scaled box
+        from synth.configs import CONFIGS
+        c = CONFIGS[args.config]
+        over = dict(n=args.atoms, L=c["L"] * (args.atoms / c["n"]) ** (1.0 / 3.0))
+    s, arch, w = make_config(args.config, **over)
     blob = weights_to_blob(arch, w)
     N = s.n_atoms
     pos = torch.tensor(s.pos, device=dev)
@@ -405,7 +419,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "atoms": N, "edges": n_edges,
+            "config": {"workload": _workload(args, s), "atoms": N, "edges": n_edges,
                        "step": "neighbour rebuild + E + F + virial, float64 reductions",
                        "l2": "inputs larger than L2 (edge arrays of several GB per step)",
                        "parallelism": f"replicas x{ws}"},
@@ -441,6 +455,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c4")
+    ap.add_argument("--atoms", type=int, default=0, help="scale the configuration's box to this many atoms "
+                                                           "(same density; lattice configurations)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--skip-fp32", action="store_true")

@@ -477,7 +477,7 @@ struct WS {
   void* wbar01; int ld_wbar01;
   void* wbar2; int ld_wbar2;
   float* xbar; int ld_xbar;
-  float* Y; float* Ybar[3]; float* u; float* ubar; float* sig;
+  float* Y; float* Ybar[2]; float* u; float* ubar; float* sig;
   float* G1; float* G2;
 };
 
@@ -526,7 +526,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->ld_xbar = pad8(std::max(a.tb.back(), a.lat.back()));
   w->xbar = (float*)take((size_t)Ec * w->ld_xbar * 4);
   w->Y = (float*)take((size_t)Ec * S * 4);
-  for (int k = 0; k < 3; ++k) w->Ybar[k] = (float*)take((size_t)Ec * S * 4);
+  for (int k = 0; k < 2; ++k) w->Ybar[k] = (float*)take((size_t)Ec * S * 4);
   w->u = (float*)take((size_t)Ec * 4);
   w->ubar = (float*)take((size_t)Ec * 4);
   w->sig = (float*)take((size_t)Ec * 4);
@@ -940,7 +940,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                     a.Klat(nl - 1) + a.C, EPI_LINEAR)) != ALLEGRO_OK)
     return s;
   io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2;
-  for (int k = 0; k < 3; ++k) io.Ybar[k] = w.Ybar[k];
+  for (int k = 0; k < 2; ++k) io.Ybar[k] = w.Ybar[k];
   if (nl == 1) {
     io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
     auto ps = row_scope("row_bwd_last", 2.0 * nw * act + C * act + S * 4 + 2.0 * nw * act + 2 * S * 4, C * S * 4.0);
@@ -970,7 +970,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
         ALLEGRO_OK)
       return s;
     io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
-    auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * act + S * 4 + 2.0 * nw * act + 2 * S * 4,
+    auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * act + S * 4 + 2.0 * nw * act + S * 4,
                         2.0 * C * S * 4);
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }
@@ -999,8 +999,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   }
   {
     ProfScope ps(c, "geom_bwd", 2.0 * Ec * a.tb[0] * a.nb,
-                 (double)Ec * (24 + a.tb[0] * act + 4 + (nl == 2 ? 3 : 2) * S * 4 + 12));
-    YbarParts yb{{w.Ybar[0], w.Ybar[1], nl == 2 ? w.Ybar[2] : nullptr}};
+                 (double)Ec * (24 + a.tb[0] * act + 4 + 2 * S * 4 + 12));
+    YbarParts yb{{w.Ybar[0], w.Ybar[1]}};
     edge_geom_bwd<T>(Ec, e0, c->d_ed, a, (const T*)w.H[cur0], w.ld_H, c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb,
                      c->d_g, st);
   }

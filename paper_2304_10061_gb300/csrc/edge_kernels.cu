@@ -329,13 +329,9 @@ __global__ void __launch_bounds__(kGeomBlock)
     const float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
     dEdr += ubar[e] * du * bc.inv_rc;
   }
-  // Ybar arrives in up to three partial arrays (one per row-kernel pass), summed in a fixed order
+  // Ybar arrives in two partial arrays (from two row-kernel passes), summed in a fixed order
   float Yb[kMaxS];
-  for (int a = 0; a < bc.S; ++a) {
-    float t = yb.p[0][(size_t)e * bc.S + a] + yb.p[1][(size_t)e * bc.S + a];
-    if (yb.p[2]) t += yb.p[2][(size_t)e * bc.S + a];
-    Yb[a] = t;
-  }
+  for (int a = 0; a < bc.S; ++a) Yb[a] = yb.p[0][(size_t)e * bc.S + a] + yb.p[1][(size_t)e * bc.S + a];
   float G[3];
   sh_vjp(bc.lmax, x, y, z, Yb, G);
   const float rg = x * G[0] + y * G[1] + z * G[2];

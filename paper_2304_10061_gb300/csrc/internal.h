@@ -168,9 +168,9 @@ template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
                    const Arch& a, float* Y, float* u, const double* sigma, float* sig, const float* W0t, int ldW,
                    T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st);
-// Partial adjoints of Y [Ec][S] written by the row-kernel passes (p[2] may be null)
+// Partial adjoints of Y [Ec][S] written by the row-kernel passes
 struct YbarParts {
-  const float* p[3];
+  const float* p[2];
 };
 // edge forces g_ij from zbar0 (adjoint of the first two-body pre-activation), ubar and Ybar
 template <typename T>
@@ -210,8 +210,8 @@ struct RowIO {
   void* wbar2 = nullptr; int ld_wbar2 = 0;    // T
   // partial adjoints of Y, [Ec][S] each, written (not accumulated) by one pass each:
   //   one layer:  row_bwd_last pass 1 -> Ybar[0], pass 2 -> Ybar[1]
-  //   two layers: row_bwd_last -> Ybar[0], row_bwd_mid pass 1 -> Ybar[1], pass 2 -> Ybar[2]
-  float* Ybar[3] = {nullptr, nullptr, nullptr};
+  //   two layers: row_bwd_last -> Ybar[0], row_bwd_mid (second pass) -> Ybar[1]
+  float* Ybar[2] = {nullptr, nullptr};
 };
 template <typename T>
 void row_fwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st);

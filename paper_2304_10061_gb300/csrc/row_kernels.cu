@@ -615,11 +615,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
 
 // ---------------------------------------------------------------------------
 // adjoint, layer 1 of a two-layer model (factorised, see above):
-//   per atom first: T1, T2 (from Gamma^1, Gamma^2)
-//   pass 1: Q1 = sum_e sbar^1 V^0, Q2 = sum_e sbar^2 V^0;
-//           V^0bar = sbar^2 T2 + sbar^1 T1;  wbar^0_l = sum_m V^0bar Y;  Ybar += sum_u w^0 V^0bar
-//   per atom: Gamma^1bar (pre-scaled by nu)
-//   pass 2: wbar^1_l = nu sum_m Gamma^1bar Y;  Ybar += sum_u nu w^1 Gamma^1bar
+//   pass 1: Q1 = sum_e sbar^1 V^0, Q2 = sum_e sbar^2 V^0
+//   per atom: T1, T2 (from Gamma^1, Gamma^2) and Gamma^1bar (pre-scaled by nu)
+//   pass 2: V^0bar = sbar^2 T2 + sbar^1 T1;  wbar^0_l = sum_m V^0bar Y;
+//           wbar^1_l = nu sum_m Gamma^1bar Y;  Ybar = sum_u (w^0 V^0bar + nu w^1 Gamma^1bar)
+// The second pass reads the row's w^0 and sbar again (from L2: the row was
+// just read) so that each pass keeps only half the per-channel state.
 // ---------------------------------------------------------------------------
 template <typename T, int LMAX, int CPL>
 __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, TPConst tp) {
@@ -632,7 +633,44 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
   const int nw = io.C * LM;
   const T* W01 = reinterpret_cast<const T*>(io.W01);
   T* wb = reinterpret_cast<T*>(io.wbar01);
-  float T1[CPL][S], T2[CPL][S];
+  using WS = WSpan<T, CPL, LM>;
+  float Q1[CPL][S], Q2[CPL][S];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int b = 0; b < S; ++b) { Q1[j][b] = 0.0f; Q2[j][b] = 0.0f; }
+  int staged = -1;
+  for (int sb = r.rb; sb < r.re; sb += kYSeg) {
+    const int cnt = min(kYSeg, r.re - sb);
+    ys.load(io.Y, sb, cnt, r.lane);
+    staged = sb;
+    uint32_t raw[kBatchLight][WS::NW];
+    typename RawOf<T>::type s1r[kBatchLight][CPL], s2r[kBatchLight][CPL];
+    edge_batches<kBatchLight>(
+        cnt,
+        [&](int u, int k) {
+          ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
+          ld_sbar<T, CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
+          ld_sbar<T, CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
+        },
+        [&](int u, int k) {
+          float y[S], w0[WS::N];
+          ys.get(k, y);
+          unpack_span<T, WS::N>(raw[u], w0);
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
+#pragma unroll
+            for (int b = 0; b < S; ++b) {
+              const float v0 = w0[j * LM + lof<LMAX>(b)] * y[b];
+              Q1[j][b] += s1 * v0;
+              Q2[j][b] += s2 * v0;
+            }
+          }
+        });
+  }
+  // per atom: T1, T2, Gamma^1bar
+  float T1[CPL][S], T2[CPL][S], G1b[CPL][S];
   {
     float G1[CPL][S], cg2[CPL][S];
     ld_atom<CPL, S>(io.G1, io, r, G1);
@@ -650,67 +688,6 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
           if (tp_nonzero(p, b, 0)) t += tp.W1[(p * S + b) * S + 0] * G1[j][b];
         T1[j][p] = t;
       }
-    }
-  }
-  float Q1[CPL][S], Q2[CPL][S];
-#pragma unroll
-  for (int j = 0; j < CPL; ++j)
-#pragma unroll
-    for (int b = 0; b < S; ++b) { Q1[j][b] = 0.0f; Q2[j][b] = 0.0f; }
-  int staged = -1;
-  using WS = WSpan<T, CPL, LM>;
-  for (int sb = r.rb; sb < r.re; sb += kYSeg) {
-    const int cnt = min(kYSeg, r.re - sb);
-    ys.load(io.Y, sb, cnt, r.lane);
-    staged = sb;
-    uint32_t raw[kBatchHeavy][WS::NW];
-    typename RawOf<T>::type s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
-    edge_batches<kBatchHeavy>(
-        cnt,
-        [&](int u, int k) {
-          ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
-          ld_sbar<T, CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
-          ld_sbar<T, CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
-        },
-        [&](int u, int k) {
-          const int e = sb + k;
-          float y[S], w0[WS::N], g0[WS::N], yc[S];
-          ys.get(k, y);
-          unpack_span<T, WS::N>(raw[u], w0);
-#pragma unroll
-          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
-#pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
-            float t1[LM], t2[LM];
-#pragma unroll
-            for (int l = 0; l < LM; ++l) {
-              t1[l] = s1 * w0[j * LM + l];
-              t2[l] = s2 * w0[j * LM + l];
-              g0[j * LM + l] = 0.0f;
-            }
-#pragma unroll
-            for (int b = 0; b < S; ++b) {
-              Q1[j][b] += t1[lof<LMAX>(b)] * y[b];
-              Q2[j][b] += t2[lof<LMAX>(b)] * y[b];
-              const float v0b = s2 * T2[j][b] + s1 * T1[j][b];
-              g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
-              yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b;
-            }
-          }
-          st_w<T, CPL, LM>(wb, io.ld_wbar01, 0, e, r, g0);
-          warp_channel_sum<S>(yc, r.lane, io.Ybar[1] + (size_t)e * S);
-        });
-  }
-  // Gamma^1bar_b = nu sum_{a,c} W1[a][b][c] (cg2_c Q2_a + [c = 0] Q1_a)
-  float G1b[CPL][S];
-  {
-    float cg2[CPL][S];
-    ld_atom<CPL, S>(io.G2, io, r, cg2);
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-#pragma unroll
-      for (int b = 0; b < S; ++b) cg2[j][b] *= tp.clast[b];
       // gather order (one output at a time) keeps few values live
 #pragma unroll
       for (int b = 0; b < S; ++b) {
@@ -735,28 +712,40 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
     const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
     if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
-    uint32_t raw[kBatchLight][WS::NW];
-    edge_batches<kBatchLight>(
-        cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(W01, io.ld01, nw, sb + k, r, raw[u]); },
+    uint32_t raw0[kBatchHeavy][WS::NW], raw1[kBatchHeavy][WS::NW];
+    typename RawOf<T>::type s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
+    edge_batches<kBatchHeavy>(
+        cnt,
+        [&](int u, int k) {
+          ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw0[u]);
+          ld_w_raw<T, CPL, LM>(W01, io.ld01, nw, sb + k, r, raw1[u]);
+          ld_sbar<T, CPL>(io.sbar1, io.ld_sbar1, sb + k, r, s1r[u]);
+          ld_sbar<T, CPL>(io.sbar2, io.ld_sbar2, sb + k, r, s2r[u]);
+        },
         [&](int u, int k) {
           const int e = sb + k;
-          float y[S], w1[WS::N], g1[WS::N], yc[S];
+          float y[S], w0[WS::N], w1[WS::N], g0[WS::N], g1[WS::N], yc[S];
           ys.get(k, y);
-          unpack_span<T, WS::N>(raw[u], w1);
+          unpack_span<T, WS::N>(raw0[u], w0);
+          unpack_span<T, WS::N>(raw1[u], w1);
 #pragma unroll
           for (int b = 0; b < S; ++b) yc[b] = 0.0f;
 #pragma unroll
           for (int j = 0; j < CPL; ++j) {
+            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
 #pragma unroll
-            for (int l = 0; l < LM; ++l) g1[j * LM + l] = 0.0f;
+            for (int l = 0; l < LM; ++l) { g0[j * LM + l] = 0.0f; g1[j * LM + l] = 0.0f; }
 #pragma unroll
             for (int b = 0; b < S; ++b) {
+              const float v0b = s2 * T2[j][b] + s1 * T1[j][b];
+              g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
               g1[j * LM + lof<LMAX>(b)] += G1b[j][b] * y[b];
-              yc[b] += w1[j * LM + lof<LMAX>(b)] * G1b[j][b];
+              yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b + w1[j * LM + lof<LMAX>(b)] * G1b[j][b];
             }
           }
+          st_w<T, CPL, LM>(wb, io.ld_wbar01, 0, e, r, g0);
           st_w<T, CPL, LM>(wb, io.ld_wbar01, nw, e, r, g1);
-          warp_channel_sum<S>(yc, r.lane, io.Ybar[2] + (size_t)e * S);
+          warp_channel_sum<S>(yc, r.lane, io.Ybar[1] + (size_t)e * S);
         });
   }
 }

@@ -112,6 +112,10 @@ struct allegro_ctx {
   Lin w01;                                 // [embedding ; env weights of layer 1]
   Lin env2;                                // env weights of layer 2 (two-layer models)
   std::vector<std::vector<Lin>> lat;       // latent MLP of layers 1..nl
+  // BF16 path: the adjoint of x^{L-1} in one GEMM over [wbar^L | zbar^L] (K-concatenated):
+  // B[n][k] = W_env^L[k][n] for k < K1, W_lat^L_0[k - K1][n] after; null when K1 % 64 != 0
+  bf16* headB[2] = {nullptr, nullptr};
+  int headK1[2] = {0, 0}, headK[2] = {0, 0}, headLd[2] = {0, 0};
   float* d_v = nullptr;                    // folded edge-energy vector
   double* d_sigma = nullptr;
   double* d_mu = nullptr;
@@ -406,6 +410,25 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
       if ((s = upload_lin(c, Wlat[L - 1][k], a.lat[k], fan, c->lat[L - 1][k])) != ALLEGRO_OK) return s;
       fan = a.lat[k];
     }
+  }
+  // K-concatenated adjoint maps of x^0 (layer 1: [W_emb ; W_env1] with the latent layer 1_0)
+  // and of x^1 (layer 2: W_env2 with the latent layer 2_0)
+  for (int L = 1; L <= a.nl; ++L) {
+    const std::vector<float>& We = (L == 1) ? W01 : Wenv[1];
+    const int K1 = (L == 1) ? 2 * nw : nw;
+    const int Nx = a.Klat(L - 1), K2 = a.lat[0], fanl = a.Klat(L - 1) + a.C;
+    if (K1 % 64 != 0) continue;
+    const int K = K1 + K2, ld = pad8(K);
+    std::vector<bf16> hb((size_t)Nx * ld, __float2bfloat16_rn(0.0f));
+    for (int n = 0; n < Nx; ++n) {
+      for (int k = 0; k < K1; ++k) hb[(size_t)n * ld + k] = __float2bfloat16_rn(We[(size_t)k * Nx + n]);
+      for (int k = 0; k < K2; ++k)
+        hb[(size_t)n * ld + K1 + k] = __float2bfloat16_rn(Wlat[L - 1][0][(size_t)k * fanl + n]);
+    }
+    CUDA_TRY(c, cudaMalloc(&c->headB[L - 1], hb.size() * 2));
+    c->weight_allocs.push_back(c->headB[L - 1]);
+    CUDA_TRY(c, cudaMemcpy(c->headB[L - 1], hb.data(), hb.size() * 2, cudaMemcpyHostToDevice));
+    c->headK1[L - 1] = K1; c->headK[L - 1] = K; c->headLd[L - 1] = ld;
   }
   // linear edge-energy MLP folded into one vector: E_ij = v . x  (float64 product)
   std::vector<double> rvec(1, 1.0);
@@ -908,36 +931,51 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                     (const T*)w.Zlat[nl - 1][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, true, (T*)w.H[0], w.ld_H,
                     st);
   }
+  // Adjoint of an MLP: transposed GEMMs down to the input adjoint (columns [col0, Kin) of the
+  // input, written at dst + col0); *zin receives the adjoint of layer 0's pre-activation (the
+  // last GEMM's A operand).
   auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
-                      int nlay, void* dst, int ld_dst, int Kin, int epi_dst) -> allegro_status {
+                      int nlay, void* dst, int ld_dst, int Kin, int epi_dst, int col0,
+                      const void** zin) -> allegro_status {
     int cur = 0;
     int k = nlay - 1;
+    void* dstc = col0 ? (void*)((char*)dst + (size_t)col0 * sizeof(T)) : dst;
+    auto last = [&](const void* A, const Lin& W0) {
+      GemmArgs g = mk(A, w.ld_H, W0.N, W0, true, epi_dst, dstc, ld_dst, Kin - col0);
+      g.b_row0 = col0;
+      if (zin) *zin = A;
+      return g;
+    };
     while (k >= 0) {
       const Lin& W = layers[k];
       allegro_status r;
       if (k >= 1) {
         GemmArgs g1 = mk(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]);
-        if (k - 1 >= 0) {
-          const Lin& W2 = layers[k - 1];
-          const bool to_dst = (k - 1 == 0);
-          GemmArgs g2 = to_dst ? mk(nullptr, 0, W2.N, W2, true, epi_dst, dst, ld_dst, Kin)
-                               : mk(nullptr, 0, W2.N, W2, true, EPI_BWD_SILU, w.H[cur], w.ld_H, W2.K, Z[k - 2],
-                                    ldZ[k - 2]);
-          r = run2(g1, g2);
-          if (r != ALLEGRO_OK) return r;
-          k -= 2;
-          continue;
+        const Lin& W2 = layers[k - 1];
+        if (k - 1 == 0) {
+          // layer 0 reads layer 1's output from HBM (the pair runs as separate kernels)
+          if ((r = run1(g1)) != ALLEGRO_OK) return r;
+          if ((r = run1(last(w.H[cur ^ 1], W2))) != ALLEGRO_OK) return r;
+        } else {
+          GemmArgs g2 = mk(nullptr, 0, W2.N, W2, true, EPI_BWD_SILU, w.H[cur], w.ld_H, W2.K, Z[k - 2], ldZ[k - 2]);
+          if ((r = run2(g1, g2)) != ALLEGRO_OK) return r;
         }
+        k -= 2;
+        continue;
       }
-      r = G(w.H[cur], w.ld_H, W.N, W, true, epi_dst, dst, ld_dst, Kin);
-      if (r != ALLEGRO_OK) return r;
+      if ((r = run1(last(w.H[cur], W))) != ALLEGRO_OK) return r;
       --k;
     }
     return ALLEGRO_OK;
   };
+  // BF16 path with a K-concatenated head map: the latent MLP adjoint writes only the s columns of
+  // D; the head GEMM forms the x columns from [wbar | zbar] directly
+  auto kcat = [&](int L) { return fused && c->headB[L - 1] != nullptr; };
   // D (the latent inputs' adjoint) is stored in the activation type: EPI_LINEAR
+  const void* zlat[2] = {nullptr, nullptr};
   if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
-                    a.Klat(nl - 1) + a.C, EPI_LINEAR)) != ALLEGRO_OK)
+                    a.Klat(nl - 1) + a.C, EPI_LINEAR, kcat(nl) ? a.Klat(nl - 1) : 0, &zlat[nl - 1])) !=
+      ALLEGRO_OK)
     return s;
   io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2;
   for (int k = 0; k < 2; ++k) io.Ybar[k] = w.Ybar[k];
@@ -952,7 +990,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
     }
     // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
-    if (fused) {
+    if (kcat(2)) {
+      GemmArgs g = mk(w.wbar2, w.ld_wbar2, c->headK[1], c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
+                      w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, nullptr, 0, w.ubar);
+      g.A2 = zlat[1]; g.lda2 = w.ld_H; g.K1 = c->headK1[1];
+      g.Bover = c->headB[1]; g.ldb_over = c->headLd[1];
+      if ((s = run1(g)) != ALLEGRO_OK) return s;
+    } else if (fused) {
       if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
                  w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.D[1], w.ld_D[1], w.ubar)) != ALLEGRO_OK)
         return s;
@@ -966,8 +1010,8 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                       (const T*)w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, false, (T*)w.H[0], w.ld_H,
                       st);
     }
-    if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C, EPI_LINEAR)) !=
-        ALLEGRO_OK)
+    if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C, EPI_LINEAR,
+                      kcat(1) ? a.Klat(0) : 0, &zlat[0])) != ALLEGRO_OK)
       return s;
     io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
     auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * act + S * 4 + 2.0 * nw * act + S * 4,
@@ -975,7 +1019,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }
   // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0], then the head of x^0 = u silu(z)
-  if (fused) {
+  if (kcat(1)) {
+    GemmArgs g = mk(w.wbar01, w.ld_wbar01, c->headK[0], c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
+                    w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, nullptr, 0, w.ubar);
+    g.A2 = zlat[0]; g.lda2 = w.ld_H; g.K1 = c->headK1[0];
+    g.Bover = c->headB[0]; g.ldb_over = c->headLd[0];
+    if ((s = run1(g)) != ALLEGRO_OK) return s;
+  } else if (fused) {
     if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
                w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.D[0], w.ld_D[0], w.ubar)) != ALLEGRO_OK)
       return s;

@@ -374,9 +374,9 @@ __device__ __forceinline__ float bf16_word_elem(const uint32_t (&w)[16], int j) 
 // With 18 warps five share one SM sub-partition's 16K registers: at most 96 per thread.
 template <int BN, int EPQ>
 __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ EpiMaps em, EpiParams ep, TcLayout lay, int M, int N, int K,
-                   int* __restrict__ err) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ EpiMaps em, EpiParams ep,
+                   TcLayout lay, int M, int N, int K, int K1, int* __restrict__ err) {
   const int STAGES = lay.stages;
   constexpr int kEpiWarps = 4 * EPQ;
   const int kEpiSlot = lay.epi_slot;
@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kb * kTcBK, m0);
+          if (kb * kTcBK < K1) tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kb * kTcBK, m0);
+          else tma_load_2d(sA + s * A_BYTES, &tmA2, &full[s], kb * kTcBK - K1, m0);   // columns of A2
           tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kb * kTcBK, n0);
         }
       }
@@ -1076,8 +1077,11 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 148;
   }
-  CUtensorMap ta, tb;
-  if (!make_tmap(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)g.lda * 2, kTcBK, kTcBM) ||
+  CUtensorMap ta, ta2, tb;
+  const int K1 = g.A2 ? g.K1 : g.K;
+  if (!make_tmap(&ta, g.A, (uint64_t)K1, (uint64_t)g.M, (uint64_t)g.lda * 2, kTcBK, kTcBM) ||
+      !make_tmap(&ta2, g.A2 ? g.A2 : g.A, (uint64_t)(g.A2 ? g.K - K1 : K1), (uint64_t)g.M,
+                 (uint64_t)(g.A2 ? g.lda2 : g.lda) * 2, kTcBK, kTcBM) ||
       !make_tmap(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 2, kTcBK, BN)) {
     if (why) *why = "cuTensorMapEncodeTiled failed (alignment or extent)";
     return false;
@@ -1100,17 +1104,20 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
   const size_t smem = tc_smem_bytes<BN, EPQ>(lay);
   const int tiles = ((g.M + kTcBM - 1) / kTcBM) * ((g.N + BN - 1) / BN);
   const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), smem, st>>>(ta, tb, em, make_epi(g), lay, g.M, g.N, g.K, d_err);
+  gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), smem, st>>>(ta, ta2, tb, em, make_epi(g), lay, g.M, g.N, g.K,
+                                                                  K1, d_err);
   return true;
 }
 
 bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why) {
   if (g.M <= 0 || g.N <= 0) return true;
   if (!gemm_tc_init(why)) return false;
-  const bf16* B = g.trans ? g.W->b16T : g.W->b16;
-  const int ldb = g.trans ? g.W->ldT : g.W->ld;
+  const bf16* B = g.Bover ? g.Bover : (g.trans ? g.W->b16T : g.W->b16);
+  const int ldb = g.Bover ? g.ldb_over : (g.trans ? g.W->ldT : g.W->ld);
+  B += (size_t)g.b_row0 * ldb;
   if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (g.lda % 8) ||
-      (ldb % 8)) {
+      (ldb % 8) || (g.A2 && ((reinterpret_cast<uintptr_t>(g.A2) & 15) || (g.lda2 % 8) || (g.K1 % kTcBK) ||
+                            g.K1 <= 0 || g.K1 >= g.K))) {
     if (why) *why = "tcgen05 GEMM operands must be 16-byte aligned with pitches a multiple of 8 elements";
     return false;
   }

@@ -104,7 +104,12 @@ struct GemmArgs {
   const char* label = "gemm";      // profiling label
   int M = 0, N = 0, K = 0;
   const void* A = nullptr; int lda = 0;     // [M][lda] activations (float or bf16)
+  // tcgen05 path only: columns [K1, K) of A taken from a second array A2 ([M][lda2], bf16);
+  // K1 a multiple of 64 (the operand k-block)
+  const void* A2 = nullptr; int lda2 = 0; int K1 = 0;
   const Lin* W = nullptr; bool trans = false;
+  const bf16* Bover = nullptr; int ldb_over = 0;   // tcgen05 path: B [N][ld] given directly (W unused)
+  int b_row0 = 0;                                  // tcgen05 path: first row of B (W's matrix) used
   int epi = EPI_F32;
   void* out = nullptr; int ldo = 0;
   void* pre = nullptr; int ldp = 0;

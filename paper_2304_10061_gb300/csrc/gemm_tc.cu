@@ -1043,6 +1043,287 @@ __global__ void __launch_bounds__(kChainThreads, 1)
   }
 }
 
+// ===========================================================================
+// Pipelined forward chain for narrow first layers (N1 <= 128, N2 <= 256):
+// C2 = silu(silu(A1 B1^T) B2^T) with both pre-activations stored and the
+// intermediate activation on chip.  Two epilogue warp groups run at the same
+// time: group 1 (8 warps) drains GEMM 1's accumulator (double-buffered in
+// TMEM columns [0, 128) and [128, 256)) into the swizzled A operand of GEMM 2,
+// group 2 (8 warps) drains GEMM 2's accumulator (columns [256, 512)) to HBM.
+// The MMA thread issues GEMM 1 of tile i + 1 before GEMM 2 of tile i, so the
+// tensor pipe, both epilogues and the TMA streams overlap across tiles; the
+// operand ring carries [A1 | B1] k-blocks for GEMM 1 and B2 k-blocks for
+// GEMM 2 in that same job order.
+// ===========================================================================
+constexpr int kCfWarps = 16;                       // 8 per epilogue group
+constexpr int kCfThreads = 64 + 32 * kCfWarps;
+constexpr int kCfStages = 2;
+
+__host__ __device__ constexpr int cf_stage_bytes(int n1, int n2) {
+  return kTcBM * kTcBK * 2 + (n1 > n2 ? n1 : n2) * kTcBK * 2;
+}
+__host__ __device__ constexpr size_t cf_smem_bytes(int n1, int n2) {
+  // ring + A2 + group-1 staging (2 x 2 KB per warp) + group-2 staging (2 x 4 KB per warp) + align + misc
+  return (size_t)kCfStages * cf_stage_bytes(n1, n2) + (size_t)n1 * kTcBM * 2 + 8 * 4096 + 8 * 8192 + 1024 + 1024;
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(kCfThreads, 1)
+    gemm_chain_fwd_kernel(const __grid_constant__ ChainMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1,
+                          int* __restrict__ err) {
+  static_assert(N1 % 64 == 0 && N1 <= 128 && N2 % 32 == 0 && N2 <= 256, "pipelined chain shapes");
+  constexpr uint32_t STAGE = cf_stage_bytes(N1, N2);
+  constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
+  constexpr int NK2 = N1 / kTcBK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ring = smem;
+  uint8_t* sA2 = ring + kCfStages * STAGE;
+  uint8_t* sE1 = sA2 + NK2 * A_BYTES;                // group 1: 8 warps x 2 x 2 KB
+  uint8_t* sE2 = sE1 + 8 * 4096;                     // group 2: 8 warps x 2 x 4 KB
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE2 + 8 * 8192);
+  uint64_t* empty = full + kCfStages;
+  uint64_t* t1full = empty + kCfStages;    // [2]
+  uint64_t* t1empty = t1full + 2;          // [2]
+  uint64_t* a2full = t1empty + 2;
+  uint64_t* a2empty = a2full + 1;
+  uint64_t* t2full = a2empty + 1;
+  uint64_t* t2empty = t2full + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(t2empty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk1 = (K1 + kTcBK - 1) / kTcBK;
+  const int ntiles = (M + kTcBM - 1) / kTcBM;
+  const int T = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s2 = 0; s2 < kCfStages; ++s2) {
+      mbar_init(&full[s2], 1);
+      mbar_init(&empty[s2], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&t1full[b], 1);
+      mbar_init(&t1empty[b], 8);
+    }
+    mbar_init(a2full, 8);
+    mbar_init(a2empty, 1);
+    mbar_init(t2full, 1);
+    mbar_init(t2empty, 8);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tc_alloc(tslot, 512);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  auto fail = [&]() {
+    if (lane == 0) atomicOr(err, kErrTimeout);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // producer: jobs in MMA order: G1(0), then for i >= 1: G1(i) (if any), G2(i - 1)
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int i = 0; i <= T && ok; ++i) {
+        if (i < T) {
+          const int m0 = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM;
+          for (int kb = 0; kb < nk1 && ok; ++kb, ++g) {
+            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+            if (g >= (uint32_t)kCfStages && !mbar_wait(&empty[s2], (r - 1) & 1)) { fail(); ok = false; break; }
+            if (*abort_flag) { ok = false; break; }
+            uint8_t* st = ring + s2 * STAGE;
+            mbar_expect_tx(&full[s2], A_BYTES + N1 * kTcBK * 2);
+            tma_load_2d(st, &cm.a1, &full[s2], kb * kTcBK, m0);
+            tma_load_2d(st + A_BYTES, &cm.b1, &full[s2], kb * kTcBK, 0);
+          }
+        }
+        if (i >= 1 && ok) {
+          for (int kb = 0; kb < NK2 && ok; ++kb, ++g) {
+            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+            if (g >= (uint32_t)kCfStages && !mbar_wait(&empty[s2], (r - 1) & 1)) { fail(); ok = false; break; }
+            if (*abort_flag) { ok = false; break; }
+            uint8_t* st = ring + s2 * STAGE;
+            mbar_expect_tx(&full[s2], N2 * kTcBK * 2);
+            tma_load_2d(st + A_BYTES, &cm.b2, &full[s2], kb * kTcBK, 0);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id1 = idesc_bf16<N1>();
+      constexpr uint32_t id2 = idesc_bf16<N2>();
+      uint32_t g = 0;
+      bool ok = true;
+      for (int i = 0; i <= T && ok; ++i) {
+        if (i < T) {   // GEMM 1 of tile i into acc1[i & 1]
+          const int b = i & 1, u = i >> 1;
+          if (*abort_flag || !mbar_wait(&t1empty[b], (u & 1) ^ 1)) { fail(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(b * 128);
+          for (int kb = 0; kb < nk1; ++kb, ++g) {
+            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+            if (!mbar_wait(&full[s2], r & 1)) { fail(); ok = false; break; }
+            tc_fence_after();
+            const uint32_t a = smem_u32(ring + s2 * STAGE), bb = a + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < kTcBK / 16; ++k)
+              tc_mma(d, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id1, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[s2]);
+          }
+          tc_commit(&t1full[b]);
+          if (!ok) break;
+        }
+        if (i >= 1) {  // GEMM 2 of tile i - 1 into acc2, A = the on-chip activation
+          const int j = i - 1;
+          if (*abort_flag || !mbar_wait(a2full, j & 1) || !mbar_wait(t2empty, (j & 1) ^ 1)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int kb = 0; kb < NK2; ++kb, ++g) {
+            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+            if (!mbar_wait(&full[s2], r & 1)) { fail(); ok = false; break; }
+            tc_fence_after();
+            const uint32_t a = smem_u32(sA2 + kb * A_BYTES), bb = smem_u32(ring + s2 * STAGE) + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < kTcBK / 16; ++k)
+              tc_mma(tmem + 256, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id2, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[s2]);
+          }
+          tc_commit(t2full);
+          tc_commit(a2empty);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp < 10) {
+    // group 1: acc1 -> silu -> pre-activation to HBM, activation into A2 (K-major, 128-byte swizzle)
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    uint8_t* my = sE1 + (warp - 2) * 4096;
+    const bool pre_out = ep1.pre != nullptr;
+    int oc = 0;
+    for (int i = 0; i < T; ++i) {
+      const int b = i & 1, u = i >> 1;
+      const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
+      if (!mbar_wait(&t1full[b], u & 1) || !mbar_wait(a2empty, (i & 1) ^ 1)) { fail(); break; }
+      tc_fence_after();
+      if (*abort_flag) break;
+      const uint32_t base = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+      for (int c = h; c < N1 / 32; c += 2) {
+        uint8_t* ob = my + (oc & 1) * 2048;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int nl = 32 * c + 16 * hh;
+          float v[16], o2[16];
+          tc_ld16(base + (uint32_t)nl, v);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            o2[jj] = v[jj];
+            v[jj] = v[jj] * fast_sigmoid(v[jj]);
+          }
+          uint8_t* kbase = sA2 + (nl / kTcBK) * A_BYTES;
+          const int r = q * 32 + lane;
+#pragma unroll
+          for (int uu = 0; uu < 2; ++uu) {
+            const int unit = ((nl % kTcBK) >> 3) + uu;
+            uint4 x = make_uint4(pack_bf16x2(v[8 * uu + 0], v[8 * uu + 1]), pack_bf16x2(v[8 * uu + 2], v[8 * uu + 3]),
+                                 pack_bf16x2(v[8 * uu + 4], v[8 * uu + 5]), pack_bf16x2(v[8 * uu + 6], v[8 * uu + 7]));
+            *reinterpret_cast<uint4*>(kbase + r * 128 + ((unit ^ (r & 7)) << 4)) = x;
+          }
+          if (pre_out) {
+            if (hh == 0) {
+              if (lane == 0) bulk_wait_read1();
+              __syncwarp();
+            }
+            st_bf16_half(ob, lane, hh, o2);
+          }
+        }
+        if (pre_out) {
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&cm.pre1, ob, 32 * c, mrow);
+            bulk_commit();
+          }
+          ++oc;
+        }
+      }
+      tc_fence_before();
+      fence_async_smem();          // generic-proxy writes of A2 -> visible to the tensor core
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&t1empty[b]);
+        mbar_arrive(a2full);
+      }
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+  } else {
+    // group 2: acc2 -> silu (x rowscale) -> pre-activation and activation to HBM
+    const int q = warp & 3, h = (warp - 10) >> 2;
+    uint8_t* my = sE2 + (warp - 10) * 8192;
+    const bool pre_out = ep2.pre != nullptr;
+    int oc = 0;
+    for (int i = 0; i < T; ++i) {
+      const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
+      const int m = mrow + lane;
+      const float rs = (m < M && ep2.rowscale) ? ep2.rowscale[m] : 1.0f;
+      if (!mbar_wait(t2full, i & 1)) { fail(); break; }
+      tc_fence_after();
+      if (*abort_flag) break;
+      const uint32_t base = tmem + 256u + ((uint32_t)(q * 32) << 16);
+      for (int c = h; c < N2 / 32; c += 2) {
+        uint8_t* ob = my + (oc & 1) * 4096;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float v[16], o2[16];
+          tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            o2[jj] = v[jj];
+            v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+          }
+          if (hh == 0) {
+            if (lane == 0) bulk_wait_read1();
+            __syncwarp();
+          }
+          st_bf16_half(ob, lane, hh, v);
+          if (pre_out) st_bf16_half(ob + 2048, lane, hh, o2);
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&cm.out2, ob, 32 * c, mrow);
+          if (pre_out) tma_store_2d(&cm.pre2, ob + 2048, 32 * c, mrow);
+          bulk_commit();
+        }
+        ++oc;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(t2empty);
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, 512);
+  }
+}
+
 static int g_num_sms = 0;
 
 // 2-D tensor map over a row-major [rows][ld] array of `esize`-byte elements,
@@ -1193,6 +1474,48 @@ static bool launch_chain(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st
   return true;
 }
 
+template <int N1, int N2>
+static bool launch_chain_fwd(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why) {
+  constexpr size_t smem = cf_smem_bytes(N1, N2);
+  static_assert(smem <= 232448, "pipelined chain shared memory");
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_chain_fwd_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) {
+      if (why) *why = std::string("cudaFuncSetAttribute (chain): ") + cudaGetErrorString(e);
+      return false;
+    }
+    attr_set = true;
+  }
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  const bf16* B1 = g1.trans ? g1.W->b16T : g1.W->b16;
+  const int ldb1 = g1.trans ? g1.W->ldT : g1.W->ld;
+  const bf16* B2 = g2.trans ? g2.W->b16T : g2.W->b16;
+  const int ldb2 = g2.trans ? g2.W->ldT : g2.W->ld;
+  ChainMaps cm;
+  memset(&cm, 0, sizeof cm);
+  bool ok = make_tmap(&cm.a1, g1.A, (uint64_t)g1.K, (uint64_t)g1.M, (uint64_t)g1.lda * 2, kTcBK, kTcBM) &&
+            make_tmap(&cm.b1, B1, (uint64_t)g1.K, (uint64_t)g1.N, (uint64_t)ldb1 * 2, kTcBK, N1) &&
+            make_tmap(&cm.b2, B2, (uint64_t)g2.K, (uint64_t)g2.N, (uint64_t)ldb2 * 2, kTcBK, N2);
+  if (ok && g1.pre) ok = make_box_map(&cm.pre1, g1.pre, g1.N, g1.M, g1.ldp, 2);
+  if (ok) ok = make_box_map(&cm.out2, g2.out, g2.N, g2.M, g2.ldo, 2);
+  if (ok && g2.pre) ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
+  if (!ok) {
+    if (why) *why = "cuTensorMapEncodeTiled failed (chain)";
+    return false;
+  }
+  const int tiles = (g1.M + kTcBM - 1) / kTcBM;
+  const int grid = tiles < g_num_sms ? tiles : g_num_sms;
+  gemm_chain_fwd_kernel<N1, N2><<<grid, kCfThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M, g1.K, d_err);
+  return true;
+}
+
 // Two consecutive layers in one kernel (see gemm_chain_kernel).  Returns
 // false with `why` empty when the shapes are not supported (the caller then
 // runs the two GEMMs separately).
@@ -1213,6 +1536,9 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
       (reinterpret_cast<uintptr_t>(B2) & 15) || (g1.lda % 8))
     return false;
   const int bn2 = (g2.N + 31) / 32 * 32;
+  // narrow SiLU -> SiLU forward pairs: the pipelined kernel (two epilogue groups)
+  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU && g1.N == 128 && g2.N == 256 && !g1.rowscale)
+    return launch_chain_fwd<128, 256>(g1, g2, st, d_err, why);
   if (g1.N == 256 && bn2 == 256) return launch_chain<256, 256>(g1, g2, st, d_err, why);
   if (g1.N == 256 && bn2 == 320) return launch_chain<256, 320>(g1, g2, st, d_err, why);
   if (g1.N == 128 && bn2 == 256) return launch_chain<128, 256>(g1, g2, st, d_err, why);

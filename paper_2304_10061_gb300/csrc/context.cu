@@ -790,10 +790,9 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   };
   // Two consecutive layers: one fused kernel when the shapes allow (BF16 path), else two GEMMs.
   auto run2 = [&](const GemmArgs& g1, const GemmArgs& g2) -> allegro_status {
-    // Fused pairs measured faster only for narrow SiLU -> SiLU forward layers
-    // (the two-body MLP, N1 <= 128); the others run as separate kernels,
-    // which keep more of the HBM stream in flight.
-    const bool want_chain = g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU && g1.N <= 128;
+    // SiLU -> SiLU forward pairs run as the pipelined chain kernel; the other
+    // pairs run as separate kernels (measured faster).
+    const bool want_chain = g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU;
     if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
       std::string why;
       static std::vector<std::string> names;

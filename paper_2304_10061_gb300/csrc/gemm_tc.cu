@@ -1062,16 +1062,21 @@ constexpr int kCfStages = 2;
 __host__ __device__ constexpr int cf_stage_bytes(int n1, int n2) {
   return kTcBM * kTcBK * 2 + (n1 > n2 ? n1 : n2) * kTcBK * 2;
 }
+// group-2 output buffers per warp: two when shared memory allows, one for 256-wide first layers
+__host__ __device__ constexpr int cf_nb2(int n1) { return n1 <= 128 ? 2 : 1; }
 __host__ __device__ constexpr size_t cf_smem_bytes(int n1, int n2) {
-  // ring + A2 + group-1 staging (2 x 2 KB per warp) + group-2 staging (2 x 4 KB per warp) + align + misc
-  return (size_t)kCfStages * cf_stage_bytes(n1, n2) + (size_t)n1 * kTcBM * 2 + 8 * 4096 + 8 * 8192 + 1024 + 1024;
+  // ring + A2 + group-1 staging (2 x 2 KB per warp) + group-2 staging (nb2 x 4 KB per warp) + align + misc
+  return (size_t)kCfStages * cf_stage_bytes(n1, n2) + (size_t)n1 * kTcBM * 2 + 8 * 4096 + 8 * 4096 * cf_nb2(n1) +
+         1024 + 1024;
 }
 
 template <int N1, int N2>
 __global__ void __launch_bounds__(kCfThreads, 1)
     gemm_chain_fwd_kernel(const __grid_constant__ ChainMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1,
                           int* __restrict__ err) {
-  static_assert(N1 % 64 == 0 && N1 <= 128 && N2 % 32 == 0 && N2 <= 256, "pipelined chain shapes");
+  static_assert(N1 % 64 == 0 && N1 <= 256 && N2 % 32 == 0 && N2 <= 256, "pipelined chain shapes");
+  constexpr int NB1 = N1 <= 128 ? 2 : 1;            // GEMM-1 accumulator buffers in TMEM [0, 256)
+  constexpr int NB2 = cf_nb2(N1);
   constexpr uint32_t STAGE = cf_stage_bytes(N1, N2);
   constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
   constexpr int NK2 = N1 / kTcBK;
@@ -1080,8 +1085,8 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   uint8_t* ring = smem;
   uint8_t* sA2 = ring + kCfStages * STAGE;
   uint8_t* sE1 = sA2 + NK2 * A_BYTES;                // group 1: 8 warps x 2 x 2 KB
-  uint8_t* sE2 = sE1 + 8 * 4096;                     // group 2: 8 warps x 2 x 4 KB
-  uint64_t* full = reinterpret_cast<uint64_t*>(sE2 + 8 * 8192);
+  uint8_t* sE2 = sE1 + 8 * 4096;                     // group 2: 8 warps x NB2 x 4 KB
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE2 + 8 * 4096 * NB2);
   uint64_t* empty = full + kCfStages;
   uint64_t* t1full = empty + kCfStages;    // [2]
   uint64_t* t1empty = t1full + 2;          // [2]
@@ -1164,8 +1169,8 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       uint32_t g = 0;
       bool ok = true;
       for (int i = 0; i <= T && ok; ++i) {
-        if (i < T) {   // GEMM 1 of tile i into acc1[i & 1]
-          const int b = i & 1, u = i >> 1;
+        if (i < T) {   // GEMM 1 of tile i into acc1[i % NB1]
+          const int b = i % NB1, u = i / NB1;
           if (*abort_flag || !mbar_wait(&t1empty[b], (u & 1) ^ 1)) { fail(); ok = false; break; }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(b * 128);
@@ -1213,7 +1218,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
     const bool pre_out = ep1.pre != nullptr;
     int oc = 0;
     for (int i = 0; i < T; ++i) {
-      const int b = i & 1, u = i >> 1;
+      const int b = i % NB1, u = i / NB1;
       const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
       if (!mbar_wait(&t1full[b], u & 1) || !mbar_wait(a2empty, (i & 1) ^ 1)) { fail(); break; }
       tc_fence_after();
@@ -1271,7 +1276,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   } else {
     // group 2: acc2 -> silu (x rowscale) -> pre-activation and activation to HBM
     const int q = warp & 3, h = (warp - 10) >> 2;
-    uint8_t* my = sE2 + (warp - 10) * 8192;
+    uint8_t* my = sE2 + (warp - 10) * 4096 * NB2;
     const bool pre_out = ep2.pre != nullptr;
     int oc = 0;
     for (int i = 0; i < T; ++i) {
@@ -1283,7 +1288,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       if (*abort_flag) break;
       const uint32_t base = tmem + 256u + ((uint32_t)(q * 32) << 16);
       for (int c = h; c < N2 / 32; c += 2) {
-        uint8_t* ob = my + (oc & 1) * 4096;
+        uint8_t* ob = my + (oc % NB2) * 4096;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           float v[16], o2[16];
@@ -1294,7 +1299,10 @@ __global__ void __launch_bounds__(kCfThreads, 1)
             v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
           }
           if (hh == 0) {
-            if (lane == 0) bulk_wait_read1();
+            if (lane == 0) {
+              if (NB2 == 1) bulk_wait_read0();
+              else bulk_wait_read1();
+            }
             __syncwarp();
           }
           st_bf16_half(ob, lane, hh, v);
@@ -1537,8 +1545,10 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
     return false;
   const int bn2 = (g2.N + 31) / 32 * 32;
   // narrow SiLU -> SiLU forward pairs: the pipelined kernel (two epilogue groups)
-  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU && g1.N == 128 && g2.N == 256 && !g1.rowscale)
-    return launch_chain_fwd<128, 256>(g1, g2, st, d_err, why);
+  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU && g2.N == 256 && !g1.rowscale) {
+    if (g1.N == 128) return launch_chain_fwd<128, 256>(g1, g2, st, d_err, why);
+    if (g1.N == 256) return launch_chain_fwd<256, 256>(g1, g2, st, d_err, why);
+  }
   if (g1.N == 256 && bn2 == 256) return launch_chain<256, 256>(g1, g2, st, d_err, why);
   if (g1.N == 256 && bn2 == 320) return launch_chain<256, 320>(g1, g2, st, d_err, why);
   if (g1.N == 128 && bn2 == 256) return launch_chain<128, 256>(g1, g2, st, d_err, why);

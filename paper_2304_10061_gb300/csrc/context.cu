@@ -790,9 +790,9 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   };
   // Two consecutive layers: one fused kernel when the shapes allow (BF16 path), else two GEMMs.
   auto run2 = [&](const GemmArgs& g1, const GemmArgs& g2) -> allegro_status {
-    // SiLU -> SiLU forward pairs run as the pipelined chain kernel; the other
-    // pairs run as separate kernels (measured faster).
-    const bool want_chain = g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU;
+    // SiLU -> SiLU and SiLU -> last-layer forward pairs run as the pipelined
+    // chain kernel; the other pairs run as separate kernels (measured faster).
+    const bool want_chain = g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_LAST);
     if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
       std::string why;
       static std::vector<std::string> names;

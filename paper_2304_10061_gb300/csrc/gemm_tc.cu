@@ -1044,9 +1044,10 @@ __global__ void __launch_bounds__(kChainThreads, 1)
 }
 
 // ===========================================================================
-// Pipelined forward chain for narrow first layers (N1 <= 128, N2 <= 256):
-// C2 = silu(silu(A1 B1^T) B2^T) with both pre-activations stored and the
-// intermediate activation on chip.  Two epilogue warp groups run at the same
+// Pipelined forward chain (N1 <= 256, N2 <= 256): C2 = epi2(silu(A1 B1^T) B2^T)
+// with the intermediate activation on chip; epi2 is the SiLU forward (both
+// pre-activations stored) or the last latent layer (folded edge energy,
+// per-row energy and the start of the adjoint, as in the single GEMM).  Two epilogue warp groups run at the same
 // time: group 1 (8 warps) drains GEMM 1's accumulator (double-buffered in
 // TMEM columns [0, 128) and [128, 256)) into the swizzled A operand of GEMM 2,
 // group 2 (8 warps) drains GEMM 2's accumulator (columns [256, 512)) to HBM.
@@ -1094,8 +1095,10 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   uint64_t* a2empty = a2full + 1;
   uint64_t* t2full = a2empty + 1;
   uint64_t* t2empty = t2full + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(t2empty + 1);
+  uint64_t* rsbar = t2empty + 1;           // [4]: a quarter's second partial row sum is written
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(rsbar + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  float* rowpart = reinterpret_cast<float*>(tslot + 4);   // [4][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk1 = (K1 + kTcBK - 1) / kTcBK;
@@ -1115,6 +1118,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
     mbar_init(a2empty, 1);
     mbar_init(t2full, 1);
     mbar_init(t2empty, 8);
+    for (int q = 0; q < 4; ++q) mbar_init(&rsbar[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1274,15 +1278,19 @@ __global__ void __launch_bounds__(kCfThreads, 1)
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   } else {
-    // group 2: acc2 -> silu (x rowscale) -> pre-activation and activation to HBM
+    // group 2: acc2 -> silu (x rowscale) -> pre-activation and activation to HBM,
+    // or (last layer) the adjoint of the pre-activation, E_ij and ubar_ij
     const int q = warp & 3, h = (warp - 10) >> 2;
     uint8_t* my = sE2 + (warp - 10) * 4096 * NB2;
-    const bool pre_out = ep2.pre != nullptr;
+    const bool last = ep2.epi == EPI_LAST;
+    const bool pre_out = ep2.pre != nullptr && !last;
     int oc = 0;
     for (int i = 0; i < T; ++i) {
       const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
       const int m = mrow + lane;
       const float rs = (m < M && ep2.rowscale) ? ep2.rowscale[m] : 1.0f;
+      const float srs = (last && m < M) ? ep2.rowsig[m] * rs : 0.0f;
+      float acc1 = 0.0f;
       if (!mbar_wait(t2full, i & 1)) { fail(); break; }
       tc_fence_after();
       if (*abort_flag) break;
@@ -1293,10 +1301,27 @@ __global__ void __launch_bounds__(kCfThreads, 1)
         for (int hh = 0; hh < 2; ++hh) {
           float v[16], o2[16];
           tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
+          if (!last) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            o2[jj] = v[jj];
-            v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+            for (int jj = 0; jj < 16; ++jj) {
+              o2[jj] = v[jj];
+              v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+            }
+          } else {
+            // E_ij = rowscale * sum_n v_n silu(z_n); the pre-activation adjoint
+            // sigma_i rowscale v_n silu'(z_n) is the GEMM input of the backward pass
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const float4 x = __ldg(reinterpret_cast<const float4*>(ep2.v + 32 * c + 16 * hh) + k4);
+              const float vv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int t4 = 0; t4 < 4; ++t4) {
+                const int jj = 4 * k4 + t4;
+                const float sgm = fast_sigmoid(v[jj]);
+                acc1 += vv[t4] * v[jj] * sgm;
+                v[jj] = srs * vv[t4] * sgm * (1.0f + v[jj] * (1.0f - sgm));
+              }
+            }
           }
           if (hh == 0) {
             if (lane == 0) {
@@ -1319,7 +1344,27 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(t2empty);
+      if (!last) {
+        if (lane == 0) mbar_arrive(t2empty);
+      } else if (h == 1) {
+        // the second partial row sum; the slot is free again once warp h = 0
+        // has read it (it releases the accumulator only after that)
+        rowpart[q * 32 + lane] = acc1;
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&rsbar[q]);
+          mbar_arrive(t2empty);
+        }
+      } else {
+        if (!mbar_wait(&rsbar[q], i & 1)) fail();
+        const float tot = acc1 + rowpart[q * 32 + lane];
+        if (m < M) {
+          ep2.Eout[m] = rs * tot;
+          ep2.ubar[m] = ep2.rowsig[m] * tot;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(t2empty);
+      }
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -1513,7 +1558,7 @@ static bool launch_chain_fwd(const GemmArgs& g1, const GemmArgs& g2, cudaStream_
             make_tmap(&cm.b2, B2, (uint64_t)g2.K, (uint64_t)g2.N, (uint64_t)ldb2 * 2, kTcBK, N2);
   if (ok && g1.pre) ok = make_box_map(&cm.pre1, g1.pre, g1.N, g1.M, g1.ldp, 2);
   if (ok) ok = make_box_map(&cm.out2, g2.out, g2.N, g2.M, g2.ldo, 2);
-  if (ok && g2.pre) ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
+  if (ok && g2.pre && g2.epi != EPI_LAST) ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
   if (!ok) {
     if (why) *why = "cuTensorMapEncodeTiled failed (chain)";
     return false;
@@ -1544,8 +1589,10 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
       (reinterpret_cast<uintptr_t>(B2) & 15) || (g1.lda % 8))
     return false;
   const int bn2 = (g2.N + 31) / 32 * 32;
-  // narrow SiLU -> SiLU forward pairs: the pipelined kernel (two epilogue groups)
-  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU && g2.N == 256 && !g1.rowscale) {
+  // SiLU -> SiLU forward and SiLU -> last-layer pairs: the pipelined kernel (two epilogue groups)
+  const bool last_ok = g2.epi == EPI_LAST && g2.v && g2.rowsig && g2.Eout && g2.ubar &&
+                       (reinterpret_cast<uintptr_t>(g2.v) & 15) == 0;
+  if (g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || last_ok) && g2.N == 256 && !g1.rowscale) {
     if (g1.N == 128) return launch_chain_fwd<128, 256>(g1, g2, st, d_err, why);
     if (g1.N == 256) return launch_chain_fwd<256, 256>(g1, g2, st, d_err, why);
   }

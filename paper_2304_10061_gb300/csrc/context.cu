@@ -790,9 +790,12 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   };
   // Two consecutive layers: one fused kernel when the shapes allow (BF16 path), else two GEMMs.
   auto run2 = [&](const GemmArgs& g1, const GemmArgs& g2) -> allegro_status {
-    // SiLU -> SiLU and SiLU -> last-layer forward pairs run as the pipelined
-    // chain kernel; the other pairs run as separate kernels (measured faster).
-    const bool want_chain = g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_LAST);
+    // Pairs the pipelined chain kernel takes: SiLU -> SiLU and SiLU -> last
+    // layer forward, adjoint head -> SiLU adjoint, SiLU adjoint -> linear.  The
+    // other pairs run as separate kernels (measured faster).
+    const bool want_chain = (g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_LAST)) ||
+                            (g1.epi == EPI_HEAD && g2.epi == EPI_BWD_SILU) ||
+                            (g1.epi == EPI_BWD_SILU && g2.epi == EPI_LINEAR && g2.N <= 256);
     if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
       std::string why;
       static std::vector<std::string> names;
@@ -932,12 +935,18 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   }
   // Adjoint of an MLP: transposed GEMMs down to the input adjoint (columns [col0, Kin) of the
   // input, written at dst + col0); *zin receives the adjoint of layer 0's pre-activation (the
-  // last GEMM's A operand).
+  // last GEMM's A operand).  `head`, if given, is the GEMM that forms the adjoint of the last
+  // layer's pre-activation (into H[0]); it runs paired with the first transposed GEMM.
   auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
-                      int nlay, void* dst, int ld_dst, int Kin, int epi_dst, int col0,
-                      const void** zin) -> allegro_status {
+                      int nlay, void* dst, int ld_dst, int Kin, int epi_dst, int col0, const void** zin,
+                      const GemmArgs* head) -> allegro_status {
     int cur = 0;
     int k = nlay - 1;
+    if (head && nlay < 2) {
+      allegro_status r = run1(*head);
+      if (r != ALLEGRO_OK) return r;
+      head = nullptr;
+    }
     void* dstc = col0 ? (void*)((char*)dst + (size_t)col0 * sizeof(T)) : dst;
     auto last = [&](const void* A, const Lin& W0) {
       GemmArgs g = mk(A, w.ld_H, W0.N, W0, true, epi_dst, dstc, ld_dst, Kin - col0);
@@ -951,10 +960,18 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       if (k >= 1) {
         GemmArgs g1 = mk(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]);
         const Lin& W2 = layers[k - 1];
+        if (head) {
+          // the head's product stays on chip as the A operand of this layer's GEMM
+          if ((r = run2(*head, g1)) != ALLEGRO_OK) return r;
+          head = nullptr;
+          cur ^= 1;
+          --k;
+          continue;
+        }
         if (k - 1 == 0) {
-          // layer 0 reads layer 1's output from HBM (the pair runs as separate kernels)
-          if ((r = run1(g1)) != ALLEGRO_OK) return r;
-          if ((r = run1(last(w.H[cur ^ 1], W2))) != ALLEGRO_OK) return r;
+          // layer 1's product (written to HBM for the head GEMM of the layer below) stays on chip
+          // as the A operand of layer 0's GEMM
+          if ((r = run2(g1, last(w.H[cur ^ 1], W2))) != ALLEGRO_OK) return r;
         } else {
           GemmArgs g2 = mk(nullptr, 0, W2.N, W2, true, EPI_BWD_SILU, w.H[cur], w.ld_H, W2.K, Z[k - 2], ldZ[k - 2]);
           if ((r = run2(g1, g2)) != ALLEGRO_OK) return r;
@@ -973,7 +990,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   // D (the latent inputs' adjoint) is stored in the activation type: EPI_LINEAR
   const void* zlat[2] = {nullptr, nullptr};
   if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
-                    a.Klat(nl - 1) + a.C, EPI_LINEAR, kcat(nl) ? a.Klat(nl - 1) : 0, &zlat[nl - 1])) !=
+                    a.Klat(nl - 1) + a.C, EPI_LINEAR, kcat(nl) ? a.Klat(nl - 1) : 0, &zlat[nl - 1], nullptr)) !=
       ALLEGRO_OK)
     return s;
   io.wbar01 = w.wbar01; io.ld_wbar01 = w.ld_wbar01; io.wbar2 = w.wbar2; io.ld_wbar2 = w.ld_wbar2;
@@ -989,12 +1006,14 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       row_bwd<T>(2, 2, a.lmax, io, c->tp, st);
     }
     // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
+    GemmArgs head1;
+    const GemmArgs* head1p = nullptr;
     if (kcat(2)) {
-      GemmArgs g = mk(w.wbar2, w.ld_wbar2, c->headK[1], c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
-                      w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, nullptr, 0, w.ubar);
-      g.A2 = zlat[1]; g.lda2 = w.ld_H; g.K1 = c->headK1[1];
-      g.Bover = c->headB[1]; g.ldb_over = c->headLd[1];
-      if ((s = run1(g)) != ALLEGRO_OK) return s;
+      head1 = mk(w.wbar2, w.ld_wbar2, c->headK[1], c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
+                 w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, nullptr, 0, w.ubar);
+      head1.A2 = zlat[1]; head1.lda2 = w.ld_H; head1.K1 = c->headK1[1];
+      head1.Bover = c->headB[1]; head1.ldb_over = c->headLd[1];
+      head1p = &head1;   // runs paired with the first GEMM of the latent MLP adjoint below
     } else if (fused) {
       if ((s = G(w.wbar2, w.ld_wbar2, nw, c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
                  w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.D[1], w.ld_D[1], w.ubar)) != ALLEGRO_OK)
@@ -1010,7 +1029,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                       st);
     }
     if ((s = back_mlp(c->lat[0], w.Zlat[0], w.ld_Zlat, nlat, w.D[0], w.ld_D[0], a.Klat(0) + a.C, EPI_LINEAR,
-                      kcat(1) ? a.Klat(0) : 0, &zlat[0])) != ALLEGRO_OK)
+                      kcat(1) ? a.Klat(0) : 0, &zlat[0], head1p)) != ALLEGRO_OK)
       return s;
     io.sbar1 = (const T*)w.D[0] + a.Klat(0); io.ld_sbar1 = w.ld_D[0];
     auto ps = row_scope("row_bwd_mid", 2.0 * nw * act + 2.0 * C * act + S * 4 + 2.0 * nw * act + S * 4,
@@ -1018,12 +1037,15 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     row_bwd<T>(1, 2, a.lmax, io, c->tp, st);
   }
   // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0], then the head of x^0 = u silu(z)
+  GemmArgs head0;
+  bool head0_pending = false;
   if (kcat(1)) {
-    GemmArgs g = mk(w.wbar01, w.ld_wbar01, c->headK[0], c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
-                    w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, nullptr, 0, w.ubar);
-    g.A2 = zlat[0]; g.lda2 = w.ld_H; g.K1 = c->headK1[0];
-    g.Bover = c->headB[0]; g.ldb_over = c->headLd[0];
-    if ((s = run1(g)) != ALLEGRO_OK) return s;
+    head0 = mk(w.wbar01, w.ld_wbar01, c->headK[0], c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
+               w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, nullptr, 0, w.ubar);
+    head0.A2 = zlat[0]; head0.lda2 = w.ld_H; head0.K1 = c->headK1[0];
+    head0.Bover = c->headB[0]; head0.ldb_over = c->headLd[0];
+    if (ntb >= 2) head0_pending = true;   // paired with the last two-body layer's GEMM below
+    else if ((s = run1(head0)) != ALLEGRO_OK) return s;
   } else if (fused) {
     if ((s = G(w.wbar01, w.ld_wbar01, 2 * nw, c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
                w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, w.D[0], w.ld_D[0], w.ubar)) != ALLEGRO_OK)
@@ -1041,9 +1063,15 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   int cur0 = 0;
   for (int k = ntb - 1; k >= 1; --k) {
     const Lin& W = c->tb[k];
-    if ((s = G(w.H[cur0], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur0 ^ 1], w.ld_H, W.K, w.Ztb[k - 1],
-               w.ld_Ztb[k - 1])) != ALLEGRO_OK)
-      return s;
+    GemmArgs g = mk(w.H[cur0], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur0 ^ 1], w.ld_H, W.K, w.Ztb[k - 1],
+                    w.ld_Ztb[k - 1]);
+    if (head0_pending) {
+      s = run2(head0, g);
+      head0_pending = false;
+    } else {
+      s = run1(g);
+    }
+    if (s != ALLEGRO_OK) return s;
     cur0 ^= 1;
   }
   {

@@ -1044,39 +1044,61 @@ __global__ void __launch_bounds__(kChainThreads, 1)
 }
 
 // ===========================================================================
-// Pipelined forward chain (N1 <= 256, N2 <= 256): C2 = epi2(silu(A1 B1^T) B2^T)
-// with the intermediate activation on chip; epi2 is the SiLU forward (both
-// pre-activations stored) or the last latent layer (folded edge energy,
-// per-row energy and the start of the adjoint, as in the single GEMM).  Two epilogue warp groups run at the same
-// time: group 1 (8 warps) drains GEMM 1's accumulator (double-buffered in
-// TMEM columns [0, 128) and [128, 256)) into the swizzled A operand of GEMM 2,
-// group 2 (8 warps) drains GEMM 2's accumulator (columns [256, 512)) to HBM.
-// The MMA thread issues GEMM 1 of tile i + 1 before GEMM 2 of tile i, so the
-// tensor pipe, both epilogues and the TMA streams overlap across tiles; the
-// operand ring carries [A1 | B1] k-blocks for GEMM 1 and B2 k-blocks for
-// GEMM 2 in that same job order.
+// Pipelined chain (N1 = 128 or 256, N2 <= 256): C2 = epi2(epi1(A1 B1^T) B2^T)
+// with the intermediate activation kept on chip.  GEMM 1 runs as NH = N1/128
+// jobs of 128 output columns each, into a two-slot ring of 128-column TMEM
+// accumulators (columns [0, 128) and [128, 256)); GEMM 2 accumulates in
+// columns [256, 256 + N2).  Two epilogue warp groups run at the same time:
+// group 1 (8 warps) drains each GEMM-1 job into its half of the swizzled A
+// operand of GEMM 2 (on chip, never written to HBM), group 2 (8 warps) drains
+// GEMM 2's accumulator to HBM.  GEMM 2 consumes its A operand half by half,
+// each half released to group 1 as soon as its MMAs complete.  MMA job order:
+//   NH = 1:  G1(0); per tile i: G1(i+1), G2(i)
+//   NH = 2:  G1(0,a); per tile i: G1(i,b), G2(i,a), G1(i+1,a), G2(i,b)
+// so that the tensor pipe works on one job while group 1 drains the previous
+// one.  The operand ring (3 stages of 32 KB) carries [A1 k-block | B1 rows of
+// the job] for GEMM-1 jobs and B2 k-blocks for GEMM-2 halves in that order.
+// GEMM 1's A operand may be the K-concatenation [A1 | A1b] (split at K1a, a
+// multiple of 64 columns).
+//   epi1: FWD_SILU (pre-activation stored), HEAD (pre-activation loaded, row
+//         sums added to ubar) or BWD_SILU (pre-activation loaded, the product
+//         also stored to HBM);
+//   epi2: FWD_SILU (pre-activation stored), LAST (the single GEMM's last-layer
+//         epilogue), BWD_SILU (pre-activation loaded) or LINEAR.
+// HEAD and LAST are not combined in one launch (they share the row-sum slot).
 // ===========================================================================
 constexpr int kCfWarps = 16;                       // 8 per epilogue group
 constexpr int kCfThreads = 64 + 32 * kCfWarps;
-constexpr int kCfStages = 2;
+constexpr int kCfStages = 3;
+constexpr int kCfJobN = 128;                       // output columns of one GEMM-1 job
 
 __host__ __device__ constexpr int cf_stage_bytes(int n1, int n2) {
-  return kTcBM * kTcBK * 2 + (n1 > n2 ? n1 : n2) * kTcBK * 2;
+  // [A1 k-block | 128 rows of B1] or [N2 rows of B2]
+  return (kTcBM * kTcBK * 2 + kCfJobN * kTcBK * 2) > n2 * kTcBK * 2 ? (kTcBM * kTcBK * 2 + kCfJobN * kTcBK * 2)
+                                                                     : n2 * kTcBK * 2;
 }
-// group-2 output buffers per warp: two when shared memory allows, one for 256-wide first layers
+// group-2 staging buffers per warp: two when shared memory allows, one for 256-wide first layers
 __host__ __device__ constexpr int cf_nb2(int n1) { return n1 <= 128 ? 2 : 1; }
 __host__ __device__ constexpr size_t cf_smem_bytes(int n1, int n2) {
-  // ring + A2 + group-1 staging (2 x 2 KB per warp) + group-2 staging (nb2 x 4 KB per warp) + align + misc
+  // ring + A2 + group-1 staging (4 KB per warp) + group-2 staging (nb2 x 4 KB per warp) + align + misc
   return (size_t)kCfStages * cf_stage_bytes(n1, n2) + (size_t)n1 * kTcBM * 2 + 8 * 4096 + 8 * 4096 * cf_nb2(n1) +
          1024 + 1024;
 }
 
-template <int N1, int N2>
+struct PipeMaps {
+  CUtensorMap a1, a1b, b1, b2;
+  CUtensorMap pre1, out1, pre2, out2;
+};
+
+template <int N1, int N2, int E1, int E2>
 __global__ void __launch_bounds__(kCfThreads, 1)
-    gemm_chain_fwd_kernel(const __grid_constant__ ChainMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1,
-                          int* __restrict__ err) {
-  static_assert(N1 % 64 == 0 && N1 <= 256 && N2 % 32 == 0 && N2 <= 256, "pipelined chain shapes");
-  constexpr int NB1 = N1 <= 128 ? 2 : 1;            // GEMM-1 accumulator buffers in TMEM [0, 256)
+    gemm_chain_pipe_kernel(const __grid_constant__ PipeMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1,
+                           int K1a, int* __restrict__ err) {
+  static_assert((N1 == 128 || N1 == 256) && N2 % 32 == 0 && N2 <= 256, "pipelined chain shapes");
+  static_assert(E1 == EPI_FWD_SILU || E1 == EPI_HEAD || E1 == EPI_BWD_SILU, "pipelined chain: epilogue 1");
+  static_assert(E2 == EPI_FWD_SILU || E2 == EPI_LAST || E2 == EPI_BWD_SILU || E2 == EPI_LINEAR,
+                "pipelined chain: epilogue 2");
+  constexpr int NH = N1 / kCfJobN;                  // GEMM-1 jobs per tile
   constexpr int NB2 = cf_nb2(N1);
   constexpr uint32_t STAGE = cf_stage_bytes(N1, N2);
   constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
@@ -1085,17 +1107,19 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem;
   uint8_t* sA2 = ring + kCfStages * STAGE;
-  uint8_t* sE1 = sA2 + NK2 * A_BYTES;                // group 1: 8 warps x 2 x 2 KB
+  uint8_t* sE1 = sA2 + NK2 * A_BYTES;                // group 1: 8 warps x 4 KB
   uint8_t* sE2 = sE1 + 8 * 4096;                     // group 2: 8 warps x NB2 x 4 KB
   uint64_t* full = reinterpret_cast<uint64_t*>(sE2 + 8 * 4096 * NB2);
   uint64_t* empty = full + kCfStages;
-  uint64_t* t1full = empty + kCfStages;    // [2]
+  uint64_t* t1full = empty + kCfStages;    // [2]: accumulator slots
   uint64_t* t1empty = t1full + 2;          // [2]
-  uint64_t* a2full = t1empty + 2;
-  uint64_t* a2empty = a2full + 1;
-  uint64_t* t2full = a2empty + 1;
+  uint64_t* a2full = t1empty + 2;          // [2]: halves of the on-chip A operand
+  uint64_t* a2empty = a2full + 2;          // [2]
+  uint64_t* t2full = a2empty + 2;
   uint64_t* t2empty = t2full + 1;
-  uint64_t* rsbar = t2empty + 1;           // [4]: a quarter's second partial row sum is written
+  uint64_t* inb1 = t2empty + 1;            // [8]: group-1 input slots
+  uint64_t* inb2 = inb1 + 8;               // [8]: group-2 input slots
+  uint64_t* rsbar = inb2 + 8;              // [4]: a quarter's second partial row sum is written
   uint32_t* tslot = reinterpret_cast<uint32_t*>(rsbar + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   float* rowpart = reinterpret_cast<float*>(tslot + 4);   // [4][32]
@@ -1104,6 +1128,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   const int nk1 = (K1 + kTcBK - 1) / kTcBK;
   const int ntiles = (M + kTcBM - 1) / kTcBM;
   const int T = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  auto row0 = [&](int i) { return ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM; };
 
   if (threadIdx.x == 0) {
     for (int s2 = 0; s2 < kCfStages; ++s2) {
@@ -1113,11 +1138,15 @@ __global__ void __launch_bounds__(kCfThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&t1full[b], 1);
       mbar_init(&t1empty[b], 8);
+      mbar_init(&a2full[b], 8);
+      mbar_init(&a2empty[b], 1);
     }
-    mbar_init(a2full, 8);
-    mbar_init(a2empty, 1);
     mbar_init(t2full, 1);
     mbar_init(t2empty, 8);
+    for (int q = 0; q < 8; ++q) {
+      mbar_init(&inb1[q], 1);
+      mbar_init(&inb2[q], 1);
+    }
     for (int q = 0; q < 4; ++q) mbar_init(&rsbar[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1135,110 +1164,197 @@ __global__ void __launch_bounds__(kCfThreads, 1)
     if (lane == 0) atomicOr(err, kErrTimeout);
     *abort_flag = 1;
   };
+  // Row sums of a 32-row quarter split over its two warps (h = 0, 1), combined in
+  // that order by warp h = 0.  Warp h = 0 calls this before it releases the
+  // accumulator / activation of the tile, so warp h = 1 cannot reach the next
+  // tile (and rewrite the slot) before the slot is read.
+  auto row_total = [&](int q, int h, int i, float acc, bool& ok) -> float {
+    float* part = rowpart + q * 32;
+    if (h == 1) {
+      part[lane] = acc;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rsbar[q]);
+      return 0.0f;
+    }
+    if (!mbar_wait(&rsbar[q], i & 1)) {
+      fail();
+      ok = false;
+    }
+    return acc + part[lane];
+  };
+
+  // The MMA job sequence (see above), walked identically by the producer and the MMA thread:
+  // job(i, hf, two) calls g1(i, hf) or g2(i, hf); returns false once a wait fails.
+  auto walk = [&](auto&& g1, auto&& g2) {
+    if (T == 0) return;
+    if (!g1(0, 0)) return;
+    for (int i = 0; i < T; ++i) {
+      if (NH == 1) {
+        if (i + 1 < T && !g1(i + 1, 0)) return;
+        if (!g2(i, 0)) return;
+      } else {
+        if (!g1(i, 1)) return;
+        if (!g2(i, 0)) return;
+        if (i + 1 < T && !g1(i + 1, 0)) return;
+        if (!g2(i, 1)) return;
+      }
+    }
+  };
 
   if (warp == 0) {
-    // producer: jobs in MMA order: G1(0), then for i >= 1: G1(i) (if any), G2(i - 1)
+    // producer
     if (lane == 0) {
       uint32_t g = 0;
-      bool ok = true;
-      for (int i = 0; i <= T && ok; ++i) {
-        if (i < T) {
-          const int m0 = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM;
-          for (int kb = 0; kb < nk1 && ok; ++kb, ++g) {
-            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
-            if (g >= (uint32_t)kCfStages && !mbar_wait(&empty[s2], (r - 1) & 1)) { fail(); ok = false; break; }
-            if (*abort_flag) { ok = false; break; }
-            uint8_t* st = ring + s2 * STAGE;
-            mbar_expect_tx(&full[s2], A_BYTES + N1 * kTcBK * 2);
-            tma_load_2d(st, &cm.a1, &full[s2], kb * kTcBK, m0);
-            tma_load_2d(st + A_BYTES, &cm.b1, &full[s2], kb * kTcBK, 0);
-          }
+      auto slot_free = [&]() -> bool {
+        const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+        if (g >= (uint32_t)kCfStages && !mbar_wait(&empty[s2], (r - 1) & 1)) {
+          fail();
+          return false;
         }
-        if (i >= 1 && ok) {
-          for (int kb = 0; kb < NK2 && ok; ++kb, ++g) {
-            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
-            if (g >= (uint32_t)kCfStages && !mbar_wait(&empty[s2], (r - 1) & 1)) { fail(); ok = false; break; }
-            if (*abort_flag) { ok = false; break; }
-            uint8_t* st = ring + s2 * STAGE;
-            mbar_expect_tx(&full[s2], N2 * kTcBK * 2);
-            tma_load_2d(st + A_BYTES, &cm.b2, &full[s2], kb * kTcBK, 0);
-          }
+        return !*abort_flag;
+      };
+      auto g1 = [&](int i, int hf) -> bool {
+        const int m0 = row0(i);
+        for (int kb = 0; kb < nk1; ++kb, ++g) {
+          if (!slot_free()) return false;
+          const uint32_t s2 = g % kCfStages;
+          uint8_t* st = ring + s2 * STAGE;
+          mbar_expect_tx(&full[s2], A_BYTES + kCfJobN * kTcBK * 2);
+          if (kb * kTcBK < K1a) tma_load_2d(st, &cm.a1, &full[s2], kb * kTcBK, m0);
+          else tma_load_2d(st, &cm.a1b, &full[s2], kb * kTcBK - K1a, m0);
+          tma_load_2d(st + A_BYTES, &cm.b1, &full[s2], kb * kTcBK, hf * kCfJobN);
         }
-      }
+        return true;
+      };
+      auto g2 = [&](int, int hf) -> bool {
+        for (int kb = 2 * hf; kb < 2 * hf + 2 && kb < NK2; ++kb, ++g) {
+          if (!slot_free()) return false;
+          const uint32_t s2 = g % kCfStages;
+          mbar_expect_tx(&full[s2], N2 * kTcBK * 2);
+          tma_load_2d(ring + s2 * STAGE, &cm.b2, &full[s2], kb * kTcBK, 0);
+        }
+        return true;
+      };
+      walk(g1, g2);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t id1 = idesc_bf16<N1>();
+      constexpr uint32_t id1 = idesc_bf16<kCfJobN>();
       constexpr uint32_t id2 = idesc_bf16<N2>();
       uint32_t g = 0;
-      bool ok = true;
-      for (int i = 0; i <= T && ok; ++i) {
-        if (i < T) {   // GEMM 1 of tile i into acc1[i % NB1]
-          const int b = i % NB1, u = i / NB1;
-          if (*abort_flag || !mbar_wait(&t1empty[b], (u & 1) ^ 1)) { fail(); ok = false; break; }
+      auto g1 = [&](int i, int hf) -> bool {
+        const int sj = i * NH + hf, slot = sj & 1, u = sj >> 1;
+        if (*abort_flag || !mbar_wait(&t1empty[slot], (u & 1) ^ 1)) { fail(); return false; }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(slot * kCfJobN);
+        for (int kb = 0; kb < nk1; ++kb, ++g) {
+          const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+          if (!mbar_wait(&full[s2], r & 1)) { fail(); return false; }
           tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(b * 128);
-          for (int kb = 0; kb < nk1; ++kb, ++g) {
-            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
-            if (!mbar_wait(&full[s2], r & 1)) { fail(); ok = false; break; }
-            tc_fence_after();
-            const uint32_t a = smem_u32(ring + s2 * STAGE), bb = a + A_BYTES;
+          const uint32_t a = smem_u32(ring + s2 * STAGE), bb = a + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < kTcBK / 16; ++k)
-              tc_mma(d, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id1, (kb > 0 || k > 0) ? 1u : 0u);
-            tc_commit(&empty[s2]);
-          }
-          tc_commit(&t1full[b]);
-          if (!ok) break;
+          for (int k = 0; k < kTcBK / 16; ++k)
+            tc_mma(d, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id1, (kb > 0 || k > 0) ? 1u : 0u);
+          tc_commit(&empty[s2]);
         }
-        if (i >= 1) {  // GEMM 2 of tile i - 1 into acc2, A = the on-chip activation
-          const int j = i - 1;
-          if (*abort_flag || !mbar_wait(a2full, j & 1) || !mbar_wait(t2empty, (j & 1) ^ 1)) {
-            fail();
-            ok = false;
-            break;
-          }
+        tc_commit(&t1full[slot]);
+        return true;
+      };
+      auto g2 = [&](int i, int hf) -> bool {
+        // half hf of the on-chip A operand (k-blocks 2 hf, 2 hf + 1); the first half also needs acc2 drained
+        if (*abort_flag || !mbar_wait(&a2full[hf], i & 1) || (hf == 0 && !mbar_wait(t2empty, (i & 1) ^ 1))) {
+          fail();
+          return false;
+        }
+        tc_fence_after();
+        for (int kb = 2 * hf; kb < 2 * hf + 2 && kb < NK2; ++kb, ++g) {
+          const uint32_t s2 = g % kCfStages, r = g / kCfStages;
+          if (!mbar_wait(&full[s2], r & 1)) { fail(); return false; }
           tc_fence_after();
-          for (int kb = 0; kb < NK2; ++kb, ++g) {
-            const uint32_t s2 = g % kCfStages, r = g / kCfStages;
-            if (!mbar_wait(&full[s2], r & 1)) { fail(); ok = false; break; }
-            tc_fence_after();
-            const uint32_t a = smem_u32(sA2 + kb * A_BYTES), bb = smem_u32(ring + s2 * STAGE) + A_BYTES;
+          const uint32_t a = smem_u32(sA2 + kb * A_BYTES), bb = smem_u32(ring + s2 * STAGE);
 #pragma unroll
-            for (int k = 0; k < kTcBK / 16; ++k)
-              tc_mma(tmem + 256, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id2, (kb > 0 || k > 0) ? 1u : 0u);
-            tc_commit(&empty[s2]);
-          }
-          tc_commit(t2full);
-          tc_commit(a2empty);
+          for (int k = 0; k < kTcBK / 16; ++k)
+            tc_mma(tmem + 256, sdesc_sw128(a + k * 32), sdesc_sw128(bb + k * 32), id2, (kb > 0 || k > 0) ? 1u : 0u);
+          tc_commit(&empty[s2]);
         }
-      }
+        tc_commit(&a2empty[hf]);
+        if (hf == NH - 1) tc_commit(t2full);
+        return true;
+      };
+      walk(g1, g2);
     }
     __syncwarp();
   } else if (warp < 10) {
-    // group 1: acc1 -> silu -> pre-activation to HBM, activation into A2 (K-major, 128-byte swizzle)
-    const int q = warp & 3, h = (warp - 2) >> 2;
-    uint8_t* my = sE1 + (warp - 2) * 4096;
-    const bool pre_out = ep1.pre != nullptr;
+    // group 1: acc1 -> epi1 -> A2 (K-major, 128-byte swizzle), plus the HBM side output of the mode
+    const int q = warp & 3, ew = warp - 2, h = ew >> 2;
+    uint8_t* my = sE1 + ew * 4096;
+    uint8_t* islot = my + 2048;                // HEAD / BWD_SILU: the pre-activation chunk
+    constexpr bool in1 = (E1 == EPI_HEAD || E1 == EPI_BWD_SILU);
+    const bool st_pre = (E1 == EPI_FWD_SILU) && ep1.pre;
+    constexpr bool st_out = (E1 == EPI_BWD_SILU);
+    uint32_t ipar = 0;
+    auto fetch = [&](int i, int c) {
+      if (!in1 || i >= T) return;
+      if (lane == 0) {
+        mbar_expect_tx(&inb1[ew], 2048);
+        tma_load_2d(islot, &cm.pre1, &inb1[ew], 32 * c, row0(i) + q * 32);
+      }
+    };
+    if (h < N1 / 32) fetch(0, h);
     int oc = 0;
-    for (int i = 0; i < T; ++i) {
-      const int b = i % NB1, u = i / NB1;
-      const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
-      if (!mbar_wait(&t1full[b], u & 1) || !mbar_wait(a2empty, (i & 1) ^ 1)) { fail(); break; }
+    bool ok = true;
+    for (int i = 0; i < T && ok; ++i) {
+      const int mrow = row0(i) + q * 32;
+      const int m = mrow + lane;
+      const float rs = (m < M && ep1.rowscale) ? ep1.rowscale[m] : 1.0f;
+      float acc = 0.0f;
+      for (int hf = 0; hf < NH && ok; ++hf) {
+      // job (i, hf): accumulator slot sj & 1, columns [128 hf, 128 hf + 128) of the tile
+      const int sj = i * NH + hf, slot = sj & 1, u = sj >> 1;
+      if (!mbar_wait(&t1full[slot], u & 1) || !mbar_wait(&a2empty[hf], (i & 1) ^ 1)) { fail(); ok = false; break; }
       tc_fence_after();
-      if (*abort_flag) break;
-      const uint32_t base = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
-      for (int c = h; c < N1 / 32; c += 2) {
-        uint8_t* ob = my + (oc & 1) * 2048;
+      if (*abort_flag) { ok = false; break; }
+      const uint32_t base = tmem + (uint32_t)(slot * kCfJobN - hf * kCfJobN) + ((uint32_t)(q * 32) << 16);
+      for (int c = hf * 4 + h; c < hf * 4 + 4; c += 2) {
+        uint32_t zw[16];
+        if (in1) {
+          if (!mbar_wait(&inb1[ew], ipar)) fail();
+          ipar ^= 1u;
+          ld_bf16_row_raw(islot, lane, zw);
+          // the slot's generic reads are ordered before the next TMA write into it
+          fence_async_smem();
+          __syncwarp();
+          if (c + 2 < N1 / 32) fetch(i, c + 2);
+          else fetch(i + 1, h);
+        }
+        uint8_t* ob = st_pre ? my + (oc & 1) * 2048 : my;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int nl = 32 * c + 16 * hh;
           float v[16], o2[16];
           tc_ld16(base + (uint32_t)nl, v);
+          if constexpr (E1 == EPI_FWD_SILU) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            o2[jj] = v[jj];
-            v[jj] = v[jj] * fast_sigmoid(v[jj]);
+            for (int jj = 0; jj < 16; ++jj) {
+              o2[jj] = v[jj];
+              v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+            }
+          } else if constexpr (E1 == EPI_HEAD) {
+            // xbar -> the adjoint of the pre-activation of x = u silu(z); row sums of xbar z sigmoid(z)
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const float z = bf16_word_elem(zw, 16 * hh + jj);
+              const float sgm = fast_sigmoid(z);
+              acc += v[jj] * z * sgm;
+              v[jj] = v[jj] * rs * sgm * (1.0f + z * (1.0f - sgm));
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const float z = bf16_word_elem(zw, 16 * hh + jj);
+              const float sgm = fast_sigmoid(z);
+              v[jj] = v[jj] * sgm * (1.0f + z * (1.0f - sgm));
+            }
           }
           uint8_t* kbase = sA2 + (nl / kTcBK) * A_BYTES;
           const int r = q * 32 + lane;
@@ -1249,65 +1365,96 @@ __global__ void __launch_bounds__(kCfThreads, 1)
                                  pack_bf16x2(v[8 * uu + 4], v[8 * uu + 5]), pack_bf16x2(v[8 * uu + 6], v[8 * uu + 7]));
             *reinterpret_cast<uint4*>(kbase + r * 128 + ((unit ^ (r & 7)) << 4)) = x;
           }
-          if (pre_out) {
+          if (st_pre || st_out) {
             if (hh == 0) {
-              if (lane == 0) bulk_wait_read1();
+              if (lane == 0) {
+                if (st_pre) bulk_wait_read1();
+                else bulk_wait_read0();
+              }
               __syncwarp();
             }
-            st_bf16_half(ob, lane, hh, o2);
+            st_bf16_half(ob, lane, hh, st_pre ? o2 : v);
           }
         }
-        if (pre_out) {
+        if (st_pre || st_out) {
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            tma_store_2d(&cm.pre1, ob, 32 * c, mrow);
+            tma_store_2d(st_pre ? &cm.pre1 : &cm.out1, ob, 32 * c, mrow);
             bulk_commit();
           }
           ++oc;
+        }
+      }
+      if constexpr (E1 == EPI_HEAD) {
+        if (hf == NH - 1) {
+          const float tot = row_total(q, h, i, acc, ok);
+          if (h == 0 && m < M) ep1.ubar[m] += tot;
         }
       }
       tc_fence_before();
       fence_async_smem();          // generic-proxy writes of A2 -> visible to the tensor core
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&t1empty[b]);
-        mbar_arrive(a2full);
+        mbar_arrive(&t1empty[slot]);
+        mbar_arrive(&a2full[hf]);
+      }
       }
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   } else {
-    // group 2: acc2 -> silu (x rowscale) -> pre-activation and activation to HBM,
-    // or (last layer) the adjoint of the pre-activation, E_ij and ubar_ij
-    const int q = warp & 3, h = (warp - 10) >> 2;
-    uint8_t* my = sE2 + (warp - 10) * 4096 * NB2;
-    const bool last = ep2.epi == EPI_LAST;
-    const bool pre_out = ep2.pre != nullptr && !last;
+    // group 2: acc2 -> epi2 -> HBM
+    const int q = warp & 3, ew = warp - 10, h = ew >> 2;
+    uint8_t* my = sE2 + ew * 4096 * NB2;
+    uint8_t* islot = my + 2048;                // BWD_SILU: the pre-activation chunk
+    constexpr bool last = E2 == EPI_LAST;
+    constexpr bool in2 = E2 == EPI_BWD_SILU;
+    const bool pre_out = ep2.pre != nullptr && E2 == EPI_FWD_SILU;
+    uint32_t ipar = 0;
+    auto fetch = [&](int i, int c) {
+      if (!in2 || i >= T) return;
+      if (lane == 0) {
+        mbar_expect_tx(&inb2[ew], 2048);
+        tma_load_2d(islot, &cm.pre2, &inb2[ew], 32 * c, row0(i) + q * 32);
+      }
+    };
+    if (h < N2 / 32) fetch(0, h);
     int oc = 0;
-    for (int i = 0; i < T; ++i) {
-      const int mrow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM + q * 32;
+    bool ok = true;
+    for (int i = 0; i < T && ok; ++i) {
+      const int mrow = row0(i) + q * 32;
       const int m = mrow + lane;
       const float rs = (m < M && ep2.rowscale) ? ep2.rowscale[m] : 1.0f;
       const float srs = (last && m < M) ? ep2.rowsig[m] * rs : 0.0f;
-      float acc1 = 0.0f;
+      float acc = 0.0f;
       if (!mbar_wait(t2full, i & 1)) { fail(); break; }
       tc_fence_after();
       if (*abort_flag) break;
       const uint32_t base = tmem + 256u + ((uint32_t)(q * 32) << 16);
       for (int c = h; c < N2 / 32; c += 2) {
+        uint32_t zw[16];
+        if (in2) {
+          if (!mbar_wait(&inb2[ew], ipar)) fail();
+          ipar ^= 1u;
+          ld_bf16_row_raw(islot, lane, zw);
+          fence_async_smem();
+          __syncwarp();
+          if (c + 2 < N2 / 32) fetch(i, c + 2);
+          else fetch(i + 1, h);
+        }
         uint8_t* ob = my + (oc % NB2) * 4096;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           float v[16], o2[16];
           tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
-          if (!last) {
+          if constexpr (E2 == EPI_FWD_SILU) {
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
               o2[jj] = v[jj];
               v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
             }
-          } else {
+          } else if constexpr (last) {
             // E_ij = rowscale * sum_n v_n silu(z_n); the pre-activation adjoint
             // sigma_i rowscale v_n silu'(z_n) is the GEMM input of the backward pass
 #pragma unroll
@@ -1318,9 +1465,16 @@ __global__ void __launch_bounds__(kCfThreads, 1)
               for (int t4 = 0; t4 < 4; ++t4) {
                 const int jj = 4 * k4 + t4;
                 const float sgm = fast_sigmoid(v[jj]);
-                acc1 += vv[t4] * v[jj] * sgm;
+                acc += vv[t4] * v[jj] * sgm;
                 v[jj] = srs * vv[t4] * sgm * (1.0f + v[jj] * (1.0f - sgm));
               }
+            }
+          } else if constexpr (in2) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const float z = bf16_word_elem(zw, 16 * hh + jj);
+              const float sgm = fast_sigmoid(z);
+              v[jj] = v[jj] * sgm * (1.0f + z * (1.0f - sgm));
             }
           }
           if (hh == 0) {
@@ -1342,29 +1496,16 @@ __global__ void __launch_bounds__(kCfThreads, 1)
         }
         ++oc;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (!last) {
-        if (lane == 0) mbar_arrive(t2empty);
-      } else if (h == 1) {
-        // the second partial row sum; the slot is free again once warp h = 0
-        // has read it (it releases the accumulator only after that)
-        rowpart[q * 32 + lane] = acc1;
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&rsbar[q]);
-          mbar_arrive(t2empty);
-        }
-      } else {
-        if (!mbar_wait(&rsbar[q], i & 1)) fail();
-        const float tot = acc1 + rowpart[q * 32 + lane];
-        if (m < M) {
+      if constexpr (last) {
+        const float tot = row_total(q, h, i, acc, ok);
+        if (h == 0 && m < M) {
           ep2.Eout[m] = rs * tot;
           ep2.ubar[m] = ep2.rowsig[m] * tot;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(t2empty);
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(t2empty);
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -1527,14 +1668,15 @@ static bool launch_chain(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st
   return true;
 }
 
-template <int N1, int N2>
-static bool launch_chain_fwd(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why) {
+template <int N1, int N2, int E1, int E2>
+static bool launch_chain_pipe(const GemmArgs& g1, const GemmArgs& g2, const bf16* B1, int ldb1, const bf16* B2,
+                              int ldb2, cudaStream_t st, int* d_err, std::string* why) {
   constexpr size_t smem = cf_smem_bytes(N1, N2);
   static_assert(smem <= 232448, "pipelined chain shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_chain_fwd_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gemm_chain_pipe_kernel<N1, N2, E1, E2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       if (why) *why = std::string("cudaFuncSetAttribute (chain): ") + cudaGetErrorString(e);
       return false;
@@ -1547,55 +1689,76 @@ static bool launch_chain_fwd(const GemmArgs& g1, const GemmArgs& g2, cudaStream_
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 148;
   }
-  const bf16* B1 = g1.trans ? g1.W->b16T : g1.W->b16;
-  const int ldb1 = g1.trans ? g1.W->ldT : g1.W->ld;
-  const bf16* B2 = g2.trans ? g2.W->b16T : g2.W->b16;
-  const int ldb2 = g2.trans ? g2.W->ldT : g2.W->ld;
-  ChainMaps cm;
+  const int K1a = g1.A2 ? g1.K1 : g1.K;
+  PipeMaps cm;
   memset(&cm, 0, sizeof cm);
-  bool ok = make_tmap(&cm.a1, g1.A, (uint64_t)g1.K, (uint64_t)g1.M, (uint64_t)g1.lda * 2, kTcBK, kTcBM) &&
-            make_tmap(&cm.b1, B1, (uint64_t)g1.K, (uint64_t)g1.N, (uint64_t)ldb1 * 2, kTcBK, N1) &&
+  bool ok = make_tmap(&cm.a1, g1.A, (uint64_t)K1a, (uint64_t)g1.M, (uint64_t)g1.lda * 2, kTcBK, kTcBM) &&
+            make_tmap(&cm.a1b, g1.A2 ? g1.A2 : g1.A, (uint64_t)(g1.A2 ? g1.K - K1a : K1a), (uint64_t)g1.M,
+                      (uint64_t)(g1.A2 ? g1.lda2 : g1.lda) * 2, kTcBK, kTcBM) &&
+            make_tmap(&cm.b1, B1, (uint64_t)g1.K, (uint64_t)g1.N, (uint64_t)ldb1 * 2, kTcBK, kCfJobN) &&
             make_tmap(&cm.b2, B2, (uint64_t)g2.K, (uint64_t)g2.N, (uint64_t)ldb2 * 2, kTcBK, N2);
   if (ok && g1.pre) ok = make_box_map(&cm.pre1, g1.pre, g1.N, g1.M, g1.ldp, 2);
+  if (ok && g1.epi == EPI_BWD_SILU) ok = make_box_map(&cm.out1, g1.out, g1.N, g1.M, g1.ldo, 2);
+  if (ok && g2.pre && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_BWD_SILU))
+    ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
   if (ok) ok = make_box_map(&cm.out2, g2.out, g2.N, g2.M, g2.ldo, 2);
-  if (ok && g2.pre && g2.epi != EPI_LAST) ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
   if (!ok) {
     if (why) *why = "cuTensorMapEncodeTiled failed (chain)";
     return false;
   }
   const int tiles = (g1.M + kTcBM - 1) / kTcBM;
   const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_chain_fwd_kernel<N1, N2><<<grid, kCfThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M, g1.K, d_err);
+  gemm_chain_pipe_kernel<N1, N2, E1, E2><<<grid, kCfThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M,
+                                                                          g1.K, K1a, d_err);
   return true;
 }
 
-// Two consecutive layers in one kernel (see gemm_chain_kernel).  Returns
-// false with `why` empty when the shapes are not supported (the caller then
-// runs the two GEMMs separately).
+// Two consecutive layers in one kernel: the pipelined kernel for the pairs it
+// takes (see gemm_chain_pipe_kernel), the two-stage kernel for a few other
+// forward / adjoint shapes.  Returns false with `why` empty when the pair is
+// not supported (the caller then runs the two GEMMs separately).
 bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why) {
   if (why) why->clear();
   if (g1.M <= 0) return true;
-  if (g2.K != g1.N || g2.M != g1.M) return false;
+  if (g2.K != g1.N || g2.M != g1.M || g2.A2 || g1.add || g2.add) return false;
+  if (!gemm_tc_init(why)) return false;
+  const bf16* B1 = g1.Bover ? g1.Bover : (g1.trans ? g1.W->b16T : g1.W->b16);
+  const int ldb1 = g1.Bover ? g1.ldb_over : (g1.trans ? g1.W->ldT : g1.W->ld);
+  B1 += (size_t)g1.b_row0 * ldb1;
+  const bf16* B2 = g2.Bover ? g2.Bover : (g2.trans ? g2.W->b16T : g2.W->b16);
+  const int ldb2 = g2.Bover ? g2.ldb_over : (g2.trans ? g2.W->ldT : g2.W->ld);
+  B2 += (size_t)g2.b_row0 * ldb2;
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (!al(g1.A) || !al(B1) || !al(B2) || (g1.lda % 8) || (ldb1 % 8) || (ldb2 % 8)) return false;
+  if (g1.A2 && (!al(g1.A2) || (g1.lda2 % 8) || (g1.K1 % kTcBK) || g1.K1 <= 0 || g1.K1 >= g1.K)) return false;
+  // the pipelined kernel
+  const bool e1ok = g1.epi == EPI_FWD_SILU || (g1.epi == EPI_HEAD && g1.pre && g1.ubar) ||
+                    (g1.epi == EPI_BWD_SILU && g1.pre && g1.out);
+  const bool last_ok = g2.epi == EPI_LAST && g2.v && g2.rowsig && g2.Eout && g2.ubar && al(g2.v) &&
+                       g1.epi != EPI_HEAD;
+  const bool e2ok = g2.epi == EPI_FWD_SILU || last_ok || (g2.epi == EPI_BWD_SILU && g2.pre) || g2.epi == EPI_LINEAR;
+  if (e1ok && e2ok) {
+    // instantiated for the pairs of the MLPs' forward and adjoint passes
+#define PIPE(n1, n2, e1, e2) \
+  if (g1.N == n1 && g2.N == n2 && g1.epi == e1 && g2.epi == e2) \
+    return launch_chain_pipe<n1, n2, e1, e2>(g1, g2, B1, ldb1, B2, ldb2, st, d_err, why);
+    PIPE(128, 256, EPI_FWD_SILU, EPI_FWD_SILU)
+    PIPE(256, 256, EPI_FWD_SILU, EPI_FWD_SILU)
+    PIPE(256, 256, EPI_FWD_SILU, EPI_LAST)
+    PIPE(256, 256, EPI_HEAD, EPI_BWD_SILU)
+    PIPE(256, 128, EPI_HEAD, EPI_BWD_SILU)
+    PIPE(256, 64, EPI_BWD_SILU, EPI_LINEAR)
+#undef PIPE
+  }
+  // the two-stage kernel: plain weights only
+  if (g1.A2 || g1.Bover || g2.Bover || g1.b_row0 || g2.b_row0) return false;
   if (!(g1.epi == EPI_FWD_SILU || g1.epi == EPI_BWD_SILU)) return false;
   if (!(g2.epi == EPI_FWD_SILU || g2.epi == EPI_BWD_SILU || g2.epi == EPI_LAST || g2.epi == EPI_LINEAR ||
-        (g2.epi == EPI_F32 && !g2.add)))
+        g2.epi == EPI_F32))
     return false;
   if (g1.epi == EPI_BWD_SILU && !g1.pre) return false;
   if (g2.epi == EPI_BWD_SILU && !g2.pre) return false;
-  if (!gemm_tc_init(why)) return false;
-  const bf16* B1 = g1.trans ? g1.W->b16T : g1.W->b16;
-  const bf16* B2 = g2.trans ? g2.W->b16T : g2.W->b16;
-  if ((reinterpret_cast<uintptr_t>(g1.A) & 15) || (reinterpret_cast<uintptr_t>(B1) & 15) ||
-      (reinterpret_cast<uintptr_t>(B2) & 15) || (g1.lda % 8))
-    return false;
   const int bn2 = (g2.N + 31) / 32 * 32;
-  // SiLU -> SiLU forward and SiLU -> last-layer pairs: the pipelined kernel (two epilogue groups)
-  const bool last_ok = g2.epi == EPI_LAST && g2.v && g2.rowsig && g2.Eout && g2.ubar &&
-                       (reinterpret_cast<uintptr_t>(g2.v) & 15) == 0;
-  if (g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || last_ok) && g2.N == 256 && !g1.rowscale) {
-    if (g1.N == 128) return launch_chain_fwd<128, 256>(g1, g2, st, d_err, why);
-    if (g1.N == 256) return launch_chain_fwd<256, 256>(g1, g2, st, d_err, why);
-  }
   if (g1.N == 256 && bn2 == 256) return launch_chain<256, 256>(g1, g2, st, d_err, why);
   if (g1.N == 256 && bn2 == 320) return launch_chain<256, 320>(g1, g2, st, d_err, why);
   if (g1.N == 128 && bn2 == 256) return launch_chain<128, 256>(g1, g2, st, d_err, why);

@@ -807,7 +807,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
       bool launched;
       {
         ProfScope ps(c, label, 2.0 * Ec * ((double)g1.N * g1.K + (double)g2.N * g2.K),
-                     gbytes(g1, true, false) + gbytes(g2, false, true));
+                     gbytes(g1, true, g1.epi == EPI_BWD_SILU) + gbytes(g2, false, true));
         launched = gemm_chain_bf16(g1, g2, c->stream, c->d_err, &why);
       }
       if (launched) return ALLEGRO_OK;

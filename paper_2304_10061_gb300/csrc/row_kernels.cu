@@ -36,6 +36,14 @@ namespace {
 constexpr int kRowWarps = 4;   // atoms (warps) per block
 constexpr int kYSeg = 64;      // edges per staged segment of Y
 
+// A lane's channels are processed in pairs (2p, 2p + 1) with the packed fp32
+// operations of sm_100 and later (one FFMA2 / FMUL2 for two channels); each
+// half is an ordinary IEEE fp32 fma / multiply.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 template <int LMAX>
 __device__ __forceinline__ constexpr int lof(int a) { return a < 1 ? 0 : (a < 4 ? 1 : (a < 9 ? 2 : 3)); }
 
@@ -304,10 +312,11 @@ __device__ __forceinline__ void env_sum(const RowIO& io, const RowCtx& r, const 
                                         int& staged) {
   constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
   using WS = WSpan<T, CPL, LM>;
+  float2 G2[CPL / 2][S];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
+  for (int p = 0; p < CPL / 2; ++p)
 #pragma unroll
-    for (int b = 0; b < S; ++b) G[j][b] = 0.0f;
+    for (int b = 0; b < S; ++b) G2[p][b] = bc(0.0f);
   for (int sb = r.rb; sb < r.re; sb += kYSeg) {
     const int cnt = min(kYSeg, r.re - sb);
     ys.load(io.Y, sb, cnt, r.lane);
@@ -320,11 +329,21 @@ __device__ __forceinline__ void env_sum(const RowIO& io, const RowCtx& r, const 
           ys.get(k, y);
           unpack_span<T, WS::N>(raw[u], w);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j)
+          for (int p = 0; p < CPL / 2; ++p)
 #pragma unroll
-            for (int b = 0; b < S; ++b) G[j][b] += w[j * LM + lof<LMAX>(b)] * y[b];
+            for (int b = 0; b < S; ++b) {
+              const int l = lof<LMAX>(b);
+              G2[p][b] = fma2(pk(w[2 * p * LM + l], w[(2 * p + 1) * LM + l]), bc(y[b]), G2[p][b]);
+            }
         });
   }
+#pragma unroll
+  for (int p = 0; p < CPL / 2; ++p)
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      G[2 * p][b] = G2[p][b].x;
+      G[2 * p + 1][b] = G2[p][b].y;
+    }
 }
 
 // s[e][u] = sum_p w0[e][u][l(p)] Y[e][p] M[u][p]  (scalar output of a product), written at column xs_off + u
@@ -349,16 +368,20 @@ __device__ __forceinline__ void scalar_out(const RowIO& io, const RowCtx& r, con
           ys.get(k, y);
           unpack_span<T, WS::N>(raw[u], w);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            float t[LM];
+          for (int jp = 0; jp < CPL / 2; ++jp) {
+            float2 t[LM];
 #pragma unroll
-            for (int l = 0; l < LM; ++l) t[l] = 0.0f;
+            for (int l = 0; l < LM; ++l) t[l] = bc(0.0f);
 #pragma unroll
-            for (int p = 0; p < S; ++p) t[lof<LMAX>(p)] += y[p] * M[j][p];
-            float sv = 0.0f;
+            for (int p = 0; p < S; ++p) t[lof<LMAX>(p)] = fma2(bc(y[p]), pk(M[2 * jp][p], M[2 * jp + 1][p]), t[lof<LMAX>(p)]);
+            float2 sv = bc(0.0f);
 #pragma unroll
-            for (int l = 0; l < LM; ++l) sv += w[j * LM + l] * t[l];
-            if (r.act) xs[(size_t)e * io.ldxs + io.xs_off + r.u0 + j] = to_act2<T>(sv);
+            for (int l = 0; l < LM; ++l) sv = fma2(pk(w[2 * jp * LM + l], w[(2 * jp + 1) * LM + l]), t[l], sv);
+            if (r.act) {
+              T* o = xs + (size_t)e * io.ldxs + io.xs_off + r.u0 + 2 * jp;
+              o[0] = to_act2<T>(sv.x);
+              o[1] = to_act2<T>(sv.y);
+            }
           }
         });
   }
@@ -500,11 +523,11 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
       for (int b = 0; b < S; ++b) cG[j][b] *= tp.clast[b];
   }
   // pass 1: Q[a] = sum_e sbar_e V^0_{e,a}  (+ NL = 1: wbar^0, Ybar from w^0)
-  float Q[CPL][S];
+  float2 Q2[CPL / 2][S];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
+  for (int p = 0; p < CPL / 2; ++p)
 #pragma unroll
-    for (int b = 0; b < S; ++b) Q[j][b] = 0.0f;
+    for (int b = 0; b < S; ++b) Q2[p][b] = bc(0.0f);
   int staged = -1;
   using WS = WSpan<T, CPL, LM>;
   for (int sb = r.rb; sb < r.re; sb += kYSeg) {
@@ -521,34 +544,55 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
         },
         [&](int u, int k) {
           const int e = sb + k;
-          float y[S], w0[WS::N], yc[S], g0[WS::N];
+          float y[S], w0[WS::N], g0[WS::N];
+          float2 yc2[S];
           ys.get(k, y);
           unpack_span<T, WS::N>(raw[u], w0);
 #pragma unroll
-          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+          for (int b = 0; b < S; ++b) yc2[b] = bc(0.0f);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            const float sj = raw_f(sraw[u][j]);
-            float t[LM];
+          for (int p = 0; p < CPL / 2; ++p) {
+            const float2 sj = pk(raw_f(sraw[u][2 * p]), raw_f(sraw[u][2 * p + 1]));
+            float2 t[LM], g[LM];
 #pragma unroll
-            for (int l = 0; l < LM; ++l) { t[l] = sj * w0[j * LM + l]; g0[j * LM + l] = 0.0f; }
+            for (int l = 0; l < LM; ++l) {
+              t[l] = mul2(sj, pk(w0[2 * p * LM + l], w0[(2 * p + 1) * LM + l]));
+              g[l] = bc(0.0f);
+            }
 #pragma unroll
-            for (int b = 0; b < S; ++b) Q[j][b] += t[lof<LMAX>(b)] * y[b];
+            for (int b = 0; b < S; ++b) Q2[p][b] = fma2(t[lof<LMAX>(b)], bc(y[b]), Q2[p][b]);
             if constexpr (NL == 1) {
 #pragma unroll
               for (int b = 0; b < S; ++b) {
-                const float v0b = sj * cG[j][b];
-                g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
-                yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b;
+                const int l = lof<LMAX>(b);
+                const float2 v0b = mul2(sj, pk(cG[2 * p][b], cG[2 * p + 1][b]));
+                g[l] = fma2(v0b, bc(y[b]), g[l]);
+                yc2[b] = fma2(pk(w0[2 * p * LM + l], w0[(2 * p + 1) * LM + l]), v0b, yc2[b]);
+              }
+#pragma unroll
+              for (int l = 0; l < LM; ++l) {
+                g0[2 * p * LM + l] = g[l].x;
+                g0[(2 * p + 1) * LM + l] = g[l].y;
               }
             }
           }
           if constexpr (NL == 1) {
+            float yc[S];
+#pragma unroll
+            for (int b = 0; b < S; ++b) yc[b] = yc2[b].x + yc2[b].y;
             st_w<T, CPL, LM>(wb01, io.ld_wbar01, 0, e, r, g0);
             warp_channel_sum<S>(yc, r.lane, io.Ybar[0] + (size_t)e * S);
           }
         });
   }
+  float Q[CPL][S];
+#pragma unroll
+  for (int p = 0; p < CPL / 2; ++p)
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      Q[2 * p][b] = Q2[p][b].x;
+      Q[2 * p + 1][b] = Q2[p][b].y;
+    }
   // Gamma^NL bar, pre-scaled by nu
   float Gb[CPL][S];
   float G1[CPL][S];
@@ -583,6 +627,11 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
   const int col0 = (NL == 1) ? nw : 0;
   const int nseg = (r.re - r.rb + kYSeg - 1) / kYSeg;
   float* ybar_out = io.Ybar[NL == 1 ? 1 : 0];
+  float2 Gb2[CPL / 2][S];
+#pragma unroll
+  for (int p = 0; p < CPL / 2; ++p)
+#pragma unroll
+    for (int b = 0; b < S; ++b) Gb2[p][b] = pk(Gb[2 * p][b], Gb[2 * p + 1][b]);
   for (int q = nseg - 1; q >= 0; --q) {
     const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
     if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
@@ -593,20 +642,30 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
         [&](int u, int k) {
           const int e = sb + k;
           float y[S], w[WS::N], g[WS::N], yc[S];
+          float2 yc2[S];
           ys.get(k, y);
           unpack_span<T, WS::N>(raw[u], w);
 #pragma unroll
-          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+          for (int b = 0; b < S; ++b) yc2[b] = bc(0.0f);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) {
+          for (int p = 0; p < CPL / 2; ++p) {
+            float2 g2[LM];
 #pragma unroll
-            for (int l = 0; l < LM; ++l) g[j * LM + l] = 0.0f;
+            for (int l = 0; l < LM; ++l) g2[l] = bc(0.0f);
 #pragma unroll
             for (int b = 0; b < S; ++b) {
-              g[j * LM + lof<LMAX>(b)] += Gb[j][b] * y[b];
-              yc[b] += w[j * LM + lof<LMAX>(b)] * Gb[j][b];
+              const int l = lof<LMAX>(b);
+              g2[l] = fma2(Gb2[p][b], bc(y[b]), g2[l]);
+              yc2[b] = fma2(pk(w[2 * p * LM + l], w[(2 * p + 1) * LM + l]), Gb2[p][b], yc2[b]);
+            }
+#pragma unroll
+            for (int l = 0; l < LM; ++l) {
+              g[2 * p * LM + l] = g2[l].x;
+              g[(2 * p + 1) * LM + l] = g2[l].y;
             }
           }
+#pragma unroll
+          for (int b = 0; b < S; ++b) yc[b] = yc2[b].x + yc2[b].y;
           st_w<T, CPL, LM>(wbL, ldwb, col0, e, r, g);
           warp_channel_sum<S>(yc, r.lane, ybar_out + (size_t)e * S);
         });
@@ -634,11 +693,11 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
   const T* W01 = reinterpret_cast<const T*>(io.W01);
   T* wb = reinterpret_cast<T*>(io.wbar01);
   using WS = WSpan<T, CPL, LM>;
-  float Q1[CPL][S], Q2[CPL][S];
+  float2 Q1p[CPL / 2][S], Q2p[CPL / 2][S];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
+  for (int p = 0; p < CPL / 2; ++p)
 #pragma unroll
-    for (int b = 0; b < S; ++b) { Q1[j][b] = 0.0f; Q2[j][b] = 0.0f; }
+    for (int b = 0; b < S; ++b) { Q1p[p][b] = bc(0.0f); Q2p[p][b] = bc(0.0f); }
   int staged = -1;
   for (int sb = r.rb; sb < r.re; sb += kYSeg) {
     const int cnt = min(kYSeg, r.re - sb);
@@ -658,17 +717,27 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
           ys.get(k, y);
           unpack_span<T, WS::N>(raw[u], w0);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
+          for (int p = 0; p < CPL / 2; ++p) {
+            const float2 s1 = pk(raw_f(s1r[u][2 * p]), raw_f(s1r[u][2 * p + 1]));
+            const float2 s2 = pk(raw_f(s2r[u][2 * p]), raw_f(s2r[u][2 * p + 1]));
 #pragma unroll
             for (int b = 0; b < S; ++b) {
-              const float v0 = w0[j * LM + lof<LMAX>(b)] * y[b];
-              Q1[j][b] += s1 * v0;
-              Q2[j][b] += s2 * v0;
+              const int l = lof<LMAX>(b);
+              const float2 v0 = mul2(pk(w0[2 * p * LM + l], w0[(2 * p + 1) * LM + l]), bc(y[b]));
+              Q1p[p][b] = fma2(s1, v0, Q1p[p][b]);
+              Q2p[p][b] = fma2(s2, v0, Q2p[p][b]);
             }
           }
         });
   }
+  float Q1[CPL][S], Q2[CPL][S];
+#pragma unroll
+  for (int p = 0; p < CPL / 2; ++p)
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      Q1[2 * p][b] = Q1p[p][b].x; Q1[2 * p + 1][b] = Q1p[p][b].y;
+      Q2[2 * p][b] = Q2p[p][b].x; Q2[2 * p + 1][b] = Q2p[p][b].y;
+    }
   // per atom: T1, T2, Gamma^1bar
   float T1[CPL][S], T2[CPL][S], G1b[CPL][S];
   {
@@ -707,6 +776,15 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
       }
     }
   }
+  float2 T1p[CPL / 2][S], T2p[CPL / 2][S], G1bp[CPL / 2][S];
+#pragma unroll
+  for (int p = 0; p < CPL / 2; ++p)
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      T1p[p][b] = pk(T1[2 * p][b], T1[2 * p + 1][b]);
+      T2p[p][b] = pk(T2[2 * p][b], T2[2 * p + 1][b]);
+      G1bp[p][b] = pk(G1b[2 * p][b], G1b[2 * p + 1][b]);
+    }
   const int nseg = (r.re - r.rb + kYSeg - 1) / kYSeg;
   for (int q = nseg - 1; q >= 0; --q) {
     const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
@@ -725,24 +803,37 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
         [&](int u, int k) {
           const int e = sb + k;
           float y[S], w0[WS::N], w1[WS::N], g0[WS::N], g1[WS::N], yc[S];
+          float2 yc2[S];
           ys.get(k, y);
           unpack_span<T, WS::N>(raw0[u], w0);
           unpack_span<T, WS::N>(raw1[u], w1);
 #pragma unroll
-          for (int b = 0; b < S; ++b) yc[b] = 0.0f;
+          for (int b = 0; b < S; ++b) yc2[b] = bc(0.0f);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) {
-            const float s1 = raw_f(s1r[u][j]), s2 = raw_f(s2r[u][j]);
+          for (int p = 0; p < CPL / 2; ++p) {
+            const float2 s1 = pk(raw_f(s1r[u][2 * p]), raw_f(s1r[u][2 * p + 1]));
+            const float2 s2 = pk(raw_f(s2r[u][2 * p]), raw_f(s2r[u][2 * p + 1]));
+            float2 a0[LM], a1[LM];
 #pragma unroll
-            for (int l = 0; l < LM; ++l) { g0[j * LM + l] = 0.0f; g1[j * LM + l] = 0.0f; }
+            for (int l = 0; l < LM; ++l) { a0[l] = bc(0.0f); a1[l] = bc(0.0f); }
 #pragma unroll
             for (int b = 0; b < S; ++b) {
-              const float v0b = s2 * T2[j][b] + s1 * T1[j][b];
-              g0[j * LM + lof<LMAX>(b)] += v0b * y[b];
-              g1[j * LM + lof<LMAX>(b)] += G1b[j][b] * y[b];
-              yc[b] += w0[j * LM + lof<LMAX>(b)] * v0b + w1[j * LM + lof<LMAX>(b)] * G1b[j][b];
+              const int l = lof<LMAX>(b);
+              const float2 yy = bc(y[b]);
+              const float2 v0b = fma2(s2, T2p[p][b], mul2(s1, T1p[p][b]));
+              a0[l] = fma2(v0b, yy, a0[l]);
+              a1[l] = fma2(G1bp[p][b], yy, a1[l]);
+              yc2[b] = fma2(pk(w0[2 * p * LM + l], w0[(2 * p + 1) * LM + l]), v0b, yc2[b]);
+              yc2[b] = fma2(pk(w1[2 * p * LM + l], w1[(2 * p + 1) * LM + l]), G1bp[p][b], yc2[b]);
+            }
+#pragma unroll
+            for (int l = 0; l < LM; ++l) {
+              g0[2 * p * LM + l] = a0[l].x; g0[(2 * p + 1) * LM + l] = a0[l].y;
+              g1[2 * p * LM + l] = a1[l].x; g1[(2 * p + 1) * LM + l] = a1[l].y;
             }
           }
+#pragma unroll
+          for (int b = 0; b < S; ++b) yc[b] = yc2[b].x + yc2[b].y;
           st_w<T, CPL, LM>(wb, io.ld_wbar01, 0, e, r, g0);
           st_w<T, CPL, LM>(wb, io.ld_wbar01, nw, e, r, g1);
           warp_channel_sum<S>(yc, r.lane, io.Ybar[1] + (size_t)e * S);

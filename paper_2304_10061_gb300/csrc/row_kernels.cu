@@ -270,20 +270,48 @@ __device__ __forceinline__ void st_w(T* arr, int ld, int col0, int e, const RowC
   if (r.act) st_span<T, CPL * LM>(arr + (size_t)e * ld + col0 + r.u0 * LM, w);
 }
 
-// lane's CPL values of a per-edge adjoint row (activation type, any column
-// offset), kept as raw bits until the arithmetic so that a batch's loads are
-// not serialised behind conversions
-template <typename T> struct RawOf { typedef uint32_t type; };
-template <> struct RawOf<bf16> { typedef unsigned short type; };
-__device__ __forceinline__ float raw_f(uint32_t v) { return __uint_as_float(v); }
-__device__ __forceinline__ float raw_f(unsigned short v) { return __uint_as_float((uint32_t)v << 16); }
-
+// lane's CPL values of a per-edge adjoint row (activation type), kept as raw
+// 32-bit words until the arithmetic so that a batch's loads are not
+// serialised behind conversions.  The row pitch and column offset are even
+// (every activation array is allocated with pitches that are multiples of 8
+// elements), so a lane's CPL (even) values are whole aligned words.
+template <typename T, int CPL>
+struct SbarW {
+  static constexpr int NB = CPL * (int)sizeof(T);
+  static constexpr int NW = NB / 4;
+};
 template <typename T, int CPL>
 __device__ __forceinline__ void ld_sbar(const void* sbar, int ld, int e, const RowCtx& r,
-                                        typename RawOf<T>::type (&s)[CPL]) {
-  const typename RawOf<T>::type* p = reinterpret_cast<const typename RawOf<T>::type*>(sbar) + (size_t)e * ld + r.u0;
+                                        uint32_t (&w)[SbarW<T, CPL>::NW]) {
+  if (r.act) ld_words<SbarW<T, CPL>::NB>(reinterpret_cast<const T*>(sbar) + (size_t)e * ld + r.u0, w);
+  else {
 #pragma unroll
-  for (int j = 0; j < CPL; ++j) s[j] = r.act ? p[j] : 0;
+    for (int q = 0; q < SbarW<T, CPL>::NW; ++q) w[q] = 0u;
+  }
+}
+// the same values as CPL separate element loads (raw bits in the low bits of each word)
+template <typename T, int CPL>
+__device__ __forceinline__ void ld_sbar_el(const void* sbar, int ld, int e, const RowCtx& r, uint32_t (&w)[CPL]) {
+  const T* p = reinterpret_cast<const T*>(sbar) + (size_t)e * ld + r.u0;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    if constexpr (sizeof(T) == 2) w[j] = r.act ? (uint32_t)reinterpret_cast<const unsigned short*>(p)[j] : 0u;
+    else w[j] = r.act ? reinterpret_cast<const uint32_t*>(p)[j] : 0u;
+  }
+}
+__device__ __forceinline__ float2 sbar_el_pair(const uint32_t* w, int p, bool half) {
+  return half ? make_float2(__uint_as_float(w[2 * p] << 16), __uint_as_float(w[2 * p + 1] << 16))
+              : make_float2(__uint_as_float(w[2 * p]), __uint_as_float(w[2 * p + 1]));
+}
+// channels (2p, 2p + 1) of the lane's raw sbar words
+template <typename T, int CPL>
+__device__ __forceinline__ float2 sbar_pair(const uint32_t (&w)[SbarW<T, CPL>::NW], int p) {
+  if constexpr (sizeof(T) == 2) {
+    const uint32_t x = w[p];   // bf16 -> float is exact: the bf16 bits are the upper half of the float
+    return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+  } else {
+    return make_float2(__uint_as_float(w[2 * p]), __uint_as_float(w[2 * p + 1]));
+  }
 }
 
 // Edges of a segment in batches of D: the loads of a whole batch are issued
@@ -535,12 +563,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
     uint32_t raw[kBatchLastP1][WS::NW];
-    typename RawOf<T>::type sraw[kBatchLastP1][CPL];
+    uint32_t sraw[kBatchLastP1][CPL];
     edge_batches<kBatchLastP1>(
         cnt,
         [&](int u, int k) {
           ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
-          ld_sbar<T, CPL>(sbar, lds, sb + k, r, sraw[u]);
+          ld_sbar_el<T, CPL>(sbar, lds, sb + k, r, sraw[u]);
         },
         [&](int u, int k) {
           const int e = sb + k;
@@ -552,7 +580,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
           for (int b = 0; b < S; ++b) yc2[b] = bc(0.0f);
 #pragma unroll
           for (int p = 0; p < CPL / 2; ++p) {
-            const float2 sj = pk(raw_f(sraw[u][2 * p]), raw_f(sraw[u][2 * p + 1]));
+            const float2 sj = sbar_el_pair(sraw[u], p, sizeof(T) == 2);
             float2 t[LM], g[LM];
 #pragma unroll
             for (int l = 0; l < LM; ++l) {
@@ -704,7 +732,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
     uint32_t raw[kBatchLight][WS::NW];
-    typename RawOf<T>::type s1r[kBatchLight][CPL], s2r[kBatchLight][CPL];
+    uint32_t s1r[kBatchLight][SbarW<T, CPL>::NW], s2r[kBatchLight][SbarW<T, CPL>::NW];
     edge_batches<kBatchLight>(
         cnt,
         [&](int u, int k) {
@@ -718,8 +746,8 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
           unpack_span<T, WS::N>(raw[u], w0);
 #pragma unroll
           for (int p = 0; p < CPL / 2; ++p) {
-            const float2 s1 = pk(raw_f(s1r[u][2 * p]), raw_f(s1r[u][2 * p + 1]));
-            const float2 s2 = pk(raw_f(s2r[u][2 * p]), raw_f(s2r[u][2 * p + 1]));
+            const float2 s1 = sbar_pair<T, CPL>(s1r[u], p);
+            const float2 s2 = sbar_pair<T, CPL>(s2r[u], p);
 #pragma unroll
             for (int b = 0; b < S; ++b) {
               const int l = lof<LMAX>(b);
@@ -791,7 +819,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
     if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
     uint32_t raw0[kBatchHeavy][WS::NW], raw1[kBatchHeavy][WS::NW];
-    typename RawOf<T>::type s1r[kBatchHeavy][CPL], s2r[kBatchHeavy][CPL];
+    uint32_t s1r[kBatchHeavy][SbarW<T, CPL>::NW], s2r[kBatchHeavy][SbarW<T, CPL>::NW];
     edge_batches<kBatchHeavy>(
         cnt,
         [&](int u, int k) {
@@ -811,8 +839,8 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_mid_kernel(RowIO io, T
           for (int b = 0; b < S; ++b) yc2[b] = bc(0.0f);
 #pragma unroll
           for (int p = 0; p < CPL / 2; ++p) {
-            const float2 s1 = pk(raw_f(s1r[u][2 * p]), raw_f(s1r[u][2 * p + 1]));
-            const float2 s2 = pk(raw_f(s2r[u][2 * p]), raw_f(s2r[u][2 * p + 1]));
+            const float2 s1 = sbar_pair<T, CPL>(s1r[u], p);
+            const float2 s2 = sbar_pair<T, CPL>(s2r[u], p);
             float2 a0[LM], a1[LM];
 #pragma unroll
             for (int l = 0; l < LM; ++l) { a0[l] = bc(0.0f); a1[l] = bc(0.0f); }

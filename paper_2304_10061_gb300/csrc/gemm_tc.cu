@@ -1129,6 +1129,9 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   const int ntiles = (M + kTcBM - 1) / kTcBM;
   const int T = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   auto row0 = [&](int i) { return ((int)blockIdx.x + i * (int)gridDim.x) * kTcBM; };
+  // accumulator chunks of 32 columns read with one TMEM load (one wait) in the
+  // adjoint-head pairs, two 16-column loads otherwise (measured per pair)
+  constexpr bool kLd32 = (E1 == EPI_HEAD);
 
   if (threadIdx.x == 0) {
     for (int s2 = 0; s2 < kCfStages; ++s2) {
@@ -1328,11 +1331,18 @@ __global__ void __launch_bounds__(kCfThreads, 1)
           else fetch(i + 1, h);
         }
         uint8_t* ob = st_pre ? my + (oc & 1) * 2048 : my;
+        float v32[kLd32 ? 32 : 1];
+        if constexpr (kLd32) tc_ld32(base + (uint32_t)(32 * c), v32);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int nl = 32 * c + 16 * hh;
           float v[16], o2[16];
-          tc_ld16(base + (uint32_t)nl, v);
+          if constexpr (kLd32) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = v32[16 * hh + jj];
+          } else {
+            tc_ld16(base + (uint32_t)nl, v);
+          }
           if constexpr (E1 == EPI_FWD_SILU) {
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
@@ -1444,10 +1454,17 @@ __global__ void __launch_bounds__(kCfThreads, 1)
           else fetch(i + 1, h);
         }
         uint8_t* ob = my + (oc % NB2) * 4096;
+        float v32[kLd32 ? 32 : 1];
+        if constexpr (kLd32) tc_ld32(base + (uint32_t)(32 * c), v32);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           float v[16], o2[16];
-          tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
+          if constexpr (kLd32) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = v32[16 * hh + jj];
+          } else {
+            tc_ld16(base + (uint32_t)(32 * c + 16 * hh), v);
+          }
           if constexpr (E2 == EPI_FWD_SILU) {
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {

@@ -344,6 +344,28 @@ __device__ __forceinline__ float fast_sigmoid(float z) {
   return fmaf(0.5f, t, 0.5f);
 }
 
+// Column pairs in packed fp32 operations (FMUL2 / FFMA2, sm_100 and later);
+// each half is the ordinary IEEE fp32 operation.
+__device__ __forceinline__ float2 f2_bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// fast_sigmoid of both halves
+__device__ __forceinline__ float2 fast_sigmoid2(float2 z) {
+  const float2 h = f2_mul(f2_bc(0.5f), z);
+  float tx, ty;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(tx) : "f"(h.x));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(ty) : "f"(h.y));
+  return f2_fma(f2_bc(0.5f), make_float2(tx, ty), f2_bc(0.5f));
+}
+// silu'(z) / sigmoid(z) = 1 + z (1 - sigmoid(z)), from s = sigmoid(z)
+__device__ __forceinline__ float2 dsilu_factor2(float2 z, float2 sg) {
+  return f2_fma(z, f2_fma(sg, f2_bc(-1.0f), f2_bc(1.0f)), f2_bc(1.0f));
+}
+// elements (2k, 2k + 1) of a row of raw bf16 words
+__device__ __forceinline__ float2 bf16_word_pair(uint32_t x) {
+  return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+}
+
 struct EpiMaps {
   CUtensorMap out, pre, add;
 };
@@ -1310,7 +1332,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       const int mrow = row0(i) + q * 32;
       const int m = mrow + lane;
       const float rs = (m < M && ep1.rowscale) ? ep1.rowscale[m] : 1.0f;
-      float acc = 0.0f;
+      float2 acc2 = f2_bc(0.0f);
       for (int hf = 0; hf < NH && ok; ++hf) {
       // job (i, hf): accumulator slot sj & 1, columns [128 hf, 128 hf + 128) of the tile
       const int sj = i * NH + hf, slot = sj & 1, u = sj >> 1;
@@ -1343,28 +1365,24 @@ __global__ void __launch_bounds__(kCfThreads, 1)
           } else {
             tc_ld16(base + (uint32_t)nl, v);
           }
-          if constexpr (E1 == EPI_FWD_SILU) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              o2[jj] = v[jj];
-              v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+          for (int k = 0; k < 8; ++k) {
+            float2 x = make_float2(v[2 * k], v[2 * k + 1]);
+            if constexpr (E1 == EPI_FWD_SILU) {
+              o2[2 * k] = x.x; o2[2 * k + 1] = x.y;
+              x = f2_mul(f2_mul(x, fast_sigmoid2(x)), f2_bc(rs));
+            } else {
+              const float2 z = bf16_word_pair(zw[8 * hh + k]);
+              const float2 sg = fast_sigmoid2(z);
+              if constexpr (E1 == EPI_HEAD) {
+                // xbar -> the adjoint of the pre-activation of x = u silu(z); row sums of xbar z sigmoid(z)
+                acc2 = f2_fma(f2_mul(x, z), sg, acc2);
+                x = f2_mul(f2_mul(f2_mul(x, f2_bc(rs)), sg), dsilu_factor2(z, sg));
+              } else {
+                x = f2_mul(f2_mul(x, sg), dsilu_factor2(z, sg));
+              }
             }
-          } else if constexpr (E1 == EPI_HEAD) {
-            // xbar -> the adjoint of the pre-activation of x = u silu(z); row sums of xbar z sigmoid(z)
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const float z = bf16_word_elem(zw, 16 * hh + jj);
-              const float sgm = fast_sigmoid(z);
-              acc += v[jj] * z * sgm;
-              v[jj] = v[jj] * rs * sgm * (1.0f + z * (1.0f - sgm));
-            }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const float z = bf16_word_elem(zw, 16 * hh + jj);
-              const float sgm = fast_sigmoid(z);
-              v[jj] = v[jj] * sgm * (1.0f + z * (1.0f - sgm));
-            }
+            v[2 * k] = x.x; v[2 * k + 1] = x.y;
           }
           uint8_t* kbase = sA2 + (nl / kTcBK) * A_BYTES;
           const int r = q * 32 + lane;
@@ -1398,7 +1416,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       }
       if constexpr (E1 == EPI_HEAD) {
         if (hf == NH - 1) {
-          const float tot = row_total(q, h, i, acc, ok);
+          const float tot = row_total(q, h, i, acc2.x + acc2.y, ok);
           if (h == 0 && m < M) ep1.ubar[m] += tot;
         }
       }
@@ -1437,7 +1455,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
       const int m = mrow + lane;
       const float rs = (m < M && ep2.rowscale) ? ep2.rowscale[m] : 1.0f;
       const float srs = (last && m < M) ? ep2.rowsig[m] * rs : 0.0f;
-      float acc = 0.0f;
+      float2 acc2 = f2_bc(0.0f);
       if (!mbar_wait(t2full, i & 1)) { fail(); break; }
       tc_fence_after();
       if (*abort_flag) break;
@@ -1467,31 +1485,36 @@ __global__ void __launch_bounds__(kCfThreads, 1)
           }
           if constexpr (E2 == EPI_FWD_SILU) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              o2[jj] = v[jj];
-              v[jj] = v[jj] * fast_sigmoid(v[jj]) * rs;
+            for (int k = 0; k < 8; ++k) {
+              float2 x = make_float2(v[2 * k], v[2 * k + 1]);
+              o2[2 * k] = x.x; o2[2 * k + 1] = x.y;
+              x = f2_mul(f2_mul(x, fast_sigmoid2(x)), f2_bc(rs));
+              v[2 * k] = x.x; v[2 * k + 1] = x.y;
             }
           } else if constexpr (last) {
             // E_ij = rowscale * sum_n v_n silu(z_n); the pre-activation adjoint
             // sigma_i rowscale v_n silu'(z_n) is the GEMM input of the backward pass
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
-              const float4 x = __ldg(reinterpret_cast<const float4*>(ep2.v + 32 * c + 16 * hh) + k4);
-              const float vv[4] = {x.x, x.y, x.z, x.w};
+              const float4 w4 = __ldg(reinterpret_cast<const float4*>(ep2.v + 32 * c + 16 * hh) + k4);
 #pragma unroll
-              for (int t4 = 0; t4 < 4; ++t4) {
-                const int jj = 4 * k4 + t4;
-                const float sgm = fast_sigmoid(v[jj]);
-                acc += vv[t4] * v[jj] * sgm;
-                v[jj] = srs * vv[t4] * sgm * (1.0f + v[jj] * (1.0f - sgm));
+              for (int t2 = 0; t2 < 2; ++t2) {
+                const int jj = 4 * k4 + 2 * t2;
+                const float2 vv = t2 ? make_float2(w4.z, w4.w) : make_float2(w4.x, w4.y);
+                const float2 z = make_float2(v[jj], v[jj + 1]);
+                const float2 sg = fast_sigmoid2(z);
+                acc2 = f2_fma(f2_mul(vv, z), sg, acc2);
+                const float2 x = f2_mul(f2_mul(f2_mul(vv, f2_bc(srs)), sg), dsilu_factor2(z, sg));
+                v[jj] = x.x; v[jj + 1] = x.y;
               }
             }
           } else if constexpr (in2) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const float z = bf16_word_elem(zw, 16 * hh + jj);
-              const float sgm = fast_sigmoid(z);
-              v[jj] = v[jj] * sgm * (1.0f + z * (1.0f - sgm));
+            for (int k = 0; k < 8; ++k) {
+              const float2 z = bf16_word_pair(zw[8 * hh + k]);
+              const float2 sg = fast_sigmoid2(z);
+              const float2 x = f2_mul(f2_mul(make_float2(v[2 * k], v[2 * k + 1]), sg), dsilu_factor2(z, sg));
+              v[2 * k] = x.x; v[2 * k + 1] = x.y;
             }
           }
           if (hh == 0) {
@@ -1514,7 +1537,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
         ++oc;
       }
       if constexpr (last) {
-        const float tot = row_total(q, h, i, acc, ok);
+        const float tot = row_total(q, h, i, acc2.x + acc2.y, ok);
         if (h == 0 && m < M) {
           ep2.Eout[m] = rs * tot;
           ep2.ubar[m] = ep2.rowsig[m] * tot;

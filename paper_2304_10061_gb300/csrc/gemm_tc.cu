@@ -1077,8 +1077,12 @@ __global__ void __launch_bounds__(kChainThreads, 1)
 // each half released to group 1 as soon as its MMAs complete.  MMA job order:
 //   NH = 1:  G1(0); per tile i: G1(i+1), G2(i)
 //   NH = 2:  G1(0,a); per tile i: G1(i,b), G2(i,a), G1(i+1,a), G2(i,b)
+//            or (late GEMM 2) G1(i,b), G1(i+1,a), G2(i,a), G2(i,b)
 // so that the tensor pipe works on one job while group 1 drains the previous
-// one.  The operand ring (3 stages of 32 KB) carries [A1 k-block | B1 rows of
+// one.  The late order gives group 2 one more GEMM-1 job to drain GEMM 2 of
+// tile i - 1 (GEMM 2 of tile i needs the single GEMM-2 accumulator back); it
+// is used for the pairs it measured faster on (256-wide second layers after an
+// adjoint head, the last latent layer, the adjoint -> linear pair).  The operand ring (3 stages of 32 KB) carries [A1 k-block | B1 rows of
 // the job] for GEMM-1 jobs and B2 k-blocks for GEMM-2 halves in that order.
 // GEMM 1's A operand may be the K-concatenation [A1 | A1b] (split at K1a, a
 // multiple of 64 columns).
@@ -1154,6 +1158,7 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   // accumulator chunks of 32 columns read with one TMEM load (one wait) in the
   // adjoint-head pairs, two 16-column loads otherwise (measured per pair)
   constexpr bool kLd32 = (E1 == EPI_HEAD);
+  constexpr bool kLateG2 = N2 == 256 ? !(E1 == EPI_FWD_SILU && E2 == EPI_FWD_SILU) : (E2 == EPI_LINEAR);
 
   if (threadIdx.x == 0) {
     for (int s2 = 0; s2 < kCfStages; ++s2) {
@@ -1219,8 +1224,13 @@ __global__ void __launch_bounds__(kCfThreads, 1)
         if (!g2(i, 0)) return;
       } else {
         if (!g1(i, 1)) return;
-        if (!g2(i, 0)) return;
-        if (i + 1 < T && !g1(i + 1, 0)) return;
+        if (kLateG2) {
+          if (i + 1 < T && !g1(i + 1, 0)) return;
+          if (!g2(i, 0)) return;
+        } else {
+          if (!g2(i, 0)) return;
+          if (i + 1 < T && !g1(i + 1, 0)) return;
+        }
         if (!g2(i, 1)) return;
       }
     }

@@ -331,7 +331,7 @@ __device__ __forceinline__ void edge_batches(int cnt, Load&& load, Comp&& comp) 
 
 constexpr int kBatchLight = 8;   // edges per batch in passes with one weight array
 constexpr int kBatchHeavy = 4;   // first pass of the layer-1 adjoint (weights + two sbar, most live state)
-constexpr int kBatchLastP1 = 8;  // first pass of the last-layer adjoint (weights + one sbar)
+constexpr int kBatchLast = 6;  // both passes of the last-layer adjoint (measured: 6 beats 8 and 12 there)
 
 // Gamma-type environment sum over the row: G[j][b] = sum_e w[e][j][l(b)] Y[e][b]
 template <typename T, int LMAX, int CPL>
@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
     const int cnt = min(kYSeg, r.re - sb);
     ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
-    uint32_t raw[kBatchLastP1][WS::NW];
-    uint32_t sraw[kBatchLastP1][CPL];
-    edge_batches<kBatchLastP1>(
+    uint32_t raw[kBatchLast][WS::NW];
+    uint32_t sraw[kBatchLast][CPL];
+    edge_batches<kBatchLast>(
         cnt,
         [&](int u, int k) {
           ld_w_raw<T, CPL, LM>(W01, io.ld01, 0, sb + k, r, raw[u]);
@@ -664,8 +664,8 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_bwd_last_kernel(RowIO io, 
     const int sb = r.rb + q * kYSeg, cnt = min(kYSeg, r.re - sb);
     if (sb != staged) ys.load(io.Y, sb, cnt, r.lane);
     staged = sb;
-    uint32_t raw[kBatchLight][WS::NW];
-    edge_batches<kBatchLight>(
+    uint32_t raw[kBatchLast][WS::NW];
+    edge_batches<kBatchLast>(
         cnt, [&](int u, int k) { ld_w_raw<T, CPL, LM>(wsrc, ldw, col0, sb + k, r, raw[u]); },
         [&](int u, int k) {
           const int e = sb + k;

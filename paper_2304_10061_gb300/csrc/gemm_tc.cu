@@ -699,373 +699,6 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
 }
 
 // ===========================================================================
-// Two-layer chain: C2 = epi2( epi1(A1 B1^T) B2^T ) with the intermediate
-// activation kept on chip.  GEMM 1 accumulates in TMEM columns [0, 256), its
-// epilogue writes the bf16 activation straight into shared memory in the
-// 128-byte-swizzled K-major layout the tensor core reads (the A operand of
-// GEMM 2, never written to HBM), and GEMM 2 accumulates in columns [256, 512)
-// (its last 64 columns, for N2 = 320, in [0, 64) once epilogue 1 has drained
-// them).  Epilogue 1: SiLU forward (pre-activation stored) or SiLU adjoint
-// (pre-activation loaded); epilogue 2: SiLU forward, last layer, SiLU adjoint
-// or float32.  Used for consecutive MLP layers (Sec. "Mixed-precision
-// calculations": the MLP GEMMs are the dominant cost).
-// ===========================================================================
-constexpr int kChainEpiWarps = 8;            // warps 2..9: two per TMEM lane quarter
-constexpr int kChainThreads = 64 + 32 * kChainEpiWarps;
-constexpr int kChainEpiSmem = kChainEpiWarps * (4096 + 2048);   // per warp: one out box + one 2 KB input slot
-
-__host__ __device__ constexpr int chain_stage_bytes(int n1, int n2rows) {
-  return kTcBM * kTcBK * 2 + (n1 > n2rows ? n1 : n2rows) * kTcBK * 2;
-}
-__host__ __device__ constexpr size_t chain_smem_bytes(int n1, int n2rows) {
-  return 2 * (size_t)chain_stage_bytes(n1, n2rows) + (size_t)n1 * kTcBM * 2 + kChainEpiSmem + 1024 + 2048;
-}
-
-struct ChainMaps {
-  CUtensorMap a1, b1, b2, b2t;     // b2t: rows 256.. of B2 when N2 > 256 (64-row box)
-  CUtensorMap pre1, out2, pre2;
-};
-
-// One 16-column half of epilogue 2 (modes FWD_SILU, LAST, BWD_SILU, F32).
-__device__ __forceinline__ void epi2_half(const EpiParams& ep, int n, int N, float (&v)[16], const float* z,
-                                          float (&o2)[16], float rs, float sg, float& acc1) {
-  if (ep.epi == EPI_FWD_SILU) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      o2[j] = v[j];
-      v[j] = v[j] * fast_sigmoid(v[j]) * rs;
-    }
-  } else if (ep.epi == EPI_BWD_SILU) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float sgm = fast_sigmoid(z[j]);
-      v[j] = v[j] * sgm * (1.0f + z[j] * (1.0f - sgm));
-    }
-  } else if (ep.epi == EPI_LAST) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float vn = (n + j < N) ? ep.v[n + j] : 0.0f;
-      const float sgm = fast_sigmoid(v[j]);
-      acc1 += vn * v[j] * sgm;
-      v[j] = sg * vn * rs * sgm * (1.0f + v[j] * (1.0f - sgm));
-    }
-  }
-}
-
-template <int N1, int BN2>
-__global__ void __launch_bounds__(kChainThreads, 1)
-    gemm_chain_kernel(const __grid_constant__ ChainMaps cm, EpiParams ep1, EpiParams ep2, int M, int K1, int N2,
-                      int* __restrict__ err) {
-  constexpr int B2ROWS = BN2;                        // rows of B2 per stage (<= 320)
-  constexpr uint32_t STAGE = chain_stage_bytes(N1, B2ROWS);
-  constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
-  constexpr int NK2 = N1 / kTcBK;
-  constexpr int N2A = BN2 > 256 ? 256 : BN2;        // columns of GEMM 2 in TMEM [256, 512)
-  constexpr int N2B = BN2 > 256 ? BN2 - 256 : 0;    // columns of GEMM 2 in TMEM [0, N2B)
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* ring = smem;                              // 2 stages: [A1 | B] each
-  uint8_t* sA2 = smem + 2 * STAGE;                   // NK2 x 16 KB, the on-chip activation
-  uint8_t* sE = sA2 + NK2 * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sE + kChainEpiSmem);
-  uint64_t* empty = full + 2;
-  uint64_t* t1full = empty + 2;
-  uint64_t* t1empty = t1full + 1;
-  uint64_t* a2full = t1empty + 1;
-  uint64_t* t2full = a2full + 1;
-  uint64_t* t2empty = t2full + 1;
-  uint64_t* rsbar = t2empty + 1;        // [4]
-  uint64_t* inbar = rsbar + 4;          // [kChainEpiWarps]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(inbar + kChainEpiWarps);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-  float* rowsum = reinterpret_cast<float*>(tslot + 4);   // [4][32]
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk1 = (K1 + kTcBK - 1) / kTcBK;
-  const int ntiles = (M + kTcBM - 1) / kTcBM;
-
-  if (threadIdx.x == 0) {
-    for (int s2 = 0; s2 < 2; ++s2) {
-      mbar_init(&full[s2], 1);
-      mbar_init(&empty[s2], 1);
-    }
-    mbar_init(t1full, 1);
-    mbar_init(t1empty, kChainEpiWarps);
-    mbar_init(a2full, kChainEpiWarps);
-    mbar_init(t2full, 1);
-    mbar_init(t2empty, kChainEpiWarps);
-    for (int q = 0; q < 4; ++q) mbar_init(&rsbar[q], 1);
-    for (int q = 0; q < kChainEpiWarps; ++q) mbar_init(&inbar[q], 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 1) {
-    tc_alloc(tslot, 512);
-    tc_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      uint32_t g = 0;
-      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-        const int m0 = t * kTcBM;
-        for (int kb = 0; kb < nk1 + NK2; ++kb, ++g) {
-          const uint32_t s2 = g & 1u, r = g >> 1;
-          if (g >= 2u && !mbar_wait(&empty[s2], (r - 1) & 1)) {
-            atomicOr(err, kErrTimeout);
-            *abort_flag = 1;
-            break;
-          }
-          uint8_t* st = ring + s2 * STAGE;
-          if (kb < nk1) {
-            mbar_expect_tx(&full[s2], A_BYTES + N1 * kTcBK * 2);
-            tma_load_2d(st, &cm.a1, &full[s2], kb * kTcBK, m0);
-            tma_load_2d(st + A_BYTES, &cm.b1, &full[s2], kb * kTcBK, 0);
-          } else {
-            const int k2 = kb - nk1;
-            mbar_expect_tx(&full[s2], B2ROWS * kTcBK * 2);
-            tma_load_2d(st + A_BYTES, &cm.b2, &full[s2], k2 * kTcBK, 0);
-            if (N2B) tma_load_2d(st + A_BYTES + 256 * kTcBK * 2, &cm.b2t, &full[s2], k2 * kTcBK, 256);
-          }
-        }
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t id1 = idesc_bf16<N1>();
-      constexpr uint32_t id2a = idesc_bf16<N2A>();
-      constexpr uint32_t id2b = idesc_bf16<(N2B > 0 ? N2B : 16)>();
-      uint32_t g = 0;
-      int lt = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
-        const uint32_t pe = (lt & 1) ^ 1, pf = lt & 1;
-        bool ok = !*abort_flag && mbar_wait(t1empty, pe);
-        if (ok && N2B) ok = mbar_wait(t2empty, pe);          // acc2b shares acc1's columns
-        if (ok) {
-          tc_fence_after();
-          for (int kb = 0; kb < nk1; ++kb, ++g) {
-            const uint32_t s2 = g & 1u, r = g >> 1;
-            if (!mbar_wait(&full[s2], r & 1)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a = smem_u32(ring + s2 * STAGE), b = a + A_BYTES;
-#pragma unroll
-            for (int k = 0; k < kTcBK / 16; ++k)
-              tc_mma(tmem, sdesc_sw128(a + k * 32), sdesc_sw128(b + k * 32), id1, (kb > 0 || k > 0) ? 1u : 0u);
-            tc_commit(&empty[s2]);
-          }
-        }
-        tc_commit(t1full);
-        if (ok) ok = mbar_wait(a2full, pf);
-        if (ok && !N2B) ok = mbar_wait(t2empty, pe);
-        if (ok) {
-          tc_fence_after();
-          for (int kb = 0; kb < NK2; ++kb, ++g) {
-            const uint32_t s2 = g & 1u, r = g >> 1;
-            if (!mbar_wait(&full[s2], r & 1)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a = smem_u32(sA2 + kb * A_BYTES), b = smem_u32(ring + s2 * STAGE) + A_BYTES;
-#pragma unroll
-            for (int k = 0; k < kTcBK / 16; ++k) {
-              tc_mma(tmem + 256, sdesc_sw128(a + k * 32), sdesc_sw128(b + k * 32), id2a, (kb > 0 || k > 0) ? 1u : 0u);
-              if (N2B)
-                tc_mma(tmem, sdesc_sw128(a + k * 32), sdesc_sw128(b + 256 * 128 + k * 32), id2b,
-                       (kb > 0 || k > 0) ? 1u : 0u);
-            }
-            tc_commit(&empty[s2]);
-          }
-        }
-        tc_commit(t2full);
-        if (!ok) {
-          atomicOr(err, kErrTimeout);
-          *abort_flag = 1;
-          break;
-        }
-      }
-    }
-    __syncwarp();
-  } else {
-    const int q = warp & 3;
-    const int ew = warp - 2;
-    const int h = ew >> 2;
-    uint8_t* ob = sE + ew * (4096 + 2048);
-    uint8_t* ib = ob + 4096;
-    uint32_t in_par = 0;
-    const bool pre1_in = (ep1.epi == EPI_BWD_SILU);
-    const bool pre1_out = (ep1.epi == EPI_FWD_SILU) && ep1.pre;
-    const bool pre2_in = (ep2.epi == EPI_BWD_SILU);
-    const bool pre2_out = (ep2.epi == EPI_FWD_SILU) && ep2.pre;
-    const bool out2_f32 = (ep2.epi == EPI_F32);
-    const bool rows2 = (ep2.epi == EPI_LAST);
-    auto fetch = [&](const CUtensorMap* tm, int nb, int mb) {
-      if (lane == 0) {
-        mbar_expect_tx(&inbar[ew], 2048);
-        tma_load_2d(ib, tm, &inbar[ew], nb, mb);
-      }
-    };
-    auto take = [&](float (&zc)[32]) {
-      if (!mbar_wait(&inbar[ew], in_par)) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        *abort_flag = 1;
-      }
-      in_par ^= 1u;
-      ld_bf16_row(ib, lane, zc);
-      fence_async_smem();      // the slot's generic reads are ordered before the next TMA write into it
-      __syncwarp();
-    };
-    auto out_wait = [&]() {
-      if (lane == 0) bulk_wait_read0();
-      __syncwarp();
-    };
-    int lt = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
-      const uint32_t pf = lt & 1;
-      const int m0 = t * kTcBM, mrow = m0 + q * 32, m = mrow + lane;
-      const bool live = m < M;
-      const float rs1 = (live && ep1.rowscale) ? ep1.rowscale[m] : 1.0f;
-      const float rs2 = (live && ep2.rowscale) ? ep2.rowscale[m] : 1.0f;
-      const float sg2 = (live && ep2.rowsig) ? ep2.rowsig[m] : 1.0f;
-      const uint32_t lanebase = (uint32_t)(q * 32) << 16;
-      // ---- epilogue 1: acc1 -> on-chip activation (and pre-activation out) ----
-      if (!mbar_wait(t1full, pf)) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      if (pre1_in) fetch(&cm.pre1, 32 * h, mrow);
-      for (int c = h; c < N1 / 32; c += 2) {
-        float zc[32];
-        if (pre1_in) {
-          take(zc);
-          if (c + 2 < N1 / 32) fetch(&cm.pre1, 32 * (c + 2), mrow);
-        }
-        if (pre1_out) out_wait();
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int nl = 32 * c + 16 * hh;
-          float v[16], o2[16];
-          tc_ld16(tmem + lanebase + (uint32_t)nl, v);
-          if (ep1.epi == EPI_FWD_SILU) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              o2[j] = v[j];
-              v[j] = v[j] * fast_sigmoid(v[j]) * rs1;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float z = zc[16 * hh + j];
-              const float sgm = fast_sigmoid(z);
-              v[j] = v[j] * sgm * (1.0f + z * (1.0f - sgm));
-            }
-          }
-          // activation into the swizzled K-major A2 tile: k-block nl/64, 16-byte units (nl%64)/8 + {0,1}
-          uint8_t* kbase = sA2 + (nl / kTcBK) * A_BYTES;
-          const int r = q * 32 + lane;
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int unit = ((nl % kTcBK) >> 3) + u;
-            uint4 x = make_uint4(pack_bf16x2(v[8 * u + 0], v[8 * u + 1]), pack_bf16x2(v[8 * u + 2], v[8 * u + 3]),
-                                 pack_bf16x2(v[8 * u + 4], v[8 * u + 5]), pack_bf16x2(v[8 * u + 6], v[8 * u + 7]));
-            *reinterpret_cast<uint4*>(kbase + r * 128 + ((unit ^ (r & 7)) << 4)) = x;
-          }
-          if (pre1_out) st_bf16_half(ob, lane, hh, o2);
-        }
-        if (pre1_out) {
-          fence_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            tma_store_2d(&cm.pre1, ob, 32 * c, mrow);
-            bulk_commit();
-          }
-        }
-      }
-      tc_fence_before();
-      fence_async_smem();          // generic-proxy writes of A2 -> visible to the tensor core
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(t1empty);
-        mbar_arrive(a2full);
-      }
-      // ---- epilogue 2 ----
-      if (!mbar_wait(t2full, pf)) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      const int nch2 = (N2 + 31) / 32;
-      float acc1 = 0.0f;
-      if (pre2_in && h < nch2) fetch(&cm.pre2, 32 * h, mrow);
-      for (int c = h; c < nch2; c += 2) {
-        float zc[32];
-        if (pre2_in) {
-          take(zc);
-          if (c + 2 < nch2) fetch(&cm.pre2, 32 * (c + 2), mrow);
-        }
-        out_wait();
-        const uint32_t col = (32 * c < 256) ? 256u + 32u * c : (uint32_t)(32 * c - 256);
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int n = 32 * c + 16 * hh;
-          float v[16], o2[16];
-          tc_ld16(tmem + lanebase + col + 16 * hh, v);
-          epi2_half(ep2, n, N2, v, pre2_in ? zc + 16 * hh : zc, o2, rs2, sg2, acc1);
-          if (out2_f32) st_f32_half(ob, lane, hh, v);
-          else st_bf16_half(ob, lane, hh, v);
-          if (pre2_out) st_bf16_half(ob + 2048, lane, hh, o2);
-        }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          tma_store_2d(&cm.out2, ob, 32 * c, mrow);
-          if (pre2_out) tma_store_2d(&cm.pre2, ob + 2048, 32 * c, mrow);
-          bulk_commit();
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (!rows2 || h == 1) {
-        if (lane == 0) mbar_arrive(t2empty);
-      }
-      if (rows2) {
-        float* rsum = rowsum + q * 32;
-        if (h == 1) {
-          rsum[lane] = acc1;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&rsbar[q]);
-        } else {
-          if (!mbar_wait(&rsbar[q], pf)) {
-            if (lane == 0) atomicOr(err, kErrTimeout);
-            *abort_flag = 1;
-          }
-          const float tot = acc1 + rsum[lane];
-          if (live) {
-            ep2.Eout[m] = rs2 * tot;
-            ep2.ubar[m] = sg2 * tot;
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(t2empty);
-        }
-      }
-    }
-    if (lane == 0) bulk_wait_all();
-    __syncwarp();
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tc_dealloc(tmem, 512);
-  }
-}
-
-// ===========================================================================
 // Pipelined chain (N1 = 128 or 256, N2 <= 256): C2 = epi2(epi1(A1 B1^T) B2^T)
 // with the intermediate activation kept on chip.  GEMM 1 runs as NH = N1/128
 // jobs of 128 output columns each, into a two-slot ring of 128-column TMEM
@@ -1675,49 +1308,6 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
 }
 
 
-template <int N1, int BN2>
-static bool launch_chain(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why) {
-  constexpr size_t smem = chain_smem_bytes(N1, BN2);
-  static_assert(smem <= 232448, "chain kernel shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_chain_kernel<N1, BN2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) {
-      if (why) *why = std::string("cudaFuncSetAttribute (chain): ") + cudaGetErrorString(e);
-      return false;
-    }
-    attr_set = true;
-  }
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
-  const bf16* B1 = g1.trans ? g1.W->b16T : g1.W->b16;
-  const int ldb1 = g1.trans ? g1.W->ldT : g1.W->ld;
-  const bf16* B2 = g2.trans ? g2.W->b16T : g2.W->b16;
-  const int ldb2 = g2.trans ? g2.W->ldT : g2.W->ld;
-  ChainMaps cm;
-  memset(&cm, 0, sizeof cm);
-  bool ok = make_tmap(&cm.a1, g1.A, (uint64_t)g1.K, (uint64_t)g1.M, (uint64_t)g1.lda * 2, kTcBK, kTcBM) &&
-            make_tmap(&cm.b1, B1, (uint64_t)g1.K, (uint64_t)g1.N, (uint64_t)ldb1 * 2, kTcBK, N1) &&
-            make_tmap(&cm.b2, B2, (uint64_t)g2.K, (uint64_t)g2.N, (uint64_t)ldb2 * 2, kTcBK, BN2 > 256 ? 256 : BN2);
-  if (ok && BN2 > 256) ok = make_tmap(&cm.b2t, B2, (uint64_t)g2.K, (uint64_t)g2.N, (uint64_t)ldb2 * 2, kTcBK, 64);
-  if (ok && g1.pre) ok = make_box_map(&cm.pre1, g1.pre, g1.N, g1.M, g1.ldp, 2);
-  if (ok) ok = make_box_map(&cm.out2, g2.out, g2.N, g2.M, g2.ldo, g2.epi == EPI_F32 ? 4 : 2);
-  if (ok && g2.pre) ok = make_box_map(&cm.pre2, g2.pre, g2.N, g2.M, g2.ldp, 2);
-  if (!ok) {
-    if (why) *why = "cuTensorMapEncodeTiled failed (chain)";
-    return false;
-  }
-  const int tiles = (g1.M + kTcBM - 1) / kTcBM;
-  const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-  gemm_chain_kernel<N1, BN2><<<grid, kChainThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M, g1.K, g2.N, d_err);
-  return true;
-}
-
 template <int N1, int N2, int E1, int E2>
 static bool launch_chain_pipe(const GemmArgs& g1, const GemmArgs& g2, const bf16* B1, int ldb1, const bf16* B2,
                               int ldb2, cudaStream_t st, int* d_err, std::string* why) {
@@ -1763,10 +1353,9 @@ static bool launch_chain_pipe(const GemmArgs& g1, const GemmArgs& g2, const bf16
   return true;
 }
 
-// Two consecutive layers in one kernel: the pipelined kernel for the pairs it
-// takes (see gemm_chain_pipe_kernel), the two-stage kernel for a few other
-// forward / adjoint shapes.  Returns false with `why` empty when the pair is
-// not supported (the caller then runs the two GEMMs separately).
+// Two consecutive layers in one kernel (see gemm_chain_pipe_kernel) for the
+// pairs it is instantiated for.  Returns false with `why` empty when the pair
+// is not supported (the caller then runs the two GEMMs separately).
 bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why) {
   if (why) why->clear();
   if (g1.M <= 0) return true;
@@ -1800,19 +1389,6 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
     PIPE(256, 64, EPI_BWD_SILU, EPI_LINEAR)
 #undef PIPE
   }
-  // the two-stage kernel: plain weights only
-  if (g1.A2 || g1.Bover || g2.Bover || g1.b_row0 || g2.b_row0) return false;
-  if (!(g1.epi == EPI_FWD_SILU || g1.epi == EPI_BWD_SILU)) return false;
-  if (!(g2.epi == EPI_FWD_SILU || g2.epi == EPI_BWD_SILU || g2.epi == EPI_LAST || g2.epi == EPI_LINEAR ||
-        g2.epi == EPI_F32))
-    return false;
-  if (g1.epi == EPI_BWD_SILU && !g1.pre) return false;
-  if (g2.epi == EPI_BWD_SILU && !g2.pre) return false;
-  const int bn2 = (g2.N + 31) / 32 * 32;
-  if (g1.N == 256 && bn2 == 256) return launch_chain<256, 256>(g1, g2, st, d_err, why);
-  if (g1.N == 256 && bn2 == 320) return launch_chain<256, 320>(g1, g2, st, d_err, why);
-  if (g1.N == 128 && bn2 == 256) return launch_chain<128, 256>(g1, g2, st, d_err, why);
-  if (g1.N == 128 && bn2 == 64) return launch_chain<128, 64>(g1, g2, st, d_err, why);
   return false;
 }
 

@@ -22,6 +22,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -726,9 +728,20 @@ bool invert3(const double* m, double* inv) {
   return true;
 }
 
+// Interned profiling labels: the returned pointer stays valid for the life of
+// the process (a deque never moves its elements), from any thread.
+static const char* intern_label(const std::string& n) {
+  static std::mutex mu;
+  static std::deque<std::string> names;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& x : names)
+    if (x == n) return x.c_str();
+  names.push_back(n);
+  return names.back().c_str();
+}
+
 // Stable profiling label of a GEMM: which linear map, forward or transposed.
 const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
-  static std::vector<std::string> names;
   std::string n;
   for (size_t k = 0; k < c->tb.size(); ++k)
     if (W == &c->tb[k]) n = "two_body." + std::to_string(k);
@@ -740,10 +753,7 @@ const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
   const char* en[] = {"silu", "f32", "dsilu", "head", "last", "linear"};
   n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : "gemm_simt/") + n + (trans ? "^T" : "") + ":" +
       en[epi];
-  for (auto& x : names)
-    if (x == n) return x.c_str();
-  names.push_back(n);
-  return names.back().c_str();
+  return intern_label(n);
 }
 
 template <typename T>
@@ -798,12 +808,9 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
                             (g1.epi == EPI_BWD_SILU && g2.epi == EPI_LINEAR && g2.N <= 256);
     if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
       std::string why;
-      static std::vector<std::string> names;
-      std::string nm = std::string(gemm_label(c, g1.W, g1.trans, g1.epi)) + "+" +
-                       std::string(gemm_label(c, g2.W, g2.trans, g2.epi)).substr(8);
-      const char* label = nullptr;
-      for (auto& x : names) if (x == nm) label = x.c_str();
-      if (!label) { names.push_back(nm); label = names.back().c_str(); }
+      const std::string l2 = gemm_label(c, g2.W, g2.trans, g2.epi);
+      const char* label = intern_label(std::string(gemm_label(c, g1.W, g1.trans, g1.epi)) + "+" +
+                                       l2.substr(l2.find('/') + 1));
       bool launched;
       {
         ProfScope ps(c, label, 2.0 * Ec * ((double)g1.N * g1.K + (double)g2.N * g2.K),

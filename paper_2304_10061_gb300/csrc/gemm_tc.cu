@@ -1201,7 +1201,36 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   }
 }
 
-static int g_num_sms = 0;
+// Per-device launch state: a kernel's opt-in to large dynamic shared memory is
+// a per-device function attribute, and the SM count sizes the persistent grids.
+constexpr int kMaxDevices = 64;
+static int g_num_sms[kMaxDevices] = {};
+
+static int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return (d >= 0 && d < kMaxDevices) ? d : 0;
+}
+static int num_sms(int dev) {
+  if (!g_num_sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms[dev] = n > 0 ? n : 148;
+  }
+  return g_num_sms[dev];
+}
+// opt `kernel` in to `bytes` of dynamic shared memory on device `dev` (once per device)
+template <typename K>
+static bool smem_opt_in(K kernel, int bytes, bool (&done)[kMaxDevices], int dev, std::string* why) {
+  if (done[dev]) return true;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) {
+    if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+    return false;
+  }
+  done[dev] = true;
+  return true;
+}
 
 // 2-D tensor map over a row-major [rows][ld] array of `esize`-byte elements,
 // box 32 x 32, swizzle matched to the row width of the box.
@@ -1219,22 +1248,10 @@ static bool make_box_map(CUtensorMap* tm, const void* base, int cols, int rows, 
 
 template <int BN, int EPQ>
 static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st, int* d_err, std::string* why) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, EPQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTcSmemMax);
-    if (e != cudaSuccess) {
-      if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
-      return false;
-    }
-    attr_set = true;
-  }
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
+  static bool attr_set[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!smem_opt_in(gemm_tc_kernel<BN, EPQ>, kTcSmemMax, attr_set, dev, why)) return false;
+  const int nsm = num_sms(dev);
   CUtensorMap ta, ta2, tb;
   const int K1 = g.A2 ? g.K1 : g.K;
   if (!make_tmap(&ta, g.A, (uint64_t)K1, (uint64_t)g.M, (uint64_t)g.lda * 2, kTcBK, kTcBM) ||
@@ -1261,7 +1278,7 @@ static bool launch_bn(const GemmArgs& g, const bf16* B, int ldb, cudaStream_t st
   }
   const size_t smem = tc_smem_bytes<BN, EPQ>(lay);
   const int tiles = ((g.M + kTcBM - 1) / kTcBM) * ((g.N + BN - 1) / BN);
-  const int grid = tiles < g_num_sms ? tiles : g_num_sms;
+  const int grid = tiles < nsm ? tiles : nsm;
   gemm_tc_kernel<BN, EPQ><<<grid, tc_threads<EPQ>(), smem, st>>>(ta, ta2, tb, em, make_epi(g), lay, g.M, g.N, g.K,
                                                                   K1, d_err);
   return true;
@@ -1313,22 +1330,10 @@ static bool launch_chain_pipe(const GemmArgs& g1, const GemmArgs& g2, const bf16
                               int ldb2, cudaStream_t st, int* d_err, std::string* why) {
   constexpr size_t smem = cf_smem_bytes(N1, N2);
   static_assert(smem <= 232448, "pipelined chain shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_chain_pipe_kernel<N1, N2, E1, E2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-      if (why) *why = std::string("cudaFuncSetAttribute (chain): ") + cudaGetErrorString(e);
-      return false;
-    }
-    attr_set = true;
-  }
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
+  static bool attr_set[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!smem_opt_in(gemm_chain_pipe_kernel<N1, N2, E1, E2>, (int)smem, attr_set, dev, why)) return false;
+  const int nsm = num_sms(dev);
   const int K1a = g1.A2 ? g1.K1 : g1.K;
   PipeMaps cm;
   memset(&cm, 0, sizeof cm);
@@ -1347,7 +1352,7 @@ static bool launch_chain_pipe(const GemmArgs& g1, const GemmArgs& g2, const bf16
     return false;
   }
   const int tiles = (g1.M + kTcBM - 1) / kTcBM;
-  const int grid = tiles < g_num_sms ? tiles : g_num_sms;
+  const int grid = tiles < nsm ? tiles : nsm;
   gemm_chain_pipe_kernel<N1, N2, E1, E2><<<grid, kCfThreads, smem, st>>>(cm, make_epi(g1), make_epi(g2), g1.M,
                                                                           g1.K, K1a, d_err);
   return true;

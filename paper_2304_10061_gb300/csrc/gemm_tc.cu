@@ -1,20 +1,26 @@
-// BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
+// BF16 GEMMs on the 5th-generation tensor cores (tcgen05, sm_103a):
 //   C[M x N] = A[M x K] B^T,  A = edge activations (bf16, row-major, K contiguous),
 //   B = weights (bf16, [N][K], K contiguous), float32 accumulation in TMEM,
-// with the epilogues of epilogue.cuh (SiLU forward with pre-activation store,
-// float32 output with addend, SiLU adjoint).  These are the MLP GEMMs of the
+// with fused epilogues (SiLU forward with pre-activation store, SiLU adjoint,
+// the adjoint head of x = u silu(z), the last latent layer with the folded
+// edge energy, linear / float32 outputs).  These are the MLP GEMMs of the
 // two-body, latent and embedding/env-weight maps (Sec. "Mixed-precision
 // calculations": matrix multiplications carry most of the cost).
 //
-// One CTA computes a 128 x BN tile: warp 0 issues TMA loads of 128 x 64 (A)
-// and BN x 64 (B) bf16 tiles into a STAGES-deep shared-memory ring (128-byte
-// swizzle), warp 1 allocates BN TMEM columns and issues
-// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = BN, K = 16 per instruction)
-// from one thread, committing each stage back to the producer through an
-// mbarrier; warps 2-5 read the accumulator with tcgen05.ld (each warp its
-// 32-lane quarter of TMEM) and run the epilogue.  Every mbarrier wait is
-// bounded (clock64 limit); on expiry the kernel sets the error word and
-// unwinds (the host reports ALLEGRO_E_TIMEOUT).
+// gemm_tc_kernel<BN, EPQ>: one layer.  Persistent: one CTA per SM walks 128 x BN
+// tiles (the column blocks of a row block on neighbouring CTAs, so A rows are
+// shared through L2).  Warp 0 issues TMA loads of 128 x 64 (A) and BN x 64 (B)
+// bf16 tiles into a shared-memory ring (128-byte swizzle), warp 1 allocates
+// two BN-column TMEM accumulators and issues tcgen05.mma.cta_group::1.kind::f16
+// (M = 128, N = BN, K = 16 per instruction) from one thread, 4 x EPQ epilogue
+// warps (EPQ per 32-lane TMEM quarter) drain the other accumulator with
+// tcgen05.ld and write 32 x 32 boxes through shared memory with TMA stores.
+//
+// gemm_chain_pipe_kernel<N1, N2, E1, E2>: two consecutive layers with the
+// intermediate activation kept on chip (described at the kernel).
+//
+// Every mbarrier wait is bounded (clock64 limit); on expiry the kernel sets the
+// error word and unwinds (the host reports ALLEGRO_E_TIMEOUT).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>

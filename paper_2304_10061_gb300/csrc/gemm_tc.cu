@@ -393,13 +393,15 @@ __device__ __forceinline__ float bf16_word_elem(const uint32_t (&w)[16], int j) 
 // Persistent kernel: CTA b handles tiles b, b + gridDim.x, ...  Two TMEM
 // accumulator buffers: the MMA warp fills buffer (t & 1) while the epilogue
 // warps drain the other, and the TMA producer runs ahead through the
-// shared-memory ring across tile boundaries.  Four epilogue warps share each
-// 32-lane quarter of TMEM (warp h takes the 32-column chunks h, h + 4, ...);
-// per chunk a warp takes its epilogue inputs (pre-activation, addend; fetched
-// by TMA one chunk ahead), computes in registers 16 columns at a time, stages
-// the results in swizzled shared memory and writes them back with TMA bulk
-// stores.
-// With 18 warps five share one SM sub-partition's 16K registers: at most 96 per thread.
+// shared-memory ring across tile boundaries.  EPQ (2 or 4) epilogue warps
+// share each 32-lane quarter of TMEM (warp h takes the 32-column chunks h,
+// h + EPQ, ...); per chunk a warp takes its epilogue inputs (pre-activation,
+// addend; fetched by TMA one chunk ahead), computes in registers 16 columns
+// at a time, stages the results in swizzled shared memory and writes them
+// back with TMA bulk stores.  The head and last-layer modes combine a
+// quarter's partial row sums in a fixed warp order.
+// With 18 warps (EPQ = 4) five share one SM sub-partition's 16K registers: at
+// most 96 per thread.
 template <int BN, int EPQ>
 __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,

@@ -23,6 +23,11 @@ Readings where the paper defers to the Allegro paper or is silent:
   * Edge energy  E_ij = MLP_E(x^{L_max});  E_i = sum_j E_ij;
     Etilde_i = sigma_{Z_i} E_i + mu_{Z_i};  E = sum_i Etilde_i  (float64).
   * Virial  W_ab = - sum_e d_{e,a} dE/dd_{e,b}.
+  * Per-ordered-species-pair cutoffs (Sec. "Species-dependent cutoffs", values in
+    "Training details"), when the architecture carries a table: edge (i, j) takes
+    r_c = pair_rc[Z_i][Z_j] (row = centre species) in the neighbour rule, the
+    Bessel basis and the envelope alike, so each pair's basis spans its own range
+    and its terms vanish smoothly at its own cutoff.
 """
 from __future__ import annotations
 
@@ -40,6 +45,13 @@ torch_f64 = torch.float64
 def bessel(r: torch.Tensor, r_c: float, n: int) -> torch.Tensor:
     k = torch.arange(1, n + 1, dtype=r.dtype)
     return math.sqrt(2.0 / r_c) * torch.sin(k * math.pi * r[..., None] / r_c) / r[..., None]
+
+
+def bessel_pair(r: torch.Tensor, r_c: torch.Tensor, n: int) -> torch.Tensor:
+    """The Bessel basis with a per-edge cutoff r_c [E] (same formula as `bessel`)."""
+    k = torch.arange(1, n + 1, dtype=r.dtype)
+    rc = r_c[..., None]
+    return torch.sqrt(2.0 / rc) * torch.sin(k * math.pi * r[..., None] / rc) / r[..., None]
 
 
 def envelope(x: torch.Tensor, p: int) -> torch.Tensor:
@@ -92,10 +104,15 @@ class AllegroOracle:
         a = self.arch
         r = torch.sqrt((d * d).sum(-1))
         rhat = d / r[:, None]
-        B = bessel(r, a.r_c, a.n_bessel)
-        u = envelope(r / a.r_c, a.p_env)[:, None]
-        Y = so3.real_sh(a.lmax, rhat)                                    # [E, S]
         Z = torch.as_tensor(np.asarray(species), dtype=torch.int64)
+        if a.pair_rc is None:
+            B = bessel(r, a.r_c, a.n_bessel)
+            u = envelope(r / a.r_c, a.p_env)[:, None]
+        else:
+            rc = torch.tensor(a.pair_rc, dtype=torch_f64)[Z[torch.as_tensor(i)], Z[torch.as_tensor(j)]]
+            B = bessel_pair(r, rc, a.n_bessel)
+            u = envelope(r / rc, a.p_env)[:, None]
+        Y = so3.real_sh(a.lmax, rhat)                                    # [E, S]
         Zi = torch.nn.functional.one_hot(Z[torch.as_tensor(i)], a.n_species).to(torch_f64)
         Zj = torch.nn.functional.one_hot(Z[torch.as_tensor(j)], a.n_species).to(torch_f64)
         h = torch.cat([Zi, Zj, B], dim=1)

@@ -17,6 +17,11 @@ positions this is the usual ceil(r_c / w_k) plus one layer, which adds
 candidates, never edges).  numpy evaluates elementwise float64 operations without
 contraction, so the arithmetic above is what runs.
 
+Per-ordered-species-pair cutoffs (Sec. "Species-dependent cutoffs"): with a
+table pair_rc[Z_i][Z_j] (row = centre species) the test is r2 < rc*rc with
+rc = pair_rc[Z_i][Z_j] for the candidate's ordered pair, every other part of
+the rule unchanged; the image range uses the largest entry.
+
 `brute_force` is the definition, applied to every candidate.
 `neighbor_list` applies the same test to a superset of candidates found with
 a k-d tree at radius r_c (1 + 1e-6) + 1e-9; it is checked against
@@ -75,11 +80,22 @@ def _sort(i, j, S):
     return i[order], j[order], S[order]
 
 
-def brute_force(pos, cell, pbc, r_c, centers=None):
-    """Every (i, j, S) candidate tested with the exact FP64 rule."""
+def _pair_rc2(species, pair_rc, ii, jj):
+    """Squared cutoff of each candidate's ordered (centre, neighbour) species pair."""
+    t = np.asarray(pair_rc, dtype=np.float64)
+    z = np.asarray(species, dtype=np.int64)
+    rc = t[z[ii], z[jj]]
+    return rc * rc
+
+
+def brute_force(pos, cell, pbc, r_c, centers=None, species=None, pair_rc=None):
+    """Every (i, j, S) candidate tested with the exact FP64 rule (per ordered
+    species pair when `pair_rc` is given; `r_c` is then its largest entry)."""
     pos = np.asarray(pos, dtype=np.float64)
     n = pos.shape[0]
     centers = np.arange(n) if centers is None else np.asarray(centers, dtype=np.int64)
+    if pair_rc is not None:
+        r_c = float(np.max(np.asarray(pair_rc, dtype=np.float64)))
     rc2 = float(r_c) * float(r_c)
     I, J, SS = [], [], []
     for S in _images(cell, pbc, r_c, pos):
@@ -87,7 +103,7 @@ def brute_force(pos, cell, pbc, r_c, centers=None):
         ii = np.repeat(centers, n)
         jj = np.tile(np.arange(n), len(centers))
         Sa = np.tile(np.array(S, dtype=np.int64), (ii.size, 1))
-        keep = _exact_test(pos, ii, jj, Sa, off, rc2)
+        keep = _exact_test(pos, ii, jj, Sa, off, rc2 if pair_rc is None else _pair_rc2(species, pair_rc, ii, jj))
         I.append(ii[keep]); J.append(jj[keep]); SS.append(Sa[keep])
     i = np.concatenate(I).astype(np.int64)
     j = np.concatenate(J).astype(np.int64)
@@ -95,7 +111,7 @@ def brute_force(pos, cell, pbc, r_c, centers=None):
     return _sort(i, j, S)
 
 
-def neighbor_list(pos, cell, pbc, r_c, centers=None):
+def neighbor_list(pos, cell, pbc, r_c, centers=None, species=None, pair_rc=None):
     """Same result as `brute_force`, with k-d tree candidate pruning."""
     from scipy.spatial import cKDTree
 
@@ -104,6 +120,8 @@ def neighbor_list(pos, cell, pbc, r_c, centers=None):
     centers = np.arange(n) if centers is None else np.asarray(centers, dtype=np.int64)
     if n == 0 or centers.size == 0:
         return (np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros((0, 3), np.int64))
+    if pair_rc is not None:
+        r_c = float(np.max(np.asarray(pair_rc, dtype=np.float64)))
     rc2 = float(r_c) * float(r_c)
     rad = float(r_c) * (1.0 + 1e-6) + 1e-9
     lo = pos[centers].min(0) - rad
@@ -127,7 +145,7 @@ def neighbor_list(pos, cell, pbc, r_c, centers=None):
     cell_arr = np.zeros((3, 3)) if cell is None else np.asarray(cell, dtype=np.float64)
     off = (Sa[:, 0:1].astype(np.float64) * cell_arr[0] + Sa[:, 1:2].astype(np.float64) * cell_arr[1]) \
         + Sa[:, 2:3].astype(np.float64) * cell_arr[2]
-    keep = _exact_test(pos, ii, jj, Sa, off, rc2)
+    keep = _exact_test(pos, ii, jj, Sa, off, rc2 if pair_rc is None else _pair_rc2(species, pair_rc, ii, jj))
     return _sort(ii[keep], jj[keep], Sa[keep])
 
 

@@ -14,6 +14,7 @@ from .structures import (
     SPECIES_NAMES,
     SPECIES_MASSES,
     WATER_MIX,
+    paper_pair_cutoffs,
 )
 from .weights import Arch, make_weights, weights_to_blob, blob_to_weights, ARCHS
 from .configs import CONFIGS, make_config

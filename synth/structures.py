@@ -21,6 +21,16 @@ import numpy as np
 SPECIES_NAMES = ("H", "O", "C", "N", "S")
 # Atomic masses in amu, same order.
 SPECIES_MASSES = (1.008, 15.999, 12.011, 14.007, 32.06)
+def paper_pair_cutoffs(names=None, default: float = 4.0):
+    """Per-ordered-species-pair cutoffs of the paper's production model (Sec. "Training
+    details"): H-H 3.0, H-C 1.25, H-O 1.25, O-H 3.0 Angstrom, every other ordered pair
+    `default`.  Row = centre species, column = neighbour species, so H-C (an H centre
+    with a C neighbour) is 1.25 while C-H keeps the default."""
+    names = SPECIES_NAMES if names is None else tuple(names)
+    special = {("H", "H"): 3.0, ("H", "C"): 1.25, ("H", "O"): 1.25, ("O", "H"): 3.0}
+    return tuple(tuple(float(special.get((a, b), default)) for b in names) for a in names)
+
+
 # Water / solvated-protein-like composition: H 63 %, O 30 %, C 5 %, N 1.5 %, S 0.5 %.
 WATER_MIX = (0.63, 0.30, 0.05, 0.015, 0.005)
 

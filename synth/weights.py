@@ -24,7 +24,7 @@ from __future__ import annotations
 
 import struct
 from dataclasses import dataclass, asdict
-from typing import Dict, List, Tuple
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -45,6 +45,14 @@ class Arch:
     p_env: int = 6
     r_c: float = 4.0
     avg_num_neighbors: float = 27.0
+    # cutoff per ordered (centre species, neighbour species) pair; None: r_c for every pair.
+    # Not part of the weights blob (the float32 / BF16 library path takes one r_c).
+    pair_rc: Optional[Tuple[Tuple[float, ...], ...]] = None
+
+    @property
+    def max_rc(self) -> float:
+        """Largest cutoff of any ordered pair (the neighbour search radius)."""
+        return max(max(row) for row in self.pair_rc) if self.pair_rc is not None else self.r_c
 
     @property
     def n_in_two_body(self) -> int:

@@ -88,6 +88,21 @@ allegro_status allegro_reserve(allegro_ctx* ctx, int64_t atom_cap, int64_t edge_
                                int32_t fixed, int64_t chunk_edges);
 
 /*
+ * allegro_set_pair_cutoffs -- per-ordered-species-pair cutoffs (Sec.
+ * "Species-dependent cutoffs"): edge (i, j) exists iff |d|^2 < rc^2 with
+ * rc = pair_rc[Z_i * n_species + Z_j] (row = the centre atom's model species,
+ * column = the neighbour's), and its Bessel basis and envelope use that rc
+ * (B_n(r) = sqrt(2/rc) sin(n pi r / rc) / r, u(r / rc)).
+ *   pair_rc: host memory, n_species x n_species float64, every entry in
+ *       (0, r_c] of the model; NULL restores the model cutoff for every pair.
+ *   n_species: must equal the model's species count.
+ * The neighbour list must be rebuilt afterwards (energy_forces returns
+ * ALLEGRO_E_STATE until then).  allegro_neighbors_noalloc ignores the table.
+ * Errors: ALLEGRO_E_INVALID (bad count or entry), ALLEGRO_E_CUDA.
+ */
+allegro_status allegro_set_pair_cutoffs(allegro_ctx* ctx, const double* pair_rc, int32_t n_species);
+
+/*
  * allegro_neighbors -- build the ordered neighbour list of one structure.
  * An edge is (i, j, S), S in Z^3 an image shift, displacement
  *   d = (pos_j + (S0 a + S1 b) + S2 c) - pos_i  evaluated in float64 in that

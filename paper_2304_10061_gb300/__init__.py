@@ -102,6 +102,17 @@ class Allegro:
         self._check(self._L.allegro_reserve(self._ctx, int(atom_cap), int(edge_cap), int(bool(fixed)),
                                             int(chunk_edges)))
 
+    def set_pair_cutoffs(self, pair_rc=None):
+        """Per-ordered-species-pair cutoffs [n_species][n_species] (row = centre species), or None
+        for the model cutoff everywhere; rebuild the neighbour list afterwards."""
+        if pair_rc is None:
+            self._check(self._L.allegro_set_pair_cutoffs(self._ctx, None, 0))
+            return
+        t = np.ascontiguousarray(np.asarray(pair_rc, dtype=np.float64))
+        if t.ndim != 2 or t.shape[0] != t.shape[1]:
+            raise ValueError("pair_rc must be a square [n_species][n_species] table")
+        self._check(self._L.allegro_set_pair_cutoffs(self._ctx, t.ctypes.data, int(t.shape[0])))
+
     def neighbors(self, pos, types, cell=None, pbc=None) -> int:
         pos = _as(pos, np.float64)
         types = _as(types, np.int32)

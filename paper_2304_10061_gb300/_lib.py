@@ -18,7 +18,7 @@ STATUS_NAMES = {
 }
 PREC = {"fp32": 0, "bf16": 1}
 
-EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_reserve", "allegro_neighbors",
+EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
            "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_last_error",
            "allegro_destroy")
@@ -38,6 +38,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_create.argtypes = [vp, sz, vp, i32, ctypes.c_double, i32, i32, ctypes.POINTER(vp)]
     L.allegro_set_stream.argtypes = [vp, vp]
     L.allegro_reserve.argtypes = [vp, i64, i64, i32, i64]
+    L.allegro_set_pair_cutoffs.argtypes = [vp, dp, i32]
     L.allegro_neighbors.argtypes = [vp, i64, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_neighbors_batched.argtypes = [vp, i32, dp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_energy_forces.argtypes = [vp, dp, dp, dp, dp]

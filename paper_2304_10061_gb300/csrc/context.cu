@@ -108,6 +108,9 @@ struct allegro_ctx {
   Arch arch;
   std::vector<int> species_map;
   std::string err;
+  // per-ordered-species-pair cutoffs (arch.pair_basis / arch.pair_rc2 point here)
+  float* d_pair_basis = nullptr;
+  double* d_pair_rc2 = nullptr;
 
   // model on the device
   std::vector<Lin> tb;                     // two-body layers
@@ -1085,7 +1088,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     ProfScope ps(c, "geom_bwd", 2.0 * Ec * a.tb[0] * a.nb,
                  (double)Ec * (24 + a.tb[0] * act + 4 + 2 * S * 4 + 12));
     YbarParts yb{{w.Ybar[0], w.Ybar[1]}};
-    edge_geom_bwd<T>(Ec, e0, c->d_ed, a, (const T*)w.H[cur0], w.ld_H, c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb,
+    edge_geom_bwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, (const T*)w.H[cur0], w.ld_H, c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb,
                      c->d_g, st);
   }
   return ALLEGRO_OK;
@@ -1231,6 +1234,42 @@ allegro_status allegro_set_stream(allegro_ctx* c, void* stream) {
   return ALLEGRO_OK;
 }
 
+allegro_status allegro_set_pair_cutoffs(allegro_ctx* c, const double* pair_rc, int32_t n_species) {
+  if (!c) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  c->have_nb = false;
+  if (!pair_rc) {
+    c->arch.pair_basis = nullptr;
+    c->arch.pair_rc2 = nullptr;
+    return ALLEGRO_OK;
+  }
+  const int ns = c->arch.ns;
+  if (n_species != ns) return fail(c, ALLEGRO_E_INVALID, "n_species %d differs from the model's %d", n_species, ns);
+  std::vector<float> basis(2 * (size_t)ns * ns);
+  std::vector<double> rc2((size_t)ns * ns);
+  for (int q = 0; q < ns * ns; ++q) {
+    const double rc = pair_rc[q];
+    // the cell grid and the prefilter band are built for the model cutoff, the largest allowed
+    if (!(rc > 0.0) || !(rc <= c->arch.rc))
+      return fail(c, ALLEGRO_E_INVALID, "pair cutoff [%d][%d] = %g outside (0, %g]", q / ns, q % ns, rc, c->arch.rc);
+    basis[2 * q] = (float)(1.0 / rc);
+    basis[2 * q + 1] = (float)std::sqrt(2.0 / rc);
+    rc2[q] = rc * rc;
+  }
+  if (!c->d_pair_basis) {
+    CUDA_TRY(c, cudaMalloc(&c->d_pair_basis, 2 * sizeof(float) * kMaxSpecies * kMaxSpecies));
+    CUDA_TRY(c, cudaMalloc(&c->d_pair_rc2, sizeof(double) * kMaxSpecies * kMaxSpecies));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_pair_basis, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_pair_rc2, rc2.data(), rc2.size() * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->arch.pair_basis = c->d_pair_basis;
+  c->arch.pair_rc2 = c->d_pair_rc2;
+  return ALLEGRO_OK;
+}
+
 allegro_status allegro_reserve(allegro_ctx* c, int64_t atom_cap, int64_t edge_cap, int32_t fixed,
                                int64_t chunk_edges) {
   if (!c || atom_cap < 0 || edge_cap < 0 || chunk_edges < 0) return ALLEGRO_E_INVALID;
@@ -1357,7 +1396,7 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
     CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cursor, 0, (size_t)(ncell + 1) * 4, st));
     nb_place(c->d_cell_of, n, c->d_cell_start, c->d_cell_cursor, c->d_sorted, st);
     nb_sort_cells(c->d_cell_start, (int)ncell, c->d_sorted, st);
-    nb_pos4(c->d_pos, n, g, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, st);
+    nb_pos4(c->d_pos, c->d_species, n, g, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, st);
   }
   // Error band of the float32 prefilter: bound X on |wrapped coordinate| and
   // |image offset|, per-component error <= 8 ulp(X), squared-distance error
@@ -1382,7 +1421,7 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   {
     ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
     nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
-              band, c->d_count,
+              band, c->arch.pair_rc2, c->arch.ns, c->d_count,
               nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
     exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
   }
@@ -1395,7 +1434,7 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   {
     ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
     nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
-              band, nullptr,
+              band, c->arch.pair_rc2, c->arch.ns, nullptr,
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
@@ -1472,7 +1511,7 @@ allegro_status allegro_neighbors_batched(allegro_ctx* c, int32_t n_struct, const
   atom_struct_kernel<<<n_struct, 128, 0, st>>>(c->d_offs, n_struct, c->d_atom_struct);
   const double rc2 = rc * rc;
   nb_bruteforce_batched(false, c->d_pos, c->d_offs, n_struct, cells ? c->d_cells : nullptr, c->d_pbc, c->d_nimg, rc2,
-                        c->d_atom_struct, n, c->d_count, nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
+                        c->d_species, c->arch.pair_rc2, c->arch.ns, c->d_atom_struct, n, c->d_count, nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
   exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
   int hE = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&hE, c->d_row_ptr + n, 4, cudaMemcpyDeviceToHost, st));
@@ -1480,7 +1519,7 @@ allegro_status allegro_neighbors_batched(allegro_ctx* c, int32_t n_struct, const
   CUDA_TRY(c, cudaGetLastError());
   if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
   nb_bruteforce_batched(true, c->d_pos, c->d_offs, n_struct, cells ? c->d_cells : nullptr, c->d_pbc, c->d_nimg, rc2,
-                        c->d_atom_struct, n, nullptr, c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
+                        c->d_species, c->arch.pair_rc2, c->arch.ns, c->d_atom_struct, n, nullptr, c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
   c->nstruct = n_struct;
   c->batched = true;
@@ -1655,7 +1694,7 @@ void allegro_destroy(allegro_ctx* c) {
                   c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
                   c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,
                   c->d_md_pos, c->d_md_vel, c->d_md_invm, c->d_md_types, c->d_md_masses, c->d_md_E, c->d_md_K,
-                  c->d_md_part};
+                  c->d_md_part, c->d_pair_basis, c->d_pair_rc2};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

@@ -35,7 +35,13 @@ struct BasisConst {
   int ns, nb, p, lmax, S;
   float rc, inv_rc, pref;       // pref = sqrt(2/r_c)
   float c0, c1, c2;             // envelope coefficients
+  const float2* pair;           // per ordered species pair {1/rc, sqrt(2/rc)}, or null (rc for every pair)
 };
+
+// 1/rc and sqrt(2/rc) of the ordered pair (Z_i, Z_j)
+__device__ __forceinline__ float2 pair_basis(const BasisConst& bc, int zi, int zj) {
+  return bc.pair ? bc.pair[zi * bc.ns + zj] : make_float2(bc.inv_rc, bc.pref);
+}
 
 static BasisConst make_basis(const Arch& a) {
   BasisConst b;
@@ -44,6 +50,7 @@ static BasisConst make_basis(const Arch& a) {
   b.c0 = (float)((a.p + 1.0) * (a.p + 2.0) / 2.0);
   b.c1 = (float)(a.p * (a.p + 2.0));
   b.c2 = (float)(a.p * (a.p + 1.0) / 2.0);
+  b.pair = reinterpret_cast<const float2*>(a.pair_basis);
   return b;
 }
 
@@ -168,18 +175,19 @@ __global__ void __launch_bounds__(kGeomBlock)
 #pragma unroll
       for (int a = 0; a < kMaxS; ++a)
         if (a < bc.S) sY[tl * bc.S + a] = Y[a];
-      const float xr = r * bc.inv_rc;
+      zi = species[ei[eg]];
+      zj = species[ej[eg]];
+      const float2 pb = pair_basis(bc, zi, zj);   // the pair's 1/rc and sqrt(2/rc)
+      const float xr = r * pb.x;
       if (xr < 1.0f) {
         const float xp = ipow(xr, bc.p);
         u = 1.0f - xp * (bc.c0 - xr * (bc.c1 - bc.c2 * xr));
       }
       uout[e] = u;
-      zi = species[ei[eg]];
-      zj = species[ej[eg]];
       if (sig) sig[e] = (float)sigma[zi];
 #pragma unroll
       for (int n = 0; n < kMaxBessel; ++n)
-        B[n] = (n < bc.nb) ? bc.pref * sinpif((float)(n + 1) * xr) * ir32 : 0.0f;
+        B[n] = (n < bc.nb) ? pb.y * sinpif((float)(n + 1) * xr) * ir32 : 0.0f;
     }
     const float rsc = scale_u ? u : 1.0f;
     for (int c0 = 0; c0 < N0; c0 += kGeomCols) {
@@ -253,7 +261,9 @@ template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int
 // Bessel rows of W0t held in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(kGeomBlock)
-    geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, BasisConst bc, const T* __restrict__ zbar0,
+    geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
+                    const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
+                    const T* __restrict__ zbar0,
                     int ldz, const float* __restrict__ W0t, int ldW, int N0, const float* __restrict__ ubar,
                     YbarParts yb, float* __restrict__ g) {
   extern __shared__ __align__(16) float wb_sm[];   // [nb][N0]: Bessel rows of W0t
@@ -272,7 +282,9 @@ __global__ void __launch_bounds__(kGeomBlock)
   const float ir32 = rsqrtf(r2);
   const float r = r2 * ir32;
   const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
-  const float xr = r * bc.inv_rc;
+  const float2 pb = pair_basis(bc, bc.pair ? species[ei[eg]] : 0, bc.pair ? species[ej[eg]] : 0);
+  const float inv_rc = pb.x, pref = pb.y;
+  const float xr = r * inv_rc;
   // Bbar = zbar0 . W0[:, 2 ns:]
   float Bb[kMaxBessel];
 #pragma unroll
@@ -320,14 +332,14 @@ __global__ void __launch_bounds__(kGeomBlock)
     if (n > bc.nb) break;
     float sn, cn;
     sincospif((float)n * xr, &sn, &cn);
-    const float kk = (float)n * 3.14159265358979323846f * bc.inv_rc;
-    const float dB = bc.pref * (kk * cn * r - sn) * ir32 * ir32;
+    const float kk = (float)n * 3.14159265358979323846f * inv_rc;
+    const float dB = pref * (kk * cn * r - sn) * ir32 * ir32;
     dEdr += Bb[n - 1] * dB;
   }
   if (xr < 1.0f) {
     const float xp1 = ipow(xr, bc.p - 1);
     const float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
-    dEdr += ubar[e] * du * bc.inv_rc;
+    dEdr += ubar[e] * du * inv_rc;
   }
   // Ybar arrives in two partial arrays (from two row-kernel passes), summed in a fixed order
   float Yb[kMaxS];
@@ -341,19 +353,22 @@ __global__ void __launch_bounds__(kGeomBlock)
 }
 
 template <typename T>
-void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const T* zbar0, int ldz, const float* W0t,
-                   int ldW, const float* ubar, const YbarParts& yb, float* g, cudaStream_t st) {
+void edge_geom_bwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
+                   const Arch& a, const T* zbar0, int ldz, const float* W0t, int ldW, const float* ubar,
+                   const YbarParts& yb, float* g, cudaStream_t st) {
   if (Ec <= 0) return;
   const size_t smem = (size_t)a.nb * a.tb[0] * 4;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(geom_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   geom_bwd_kernel<T><<<(Ec + kGeomBlock - 1) / kGeomBlock, kGeomBlock, smem, st>>>(
-      Ec, e0, ed, make_basis(a), zbar0, ldz, W0t, ldW, a.tb[0], ubar, yb, g);
+      Ec, e0, ed, ei, ej, species, make_basis(a), zbar0, ldz, W0t, ldW, a.tb[0], ubar, yb, g);
 }
-template void edge_geom_bwd<float>(int, int, const double*, const Arch&, const float*, int, const float*, int,
-                                   const float*, const YbarParts&, float*, cudaStream_t);
-template void edge_geom_bwd<bf16>(int, int, const double*, const Arch&, const bf16*, int, const float*, int,
-                                  const float*, const YbarParts&, float*, cudaStream_t);
+template void edge_geom_bwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
+                                   const float*, int, const float*, int, const float*, const YbarParts&, float*,
+                                   cudaStream_t);
+template void edge_geom_bwd<bf16>(int, int, const double*, const int*, const int*, const int*, const Arch&,
+                                  const bf16*, int, const float*, int, const float*, const YbarParts&, float*,
+                                  cudaStream_t);
 
 // Adjoint head of an MLP whose output is x = u * silu(z):  given xbar,
 //   ubar += sum_n xbar_n silu(z_n),   zbar_n = xbar_n u silu'(z_n).

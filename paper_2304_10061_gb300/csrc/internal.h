@@ -35,6 +35,12 @@ enum DevErr : int {
 struct Arch {
   int ns = 0, nb = 0, p = 0, lmax = 0, nl = 0, C = 0;
   double rc = 0, ann = 0;
+  // per-ordered-species-pair cutoffs (Sec. "Species-dependent cutoffs"), set by
+  // allegro_set_pair_cutoffs: device [ns * ns][2] = {1/rc, sqrt(2/rc)} of pair
+  // (Z_i, Z_j) for the basis and envelope, and device [ns * ns] rc^2 for the
+  // neighbour test; null: the model cutoff rc for every pair
+  const float* pair_basis = nullptr;
+  const double* pair_rc2 = nullptr;
   std::vector<int> tb, lat, edge;
   int S() const { return (lmax + 1) * (lmax + 1); }
   int n_w() const { return C * (lmax + 1); }
@@ -148,14 +154,18 @@ void nb_bin(const double* pos, int n, const CellGrid& g, int* cell_of, int* wrap
 void nb_place(const int* cell_of, int n, const int* cell_start, int* cell_cursor, int* sorted,
               cudaStream_t st);
 void nb_sort_cells(const int* cell_start, int n_cells, int* sorted, cudaStream_t st);
-void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
-             double* pw, cudaStream_t st);
+// pos4[s].w carries the model species of atom sorted[s] (its bits)
+void nb_pos4(const double* pos, const int* species, int n, const CellGrid& g, const int* wrap, const int* sorted,
+             float4* pos4, double* pw, cudaStream_t st);
+// pair_rc2: null, or device [ns * ns] squared cutoffs per ordered species pair
+// (each <= rc2, the search radius; `band` is the prefilter band of rc2)
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
                const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
-               double rc2, float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed,
-               int* d_err, cudaStream_t st);
+               double rc2, float band, const double* pair_rc2, int ns, int* count, const int* row_ptr, int* ej,
+               int* ei, int* eS, double* ed, int* d_err, cudaStream_t st);
 void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,
                            const double* cells, const int* pbc, const int* nimg, double rc2,
+                           const int* species, const double* pair_rc2, int ns,
                            const int* atom_struct, int n, int* count, const int* row_ptr, int* ej,
                            int* ei, int* eS, double* ed, int* d_err, cudaStream_t st);
 void nb_columns(const int* ej, int E, int n, int* col_count, cudaStream_t st);
@@ -179,8 +189,9 @@ struct YbarParts {
 };
 // edge forces g_ij from zbar0 (adjoint of the first two-body pre-activation), ubar and Ybar
 template <typename T>
-void edge_geom_bwd(int Ec, int e0, const double* ed, const Arch& a, const T* zbar0, int ldz, const float* W0t,
-                   int ldW, const float* ubar, const YbarParts& yb, float* g, cudaStream_t st);
+void edge_geom_bwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
+                   const Arch& a, const T* zbar0, int ldz, const float* W0t, int ldW, const float* ubar,
+                   const YbarParts& yb, float* g, cudaStream_t st);
 template <typename T>
 void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
                   const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,

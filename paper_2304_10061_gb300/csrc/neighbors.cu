@@ -276,8 +276,9 @@ __device__ __forceinline__ bool pair_test(const double* __restrict__ pi, const d
 // Wrapped positions pw = pos - wrap . cell in cell-sorted order (pos4[s] and
 // pw[3 s ..] belong to atom sorted[s]): float32 for the prefilter, float64 for
 // the displacements of accepted edges.
-__global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, const int* __restrict__ wrap,
-                            const int* __restrict__ sorted, float4* __restrict__ pos4, double* __restrict__ pw) {
+__global__ void pos4_kernel(const double* __restrict__ pos, const int* __restrict__ species, int n, CellGrid g,
+                            const int* __restrict__ wrap, const int* __restrict__ sorted,
+                            float4* __restrict__ pos4, double* __restrict__ pw) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int j = sorted[s];
@@ -288,7 +289,7 @@ __global__ void pos4_kernel(const double* __restrict__ pos, int n, CellGrid g, c
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[x] -= (double)wrap[3 * (size_t)j + k] * g.cell[k * 3 + x];
   }
-  pos4[s] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.0f);
+  pos4[s] = make_float4((float)p[0], (float)p[1], (float)p[2], __int_as_float(species[j]));
   pw[3 * (size_t)s] = p[0];
   pw[3 * (size_t)s + 1] = p[1];
   pw[3 * (size_t)s + 2] = p[2];
@@ -308,6 +309,7 @@ __global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g
                               const int* __restrict__ cell_of, const int* __restrict__ wrap,
                               const int* __restrict__ cell_start, const int* __restrict__ sorted,
                               const float4* __restrict__ pos4, const double* __restrict__ pw, double rc2, float band,
+                              const double* __restrict__ pair_rc2, int ns,
                               int* __restrict__ count, const int* __restrict__ row_ptr,
                               int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS,
                               double* __restrict__ ed, int* __restrict__ d_err) {
@@ -325,6 +327,9 @@ __global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g
   const double pwi[3] = {pw[3 * (size_t)t], pw[3 * (size_t)t + 1], pw[3 * (size_t)t + 2]};
   const float rc2f = (float)rc2;
   const float lo2 = rc2f - band, hi2 = rc2f + band;
+  // per-ordered-pair cutoffs: row of the centre's species (the band of the largest
+  // cutoff bounds the float32 error of every smaller one)
+  const double* prow = pair_rc2 ? pair_rc2 + (size_t)__float_as_int(pi4.w) * ns : nullptr;
   float cf[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) cf[k] = (float)g.cell[k];
@@ -361,14 +366,22 @@ __global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g
           const float dx = pj.x + ox, dy = pj.y + oy, dz = pj.z + oz;
           const float r2f = dx * dx + dy * dy + dz * dz;
           if (r2f > hi2) continue;
+          double rc2p = rc2;
+          float lo2p = lo2;
+          if (prow) {
+            rc2p = prow[__float_as_int(pj.w)];
+            const float rc2pf = (float)rc2p;
+            if (r2f > rc2pf + band) continue;
+            lo2p = rc2pf - band;
+          }
           const int j = sorted[s];
           int S0 = g.pbc[0] ? q0 - wrap[3 * (size_t)j] + wi0 : 0;
           int S1 = g.pbc[1] ? q1 - wrap[3 * (size_t)j + 1] + wi1 : 0;
           int S2 = g.pbc[2] ? q2 - wrap[3 * (size_t)j + 2] + wi2 : 0;
           if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
           double d[3];
-          if (r2f >= lo2) {
-            if (!pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2, d)) continue;
+          if (r2f >= lo2p) {
+            if (!pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2p, d)) continue;
           } else if constexpr (fill) {
 #pragma unroll
             for (int x = 0; x < 3; ++x) d[x] = (pw[3 * (size_t)s + x] + qoff[x]) - pwi[x];
@@ -394,23 +407,23 @@ __global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g
   }
 }
 
-void nb_pos4(const double* pos, int n, const CellGrid& g, const int* wrap, const int* sorted, float4* pos4,
-             double* pw, cudaStream_t st) {
+void nb_pos4(const double* pos, const int* species, int n, const CellGrid& g, const int* wrap, const int* sorted,
+             float4* pos4, double* pw, cudaStream_t st) {
   if (n <= 0) return;
-  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, n, g, wrap, sorted, pos4, pw);
+  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, species, n, g, wrap, sorted, pos4, pw);
 }
 
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
                const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
-               double rc2, float band, int* count, const int* row_ptr, int* ej, int* ei, int* eS, double* ed,
-               int* d_err, cudaStream_t st) {
+               double rc2, float band, const double* pair_rc2, int ns, int* count, const int* row_ptr, int* ej,
+               int* ei, int* eS, double* ed, int* d_err, cudaStream_t st) {
   if (n <= 0) return;
   if (fill)
     search_kernel<true><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
-                                                         band, count, row_ptr, ej, ei, eS, ed, d_err);
+                                                         band, pair_rc2, ns, count, row_ptr, ej, ei, eS, ed, d_err);
   else
     search_kernel<false><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
-                                                          band, count, row_ptr, ej, ei, eS, ed, d_err);
+                                                          band, pair_rc2, ns, count, row_ptr, ej, ei, eS, ed, d_err);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,7 +432,9 @@ void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int
 __global__ void brute_batched_kernel(bool fill, const double* __restrict__ pos,
                                      const int64_t* __restrict__ offs, const double* __restrict__ cells,
                                      const int* __restrict__ pbc, const int* __restrict__ nimg,
-                                     double rc2, const int* __restrict__ atom_struct, int n,
+                                     double rc2, const int* __restrict__ species,
+                                     const double* __restrict__ pair_rc2, int ns,
+                                     const int* __restrict__ atom_struct, int n,
                                      int* __restrict__ count, const int* __restrict__ row_ptr,
                                      int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS,
                                      double* __restrict__ ed, int* __restrict__ d_err) {
@@ -436,13 +451,15 @@ __global__ void brute_batched_kernel(bool fill, const double* __restrict__ pos,
   int k = 0;
   const int base = fill ? row_ptr[i] : 0;
   const int cap = fill ? (row_ptr[i + 1] - base) : 0;
+  const double* prow = pair_rc2 ? pair_rc2 + (size_t)species[i] * ns : nullptr;
   for (int j = j0; j < j1; ++j) {
+    const double rc2p = prow ? prow[species[j]] : rc2;   // the ordered pair's cutoff
     for (int S0 = -nI[0]; S0 <= nI[0]; ++S0)
       for (int S1 = -nI[1]; S1 <= nI[1]; ++S1)
         for (int S2 = -nI[2]; S2 <= nI[2]; ++S2) {
           if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
           double d[3];
-          if (!pair_test(pi, pos + 3 * (size_t)j, cell, S0, S1, S2, rc2, d)) continue;
+          if (!pair_test(pi, pos + 3 * (size_t)j, cell, S0, S1, S2, rc2p, d)) continue;
           if (fill && k < cap) {
             size_t o = (size_t)base + k;
             ej[o] = j;
@@ -462,12 +479,13 @@ __global__ void brute_batched_kernel(bool fill, const double* __restrict__ pos,
 
 void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,
                            const double* cells, const int* pbc, const int* nimg, double rc2,
+                           const int* species, const double* pair_rc2, int ns,
                            const int* atom_struct, int n, int* count, const int* row_ptr, int* ej,
                            int* ei, int* eS, double* ed, int* d_err, cudaStream_t st) {
   (void)nstruct;
   if (n <= 0) return;
-  brute_batched_kernel<<<(n + 127) / 128, 128, 0, st>>>(fill, pos, offs, cells, pbc, nimg, rc2,
-                                                        atom_struct, n, count, row_ptr, ej, ei, eS, ed,
+  brute_batched_kernel<<<(n + 127) / 128, 128, 0, st>>>(fill, pos, offs, cells, pbc, nimg, rc2, species, pair_rc2,
+                                                        ns, atom_struct, n, count, row_ptr, ej, ei, eS, ed,
                                                         d_err);
 }
 

@@ -43,6 +43,7 @@ def test_null_arguments_rejected_without_gpu():
     out = ctypes.c_void_p()
     assert L.allegro_create(None, 0, None, 0, 0.0, 0, 0, ctypes.byref(out)) == 1
     assert L.allegro_energy_forces(None, None, None, None, None) == 1
+    assert L.allegro_set_pair_cutoffs(None, None, 0) == 1
     assert L.allegro_last_error(None) == b"null context"
     L.allegro_destroy(None)
 

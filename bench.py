@@ -34,13 +34,34 @@ WORKLOAD = ("1,048,576-atom periodic water-density box (218.9 A cube, jittered l
             "latent 2x256, edge 256->128->1, r_c 4 A, seeded random weights")
 
 
+PAIR_NOTE = ", per-ordered-species-pair cutoffs (H-H 3.0, H-C 1.25, H-O 1.25, O-H 3.0 A, others 4.0 A)"
+
+
 def _workload(args, s) -> str:
-    """The workload string: the headline box, or what --config / --atoms selected."""
+    """The workload string: the headline box, or what --config / --atoms / --pair-cutoffs selected."""
+    note = PAIR_NOTE if getattr(args, "pair_cutoffs", False) else ""
     if args.config == "c4" and not args.atoms:
-        return WORKLOAD
+        return WORKLOAD + note
     L = float(abs(s.cell[0][0])) if s.cell is not None else 0.0
     return (f"{s.n_atoms:,}-atom periodic box ({L:.1f} A cube, config {args.config}), same model family and "
-            "seeded random weights")
+            "seeded random weights" + note)
+
+
+def _pair_arch(args, arch):
+    """The architecture with the paper's per-ordered-species-pair cutoff table when --pair-cutoffs is set."""
+    if not getattr(args, "pair_cutoffs", False):
+        return arch
+    from dataclasses import replace
+    from synth import paper_pair_cutoffs
+    return replace(arch, pair_rc=paper_pair_cutoffs(default=arch.r_c))
+
+
+def _edges(arch, s):
+    """The oracle's neighbour list of `s` under the architecture's cutoff rule."""
+    from oracle.neighbors import neighbor_list
+    if arch.pair_rc is None:
+        return neighbor_list(s.pos, s.cell, s.pbc, arch.r_c)
+    return neighbor_list(s.pos, s.cell, s.pbc, arch.r_c, species=s.species, pair_rc=arch.pair_rc)
 
 
 def _dist():
@@ -204,12 +225,11 @@ def _cpu_baseline(arch, w, blob, precision_models: dict):
     import numpy as np
     import torch
     from oracle.allegro import AllegroOracle
-    from oracle.neighbors import neighbor_list
     from synth import make_config
     torch.set_num_threads(os.cpu_count() or 1)
     s, _, _ = make_config("c4sub")
     t0 = time.perf_counter()
-    i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c)
+    i, j, S = _edges(arch, s)
     E0, Ea0, F0, W0 = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, i, j, S)
     dt = time.perf_counter() - t0
     errs = {}
@@ -234,14 +254,14 @@ def run_reference(args):
         return
     import torch
     from oracle.allegro import AllegroOracle
-    from oracle.neighbors import neighbor_list
     from synth import make_config
     torch.set_num_threads(os.cpu_count() or 1)
     s, arch, w = make_config("c4sub")
+    arch = _pair_arch(args, arch)
     orc = AllegroOracle(arch, w)
 
     def step():
-        i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c)
+        i, j, S = _edges(arch, s)
         orc.energy_forces(s.pos, s.species, s.cell, i, j, S)
 
     for _ in range(args.warmup):
@@ -254,7 +274,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "each step: the 4,096-atom box of the same density "
+            "config": {"workload": _workload(args, s), "sample": "each step: the 4,096-atom box of the same density "
                                                        "and model (bounded sample for the CPU)"},
             "cpu_baseline": {"kind": "oracle", "cores": torch.get_num_threads(), "value": v, "unit": UNIT,
                              "sample": "4,096-atom box, neighbours + E + F + virial per step"},
@@ -284,6 +304,7 @@ def run_ours(args):
         over = dict(n=args.atoms, L=c["L"] * (args.atoms / c["n"]) ** (1.0 / 3.0))
     s, arch, w = make_config(args.config, **over)
     blob = weights_to_blob(arch, w)
+    arch = _pair_arch(args, arch)
     N = s.n_atoms
     pos = torch.tensor(s.pos, device=dev)
     types = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -295,6 +316,8 @@ def run_ours(args):
         m.set_stream(stream.cuda_stream)
         if args.chunk_edges:
             m.reserve(0, 0, False, args.chunk_edges)
+        if arch.pair_rc is not None:
+            m.set_pair_cutoffs(arch.pair_rc)
         return m
 
     def timed(m, K, W, out):
@@ -463,6 +486,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--chunk-edges", type=int, default=0, help="edges per model pass (0 = automatic)")
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched-molecule and MD context runs")
+    ap.add_argument("--pair-cutoffs", action="store_true",
+                    help="per-ordered-species-pair cutoffs of the paper's production model (H-H 3.0, H-C 1.25, "
+                         "H-O 1.25, O-H 3.0 A, every other pair the model cutoff)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -723,8 +723,9 @@ __global__ void __launch_bounds__(tc_threads<EPQ>(), 1)
 // one.  The late order gives group 2 one more GEMM-1 job to drain GEMM 2 of
 // tile i - 1 (GEMM 2 of tile i needs the single GEMM-2 accumulator back); it
 // is used for the pairs it measured faster on (256-wide second layers after an
-// adjoint head, the last latent layer, the adjoint -> linear pair).  The operand ring (3 stages of 32 KB) carries [A1 k-block | B1 rows of
-// the job] for GEMM-1 jobs and B2 k-blocks for GEMM-2 halves in that order.
+// adjoint head, the last latent layer, the adjoint -> linear pair).  The
+// operand ring (3 stages of 32 KB) carries [A1 k-block | B1 rows of the job]
+// for GEMM-1 jobs and B2 k-blocks for GEMM-2 halves, in job order.
 // GEMM 1's A operand may be the K-concatenation [A1 | A1b] (split at K1a, a
 // multiple of 64 columns).
 //   epi1: FWD_SILU (pre-activation stored), HEAD (pre-activation loaded, row
@@ -740,9 +741,8 @@ constexpr int kCfStages = 3;
 constexpr int kCfJobN = 128;                       // output columns of one GEMM-1 job
 
 __host__ __device__ constexpr int cf_stage_bytes(int n1, int n2) {
-  // [A1 k-block | 128 rows of B1] or [N2 rows of B2]
-  return (kTcBM * kTcBK * 2 + kCfJobN * kTcBK * 2) > n2 * kTcBK * 2 ? (kTcBM * kTcBK * 2 + kCfJobN * kTcBK * 2)
-                                                                     : n2 * kTcBK * 2;
+  // the larger of [A1 k-block | 128 rows of B1] and [N2 rows of B2]
+  return (kTcBM + kCfJobN) * kTcBK * 2 > n2 * kTcBK * 2 ? (kTcBM + kCfJobN) * kTcBK * 2 : n2 * kTcBK * 2;
 }
 // group-2 staging buffers per warp: two when shared memory allows, one for 256-wide first layers
 __host__ __device__ constexpr int cf_nb2(int n1) { return n1 <= 128 ? 2 : 1; }
@@ -855,7 +855,8 @@ __global__ void __launch_bounds__(kCfThreads, 1)
   };
 
   // The MMA job sequence (see above), walked identically by the producer and the MMA thread:
-  // job(i, hf, two) calls g1(i, hf) or g2(i, hf); returns false once a wait fails.
+  // g1(i, hf) is GEMM-1 job hf of tile i, g2(i, hf) half hf of tile i's GEMM 2; the walk
+  // stops at the first job that returns false (a wait ran out or the kernel is aborting).
   auto walk = [&](auto&& g1, auto&& g2) {
     if (T == 0) return;
     if (!g1(0, 0)) return;

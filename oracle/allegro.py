@@ -28,6 +28,7 @@ Readings where the paper defers to the Allegro paper or is silent:
     r_c = pair_rc[Z_i][Z_j] (row = centre species) in the neighbour rule, the
     Bessel basis and the envelope alike, so each pair's basis spans its own range
     and its terms vanish smoothly at its own cutoff.
+  * ZBL repulsion (when the architecture lists atomic numbers): `oracle/zbl.py`.
 """
 from __future__ import annotations
 
@@ -37,7 +38,7 @@ from typing import Dict, Optional
 import numpy as np
 import torch
 
-from . import so3
+from . import so3, zbl
 
 torch_f64 = torch.float64
 
@@ -105,13 +106,8 @@ class AllegroOracle:
         r = torch.sqrt((d * d).sum(-1))
         rhat = d / r[:, None]
         Z = torch.as_tensor(np.asarray(species), dtype=torch.int64)
-        if a.pair_rc is None:
-            B = bessel(r, a.r_c, a.n_bessel)
-            u = envelope(r / a.r_c, a.p_env)[:, None]
-        else:
-            rc = torch.tensor(a.pair_rc, dtype=torch_f64)[Z[torch.as_tensor(i)], Z[torch.as_tensor(j)]]
-            B = bessel_pair(r, rc, a.n_bessel)
-            u = envelope(r / rc, a.p_env)[:, None]
+        B, u = self._radial(r, Z, i, j)
+        u = u[:, None]
         Y = so3.real_sh(a.lmax, rhat)                                    # [E, S]
         Zi = torch.nn.functional.one_hot(Z[torch.as_tensor(i)], a.n_species).to(torch_f64)
         Zj = torch.nn.functional.one_hot(Z[torch.as_tensor(j)], a.n_species).to(torch_f64)
@@ -142,6 +138,24 @@ class AllegroOracle:
             e = e @ Wk.T
         return e[:, 0]
 
+    def _radial(self, r, Z, i, j):
+        """Bessel basis [E, n_bessel] and envelope [E] with each edge's cutoff."""
+        a = self.arch
+        if a.pair_rc is None:
+            return bessel(r, a.r_c, a.n_bessel), envelope(r / a.r_c, a.p_env)
+        rc = torch.tensor(a.pair_rc, dtype=torch_f64)[Z[torch.as_tensor(i)], Z[torch.as_tensor(j)]]
+        return bessel_pair(r, rc, a.n_bessel), envelope(r / rc, a.p_env)
+
+    def repulsion(self, d, species, i, j, n_atoms):
+        """Per-atom ZBL energies [n] (zeros without atomic numbers in the architecture)."""
+        if self.arch.zbl_z is None or len(i) == 0:
+            return torch.zeros(n_atoms, dtype=torch_f64)
+        r = torch.sqrt((d * d).sum(-1))
+        Z = torch.as_tensor(np.asarray(species), dtype=torch.int64)
+        _, u = self._radial(r, Z, i, j)
+        ez = zbl.edge_energies(r, u, self.arch.zbl_z, species, i, j)
+        return torch.zeros(n_atoms, dtype=torch_f64).index_add_(0, torch.as_tensor(i), ez)
+
     def energy(self, pos, species, cell, i, j, S, n_atoms=None):
         """Total energy and per-atom energies (float64)."""
         n = pos.shape[0] if n_atoms is None else n_atoms
@@ -149,7 +163,7 @@ class AllegroOracle:
         Eij = self.edge_energies(d, species, i, j, n)
         Ei = torch.zeros(n, dtype=torch_f64).index_add_(0, torch.as_tensor(i), Eij)
         Z = torch.as_tensor(np.asarray(species), dtype=torch.int64)
-        Et = self.sigma[Z] * Ei + self.mu[Z]
+        Et = self.sigma[Z] * Ei + self.mu[Z] + self.repulsion(d, species, i, j, n)
         return Et.sum(), Et
 
     def energy_forces(self, pos_np, species, cell, i, j, S, chunk_atoms: int = 2048,
@@ -177,10 +191,12 @@ class AllegroOracle:
             if sel.size:
                 Eij = self.edge_energies(d, species, i[sel], j[sel], n)
                 Ei = torch.zeros(n, dtype=torch_f64).index_add_(0, torch.as_tensor(i[sel]), Eij)
+                Er = self.repulsion(d, species, i[sel], j[sel], n)
             else:
                 Ei = torch.zeros(n, dtype=torch_f64)
+                Er = torch.zeros(n, dtype=torch_f64)
             cs_t = torch.as_tensor(cs)
-            Et = self.sigma[Z[cs_t]] * Ei[cs_t] + self.mu[Z[cs_t]]
+            Et = self.sigma[Z[cs_t]] * Ei[cs_t] + self.mu[Z[cs_t]] + Er[cs_t]
             Ec = Et.sum()
             if sel.size:
                 gpos, gd = torch.autograd.grad(Ec, [pos, d], allow_unused=True)

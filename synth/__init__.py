@@ -13,6 +13,7 @@ from .structures import (
     molecule_batch,
     SPECIES_NAMES,
     SPECIES_MASSES,
+    SPECIES_Z,
     WATER_MIX,
     paper_pair_cutoffs,
 )

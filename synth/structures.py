@@ -21,6 +21,7 @@ import numpy as np
 SPECIES_NAMES = ("H", "O", "C", "N", "S")
 # Atomic masses in amu, same order.
 SPECIES_MASSES = (1.008, 15.999, 12.011, 14.007, 32.06)
+SPECIES_Z = (1, 8, 6, 7, 16)   # atomic numbers of SPECIES_NAMES
 def paper_pair_cutoffs(names=None, default: float = 4.0):
     """Per-ordered-species-pair cutoffs of the paper's production model (Sec. "Training
     details"): H-H 3.0, H-C 1.25, H-O 1.25, O-H 3.0 Angstrom, every other ordered pair

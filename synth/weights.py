@@ -48,6 +48,9 @@ class Arch:
     # cutoff per ordered (centre species, neighbour species) pair; None: r_c for every pair.
     # Not part of the weights blob (the float32 / BF16 library path takes one r_c).
     pair_rc: Optional[Tuple[Tuple[float, ...], ...]] = None
+    # atomic number of each model species for the ZBL repulsion term; None: no ZBL term.
+    # Not part of the weights blob (the library does not evaluate it yet).
+    zbl_z: Optional[Tuple[int, ...]] = None
 
     @property
     def max_rc(self) -> float:

@@ -270,3 +270,98 @@ def test_c1_runs_and_is_finite():
     E, Ea, F, W = _ef(m, s)
     assert np.isfinite(E) and np.all(np.isfinite(F)) and np.all(np.isfinite(W))
     assert abs(Ea.sum() - E) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Heteronuclear closed forms: which atom an edge energy belongs to, and which
+# one-hot block carries the centre's species, written out by hand.
+# ---------------------------------------------------------------------------
+HETERO = Arch(n_species=2, lmax=0, n_layers=1, channels=1, two_body=(2,), latent=(2,), edge=(2,),
+              n_bessel=1)
+
+
+def _hetero_weights():
+    """Two species with different sigma and mu, a two-body layer whose centre
+    and neighbour one-hot columns differ, a two-wide latent MLP and a linear
+    edge MLP with one hidden layer (so E_ij = W_e1 W_e0 x^1)."""
+    w = make_weights(HETERO, 0)
+    #                      Zi=0   Zi=1   Zj=0   Zj=1   B
+    w["two_body.0"][:] = [[0.40, -0.70, 1.10, 0.20, 0.90],
+                          [-0.50, 0.30, 0.60, -1.20, 0.45]]
+    w["embed"][:] = [[1.7, -0.4]]
+    w["env.1"][:] = [[-0.8, 0.55]]
+    w["tp.1"][:] = 0.0
+    w["tp.1"][0, 0, 0, 0, 0] = 1.3
+    w["latent.1.0"][:] = [[0.6, -0.9, 2.0],
+                          [0.25, 0.7, -1.5]]
+    w["edge.0"][:] = [[1.5, -0.3],
+                      [0.2, 0.8]]
+    w["edge.1"][:] = [[0.9, -1.1]]
+    w["sigma"][:] = [1.2, 0.7]
+    w["mu"][:] = [-3.0, 2.5]
+    return w
+
+
+def _hand_energies(pos, spec, w, to_neighbour=False, swap_blocks=False):
+    """Per-atom energies of a 1-layer, l_max 0, one-channel model by hand:
+    the Allegro sums of Sec. "Allegro" with E_i = sum over the edges whose
+    CENTRE is i, the two-body input [onehot(Z_i) | onehot(Z_j) | B(r_ij)],
+    Gamma_i = nu sum_{k in N(i)} w^1_ik Y_00 (Y_00 = 1 in the component
+    normalisation), V^1_ij = theta V^0_ij Gamma_i, all in plain floats.
+    `to_neighbour` / `swap_blocks` make the two plausible mistakes on purpose
+    (edge energy given to j; one-hot blocks in the order Z_j, Z_i)."""
+    f = lambda a: [[float(np.float32(x)) for x in row] for row in np.atleast_2d(a)]
+    W2, We, Wv, Wl, E0, E1 = (f(w[k]) for k in ("two_body.0", "embed", "env.1", "latent.1.0",
+                                                  "edge.0", "edge.1"))
+    th = float(np.float32(1.3))
+    sig, mu = w["sigma"], w["mu"]
+    sil = lambda z: z / (1.0 + math.exp(-z))
+    rc, nu, n = 4.0, 1.0 / math.sqrt(27.0), len(spec)
+    edges = [(a, b) for a in range(n) for b in range(n)
+             if a != b and np.linalg.norm(pos[b] - pos[a]) < rc]
+    x0, uu = {}, {}
+    for a, b in edges:
+        r = float(np.linalg.norm(pos[b] - pos[a]))
+        B = math.sqrt(2 / rc) * math.sin(math.pi * r / rc) / r
+        x = r / rc
+        uu[a, b] = 1 - 28 * x ** 6 + 48 * x ** 7 - 21 * x ** 8
+        zc, zn = (spec[b], spec[a]) if swap_blocks else (spec[a], spec[b])
+        inp = [1.0 if zc == 0 else 0.0, 1.0 if zc == 1 else 0.0,
+               1.0 if zn == 0 else 0.0, 1.0 if zn == 1 else 0.0, B]
+        x0[a, b] = [uu[a, b] * sil(sum(W2[o][k] * inp[k] for k in range(5))) for o in range(2)]
+    gam = {a: nu * sum(Wv[0][0] * x0[c, d][0] + Wv[0][1] * x0[c, d][1] for c, d in edges if c == a)
+           for a in range(n)}
+    Eat = [0.0] * n
+    for a, b in edges:
+        V0 = We[0][0] * x0[a, b][0] + We[0][1] * x0[a, b][1]
+        s = th * V0 * gam[a]
+        h = [x0[a, b][0], x0[a, b][1], s]
+        x1 = [uu[a, b] * sil(sum(Wl[o][k] * h[k] for k in range(3))) for o in range(2)]
+        hid = [E0[o][0] * x1[0] + E0[o][1] * x1[1] for o in range(2)]
+        Eat[b if to_neighbour else a] += E1[0][0] * hid[0] + E1[0][1] * hid[1]
+    return [sig[spec[a]] * Eat[a] + mu[spec[a]] for a in range(n)]
+
+
+@pytest.mark.parametrize("case", ["dimer", "trimer"])
+def test_heteronuclear_closed_form(case):
+    """Per-atom and total energies of a heteronuclear dimer and an asymmetric
+    trimer against the hand evaluation.  Swapping centre and neighbour in the
+    per-atom sum, or the order of the one-hot blocks, changes every E_i here."""
+    w = _hetero_weights()
+    m = AllegroOracle(HETERO, w)
+    if case == "dimer":
+        pos = np.array([[0.0, 0.0, 0.0], [0.4, 2.1, -0.3]])
+        spec = np.array([0, 1])
+    else:
+        pos = np.array([[0.0, 0.0, 0.0], [1.9, 0.3, 0.0], [0.5, 2.6, 0.8]])
+        spec = np.array([1, 0, 1])
+    i, j, S = neighbor_list(pos, None, [False] * 3, 4.0)
+    E, Ea, _, _ = m.energy_forces(pos, spec, None, i, j, S)
+    ref = _hand_energies(pos, spec, w)
+    np.testing.assert_allclose(Ea, ref, rtol=0, atol=1e-12)
+    assert abs(E - sum(ref)) < 1e-12
+    # the case discriminates: attributing each edge to its neighbour, or
+    # exchanging the one-hot blocks, moves every per-atom energy
+    for bad in (dict(to_neighbour=True), dict(swap_blocks=True)):
+        wrong = _hand_energies(pos, spec, w, **bad)
+        assert min(abs(x - y) for x, y in zip(ref, wrong)) > 1e-3, bad

@@ -175,8 +175,59 @@ def _traffic_per_launch(detail: dict, steps: int, n_edges: int):
         return None
 
 
-def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int = 0):
-    """Dominant kernel (largest total time) of the timed region against its roofline."""
+def model_macs_per_edge(arch) -> int:
+    """Forward multiply-adds per edge of every MLP of the model as the architecture
+    defines it: two-body, embedding, per layer env weights and latent MLP, and the
+    edge-energy MLP (the scope table's per-edge count; the library folds the linear
+    edge MLP into one vector and forms the first two-body layer on the CUDA cores,
+    so it executes fewer)."""
+    macs, fan = 0, arch.n_in_two_body
+    for w in arch.two_body:
+        macs += fan * w
+        fan = w
+    macs += arch.latent_width(0) * arch.n_w                      # embedding
+    for L in range(1, arch.n_layers + 1):
+        kin = arch.latent_width(L - 1)
+        macs += kin * arch.n_w                                   # env weights of layer L
+        fan = kin + arch.channels
+        for w in arch.latent:
+            macs += fan * w
+            fan = w
+    fan = arch.latent_width(arch.n_layers)
+    for w in tuple(arch.edge) + (1,):
+        macs += fan * w
+        fan = w
+    return macs
+
+
+def model_flops_per_edge(arch) -> float:
+    """MLP FLOPs per edge of one energy + force evaluation: the forward and the
+    input-gradient adjoint, each 2 FLOPs per multiply-add."""
+    return 2.0 * 2.0 * model_macs_per_edge(arch)
+
+
+def step_bytes_per_edge(arch, edges_per_atom: float, act_bytes: int = 2) -> float:
+    """Algorithmic HBM bytes per edge of a whole step with fused, on-chip MLP
+    activations: the CSR entry (16 B), the latents x^0..x^L kept for the adjoint
+    (written once, read once), the per-atom environments and their adjoints
+    (C S float32 per layer, two each) shared by the row's edges, and the edge
+    force vector g_ij written and read (float32 x 3)."""
+    S = (arch.lmax + 1) ** 2
+    lat = sum(2.0 * arch.latent_width(L) * act_bytes for L in range(arch.n_layers + 1))
+    per_atom = 2.0 * arch.n_layers * arch.channels * S * 4.0
+    return 16.0 + lat + per_atom / max(edges_per_atom, 1e-9) + 24.0
+
+
+def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int = 0, arch=None,
+              n_atoms: int = 0):
+    """Dominant kernel (largest total time) of the timed region against its roofline.
+
+    The MLP GEMMs (all "gemm_tc" launches together) are a dense contraction:
+    bound "tensor", achieved = the model's MLP FLOPs per launch (the scope
+    table's per-edge count x the edges one launch covers) / the launches'
+    average CUDA-event duration, against the sustained BF16 peak (kernels timed
+    inside a long step).  Other kernels: HBM, algorithmic bytes per launch
+    against the measured copy bandwidth."""
     if not report:
         return None
     detail = report
@@ -186,65 +237,140 @@ def _roofline(report: dict, step_ms_total: float, steps: int = 1, n_edges: int =
     tensor = name.startswith("gemm_tc")
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     tc_peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-    tc_ctx = None
-    bound = "hbm"
-    if tensor:
-        # the MLP GEMMs' arithmetic intensity (algorithmic FLOPs per algorithmic byte)
-        # decides which roof binds them: below the ridge point it is HBM
-        intensity = r["flops"] / max(r["bytes"], 1.0)
-        ridge = tc_peak * 1e12 / (hbm_peak * 1e9)
-        tflops = r["flops"] / (r["ms"] * 1e-3) / 1e12
-        tc_ctx = {"achieved_tflops": round(tflops, 2), "peak_tflops": tc_peak, "frac": round(tflops / tc_peak, 4),
-                  "arithmetic_intensity_flop_per_byte": round(intensity, 1),
-                  "ridge_flop_per_byte": round(ridge, 1)}
-        bound = "tensor" if intensity >= ridge else "hbm"
-    if bound == "tensor":
-        peak, achieved, unit = tc_peak, r["flops"] / (r["ms"] * 1e-3) / 1e12, "TFLOP/s"
-    else:
-        peak, achieved, unit = hbm_peak, r["bytes"] / (r["ms"] * 1e-3) / 1e9, "GB/s"
+    L = max(r["launches"], 1)
+    ms_launch = r["ms"] / L
     share = {k: round(v["ms"] / max(step_ms_total, 1e-9), 4) for k, v in
              sorted(report.items(), key=lambda kv: -kv[1]["ms"])}
-    return {"kernel": name, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
-            "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
-            "traffic": _traffic_per_launch(detail, steps, n_edges) if tensor else None,
-            "traffic_unit": "bytes per launch (DRAM read + write)",
-            "algorithmic_bytes_per_launch": r["bytes"] / max(r["launches"], 1),
-            "launches": r["launches"], "ms_per_launch": round(r["ms"] / max(r["launches"], 1), 5),
-            "tensor": tc_ctx,
-            "share_of_timed_region": share,
-            "gemm_detail": {k.split("/", 1)[1]: {
-                                                 "share": round(v["ms"] / max(step_ms_total, 1e-9), 4),
-                                                 "TFLOP/s": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 1),
-                                                 "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
-                            for k, v in sorted(detail.items(), key=lambda kv: -kv[1]["ms"]) if "/" in k}}
+    out = {"kernel": name, "peak_source": "measured" if peaks else "fallback",
+           "launches": r["launches"], "ms_per_launch": round(ms_launch, 5), "share_of_timed_region": share}
+    if tensor and arch is not None and n_edges:
+        fpe = model_flops_per_edge(arch)
+        flops_launch = fpe * n_edges * steps / L
+        achieved = flops_launch / (ms_launch * 1e-3) / 1e12
+        traffic = _traffic_per_launch(detail, steps, n_edges)
+        edges_launch = n_edges * steps / L
+        s8d = step_bytes_per_edge(arch, n_edges / max(n_atoms, 1))
+        out.update({"bound": "tensor", "achieved": round(achieved, 2), "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / tc_peak, 4), "peak_kind": "bf16 sustained (of measured)",
+                    "model_flops_per_edge": fpe, "edges_per_launch": round(edges_launch, 1),
+                    "flops_per_launch": flops_launch,
+                    "executed_flops_per_launch": r["flops"] / L,
+                    "executed_tflops": round(r["flops"] / (r["ms"] * 1e-3) / 1e12, 2),
+                    "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write)",
+                    "traffic_bytes_per_edge_per_step": (traffic * L / (n_edges * steps)) if traffic else None,
+                    "decomposition_bytes_per_launch": r["bytes"] / L,
+                    "decomposition_gbs": round(r["bytes"] / (r["ms"] * 1e-3) / 1e9, 1),
+                    "step_bytes_per_edge": round(s8d, 1),
+                    "wasted_traffic_ratio": round(traffic * L / (n_edges * steps) / s8d, 2) if traffic else None})
+    elif tensor:
+        achieved = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        out.update({"bound": "tensor", "achieved": round(achieved, 2), "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / tc_peak, 4), "traffic": None})
+    else:
+        achieved = r["bytes"] / (r["ms"] * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                    "algorithmic_bytes_per_launch": r["bytes"] / L})
+    if arch is not None and n_edges and n_atoms:
+        s8d = step_bytes_per_edge(arch, n_edges / n_atoms)
+        step_ms = step_ms_total / max(steps, 1)
+        gbs = s8d * n_edges / (step_ms * 1e-3) / 1e9
+        out["step_hbm"] = {"bytes_per_edge": round(s8d, 1), "achieved_gbs": round(gbs, 1), "peak": hbm_peak,
+                           "frac": round(gbs / hbm_peak, 4),
+                           "note": "whole step against the fused-activation byte budget"}
+    out["kernels"] = {k: {"share": round(v["ms"] / max(step_ms_total, 1e-9), 4),
+                          "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1),
+                          "frac_hbm": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9 / hbm_peak, 4)}
+                      for k, v in sorted(report.items(), key=lambda kv: -kv[1]["ms"]) if not k.startswith("gemm")}
+    out["gemm_detail"] = {k.split("/", 1)[1]: {
+                              "share": round(v["ms"] / max(step_ms_total, 1e-9), 4),
+                              "TFLOP/s": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 1),
+                              "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
+                          for k, v in sorted(detail.items(), key=lambda kv: -kv[1]["ms"]) if "/" in k}
+    return out
 
 
-def _cpu_baseline(arch, w, blob, precision_models: dict):
-    """FP64 oracle on a bounded sample (the 4,096-atom box of the same density and model),
-    and the GPU paths' force errors against it on that sample."""
+def _force_errors(F, E, F0, E0) -> dict:
+    import numpy as np
+    rms = float(np.sqrt((F0 ** 2).mean()))
+    return {"force_rms_err_over_rms_F": float(np.sqrt(((F - F0) ** 2).mean()) / rms),
+            "force_max_err_over_rms_F": float(np.abs(F - F0).max() / rms),
+            "E_rel_err": float(abs(E - E0) / abs(E0))}
+
+
+def _cpu_baseline(arch, w, blob, precision_models: dict, timed_steps: int = 3):
+    """FP64 oracle on a bounded sample (the 4,096-atom box of the same density and
+    model): one untimed warm-up step, then `timed_steps` timed steps; and the GPU
+    paths' force errors against it on that sample."""
     import numpy as np
     import torch
     from oracle.allegro import AllegroOracle
     from synth import make_config
     torch.set_num_threads(os.cpu_count() or 1)
     s, _, _ = make_config("c4sub")
+    orc = AllegroOracle(arch, w)
+
+    def step():
+        i, j, S = _edges(arch, s)
+        return (i,) + tuple(orc.energy_forces(s.pos, s.species, s.cell, i, j, S))
+
+    i, E0, Ea0, F0, W0 = step()                      # warm-up (also the reference values)
     t0 = time.perf_counter()
-    i, j, S = _edges(arch, s)
-    E0, Ea0, F0, W0 = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, i, j, S)
-    dt = time.perf_counter() - t0
+    for _ in range(timed_steps):
+        step()
+    dt = (time.perf_counter() - t0) / timed_steps
     errs = {}
-    rms = float(np.sqrt((F0 ** 2).mean()))
     for prec, m in precision_models.items():
         m.neighbors(s.pos, s.species, s.cell)
         out = m.energy_forces()
-        F = out["F"].cpu().numpy()
-        errs[prec] = {"force_rms_err_over_rms_F": float(np.sqrt(((F - F0) ** 2).mean()) / rms),
-                      "force_max_err_over_rms_F": float(np.abs(F - F0).max() / rms),
-                      "E_rel_err": float(abs(out["E"].item() - E0) / abs(E0))}
+        errs[prec] = _force_errors(out["F"].cpu().numpy(), out["E"].item(), F0, E0)
     return {"value": s.n_atoms / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"1 step (neighbours + E + F + virial) of the {s.n_atoms}-atom periodic box at the "
-                      f"same density and model ({len(i)} edges), FP64 torch on the host cores",
-            "seconds": round(dt, 3)}, {"sample": "4,096-atom box, all atoms", "fp64_oracle_rms_F": rms, **errs}
+            "sample": f"{timed_steps} timed steps after 1 warm-up (neighbours + E + F + virial) of the "
+                      f"{s.n_atoms}-atom periodic box at the same density and model ({len(i)} edges), FP64 torch "
+                      "on the host cores",
+            "seconds_per_step": round(dt, 3)}, {"sample": "4,096-atom box, all atoms",
+                                                "fp64_oracle_rms_F": float(np.sqrt((F0 ** 2).mean())), **errs}
+
+
+def _pair_cutoff_run(args, make_model, pos, types, cell, out, N, steps: int):
+    """The same box under the paper's per-ordered-species-pair cutoff table:
+    step time and edges on the GPU, and the GPU paths' force errors against the
+    FP64 oracle on the 4,096-atom sample under the same table."""
+    import torch
+    from dataclasses import replace
+    from synth import make_config, paper_pair_cutoffs
+    from oracle.allegro import AllegroOracle
+    res = {}
+    m = make_model(args.precision, pair=True)
+    for _ in range(2):
+        m.neighbors(pos, types, cell)
+        m.energy_forces(out=out)
+    torch.cuda.synchronize()
+    st = m.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        m.neighbors(pos, types, cell)
+        m.energy_forces(out=out)
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    res.update({"ms_per_step": ms, "atom_steps_per_s": N / (ms * 1e-3), "edges": m.n_edges, "unit": UNIT,
+                "table": "H-H 3.0, H-C 1.25, H-O 1.25, O-H 3.0 A, every other ordered pair 4.0 A"})
+    if not args.skip_cpu:
+        s, arch, w = make_config("c4sub")
+        arch = replace(arch, pair_rc=paper_pair_cutoffs(default=arch.r_c))
+        i, j, S = _edges(arch, s)
+        E0, _, F0, _ = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, i, j, S)
+        for prec in (args.precision, "fp32"):
+            mm = m if prec == args.precision else make_model(prec, pair=True)
+            mm.neighbors(s.pos, s.species, s.cell)
+            o = mm.energy_forces()
+            res[f"force_err_vs_fp64_{prec}"] = _force_errors(o["F"].cpu().numpy(), o["E"].item(), F0, E0)
+            if mm is not m:
+                mm.close()
+    m.close()
+    return res
 
 
 def run_reference(args):
@@ -311,13 +437,17 @@ def run_ours(args):
     cell = torch.tensor(s.cell, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
-    def make(prec):
+    def make(prec, pair=False):
         m = Allegro(blob, precision=prec, device=local)
         m.set_stream(stream.cuda_stream)
+        m.stream = stream
         if args.chunk_edges:
             m.reserve(0, 0, False, args.chunk_edges)
         if arch.pair_rc is not None:
             m.set_pair_cutoffs(arch.pair_rc)
+        elif pair:
+            from synth import paper_pair_cutoffs
+            m.set_pair_cutoffs(paper_pair_cutoffs(default=arch.r_c))
         return m
 
     def timed(m, K, W, out):
@@ -438,6 +568,42 @@ def run_ours(args):
                                    "atom_steps_per_s": s2.n_atoms * nmd / dt_md,
                                    "energy_drift_eV_per_atom": float(abs((Ep[-1] + Ek[-1]) - (Ep[0] + Ek[0])) / s2.n_atoms),
                                    "note": "velocity Verlet on the GPU, neighbour rebuild every step"}
+        # the smaller named workloads (E + F + virial with a neighbour rebuild per step), both precisions
+        for name, label in (("c2", "c2_23552_atoms"), ("c1", "c1_64_atoms")):
+            sx, ax, wx = make_config(name)
+            bx = weights_to_blob(ax, wx)
+            px = torch.tensor(sx.pos, device=dev)
+            tx = torch.tensor(sx.species, dtype=torch.int32, device=dev)
+            cx = torch.tensor(sx.cell, device=dev)
+            rec = {"atoms": sx.n_atoms, "unit": UNIT}
+            for prec in (args.precision, "fp32"):
+                mx = Allegro(bx, precision=prec, device=local)
+                mx.set_stream(stream.cuda_stream)
+                ox = dict(E=torch.empty(1, dtype=torch.float64, device=dev),
+                          E_atom=torch.empty(sx.n_atoms, dtype=torch.float64, device=dev),
+                          F=torch.empty(sx.n_atoms, 3, dtype=torch.float64, device=dev),
+                          virial=torch.empty(1, 3, 3, dtype=torch.float64, device=dev))
+                for _ in range(3):
+                    mx.neighbors(px, tx, cx)
+                    mx.energy_forces(out=ox)
+                torch.cuda.synchronize()
+                kx = 20 if name == "c2" else 50
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                for _ in range(kx):
+                    mx.neighbors(px, tx, cx)
+                    mx.energy_forces(out=ox)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                msx = ea.elapsed_time(eb) / kx
+                rec["edges"] = mx.n_edges
+                rec[prec] = {"ms_per_step": msx, "atom_steps_per_s": sx.n_atoms / (msx * 1e-3)}
+                mx.close()
+            extra[label] = rec
+        # the headline box under the paper's per-ordered-species-pair cutoffs
+        if arch.pair_rc is None:
+            extra["pair_cutoffs_1M_atoms" if args.config == "c4" and not args.atoms else "pair_cutoffs"] = \
+                _pair_cutoff_run(args, make, pos, types, cell, out, N, max(1, min(args.steps, 5)))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -450,7 +616,7 @@ def run_ours(args):
             "e2e": {"value": N * ws / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches1 - launches0),
-            "roofline": _roofline(report, ms * args.steps, args.steps, n_edges)}
+            "roofline": _roofline(report, ms * args.steps, args.steps, n_edges, arch, N)}
     if fp32:
         line["fp32"] = fp32
     line.update(extra)

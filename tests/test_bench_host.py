@@ -1,8 +1,9 @@
 """Host logic of bench.py's roofline report (no GPU): per-kernel aggregation of
-the library's profile records, the choice of the binding roof from the
-arithmetic intensity against the measured ridge point, the achieved fraction,
-the shares of the timed region, and the DRAM traffic scaled from the committed
-capture to a run's edges per launch."""
+the library's profile records, the model's MLP FLOPs and the fused-activation
+byte budget per edge from the architecture, the MLP GEMMs against the tensor
+roof with the model's FLOPs per launch, other kernels against HBM, the shares
+of the timed region, and the DRAM traffic scaled from the committed capture to
+a run's edges per launch."""
 import json
 import os
 import sys
@@ -26,33 +27,46 @@ def test_by_kernel_sums_the_maps_of_a_kernel():
     assert out["row_bwd_mid"] == _rec(1, 0.5, 0.0, 3.0)
 
 
-def test_roofline_hbm_bound_below_the_ridge():
-    peaks = bench._peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    tc = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-    ridge = tc * 1e12 / (hbm * 1e9)
-    # one GEMM map: 2 ms, intensity half the ridge point
-    nbytes = 1e10
-    flops = 0.5 * ridge * nbytes
-    rep = {"gemm_tc/x:silu": _rec(4, 2.0, flops, nbytes), "row_fwd_mid": _rec(1, 1.0, 0.0, 1e9)}
-    r = bench._roofline(rep, step_ms_total=4.0, steps=1, n_edges=0)
-    assert r["kernel"] == "gemm_tc" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["achieved"] == pytest.approx(nbytes / 2e-3 / 1e9, rel=1e-6)
-    assert r["frac"] == pytest.approx(r["achieved"] / hbm, abs=1e-4)
-    assert r["tensor"]["arithmetic_intensity_flop_per_byte"] == pytest.approx(0.5 * ridge, abs=0.1)
-    assert r["share_of_timed_region"] == {"gemm_tc": 0.5, "row_fwd_mid": 0.25}
-    assert r["launches"] == 4 and r["ms_per_launch"] == pytest.approx(0.5)
-    assert r["gemm_detail"]["x:silu"]["share"] == 0.5
+def test_model_macs_follow_the_architecture():
+    from synth import ARCHS
+    # 2 layers, l_max 2, 64 channels, two-body 18->64->128->256, latent (256+64)->256->256,
+    # embedding and env weights 256->192, edge 256->128->1
+    assert bench.model_macs_per_edge(ARCHS["c2"]) == (18 * 64 + 64 * 128 + 128 * 256 + 256 * 192
+                                                      + 2 * (256 * 192 + 320 * 256 + 256 * 256)
+                                                      + 256 * 128 + 128) == 517_376
+    # 1 layer, l_max 1, 8 channels: 12->32, 32->16, 32->16, (32+8)->32, 32->1
+    assert bench.model_macs_per_edge(ARCHS["c1"]) == 12 * 32 + 32 * 16 + 32 * 16 + 40 * 32 + 32
+    assert bench.model_flops_per_edge(ARCHS["c2"]) == 4 * 517_376
 
 
-def test_roofline_tensor_bound_above_the_ridge():
+def test_step_bytes_per_edge():
+    from synth import ARCHS
+    # CSR 16 B + x^0, x^1, x^2 (256 bf16 each) written and read + 4 per-atom C S float32 arrays
+    # shared by ~25 edges + g written and read
+    b = bench.step_bytes_per_edge(ARCHS["c2"], 25.0)
+    assert b == pytest.approx(16 + 3 * 2 * 512 + 4 * 64 * 9 * 4 / 25.0 + 24)
+
+
+def test_gemm_roofline_is_tensor_bound_with_model_flops():
+    from synth import ARCHS
+    arch = ARCHS["c2"]
     peaks = bench._peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
     tc = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-    ridge = tc * 1e12 / (hbm * 1e9)
-    rep = {"gemm_tc/x:silu": _rec(1, 1.0, 4.0 * ridge * 1e9, 1e9)}
-    r = bench._roofline(rep, step_ms_total=1.0)
-    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["peak"] == tc
+    n_edges, n_atoms, steps = 1_000_000, 40_000, 2
+    # 20 launches over 2 steps, 3 ms each; executed flops deliberately different from the model's
+    rep = {"gemm_tc/x:silu": _rec(12, 36.0, 1e12, 1e10), "gemm_tc/y:head": _rec(8, 24.0, 5e11, 1e10),
+           "row_fwd_mid": _rec(2, 10.0, 0.0, 1e9)}
+    r = bench._roofline(rep, step_ms_total=100.0, steps=steps, n_edges=n_edges, arch=arch, n_atoms=n_atoms)
+    assert r["kernel"] == "gemm_tc" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["peak"] == tc
+    flops_launch = bench.model_flops_per_edge(arch) * n_edges * steps / 20
+    assert r["flops_per_launch"] == pytest.approx(flops_launch)
+    assert r["ms_per_launch"] == pytest.approx(3.0)
+    assert r["achieved"] == pytest.approx(flops_launch / 3e-3 / 1e12, rel=1e-4)
+    assert r["frac"] == pytest.approx(r["achieved"] / tc, abs=1e-4)
+    assert r["share_of_timed_region"] == {"gemm_tc": 0.6, "row_fwd_mid": 0.1}
+    sb = bench.step_bytes_per_edge(arch, n_edges / n_atoms)
+    assert r["step_hbm"]["achieved_gbs"] == pytest.approx(sb * n_edges / 50e-3 / 1e9, rel=1e-3)
+    assert r["gemm_detail"]["x:silu"]["share"] == 0.36
 
 
 def test_dominant_kernel_is_the_largest_total_time():

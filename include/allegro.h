@@ -190,18 +190,25 @@ allegro_status allegro_profile_report(allegro_ctx* ctx, char* buf, size_t cap, i
  * structure, computed without allocating any device memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate
  * device memory while they run (an MD engine whose memory pool owns the GPU, a
- * region under CUDA stream capture, a loop that must keep a fixed footprint),
- * and so cannot create a context.  Same pair rule as allegro_neighbors, by an
- * all-pairs search (meant for small structures).
- *   pos[n_atoms*3]: device float64; n_atoms <= 16384 (larger sizes return
- *       ALLEGRO_E_CAPACITY: the scratch is a fixed 128 KiB device array).
+ * loop that must keep a fixed footprint), and so cannot create a context.
+ * Same pair rule as allegro_neighbors (exact float64 test of every candidate
+ * image, strict r < r_c), by an all-pairs search (meant for small structures).
+ *   pos[n_atoms*3]: device float64, any positions (not necessarily wrapped
+ *       into the cell); n_atoms <= 16384 (larger sizes return
+ *       ALLEGRO_E_CAPACITY: the scratch is a fixed device array of about
+ *       128 KiB).  A non-finite position, or two positions more than 1e8 cell
+ *       widths apart, returns ALLEGRO_E_INVALID.
  *   cell[9] (rows a, b, c) and pbc[3]: HOST pointers or NULL (no cell: no
- *       periodicity).  Along periodic axes positions must lie within
- *       fractional coordinates [-0.5, 1.5).
- *   r_c > 0.  i[cap], j[cap], shift[cap*3]: device int32 outputs, rows in
- *       ascending i.  *n_edges (host): the edge count; ALLEGRO_E_CAPACITY if it
- *       exceeds cap (outputs then untouched).
- *   stream: cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ *       periodicity; pbc NULL: every axis periodic).  r_c > 0 and finite, and
+ *       r_c <= 4 perpendicular cell widths along each periodic axis, else
+ *       ALLEGRO_E_INVALID.  Inputs needing more than 6e10 (pair, image)
+ *       candidate tests return ALLEGRO_E_CAPACITY before any launch.
+ *   i[cap], j[cap], shift[cap*3]: device int32 outputs, rows in ascending i.
+ *       *n_edges (host): the edge count; ALLEGRO_E_CAPACITY if it exceeds cap
+ *       or INT32_MAX (outputs then untouched).
+ *   stream: cudaStream_t (NULL = legacy default stream).  The call reads the
+ *       edge count back to the host between its two passes and synchronises
+ *       the stream before it returns.
  * Runs on the current device.  Its scratch array lives in the library on every
  * device that loads it, until process exit.  The first call on a device looks
  * up the array's address there; make it before any stream capture.  Calls

@@ -103,6 +103,23 @@ allegro_status allegro_reserve(allegro_ctx* ctx, int64_t atom_cap, int64_t edge_
 allegro_status allegro_set_pair_cutoffs(allegro_ctx* ctx, const double* pair_rc, int32_t n_species);
 
 /*
+ * allegro_set_zbl -- add the ZBL screened nuclear repulsion (Sec. "Training
+ * details": the production potential carries a ZBL term) to every energy
+ * evaluation:  per ordered edge (i, j), half of
+ *   E_ZBL(r) = k_e Z_a Z_b / r * phi(r / a_s) * u(r / rc),
+ *   a_s = 0.8854 a_0 / (Z_a^0.23 + Z_b^0.23),  k_e = 14.399645 eV A,  a_0 = 0.529177 A,
+ *   phi(x) = 0.18175 e^-3.19980x + 0.50986 e^-0.94229x + 0.28022 e^-0.40290x + 0.02817 e^-0.20162x
+ * (the universal ZBL screening function), u the model's envelope with the
+ * edge's cutoff, is added to atom i's energy after the per-species scale and
+ * shift (E_i = sigma_Z E_i^model + mu_Z + sum_j E_ZBL(r_ij) / 2), with its
+ * forces and virial.  Evaluated in float32 per edge, summed in float64.
+ *   atomic_numbers: host, n_species int32 in 1..118 (Z of each model species);
+ *       NULL removes the term.
+ * Errors: ALLEGRO_E_INVALID (bad count or entry), ALLEGRO_E_CUDA.
+ */
+allegro_status allegro_set_zbl(allegro_ctx* ctx, const int32_t* atomic_numbers, int32_t n_species);
+
+/*
  * allegro_neighbors -- build the ordered neighbour list of one structure.
  * An edge is (i, j, S), S in Z^3 an image shift, displacement
  *   d = (pos_j + (S0 a + S1 b) + S2 c) - pos_i  evaluated in float64 in that
@@ -161,6 +178,20 @@ allegro_status allegro_md_verlet(allegro_ctx* ctx, int64_t n_atoms, double* pos,
                                  const int32_t* types, const double* masses, int32_t n_types,
                                  const double* cell, const uint8_t* pbc, double dt, int64_t n_steps,
                                  double* E_pot, double* E_kin);
+
+/*
+ * allegro_set_md_skin -- neighbour reuse with a Verlet skin in
+ * allegro_md_verlet (the paper's MD runs keep neighbour lists between
+ * rebuilds, Sec. "Results"): skin > 0 builds a candidate list at r_c + skin
+ * and rebuilds it only once some atom has moved skin/2 since; every step the
+ * exact list (the same pair rule as allegro_neighbors) is filtered from the
+ * candidates, so energies and forces are those of a rebuild every step.
+ * skin = 0 (the default) rebuilds every step.  skin in [0, 4 r_c], finite.
+ * allegro_md_rebuilds -- candidate-list builds (or full rebuilds when the
+ * skin is 0) made by the last allegro_md_verlet call, into *rebuilds.
+ */
+allegro_status allegro_set_md_skin(allegro_ctx* ctx, double skin);
+allegro_status allegro_md_rebuilds(const allegro_ctx* ctx, int64_t* rebuilds);
 
 /*
  * allegro_get_neighbors -- copy the last neighbour list out, sorted by centre

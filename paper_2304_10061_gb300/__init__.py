@@ -113,6 +113,14 @@ class Allegro:
             raise ValueError("pair_rc must be a square [n_species][n_species] table")
         self._check(self._L.allegro_set_pair_cutoffs(self._ctx, t.ctypes.data, int(t.shape[0])))
 
+    def set_zbl(self, atomic_numbers=None):
+        """ZBL repulsion with the atomic number of each model species (None removes it)."""
+        if atomic_numbers is None:
+            self._check(self._L.allegro_set_zbl(self._ctx, None, 0))
+            return
+        z = np.ascontiguousarray(np.asarray(atomic_numbers, dtype=np.int32))
+        self._check(self._L.allegro_set_zbl(self._ctx, z.ctypes.data, int(z.size)))
+
     def neighbors(self, pos, types, cell=None, pbc=None) -> int:
         pos = _as(pos, np.float64)
         types = _as(types, np.int32)
@@ -172,6 +180,16 @@ class Allegro:
                                               Ep.ctypes.data, Ek.ctypes.data))
         self.n_atoms, self.n_struct = n, 1
         return Ep, Ek
+
+    def set_md_skin(self, skin: float):
+        """Verlet skin (A) for md_verlet's neighbour reuse; 0 rebuilds every step."""
+        self._check(self._L.allegro_set_md_skin(self._ctx, float(skin)))
+
+    def md_rebuilds(self) -> int:
+        """Neighbour-list builds made by the last md_verlet call."""
+        n = ctypes.c_int64(0)
+        self._check(self._L.allegro_md_rebuilds(self._ctx, ctypes.byref(n)))
+        return int(n.value)
 
     def profile(self, enable: bool = True):
         self._check(self._L.allegro_profile(self._ctx, int(bool(enable))))

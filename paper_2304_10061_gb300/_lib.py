@@ -18,9 +18,10 @@ STATUS_NAMES = {
 }
 PREC = {"fp32": 0, "bf16": 1}
 
-EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_reserve", "allegro_neighbors",
+EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_set_zbl", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
-           "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_last_error",
+           "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_set_md_skin", "allegro_md_rebuilds",
+           "allegro_last_error",
            "allegro_destroy")
 
 _lib = None
@@ -39,6 +40,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_set_stream.argtypes = [vp, vp]
     L.allegro_reserve.argtypes = [vp, i64, i64, i32, i64]
     L.allegro_set_pair_cutoffs.argtypes = [vp, dp, i32]
+    L.allegro_set_zbl.argtypes = [vp, dp, i32]
     L.allegro_neighbors.argtypes = [vp, i64, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_neighbors_batched.argtypes = [vp, i32, dp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_energy_forces.argtypes = [vp, dp, dp, dp, dp]
@@ -48,6 +50,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_neighbors_noalloc.argtypes = [dp, i64, dp, dp, ctypes.c_double, dp, dp, dp, i64,
                                             ctypes.POINTER(i64), vp]
     L.allegro_md_verlet.argtypes = [vp, i64, dp, dp, dp, dp, i32, dp, dp, ctypes.c_double, i64, dp, dp]
+    L.allegro_set_md_skin.argtypes = [vp, ctypes.c_double]
+    L.allegro_md_rebuilds.argtypes = [vp, ctypes.POINTER(i64)]
     L.allegro_last_error.argtypes = [vp]
     L.allegro_last_error.restype = ctypes.c_char_p
     L.allegro_destroy.argtypes = [vp]

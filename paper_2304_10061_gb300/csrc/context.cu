@@ -111,6 +111,7 @@ struct allegro_ctx {
   // per-ordered-species-pair cutoffs (arch.pair_basis / arch.pair_rc2 point here)
   float* d_pair_basis = nullptr;
   double* d_pair_rc2 = nullptr;
+  float* d_zbl = nullptr;                  // ZBL pair table (arch.zbl points here)
 
   // model on the device
   std::vector<Lin> tb;                     // two-body layers
@@ -197,6 +198,17 @@ struct allegro_ctx {
   double* d_md_K = nullptr;
   double* d_md_part = nullptr;
   int64_t md_atoms = 0, md_steps = 0;
+  // Verlet-skin neighbour reuse in allegro_md_verlet: candidate list at r_c + skin
+  double md_skin = 0.0;
+  int64_t md_rebuilds = 0;
+  int* d_sk_row = nullptr;
+  int* d_sk_j = nullptr;
+  int* d_sk_S = nullptr;
+  double* d_sk_ref = nullptr;              // positions at the candidate build
+  double* d_cell9 = nullptr;               // cell of the last single-structure build (device copy)
+  unsigned long long* d_maxd = nullptr;
+  int64_t sk_row_cap = 0, sk_cap = 0, sk_S_cap = 0;
+  double h_cell[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int64_t launches = 0;                    // kernel launches issued by this context
   bool chain = true;                       // fuse consecutive MLP layers (BF16 path)
 
@@ -1145,7 +1157,7 @@ allegro_status evaluate(allegro_ctx* c, bool backward) {
   {
     ProfScope ps(c, "atom_reduce", 0.0, (double)E * (backward ? 60.0 : 4.0) + (double)n * (backward ? 128.0 : 16.0));
     atom_reduce(n, c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_Ee, c->d_g, c->d_ed, c->d_species, c->d_sigma,
-                c->d_mu, backward, c->d_Eatom, c->d_F, c->d_Wat, c->stream);
+                c->d_mu, backward, c->d_Eatom, c->d_F, c->d_Wat, c->d_ei, c->d_ej, c->arch, c->stream);
   }
   {
     ProfScope ps(c, "struct_reduce", 0.0, (double)n * (backward ? 104.0 : 8.0));
@@ -1270,6 +1282,35 @@ allegro_status allegro_set_pair_cutoffs(allegro_ctx* c, const double* pair_rc, i
   return ALLEGRO_OK;
 }
 
+allegro_status allegro_set_zbl(allegro_ctx* c, const int32_t* atomic_numbers, int32_t n_species) {
+  if (!c) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  if (!atomic_numbers) {
+    c->arch.zbl = nullptr;
+    return ALLEGRO_OK;
+  }
+  const int ns = c->arch.ns;
+  if (n_species != ns) return fail(c, ALLEGRO_E_INVALID, "n_species %d differs from the model's %d", n_species, ns);
+  for (int q = 0; q < ns; ++q)
+    if (atomic_numbers[q] < 1 || atomic_numbers[q] > 118)
+      return fail(c, ALLEGRO_E_INVALID, "atomic number of species %d = %d outside 1..118", q, atomic_numbers[q]);
+  // Coulomb constant e^2 / (4 pi eps_0) in eV A, Bohr radius in A, universal screening length
+  const double ke = 14.399645, a0 = 0.529177;
+  std::vector<float> t(2 * (size_t)ns * ns);
+  for (int za = 0; za < ns; ++za)
+    for (int zb = 0; zb < ns; ++zb) {
+      const double Za = atomic_numbers[za], Zb = atomic_numbers[zb];
+      const double as = 0.8854 * a0 / (std::pow(Za, 0.23) + std::pow(Zb, 0.23));
+      t[2 * ((size_t)za * ns + zb)] = (float)(0.5 * ke * Za * Zb);
+      t[2 * ((size_t)za * ns + zb) + 1] = (float)(1.0 / as);
+    }
+  if (!c->d_zbl) CUDA_TRY(c, cudaMalloc(&c->d_zbl, 2 * sizeof(float) * kMaxSpecies * kMaxSpecies));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_zbl, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->arch.zbl = c->d_zbl;
+  return ALLEGRO_OK;
+}
+
 allegro_status allegro_reserve(allegro_ctx* c, int64_t atom_cap, int64_t edge_cap, int32_t fixed,
                                int64_t chunk_edges) {
   if (!c || atom_cap < 0 || edge_cap < 0 || chunk_edges < 0) return ALLEGRO_E_INVALID;
@@ -1294,8 +1335,12 @@ allegro_status allegro_reserve(allegro_ctx* c, int64_t atom_cap, int64_t edge_ca
   return ALLEGRO_OK;
 }
 
-allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* pos, const int32_t* types,
-                                 const double* cell, const uint8_t* pbc, int64_t* n_edges_out) {
+// The cell-list search of one structure at `radius` (the model cutoff, or the
+// cutoff plus a Verlet skin for a candidate list), the per-pair table applied
+// only when `use_pair` is set.
+static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double* pos, const int32_t* types,
+                                   const double* cell, const uint8_t* pbc, int64_t* n_edges_out, double radius,
+                                   bool use_pair) {
   if (!c) return ALLEGRO_E_INVALID;
   c->have_nb = false;
   if (n_atoms < 0 || n_atoms > 1000000000LL) return fail(c, ALLEGRO_E_INVALID, "bad n_atoms");
@@ -1327,7 +1372,9 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
     hpbc[0] = hpbc[1] = hpbc[2] = 1;
   }
   CellGrid g{};
-  const double rc = c->arch.rc, rcm = rc * (1.0 + 1e-6);
+  const double rc = radius, rcm = rc * (1.0 + 1e-6);
+  const double* pair_rc2 = use_pair ? c->arch.pair_rc2 : nullptr;
+  memcpy(c->h_cell, hcell, sizeof hcell);
   double width[3] = {1, 1, 1};
   if (cell) {
     if (!invert3(hcell, g.inv)) return fail(c, ALLEGRO_E_INVALID, "cell is singular");
@@ -1421,7 +1468,7 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   {
     ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
     nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
-              band, c->arch.pair_rc2, c->arch.ns, c->d_count,
+              band, pair_rc2, c->arch.ns, c->d_count,
               nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
     exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
   }
@@ -1434,12 +1481,18 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
   {
     ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
     nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
-              band, c->arch.pair_rc2, c->arch.ns, nullptr,
+              band, pair_rc2, c->arch.ns, nullptr,
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
   if (n_edges_out) *n_edges_out = hE;
   return ALLEGRO_OK;
+}
+
+allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* pos, const int32_t* types,
+                                 const double* cell, const uint8_t* pbc, int64_t* n_edges_out) {
+  if (!c) return ALLEGRO_E_INVALID;
+  return build_single(c, n_atoms, pos, types, cell, pbc, n_edges_out, c->arch.rc, true);
 }
 
 allegro_status allegro_neighbors_batched(allegro_ctx* c, int32_t n_struct, const int64_t* atom_offsets,
@@ -1559,7 +1612,8 @@ allegro_status allegro_md_verlet(allegro_ctx* c, int64_t n_atoms, double* pos, d
   const int n = (int)n_atoms;
   if (n_atoms > c->md_atoms) {
     cudaFree(c->d_md_pos); cudaFree(c->d_md_vel); cudaFree(c->d_md_invm); cudaFree(c->d_md_types);
-    c->d_md_pos = c->d_md_vel = c->d_md_invm = nullptr;
+    cudaFree(c->d_sk_ref);
+    c->d_md_pos = c->d_md_vel = c->d_md_invm = c->d_sk_ref = nullptr;
     c->d_md_types = nullptr;
     c->md_atoms = 0;
     CUDA_TRY(c, cudaMalloc(&c->d_md_pos, (size_t)n * 24));
@@ -1590,14 +1644,77 @@ allegro_status allegro_md_verlet(allegro_ctx* c, int64_t n_atoms, double* pos, d
   allegro_status s = read_err(c, &err);
   if (s != ALLEGRO_OK) return s;
   if (err) return fail(c, ALLEGRO_E_INVALID, "md_verlet: a type has no positive mass");
+  // The neighbour list of the current positions: rebuilt by the cell-list
+  // search every step, or, with a Verlet skin, filtered from a candidate list
+  // built at r_c + skin, rebuilt only once some atom has moved skin/2 since
+  // that build (so every pair now within r_c was a candidate; the filter
+  // applies the exact rule, so the list equals a rebuild's as a set).
+  c->md_rebuilds = 0;
+  auto neighbours = [&](bool first) -> allegro_status {
+    if (!(c->md_skin > 0.0)) {
+      ++c->md_rebuilds;
+      return allegro_neighbors(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, nullptr);
+    }
+    bool rebuild = first;
+    if (!rebuild) {
+      nb_max_disp2(c->d_md_pos, c->d_sk_ref, n, c->d_maxd, st);
+      unsigned long long h = 0;
+      CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_maxd, sizeof h, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaStreamSynchronize(st));
+      double m2 = 0.0;
+      memcpy(&m2, &h, sizeof m2);
+      rebuild = !(2.0 * sqrt(m2) < c->md_skin * (1.0 - 1e-9));
+    }
+    allegro_status r;
+    if (rebuild) {
+      int64_t Ec = 0;
+      if ((r = build_single(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, &Ec, c->arch.rc + c->md_skin,
+                            false)) != ALLEGRO_OK)
+        return r;
+      CUDA_TRY(c, regrow(c->d_sk_row, c->sk_row_cap, (int64_t)n + 1));
+      CUDA_TRY(c, regrow(c->d_sk_j, c->sk_cap, std::max<int64_t>(Ec, 1)));
+      CUDA_TRY(c, regrow(c->d_sk_S, c->sk_S_cap, 3 * std::max<int64_t>(Ec, 1)));
+      if (!c->d_sk_ref) CUDA_TRY(c, cudaMalloc(&c->d_sk_ref, (size_t)c->md_atoms * 24));
+      if (!c->d_cell9) CUDA_TRY(c, cudaMalloc(&c->d_cell9, 9 * sizeof(double)));
+      if (!c->d_maxd) CUDA_TRY(c, cudaMalloc(&c->d_maxd, sizeof(unsigned long long)));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_sk_row, c->d_row_ptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_sk_j, c->d_ej, (size_t)Ec * 4, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_sk_S, c->d_eS, (size_t)Ec * 12, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_sk_ref, c->d_md_pos, (size_t)n * 24, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_cell9, c->h_cell, sizeof c->h_cell, cudaMemcpyHostToDevice, st));
+      ++c->md_rebuilds;
+    } else if ((r = stage_atoms(c, n, c->d_md_pos, c->d_md_types)) != ALLEGRO_OK) {
+      return r;
+    }
+    c->have_nb = false;
+    {
+      ProfScope ps(c, "nb_skin_filter", 0.0, (double)n * 64, 2);
+      nb_skin_filter(false, c->d_pos, n, c->d_cell9, c->d_sk_row, c->d_sk_j, c->d_sk_S, c->arch.rc * c->arch.rc,
+                     c->arch.pair_rc2, c->d_species, c->arch.ns, c->d_count, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, st);
+      exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
+    }
+    int hE = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&hE, c->d_row_ptr + n, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    if ((r = ensure_edges(c, hE)) != ALLEGRO_OK) return r;
+    {
+      ProfScope ps(c, "nb_skin_filter", 0.0, (double)hE * 44 + (double)n * 64);
+      nb_skin_filter(true, c->d_pos, n, c->d_cell9, c->d_sk_row, c->d_sk_j, c->d_sk_S, c->arch.rc * c->arch.rc,
+                     c->arch.pair_rc2, c->d_species, c->arch.ns, nullptr, c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS,
+                     c->d_ed, st);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    return finish_neighbors(c, n, hE);
+  };
   // forces at the initial positions
-  if ((s = allegro_neighbors(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, nullptr)) != ALLEGRO_OK) return s;
+  if ((s = neighbours(true)) != ALLEGRO_OK) return s;
   if ((s = evaluate(c, true)) != ALLEGRO_OK) return s;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_md_E, c->d_Eout, 8, cudaMemcpyDeviceToDevice, st));
   md_kinetic(n, c->d_md_vel, c->d_md_invm, c->d_md_part, c->d_md_K, st);
   for (int64_t k = 1; k <= n_steps; ++k) {
     md_kick(n, c->d_md_pos, c->d_md_vel, c->d_F, c->d_md_invm, dt, true, st);
-    if ((s = allegro_neighbors(c, n_atoms, c->d_md_pos, c->d_md_types, cell, pbc, nullptr)) != ALLEGRO_OK) return s;
+    if ((s = neighbours(false)) != ALLEGRO_OK) return s;
     if ((s = evaluate(c, true)) != ALLEGRO_OK) return s;
     md_kick(n, c->d_md_pos, c->d_md_vel, c->d_F, c->d_md_invm, dt, false, st);
     CUDA_TRY(c, cudaMemcpyAsync(c->d_md_E + k, c->d_Eout, 8, cudaMemcpyDeviceToDevice, st));
@@ -1611,6 +1728,20 @@ allegro_status allegro_md_verlet(allegro_ctx* c, int64_t n_atoms, double* pos, d
   if ((s = read_err(c, &err)) != ALLEGRO_OK) return s;
   if (err & kErrTimeout) return fail(c, ALLEGRO_E_TIMEOUT, "a bounded device wait expired; results are invalid");
   if (err & kErrNonFinite) return fail(c, ALLEGRO_E_NONFINITE, "non-finite energy or force");
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_set_md_skin(allegro_ctx* c, double skin) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (!(skin >= 0.0) || !std::isfinite(skin) || skin > 4.0 * c->arch.rc)
+    return fail(c, ALLEGRO_E_INVALID, "md skin %g outside [0, 4 r_c]", skin);
+  c->md_skin = skin;
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_md_rebuilds(const allegro_ctx* c, int64_t* rebuilds) {
+  if (!c || !rebuilds) return ALLEGRO_E_INVALID;
+  *rebuilds = c->md_rebuilds;
   return ALLEGRO_OK;
 }
 
@@ -1694,7 +1825,8 @@ void allegro_destroy(allegro_ctx* c) {
                   c->d_cell_start, c->d_cell_cursor, c->d_offs, c->d_cells, c->d_pbc, c->d_nimg, c->d_Eout,
                   c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,
                   c->d_md_pos, c->d_md_vel, c->d_md_invm, c->d_md_types, c->d_md_masses, c->d_md_E, c->d_md_K,
-                  c->d_md_part, c->d_pair_basis, c->d_pair_rc2};
+                  c->d_md_part, c->d_pair_basis, c->d_pair_rc2, c->d_zbl, c->d_sk_row, c->d_sk_j,
+                  c->d_sk_S, c->d_sk_ref, c->d_cell9, c->d_maxd};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

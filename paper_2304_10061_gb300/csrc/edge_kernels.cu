@@ -441,35 +441,93 @@ template void edge_energy<bf16>(int, int, const bf16*, int, const float*, float*
 // Per atom i (float64): Etilde_i = sigma_Z E_i + mu_Z with E_i = sum_{row i} E_ij;
 // F_i = sum_{e in row i} g_e - sum_{e with j_e = i} g_e  (g_e = dE/dd_e);
 // per-atom virial W_i = - sum_{e in row i} d_e (x) g_e.
+// ZBL repulsion of one ordered edge (Sec. "Training details": a Ziegler-
+// Biersack-Littmark term is added to the potential).  The universal ZBL pair
+// energy k_e Z_a Z_b / r phi(r / a_s), phi(x) = sum_k c_k exp(-d_k x) (the
+// published universal screening function), enveloped by u(r / rc) of the
+// edge's cutoff; half of it per ordered edge, in eV, not scaled by sigma_Z.
+// Returns the edge's energy and dE/dr (float32 arithmetic; the reduction that
+// uses them is float64).  zp = {k_e Z_a Z_b / 2, 1 / a_s} of the species pair.
+__device__ __forceinline__ void zbl_edge(float r, float2 zp, float inv_rc, const BasisConst& bc, float& e,
+                                         float& dedr) {
+  const float y = r * inv_rc;
+  if (!(y < 1.0f) || !(r > 0.0f)) {
+    e = 0.0f;
+    dedr = 0.0f;
+    return;
+  }
+  const float cz[4] = {0.18175f, 0.50986f, 0.28022f, 0.02817f};
+  const float dz[4] = {3.19980f, 0.94229f, 0.40290f, 0.20162f};
+  const float x = r * zp.y;
+  float phi = 0.0f, dphi = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float t = cz[k] * expf(-dz[k] * x);
+    phi += t;
+    dphi -= dz[k] * t;
+  }
+  const float yp1 = ipow(y, bc.p - 1), yp = yp1 * y;
+  const float u = 1.0f - bc.c0 * yp + bc.c1 * yp * y - bc.c2 * yp * y * y;
+  const float du = (-(float)bc.p * bc.c0 * yp1 + (float)(bc.p + 1) * bc.c1 * yp - (float)(bc.p + 2) * bc.c2 * yp * y) *
+                   inv_rc;
+  const float ir = 1.0f / r;
+  const float a = zp.x * ir;                     // k_e Z_a Z_b / (2 r)
+  e = a * phi * u;
+  dedr = a * (dphi * zp.y * u + phi * du - phi * u * ir);
+}
+
 __global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_ptr,
                                    const int* __restrict__ col_edge, const float* __restrict__ Ee,
                                    const float* __restrict__ g, const double* __restrict__ ed,
                                    const int* __restrict__ species, const double* __restrict__ sigma,
                                    const double* __restrict__ mu, bool want_forces, double* __restrict__ E_atom,
-                                   double* __restrict__ F, double* __restrict__ Wat) {
+                                   double* __restrict__ F, double* __restrict__ Wat, const int* __restrict__ ei,
+                                   const int* __restrict__ ej, const float2* __restrict__ zbl, BasisConst bc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = row_ptr[i], e1 = row_ptr[i + 1];
-  double Ei = 0.0;
+  const int z = species[i];
+  double Ei = 0.0, Ez = 0.0;
   double f[3] = {0, 0, 0};
   double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int e = b; e < e1; ++e) {
     Ei += (double)Ee[e];
+    double gx = 0.0, gy = 0.0, gz = 0.0;
     if (want_forces) {
-      double gx = g[3 * (size_t)e], gy = g[3 * (size_t)e + 1], gz = g[3 * (size_t)e + 2];
+      gx = g[3 * (size_t)e]; gy = g[3 * (size_t)e + 1]; gz = g[3 * (size_t)e + 2];
+    }
+    const double d0 = ed[3 * (size_t)e], d1 = ed[3 * (size_t)e + 1], d2 = ed[3 * (size_t)e + 2];
+    if (zbl) {
+      const int zj = species[ej[e]];
+      const float r = (float)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      float ez, dedr;
+      zbl_edge(r, zbl[z * bc.ns + zj], pair_basis(bc, z, zj).x, bc, ez, dedr);
+      Ez += (double)ez;
+      const double s = (double)(dedr / r);
+      gx += s * d0; gy += s * d1; gz += s * d2;
+    }
+    if (want_forces) {
       f[0] += gx; f[1] += gy; f[2] += gz;
-      double d0 = ed[3 * (size_t)e], d1 = ed[3 * (size_t)e + 1], d2 = ed[3 * (size_t)e + 2];
       W[0] -= d0 * gx; W[1] -= d0 * gy; W[2] -= d0 * gz;
       W[3] -= d1 * gx; W[4] -= d1 * gy; W[5] -= d1 * gz;
       W[6] -= d2 * gx; W[7] -= d2 * gy; W[8] -= d2 * gz;
     }
   }
-  const int z = species[i];
-  E_atom[i] = sigma[z] * Ei + mu[z];
+  E_atom[i] = sigma[z] * Ei + mu[z] + Ez;
   if (want_forces) {
     for (int k = col_ptr[i]; k < col_ptr[i + 1]; ++k) {
       size_t e = (size_t)col_edge[k];
-      f[0] -= g[3 * e]; f[1] -= g[3 * e + 1]; f[2] -= g[3 * e + 2];
+      double gx = g[3 * e], gy = g[3 * e + 1], gz = g[3 * e + 2];
+      if (zbl) {   // the ZBL part of this edge's dE/dd (edge (k -> i): centre species first)
+        const double d0 = ed[3 * e], d1 = ed[3 * e + 1], d2 = ed[3 * e + 2];
+        const int zc = species[ei[e]];
+        const float r = (float)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        float ez, dedr;
+        zbl_edge(r, zbl[zc * bc.ns + z], pair_basis(bc, zc, z).x, bc, ez, dedr);
+        const double s = (double)(dedr / r);
+        gx += s * d0; gy += s * d1; gz += s * d2;
+      }
+      f[0] -= gx; f[1] -= gy; f[2] -= gz;
     }
     F[3 * (size_t)i] = f[0]; F[3 * (size_t)i + 1] = f[1]; F[3 * (size_t)i + 2] = f[2];
     for (int q = 0; q < 9; ++q) Wat[9 * (size_t)i + q] = W[q];
@@ -478,10 +536,12 @@ __global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const
 
 void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
                  const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
-                 bool want_forces, double* E_atom, double* F, double* Wat, cudaStream_t st) {
+                 bool want_forces, double* E_atom, double* F, double* Wat, const int* ei, const int* ej,
+                 const Arch& a, cudaStream_t st) {
   if (n <= 0) return;
   atom_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, col_ptr, col_edge, Ee, g, ed, species, sigma,
-                                                      mu, want_forces, E_atom, F, Wat);
+                                                      mu, want_forces, E_atom, F, Wat, ei, ej,
+                                                      reinterpret_cast<const float2*>(a.zbl), make_basis(a));
 }
 
 // One block per structure: E_b = sum of its atoms' Etilde_i, W_b = sum of W_i

@@ -41,6 +41,9 @@ struct Arch {
   // neighbour test; null: the model cutoff rc for every pair
   const float* pair_basis = nullptr;
   const double* pair_rc2 = nullptr;
+  // ZBL repulsion (Sec. "Training details"), set by allegro_set_zbl: device
+  // [ns * ns][2] = {k_e Z_a Z_b / 2, 1 / a_s} per ordered species pair; null: no ZBL term
+  const float* zbl = nullptr;
   std::vector<int> tb, lat, edge;
   int S() const { return (lmax + 1) * (lmax + 1); }
   int n_w() const { return C * (lmax + 1); }
@@ -168,6 +171,13 @@ void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, in
                            const int* species, const double* pair_rc2, int ns,
                            const int* atom_struct, int n, int* count, const int* row_ptr, int* ej,
                            int* ei, int* eS, double* ed, int* d_err, cudaStream_t st);
+// Verlet-skin reuse: count (fill = false, into count[i]) or write (fill = true, rows at row_ptr[i]) the
+// candidates of a list built at r_c + skin (sk_row / sk_j / sk_S) that pass the exact rule now
+void nb_skin_filter(bool fill, const double* pos, int n, const double* d_cell, const int* sk_row, const int* sk_j,
+                    const int* sk_S, double rc2, const double* pair_rc2, const int* species, int ns, int* count,
+                    const int* row_ptr, int* ej, int* ei, int* eS, double* ed, cudaStream_t st);
+// max_i |pos_i - ref_i|^2 as the bits of a double in *out (cleared first)
+void nb_max_disp2(const double* pos, const double* ref, int n, unsigned long long* out, cudaStream_t st);
 void nb_columns(const int* ej, int E, int n, int* col_count, cudaStream_t st);
 void nb_fill_columns(const int* ej, int E, const int* col_ptr, int* cursor, int* col_edge,
                      cudaStream_t st);
@@ -198,9 +208,12 @@ void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vcons
                   float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st);
 template <typename T>
 void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, cudaStream_t st);
+// float64 per-atom energies sigma_Z E_i + mu_Z (+ the ZBL term when a.zbl is set), forces by row and
+// column gathers of dE/dd, per-atom virial
 void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
                  const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
-                 bool want_forces, double* E_atom, double* F, double* Wat, cudaStream_t st);
+                 bool want_forces, double* E_atom, double* F, double* Wat, const int* ei, const int* ej,
+                 const Arch& a, cudaStream_t st);
 void struct_reduce(int nstruct, const int64_t* offs, const double* E_atom, const double* Wat, const double* F,
                    bool want_w, double* E_out, double* W_out, int* d_err, double* scratch, int64_t n_atoms,
                    cudaStream_t st);

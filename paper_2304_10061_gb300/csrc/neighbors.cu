@@ -273,6 +273,93 @@ __device__ __forceinline__ bool pair_test(const double* __restrict__ pi, const d
   return r2 < rc2;
 }
 
+// ---------------------------------------------------------------------------
+// Verlet-skin reuse: the exact list of the current positions, filtered from a
+// candidate list built at r_c + skin (every pair now within r_c was within
+// r_c + skin at the build while no atom has moved skin/2 since).  One warp per
+// centre row: each lane takes candidates of the row, applies the exact rule
+// (pair_test, the pair's cutoff when a table is set), the warp counts the
+// kept ones with a ballot (count pass) or writes them in candidate order at
+// the row's offset (fill pass).
+// ---------------------------------------------------------------------------
+template <bool fill>
+__global__ void skin_filter_kernel(const double* __restrict__ pos, int n, const double* __restrict__ cellp,
+                                   const int* __restrict__ sk_row, const int* __restrict__ sk_j,
+                                   const int* __restrict__ sk_S, double rc2, const double* __restrict__ pair_rc2,
+                                   const int* __restrict__ species, int ns, int* __restrict__ count,
+                                   const int* __restrict__ row_ptr, int* __restrict__ ej, int* __restrict__ ei,
+                                   int* __restrict__ eS, double* __restrict__ ed) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  double cell[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) cell[q] = cellp[q];
+  const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+  const int zi = pair_rc2 ? species[i] : 0;
+  const int b = sk_row[i], e1 = sk_row[i + 1];
+  int out = fill ? row_ptr[i] : 0;
+  for (int e0 = b; e0 < e1; e0 += 32) {
+    const int e = e0 + lane;
+    bool keep = false;
+    int j = 0, S0 = 0, S1 = 0, S2 = 0;
+    double d[3] = {0.0, 0.0, 0.0};
+    if (e < e1) {
+      j = sk_j[e];
+      S0 = sk_S[3 * (size_t)e]; S1 = sk_S[3 * (size_t)e + 1]; S2 = sk_S[3 * (size_t)e + 2];
+      const double pj[3] = {pos[3 * (size_t)j], pos[3 * (size_t)j + 1], pos[3 * (size_t)j + 2]};
+      const double r2c = pair_rc2 ? pair_rc2[zi * ns + species[j]] : rc2;
+      keep = pair_test(pi, pj, cell, S0, S1, S2, r2c, d) && !(j == i && S0 == 0 && S1 == 0 && S2 == 0);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (fill && keep) {
+      const int o = out + __popc(m & ((1u << lane) - 1u));
+      ej[o] = j;
+      ei[o] = i;
+      eS[3 * (size_t)o] = S0; eS[3 * (size_t)o + 1] = S1; eS[3 * (size_t)o + 2] = S2;
+      ed[3 * (size_t)o] = d[0]; ed[3 * (size_t)o + 1] = d[1]; ed[3 * (size_t)o + 2] = d[2];
+    }
+    out += __popc(m);
+  }
+  if (!fill && lane == 0) count[i] = out;
+}
+
+void nb_skin_filter(bool fill, const double* pos, int n, const double* d_cell, const int* sk_row, const int* sk_j,
+                    const int* sk_S, double rc2, const double* pair_rc2, const int* species, int ns, int* count,
+                    const int* row_ptr, int* ej, int* ei, int* eS, double* ed, cudaStream_t st) {
+  if (n <= 0) return;
+  const int threads = 256, blocks = (int)(((int64_t)n * 32 + threads - 1) / threads);
+  if (fill)
+    skin_filter_kernel<true><<<blocks, threads, 0, st>>>(pos, n, d_cell, sk_row, sk_j, sk_S, rc2, pair_rc2, species,
+                                                         ns, count, row_ptr, ej, ei, eS, ed);
+  else
+    skin_filter_kernel<false><<<blocks, threads, 0, st>>>(pos, n, d_cell, sk_row, sk_j, sk_S, rc2, pair_rc2,
+                                                          species, ns, count, row_ptr, ej, ei, eS, ed);
+}
+
+// Largest squared displacement of any atom since the reference positions, as
+// the bits of a non-negative double (their order is the values' order).
+__global__ void max_disp2_kernel(const double* __restrict__ pos, const double* __restrict__ ref, int n,
+                                 unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    const double dx = pos[3 * (size_t)i] - ref[3 * (size_t)i], dy = pos[3 * (size_t)i + 1] - ref[3 * (size_t)i + 1],
+                 dz = pos[3 * (size_t)i + 2] - ref[3 * (size_t)i + 2];
+    v = dx * dx + dy * dy + dz * dz;
+    if (!(v == v)) v = 1e300;   // a NaN position forces a rebuild (which then reports it)
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+void nb_max_disp2(const double* pos, const double* ref, int n, unsigned long long* out, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (n <= 0) return;
+  max_disp2_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, ref, n, out);
+}
+
 // Wrapped positions pw = pos - wrap . cell in cell-sorted order (pos4[s] and
 // pw[3 s ..] belong to atom sorted[s]): float32 for the prefilter, float64 for
 // the displacements of accepted edges.

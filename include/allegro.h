@@ -203,6 +203,37 @@ allegro_status allegro_get_neighbors(allegro_ctx* ctx, int32_t* i, int32_t* j, i
                                      int64_t cap);
 
 /*
+ * allegro_set_autotune -- enable (1) or disable (0) the launch-configuration
+ * autotuner (Sec. "Optimized LAMMPS-Kokkos implementation": the workload's
+ * shapes fluctuate; the configuration is picked per shape).  When enabled,
+ * the first allegro_energy_forces of each shape bucket (edges and atoms at
+ * quarter-octave resolution, energy-only or with forces, single or batched)
+ * times candidate configurations by coordinate descent -- edges per chunk
+ * (the largest that fits, 1/2, 1/4, 1/8 of the list), each fused MLP layer
+ * pair on or off, epilogue warps per TMEM quarter of the arithmetic GEMM
+ * epilogues -- and keeps the fastest for that bucket (the first call takes
+ * about a dozen evaluations).  Every candidate computes the same function.
+ * Disabling restores the defaults.  An allegro_reserve chunk size overrides
+ * the tuned one.
+ *
+ * allegro_set_graphs -- enable (1) or disable (0) replay of the evaluation as
+ * a CUDA graph: the device work of allegro_energy_forces (all chunks, the
+ * MLP GEMMs, row kernels and reductions) is captured the second time the same
+ * shape, chunking, buffer addresses, configuration and stream are seen, and
+ * replayed with one cudaGraphLaunch while they stay the same (a changed edge
+ * count or a reallocation falls back to eager launches and recaptures).
+ * Ignored while allegro_profile is on.
+ *
+ * allegro_autotune_report -- JSON into buf[cap] (host): the current
+ * configuration, graph replays and kernels per graph, and per tuned bucket
+ * the chosen configuration and every trial's time in ms.
+ * ALLEGRO_E_CAPACITY if cap is too small.
+ */
+allegro_status allegro_set_autotune(allegro_ctx* ctx, int32_t enable);
+allegro_status allegro_set_graphs(allegro_ctx* ctx, int32_t enable);
+allegro_status allegro_autotune_report(allegro_ctx* ctx, char* buf, size_t cap);
+
+/*
  * allegro_profile -- enable (1) or disable (0) per-launch timing of the
  * library's kernels with CUDA events on the context's stream; enabling clears
  * earlier records.  Not part of the method: a tracing aid.

@@ -181,6 +181,20 @@ class Allegro:
         self.n_atoms, self.n_struct = n, 1
         return Ep, Ek
 
+    def set_autotune(self, enable: bool = True):
+        """Launch-configuration autotuner (chunk size, fused layer pairs, epilogue warps) per shape bucket."""
+        self._check(self._L.allegro_set_autotune(self._ctx, int(bool(enable))))
+
+    def set_graphs(self, enable: bool = True):
+        """Replay the evaluation as a CUDA graph while its shapes and buffers stay the same."""
+        self._check(self._L.allegro_set_graphs(self._ctx, int(bool(enable))))
+
+    def autotune_report(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self._L.allegro_autotune_report(self._ctx, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
     def set_md_skin(self, skin: float):
         """Verlet skin (A) for md_verlet's neighbour reuse; 0 rebuilds every step."""
         self._check(self._L.allegro_set_md_skin(self._ctx, float(skin)))

@@ -21,6 +21,7 @@ PREC = {"fp32": 0, "bf16": 1}
 EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_set_zbl", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
            "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_set_md_skin", "allegro_md_rebuilds",
+           "allegro_set_autotune", "allegro_set_graphs", "allegro_autotune_report",
            "allegro_last_error",
            "allegro_destroy")
 
@@ -51,6 +52,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                             ctypes.POINTER(i64), vp]
     L.allegro_md_verlet.argtypes = [vp, i64, dp, dp, dp, dp, i32, dp, dp, ctypes.c_double, i64, dp, dp]
     L.allegro_set_md_skin.argtypes = [vp, ctypes.c_double]
+    L.allegro_set_autotune.argtypes = [vp, i32]
+    L.allegro_set_graphs.argtypes = [vp, i32]
+    L.allegro_autotune_report.argtypes = [vp, ctypes.c_char_p, sz]
     L.allegro_md_rebuilds.argtypes = [vp, ctypes.POINTER(i64)]
     L.allegro_last_error.argtypes = [vp]
     L.allegro_last_error.restype = ctypes.c_char_p

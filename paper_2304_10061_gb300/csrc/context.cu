@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -210,7 +211,42 @@ struct allegro_ctx {
   int64_t sk_row_cap = 0, sk_cap = 0, sk_S_cap = 0;
   double h_cell[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int64_t launches = 0;                    // kernel launches issued by this context
-  bool chain = true;                       // fuse consecutive MLP layers (BF16 path)
+  // Launch configuration of the evaluation (set by the autotuner, or the defaults):
+  // edges per chunk (0 = largest that fits), which layer pairs run as one fused
+  // kernel (bit k = pair kind k, see pair_kind), epilogue warps per TMEM quarter
+  // of the arithmetic single-GEMM epilogues (2 or 4)
+  struct Tune {
+    int64_t chunk_edges = 0;
+    int chain_mask = 0x3f;
+    int epq_wide = 4;
+  } tune;
+  int autotune = 0;                        // allegro_set_autotune
+  struct TuneRec {
+    Tune best;
+    std::vector<std::pair<std::string, double>> trials;   // configuration, ms
+  };
+  std::map<std::string, TuneRec> tuned;    // shape bucket -> result
+  // CUDA-graph replay of the evaluation (allegro_set_graphs)
+  bool use_graphs = false;
+  struct GraphKey {
+    std::vector<int> bounds;
+    std::vector<const void*> ptrs;
+    int64_t n_atoms = -1, n_edges = -1;
+    int nstruct = 0;
+    bool backward = false;
+    int64_t chunk = 0;
+    int chain_mask = 0, epq = 0;
+    cudaStream_t stream = nullptr;
+    bool operator==(const GraphKey& o) const {
+      return bounds == o.bounds && ptrs == o.ptrs && n_atoms == o.n_atoms && n_edges == o.n_edges &&
+             nstruct == o.nstruct && backward == o.backward && chunk == o.chunk && chain_mask == o.chain_mask &&
+             epq == o.epq && stream == o.stream;
+    }
+  };
+  GraphKey graph_key, seen_key;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;              // kernels in the captured graph
+  int64_t graph_replays = 0;
 
   // chunk workspace
   void* ws = nullptr;
@@ -782,6 +818,17 @@ allegro_status gemm(allegro_ctx* c, GemmArgs g) {
   return ALLEGRO_OK;
 }
 
+// Kind of a pair of consecutive layers the fused pair kernel takes (bit of
+// Tune::chain_mask): 0 two-body SiLU pair, 1 latent SiLU pair, 2 latent SiLU +
+// last layer, 3 head + 256-wide SiLU adjoint, 4 head + narrower SiLU adjoint,
+// 5 SiLU adjoint + linear tail.
+int pair_kind(const GemmArgs& g1, const GemmArgs& g2) {
+  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_FWD_SILU) return g1.N < 256 ? 0 : 1;
+  if (g1.epi == EPI_FWD_SILU && g2.epi == EPI_LAST) return 2;
+  if (g1.epi == EPI_HEAD && g2.epi == EPI_BWD_SILU) return g2.N >= 256 ? 3 : 4;
+  return 5;
+}
+
 // ------------------------------------------------------------------------
 // model evaluation of one chunk of whole rows
 // ------------------------------------------------------------------------
@@ -801,6 +848,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
     g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
     g.ubar = ubar; g.Eout = Eout; g.v = c->d_v; g.rowsig = w.sig;
+    g.epq = c->tune.epq_wide;
     return g;
   };
   auto gbytes = [&](const GemmArgs& g, bool count_in, bool count_out) {
@@ -821,7 +869,7 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     const bool want_chain = (g1.epi == EPI_FWD_SILU && (g2.epi == EPI_FWD_SILU || g2.epi == EPI_LAST)) ||
                             (g1.epi == EPI_HEAD && g2.epi == EPI_BWD_SILU) ||
                             (g1.epi == EPI_BWD_SILU && g2.epi == EPI_LINEAR && g2.N <= 256);
-    if (c->prec == ALLEGRO_PREC_BF16 && c->chain && want_chain) {
+    if (c->prec == ALLEGRO_PREC_BF16 && want_chain && (c->tune.chain_mask >> pair_kind(g1, g2) & 1)) {
       std::string why;
       const std::string l2 = gemm_label(c, g2.W, g2.trans, g2.epi);
       const char* label = intern_label(std::string(gemm_label(c, g1.W, g1.trans, g1.epi)) + "+" +
@@ -1106,11 +1154,15 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   return ALLEGRO_OK;
 }
 
-allegro_status evaluate(allegro_ctx* c, bool backward) {
+// Chunks of whole rows (each centre's environment sum complete inside one
+// chunk), at most `budget` edges each (0: the largest the memory allows).
+struct Plan {
+  std::vector<int> bounds;
+  int64_t maxE = 1, maxA = 1;
+};
+
+Plan plan_chunks(allegro_ctx* c, int64_t budget) {
   const int n = (int)c->n_atoms;
-  const int64_t E = c->n_edges;
-  // chunks of whole rows
-  int64_t budget = c->chunk_edges_user;
   if (budget <= 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
@@ -1118,36 +1170,39 @@ allegro_status evaluate(allegro_ctx* c, bool backward) {
     int64_t cap_bytes = std::min<int64_t>((int64_t)(fr * 0.5) + (int64_t)c->ws_bytes, 48ll << 30);
     budget = std::max<int64_t>(cap_bytes / std::max<int64_t>(per, 1), 1 << 16);
   }
-  std::vector<int> bounds{0};
-  {
-    int a = 0;
-    while (a < n) {
-      int64_t start = c->h_row_ptr[a];
-      int b = a + 1;
-      // largest b with row_ptr[b] - start <= budget (at least one row)
-      int lo = a + 1, hi = n;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) / 2;
-        if ((int64_t)c->h_row_ptr[mid] - start <= budget) lo = mid;
-        else hi = mid - 1;
-      }
-      b = std::max(lo, a + 1);
-      bounds.push_back(b);
-      a = b;
+  Plan p;
+  p.bounds.push_back(0);
+  int a = 0;
+  while (a < n) {
+    int64_t start = c->h_row_ptr[a];
+    // largest b with row_ptr[b] - start <= budget (at least one row)
+    int lo = a + 1, hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) / 2;
+      if ((int64_t)c->h_row_ptr[mid] - start <= budget) lo = mid;
+      else hi = mid - 1;
     }
-    if (n == 0) bounds.push_back(0);
+    int b = std::max(lo, a + 1);
+    p.bounds.push_back(b);
+    a = b;
   }
-  int64_t maxE = 1, maxA = 1;
-  for (size_t q = 0; q + 1 < bounds.size(); ++q) {
-    maxE = std::max<int64_t>(maxE, (int64_t)c->h_row_ptr[bounds[q + 1]] - c->h_row_ptr[bounds[q]]);
-    maxA = std::max<int64_t>(maxA, bounds[q + 1] - bounds[q]);
+  if (n == 0) p.bounds.push_back(0);
+  for (size_t q = 0; q + 1 < p.bounds.size(); ++q) {
+    p.maxE = std::max<int64_t>(p.maxE, (int64_t)c->h_row_ptr[p.bounds[q + 1]] - c->h_row_ptr[p.bounds[q]]);
+    p.maxA = std::max<int64_t>(p.maxA, p.bounds[q + 1] - p.bounds[q]);
   }
-  WS w;
-  allegro_status s = ensure_ws(c, maxE, maxA, &w);
-  if (s != ALLEGRO_OK) return s;
+  return p;
+}
+
+// The device work of one evaluation (no host synchronisation, no allocation:
+// it can be captured into a CUDA graph).
+allegro_status run_plan(allegro_ctx* c, const Plan& p, const WS& w, bool backward) {
+  const int n = (int)c->n_atoms;
+  const int64_t E = c->n_edges;
   CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  for (size_t q = 0; q + 1 < bounds.size(); ++q) {
-    int a0 = bounds[q], a1 = bounds[q + 1];
+  allegro_status s;
+  for (size_t q = 0; q + 1 < p.bounds.size(); ++q) {
+    int a0 = p.bounds[q], a1 = p.bounds[q + 1];
     int e0 = c->h_row_ptr[a0], e1 = c->h_row_ptr[a1];
     s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk<bf16>(c, w, a0, a1, e0, e1, backward)
                                        : run_chunk<float>(c, w, a0, a1, e0, e1, backward);
@@ -1166,6 +1221,171 @@ allegro_status evaluate(allegro_ctx* c, bool backward) {
   }
   CUDA_TRY(c, cudaGetLastError());
   return ALLEGRO_OK;
+}
+
+// One evaluation with the context's current launch configuration: eager, or
+// through the cached CUDA graph when graphs are on and nothing it depends on
+// changed (chunking, buffer addresses, sizes, configuration, stream).  A graph
+// is captured the second time the same key is seen (the first run is eager,
+// so one-time set-up such as kernel attributes never happens under capture).
+allegro_status evaluate_once(allegro_ctx* c, bool backward) {
+  const int64_t budget = c->chunk_edges_user > 0 ? c->chunk_edges_user : c->tune.chunk_edges;
+  Plan p = plan_chunks(c, budget);
+  WS w;
+  allegro_status s = ensure_ws(c, p.maxE, p.maxA, &w);
+  if (s != ALLEGRO_OK) return s;
+  if (!c->use_graphs || c->prof.on) return run_plan(c, p, w, backward);
+  allegro_ctx::GraphKey key;
+  key.bounds = p.bounds;
+  for (int b : p.bounds) key.bounds.push_back(c->h_row_ptr[b]);   // edge offsets of the chunks too
+  key.ptrs = {c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_Ee, c->d_g,
+              c->d_species, c->d_Eatom, c->d_F, c->d_Wat, c->d_offs, c->d_Eout, c->d_Wout, c->d_err,
+              c->d_red_scratch, c->ws, c->arch.pair_basis, c->arch.zbl, c->d_atom_struct};
+  key.n_atoms = c->n_atoms; key.n_edges = c->n_edges; key.nstruct = c->nstruct; key.backward = backward;
+  key.chunk = budget; key.chain_mask = c->tune.chain_mask; key.epq = c->tune.epq_wide; key.stream = c->stream;
+  if (c->graph_exec && key == c->graph_key) {
+    CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_launches;
+    ++c->graph_replays;
+    return ALLEGRO_OK;
+  }
+  if (!(key == c->seen_key)) {   // first sight of this key: eager
+    c->seen_key = key;
+    return run_plan(c, p, w, backward);
+  }
+  const int64_t l0 = c->launches;
+  CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  s = run_plan(c, p, w, backward);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (s != ALLEGRO_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return s;
+  }
+  if (e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return fail(c, ALLEGRO_E_CUDA, "stream capture of the evaluation failed: %s", cudaGetErrorString(e));
+  }
+  bool updated = false;
+  if (c->graph_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(c->graph_exec, graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+  }
+  if (!updated) {
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      c->graph_exec = nullptr;
+      return fail(c, ALLEGRO_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaGraphDestroy(graph);
+  c->graph_key = key;
+  c->graph_launches = c->launches - l0;
+  CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  return ALLEGRO_OK;
+}
+
+// Shape bucket of the autotuner: precision-independent sizes at quarter-octave
+// resolution, pass kind, single or batched.
+std::string tune_bucket(const allegro_ctx* c, bool backward) {
+  char b[96];
+  const int qe = (int)std::lround(4.0 * std::log2((double)std::max<int64_t>(c->n_edges, 1)));
+  const int qa = (int)std::lround(4.0 * std::log2((double)std::max<int64_t>(c->n_atoms, 1)));
+  snprintf(b, sizeof b, "E2^%.2f/N2^%.2f/%s/%s", qe / 4.0, qa / 4.0, backward ? "EF" : "E",
+           c->nstruct > 1 ? "batched" : "single");
+  return b;
+}
+
+std::string tune_name(const allegro_ctx::Tune& t) {
+  char b[96];
+  snprintf(b, sizeof b, "chunk=%lld,chain=0x%02x,epq=%d", (long long)t.chunk_edges, t.chain_mask, t.epq_wide);
+  return b;
+}
+
+// Autotuner: the first evaluation of each shape bucket times candidate launch
+// configurations by coordinate descent (edges per chunk; each fused layer pair
+// on or off; epilogue warps of the arithmetic single GEMMs), each candidate
+// once after one untimed warm-up of the defaults, with CUDA events on the
+// context's stream, and keeps the fastest for the bucket.  Every candidate
+// computes the same function (chunking and pair fusion change only where
+// intermediates live), so the outputs of the final evaluation are the model's.
+allegro_status autotune(allegro_ctx* c, bool backward, allegro_ctx::TuneRec* rec) {
+  allegro_ctx::Tune best;     // defaults
+  cudaEvent_t ev[2];
+  CUDA_TRY(c, cudaEventCreate(&ev[0]));
+  CUDA_TRY(c, cudaEventCreate(&ev[1]));
+  auto time_cfg = [&](const allegro_ctx::Tune& t, double* ms) -> allegro_status {
+    c->tune = t;
+    cudaEventRecord(ev[0], c->stream);
+    allegro_status s = evaluate_once(c, backward);
+    cudaEventRecord(ev[1], c->stream);
+    if (s != ALLEGRO_OK) return s;
+    CUDA_TRY(c, cudaEventSynchronize(ev[1]));
+    float f = 0.0f;
+    CUDA_TRY(c, cudaEventElapsedTime(&f, ev[0], ev[1]));
+    *ms = f;
+    rec->trials.push_back({tune_name(t), (double)f});
+    return ALLEGRO_OK;
+  };
+  const bool saved_graphs = c->use_graphs;
+  c->use_graphs = false;
+  allegro_status s;
+  double best_ms = 0.0, ms = 0.0;
+  c->tune = best;
+  if ((s = evaluate_once(c, backward)) != ALLEGRO_OK) goto done;   // warm-up
+  if ((s = time_cfg(best, &best_ms)) != ALLEGRO_OK) goto done;
+  {
+    // edges per chunk: the largest that fits, then 1/2, 1/4 and 1/8 of the list
+    const int64_t E = std::max<int64_t>(c->n_edges, 1);
+    for (int64_t div : {2, 4, 8}) {
+      allegro_ctx::Tune t = best;
+      t.chunk_edges = std::max<int64_t>(E / div, 1 << 16);
+      if (t.chunk_edges >= E) continue;
+      if ((s = time_cfg(t, &ms)) != ALLEGRO_OK) goto done;
+      if (ms < best_ms) { best = t; best_ms = ms; }
+    }
+    if (c->prec == ALLEGRO_PREC_BF16) {
+      for (int k = 0; k < 6; ++k) {   // each fused layer pair on or off
+        allegro_ctx::Tune t = best;
+        t.chain_mask ^= 1 << k;
+        if ((s = time_cfg(t, &ms)) != ALLEGRO_OK) goto done;
+        if (ms < best_ms) { best = t; best_ms = ms; }
+      }
+      allegro_ctx::Tune t = best;
+      t.epq_wide = best.epq_wide == 4 ? 2 : 4;
+      if ((s = time_cfg(t, &ms)) != ALLEGRO_OK) goto done;
+      if (ms < best_ms) { best = t; best_ms = ms; }
+    }
+  }
+done:
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  c->use_graphs = saved_graphs;
+  c->tune = best;
+  rec->best = best;
+  return s;
+}
+
+allegro_status evaluate(allegro_ctx* c, bool backward) {
+  if (c->autotune) {
+    const std::string b = tune_bucket(c, backward);
+    auto it = c->tuned.find(b);
+    if (it == c->tuned.end()) {
+      allegro_ctx::TuneRec rec;
+      allegro_status s = autotune(c, backward, &rec);
+      if (s != ALLEGRO_OK) return s;
+      it = c->tuned.emplace(b, rec).first;
+    }
+    c->tune = it->second.best;
+  }
+  return evaluate_once(c, backward);
 }
 
 allegro_status copy_out(allegro_ctx* c, void* dst, const void* src, size_t bytes) {
@@ -1731,6 +1951,51 @@ allegro_status allegro_md_verlet(allegro_ctx* c, int64_t n_atoms, double* pos, d
   return ALLEGRO_OK;
 }
 
+allegro_status allegro_set_autotune(allegro_ctx* c, int32_t enable) {
+  if (!c) return ALLEGRO_E_INVALID;
+  c->autotune = enable != 0;
+  if (!c->autotune) c->tune = allegro_ctx::Tune();
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_set_graphs(allegro_ctx* c, int32_t enable) {
+  if (!c) return ALLEGRO_E_INVALID;
+  cudaSetDevice(c->device);
+  c->use_graphs = enable != 0;
+  if (!c->use_graphs && c->graph_exec) {
+    cudaStreamSynchronize(c->stream);
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    c->graph_key = allegro_ctx::GraphKey();
+  }
+  c->seen_key = allegro_ctx::GraphKey();
+  return ALLEGRO_OK;
+}
+
+allegro_status allegro_autotune_report(allegro_ctx* c, char* buf, size_t cap) {
+  if (!c || !buf || cap == 0) return ALLEGRO_E_INVALID;
+  std::string out = "{\"graph_replays\": " + std::to_string(c->graph_replays) + ", \"graph_kernels\": " +
+                    std::to_string(c->graph_launches) + ", \"current\": \"" + tune_name(c->tune) +
+                    "\", \"buckets\": {";
+  bool first = true;
+  for (auto& kv : c->tuned) {
+    out += std::string(first ? "" : ", ") + "\"" + kv.first + "\": {\"best\": \"" + tune_name(kv.second.best) +
+           "\", \"trials\": {";
+    first = false;
+    for (size_t q = 0; q < kv.second.trials.size(); ++q) {
+      char line[160];
+      snprintf(line, sizeof line, "%s\"%s#%zu\": %.4f", q ? ", " : "", kv.second.trials[q].first.c_str(), q,
+               kv.second.trials[q].second);
+      out += line;
+    }
+    out += "}}";
+  }
+  out += "}}";
+  if (out.size() + 1 > cap) return fail(c, ALLEGRO_E_CAPACITY, "report needs %zu bytes", out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return ALLEGRO_OK;
+}
+
 allegro_status allegro_set_md_skin(allegro_ctx* c, double skin) {
   if (!c) return ALLEGRO_E_INVALID;
   if (!(skin >= 0.0) || !std::isfinite(skin) || skin > 4.0 * c->arch.rc)
@@ -1817,6 +2082,8 @@ void allegro_destroy(allegro_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->weight_allocs) cudaFree(p);
   void* bufs[] = {c->d_map, c->d_pos, c->d_types, c->d_species, c->d_row_ptr, c->d_col_ptr, c->d_count,

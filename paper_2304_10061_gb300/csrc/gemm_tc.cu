@@ -1318,7 +1318,7 @@ bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* w
   bn = (bn + 31) / 32 * 32;
   // four epilogue warps per quarter for the arithmetic epilogues (instantiated
   // for the tile widths the MLP adjoints use), two for plain copies
-  const bool wide = (g.epi == EPI_BWD_SILU || g.epi == EPI_LAST);
+  const bool wide = (g.epi == EPI_BWD_SILU || g.epi == EPI_LAST) && g.epq != 2;
   switch (bn) {
     case 32: return launch_bn<32, 2>(g, B, ldb, st, d_err, why);
     case 64: return launch_bn<64, 2>(g, B, ldb, st, d_err, why);

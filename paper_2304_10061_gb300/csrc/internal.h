@@ -129,6 +129,7 @@ struct GemmArgs {
   const float* v = nullptr;        // EPI_LAST: folded edge-energy vector [N]
   const float* rowsig = nullptr;   // EPI_LAST: sigma_{Z_i} per row
   float* Eout = nullptr;           // EPI_LAST: E_ij per row
+  int epq = 4;                     // tcgen05 path: epilogue warps per TMEM quarter of SiLU-adjoint / last-layer GEMMs
 };
 
 // ---- launchers -----------------------------------------------------------

@@ -373,6 +373,60 @@ def _pair_cutoff_run(args, make_model, pos, types, cell, out, N, steps: int):
     return res
 
 
+def _precision_matrix(args, local, stream):
+    import numpy as np
+    import torch
+    from paper_2304_10061_gb300 import Allegro
+    from synth import ARCHS, lattice_box, make_weights, weights_to_blob
+    arch = ARCHS["c2"]
+    w = make_weights(arch, 1)
+    blob = weights_to_blob(arch, w)
+    s = lattice_box(3072, (3072 / 0.1) ** (1.0 / 3.0), seed=7)
+    dev = f"cuda:{local}"
+    px = torch.tensor(s.pos, device=dev)
+    tx = torch.tensor(s.species, dtype=torch.int32, device=dev)
+    cx = torch.tensor(s.cell, device=dev)
+    rows = {"tf32": "F64 final, F32 weights, TF32 compute", "fp32": "F64 final, F32 weights, F32 compute",
+            "bf16": "F64 final, F32 master weights, BF16 compute"}
+    res = {"atoms": s.n_atoms, "paper_relative_speed_A100": {"F64,F32,TF32": 1.0, "F64,F32,F32": 0.37,
+                                                             "F32,F32,TF32": 0.98, "F32,F32,F32": 0.37,
+                                                             "F64,F64,F64": 0.26}}
+    F0 = E0 = None
+    if not args.skip_cpu:
+        from oracle.allegro import AllegroOracle
+        i, j, S = _edges(arch, s)
+        E0, _, F0, _ = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, i, j, S)
+    for prec, label in rows.items():
+        m = Allegro(blob, precision=prec, device=local)
+        m.set_stream(stream.cuda_stream)
+        out = dict(E=torch.empty(1, dtype=torch.float64, device=dev),
+                   E_atom=torch.empty(s.n_atoms, dtype=torch.float64, device=dev),
+                   F=torch.empty(s.n_atoms, 3, dtype=torch.float64, device=dev),
+                   virial=torch.empty(1, 3, 3, dtype=torch.float64, device=dev))
+        for _ in range(3):
+            m.neighbors(px, tx, cx)
+            m.energy_forces(out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(20):
+            m.neighbors(px, tx, cx)
+            m.energy_forces(out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 20
+        rec = {"setting": label, "ms_per_step": ms, "atom_steps_per_s": s.n_atoms / (ms * 1e-3)}
+        if F0 is not None:
+            rec["force_err_vs_fp64"] = _force_errors(out["F"].cpu().numpy(), out["E"].item(), F0, E0)
+        res[prec] = rec
+        m.close()
+    for prec in rows:
+        res[prec]["relative_speed"] = res["tf32"]["ms_per_step"] / res[prec]["ms_per_step"]
+    res["note"] = ("step = neighbour rebuild + E + F + virial; relative speed against the TF32 row as in the "
+                   "paper's table; the all-float64 GPU row is not built (the FP64 path is the CPU oracle)")
+    return res
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores: each step one bounded sample of the workload."""
     rank, ws, _, dist = _dist()
@@ -554,20 +608,27 @@ def run_ours(args):
         masses = np.array([1.008, 15.999, 12.011, 14.007, 32.06])
         rng = np.random.default_rng(0)
         vel = rng.normal(size=(s2.n_atoms, 3)) * np.sqrt(0.0257 * 9.648533212e-3 / masses[s2.species][:, None])
-        mm = make(args.precision)
-        p2 = s2.pos.copy()
-        mm.md_verlet(p2, vel, s2.species, masses, 1.0, 2, cell=s2.cell)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nmd = 10
-        Ep, Ek = mm.md_verlet(p2, vel, s2.species, masses, 1.0, nmd, cell=s2.cell)
-        torch.cuda.synchronize()
-        dt_md = time.perf_counter() - t0
-        mm.close()
-        extra["md_23552_atoms"] = {"dt_fs": 1.0, "steps": nmd, "timesteps_per_s": nmd / dt_md,
-                                   "atom_steps_per_s": s2.n_atoms * nmd / dt_md,
-                                   "energy_drift_eV_per_atom": float(abs((Ep[-1] + Ek[-1]) - (Ep[0] + Ek[0])) / s2.n_atoms),
-                                   "note": "velocity Verlet on the GPU, neighbour rebuild every step"}
+        md = {}
+        for skin in (0.0, 1.0):
+            mm = make(args.precision)
+            mm.set_md_skin(skin)
+            p2, v2 = s2.pos.copy(), vel.copy()
+            mm.md_verlet(p2, v2, s2.species, masses, 1.0, 2, cell=s2.cell)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nmd = 20
+            Ep, Ek = mm.md_verlet(p2, v2, s2.species, masses, 1.0, nmd, cell=s2.cell)
+            torch.cuda.synchronize()
+            dt_md = time.perf_counter() - t0
+            md[f"skin_{skin:g}A"] = {"timesteps_per_s": nmd / dt_md, "atom_steps_per_s": s2.n_atoms * nmd / dt_md,
+                                     "list_builds": mm.md_rebuilds(),
+                                     "energy_drift_eV_per_atom":
+                                         float(abs((Ep[-1] + Ek[-1]) - (Ep[0] + Ek[0])) / s2.n_atoms)}
+            mm.close()
+        extra["md_23552_atoms"] = {"dt_fs": 1.0, "steps": nmd, **md,
+                                   "note": "velocity Verlet on the GPU, host inputs once per run; skin 0: neighbour "
+                                           "rebuild every step; skin 1 A: exact list filtered from a candidate list "
+                                           "at r_c + skin, rebuilt when an atom moved skin/2"}
         # the smaller named workloads (E + F + virial with a neighbour rebuild per step), both precisions
         for name, label in (("c2", "c2_23552_atoms"), ("c1", "c1_64_atoms")):
             sx, ax, wx = make_config(name)
@@ -600,6 +661,10 @@ def run_ours(args):
                 rec[prec] = {"ms_per_step": msx, "atom_steps_per_s": sx.n_atoms / (msx * 1e-3)}
                 mx.close()
             extra[label] = rec
+        # Table IV of the paper on GB300: relative speed of the precision settings on a 3,072-atom
+        # water-density box (float64 final sums throughout; weights and activations float32 for the
+        # TF32 and FP32 rows), and each setting's force error against the FP64 oracle
+        extra["table_iv_3072_atoms"] = _precision_matrix(args, local, stream)
         # the headline box under the paper's per-ordered-species-pair cutoffs
         if arch.pair_rc is None:
             extra["pair_cutoffs_1M_atoms" if args.config == "c4" and not args.atoms else "pair_cutoffs"] = \
@@ -607,7 +672,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"bf16": "bf16", "tf32": "tf32"}.get(args.precision, "f32"), "data": "synthetic",
             "config": {"workload": _workload(args, s), "atoms": N, "edges": n_edges,
                        "step": "neighbour rebuild + E + F + virial, float64 reductions",
                        "l2": "inputs larger than L2 (edge arrays of several GB per step)",
@@ -646,7 +711,7 @@ def main():
     ap.add_argument("--config", default="c4")
     ap.add_argument("--atoms", type=int, default=0, help="scale the configuration's box to this many atoms "
                                                            "(same density; lattice configurations)")
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32"])
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

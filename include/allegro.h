@@ -47,7 +47,9 @@ typedef enum {
 
 typedef enum {
   ALLEGRO_PREC_FP32 = 0,    /* all MLP GEMMs in float32 on the CUDA cores */
-  ALLEGRO_PREC_BF16 = 1     /* MLP GEMMs in bfloat16 on tcgen05 tensor cores, float32 accumulation */
+  ALLEGRO_PREC_BF16 = 1,    /* MLP GEMMs in bfloat16 on tcgen05 tensor cores, float32 accumulation */
+  ALLEGRO_PREC_TF32 = 2     /* float32 weights and activations, MLP GEMMs read as TF32 by tcgen05
+                               (kind::tf32), float32 accumulation: Table IV's production setting */
 } allegro_precision;
 
 /*

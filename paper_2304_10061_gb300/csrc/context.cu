@@ -802,7 +802,8 @@ const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
     for (size_t k = 0; k < c->lat[L].size(); ++k)
       if (W == &c->lat[L][k]) n = "latent." + std::to_string(L + 1) + "." + std::to_string(k);
   const char* en[] = {"silu", "f32", "dsilu", "head", "last", "linear"};
-  n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : "gemm_simt/") + n + (trans ? "^T" : "") + ":" +
+  n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : (c->prec == ALLEGRO_PREC_TF32 ? "gemm_tf32/" : "gemm_simt/")) +
+      n + (trans ? "^T" : "") + ":" +
       en[epi];
   return intern_label(n);
 }
@@ -812,6 +813,9 @@ allegro_status gemm(allegro_ctx* c, GemmArgs g) {
   if (c->prec == ALLEGRO_PREC_BF16) {
     std::string why;
     if (!gemm_tc_bf16(g, c->stream, c->d_err, &why)) return fail(c, ALLEGRO_E_CUDA, "tcgen05 GEMM: %s", why.c_str());
+  } else if (c->prec == ALLEGRO_PREC_TF32) {
+    std::string why;
+    if (!gemm_tc_tf32(g, c->stream, c->d_err, &why)) return fail(c, ALLEGRO_E_CUDA, "tcgen05 TF32 GEMM: %s", why.c_str());
   } else {
     gemm_simt_f32(g, c->stream);
   }
@@ -1407,7 +1411,8 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
   if (!out) return ALLEGRO_E_INVALID;
   *out = nullptr;
   if (!weights_blob || blob_bytes == 0) return ALLEGRO_E_INVALID;
-  if (precision != ALLEGRO_PREC_FP32 && precision != ALLEGRO_PREC_BF16) return ALLEGRO_E_INVALID;
+  if (precision != ALLEGRO_PREC_FP32 && precision != ALLEGRO_PREC_BF16 && precision != ALLEGRO_PREC_TF32)
+    return ALLEGRO_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -1422,7 +1427,7 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
     return s;
   };
   if (cudaSetDevice(device) != cudaSuccess) return bail(fail(c, ALLEGRO_E_CUDA, "cudaSetDevice failed"));
-  if (precision == ALLEGRO_PREC_BF16) {
+  if (precision == ALLEGRO_PREC_BF16 || precision == ALLEGRO_PREC_TF32) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, device);
     if (prop.major != 10 || prop.minor != 3)

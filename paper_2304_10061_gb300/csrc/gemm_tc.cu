@@ -1406,4 +1406,317 @@ bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, in
   return false;
 }
 
+
+// ---------------------------------------------------------------------------
+// TF32 GEMM on tcgen05 (kind::tf32) for the float32-storage precisions:
+//   C[M x N] = A[M x K] B^T, A float32 activations [M][lda], B float32 weights
+//   [N][ldb] (K contiguous), float32 accumulation in TMEM, with the float32
+//   path's epilogues (SiLU forward with the pre-activation store and the
+//   per-row scale, float32 output with an addend, SiLU adjoint, linear).
+// The tensor core reads each float32 operand as TF32 (10-bit mantissa): the
+// paper's production setting (Table IV: float64 final, float32 weights and
+// activations, TF32 matrix multiplications).
+// Persistent: CTA b walks 128 x BN tiles; warp 0 issues TMA loads of 128 x 32
+// (A) and BN x 32 (B) float32 tiles (128-byte rows, 128-byte swizzle) into a
+// shared-memory ring, warp 1 owns two BN-column TMEM accumulators and issues
+// tcgen05.mma.kind::tf32 (K = 8 per instruction) from one thread, 8 epilogue
+// warps (2 per TMEM lane quarter, alternating 32-column chunks) read the
+// accumulator with tcgen05.ld and write their rows with 16-byte stores.
+// ---------------------------------------------------------------------------
+constexpr int kT32BK = 32;                     // float32 elements per 128-byte operand row
+constexpr int kT32Threads = 64 + 8 * 32;
+
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_tf32() {
+  // D f32, A tf32, B tf32, both K-major, M = 128, N = BN
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+template <int BN>
+__host__ __device__ constexpr int t32_stage_bytes() {
+  return 128 * kT32BK * 4 + BN * kT32BK * 4;
+}
+template <int BN>
+__host__ __device__ constexpr int t32_stages() {
+  return (kTcSmemMax - 1024 - 1024) / t32_stage_bytes<BN>() > 6 ? 6
+                                                               : (kTcSmemMax - 1024 - 1024) / t32_stage_bytes<BN>();
+}
+template <int BN>
+__host__ __device__ constexpr int t32_smem_bytes() {
+  return t32_stages<BN>() * t32_stage_bytes<BN>() + 1024 + 1024;
+}
+
+// 32 consecutive float32 columns of one row: epilogue of the float32 path
+__device__ __forceinline__ void t32_epilogue(const EpiParams& ep, int m, int n, int N, float (&v)[32]) {
+  const bool full = (n + 32 <= N) && ep.vec;
+  if (ep.epi == EPI_FWD_SILU) {
+    const float rs = ep.rowscale ? ep.rowscale[m] : 1.0f;
+    if (ep.pre) {
+      float* pp = reinterpret_cast<float*>(ep.pre) + (size_t)m * ep.ldp + n;
+      if (full) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          reinterpret_cast<float4*>(pp)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (n + j < N) pp[j] = v[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = v[j] * epi_sigmoid(v[j]) * rs;
+  } else if (ep.epi == EPI_F32) {
+    if (ep.add) {
+      const float* a = reinterpret_cast<const float*>(ep.add) + (size_t)m * ep.ld_add + n;
+      if (full) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float4 x = reinterpret_cast<const float4*>(a)[k];
+          v[4 * k] += x.x; v[4 * k + 1] += x.y; v[4 * k + 2] += x.z; v[4 * k + 3] += x.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (n + j < N) v[j] += a[j];
+      }
+    }
+  } else if (ep.epi == EPI_BWD_SILU) {
+    const float* zp = reinterpret_cast<const float*>(ep.pre) + (size_t)m * ep.ldp + n;
+    float z[32];
+    if (full) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 x = reinterpret_cast<const float4*>(zp)[k];
+        z[4 * k] = x.x; z[4 * k + 1] = x.y; z[4 * k + 2] = x.z; z[4 * k + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) z[j] = (n + j < N) ? zp[j] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float sg = epi_sigmoid(z[j]);
+      v[j] = v[j] * sg * (1.0f + z[j] * (1.0f - sg));
+    }
+  }
+  float* o = reinterpret_cast<float*>(ep.out) + (size_t)m * ep.ldo + n;
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      reinterpret_cast<float4*>(o)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (n + j < N) o[j] = v[j];
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kT32Threads, 1)
+    gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiParams ep,
+                     int M, int N, int K, int* __restrict__ err) {
+  constexpr int STAGES = t32_stages<BN>();
+  constexpr uint32_t A_BYTES = 128 * kT32BK * 4;
+  constexpr uint32_t B_BYTES = BN * kT32BK * 4;
+  constexpr uint32_t COLS = tc_tmem_cols<BN>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;   // [2]
+  uint64_t* tempty = tfull + 2;       // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (K + kT32BK - 1) / kT32BK;
+  const int tiles_m = (M + 127) / 128, tiles_n = (N + BN - 1) / BN;
+  const int ntiles = tiles_m * tiles_n;
+  auto tm0 = [&](int tt) { return (tt / tiles_n) * 128; };
+  auto tn0 = [&](int tt) { return (tt % tiles_n) * BN; };
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tc_alloc(tslot, 2 * COLS);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        const int m0 = tm0(t), n0 = tn0(t);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const uint32_t q = g % STAGES, r = g / STAGES;
+          if (g >= (uint32_t)STAGES && !mbar_wait(&empty[q], (r - 1) & 1)) {
+            atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full[q], A_BYTES + B_BYTES);
+          tma_load_2d(sA + q * A_BYTES, &tmA, &full[q], kb * kT32BK, m0);
+          tma_load_2d(sB + q * B_BYTES, &tmB, &full[q], kb * kT32BK, n0);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32<BN>();
+      uint32_t g = 0;
+      int lt = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+        const int b = lt & 1, use = lt >> 1;
+        bool ok = !*abort_flag && mbar_wait(&tempty[b], (use & 1) ^ 1);
+        if (ok) {
+          tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(b * COLS);
+          for (int kb = 0; kb < nk; ++kb, ++g) {
+            const uint32_t q = g % STAGES, r = g / STAGES;
+            if (!mbar_wait(&full[q], r & 1)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(sA + q * A_BYTES), b_addr = smem_u32(sB + q * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < kT32BK / 8; ++k)   // 8 tf32 = 32 bytes per instruction
+              tc_mma_tf32(dt, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32), idesc,
+                          (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[q]);
+          }
+        }
+        if (!ok) {
+          atomicOr(err, kErrTimeout);
+          *abort_flag = 1;
+        }
+        tc_commit(&tfull[b]);
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {
+    const int q = warp & 3;        // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2; // 0 or 1: alternating 32-column chunks
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int b = lt & 1, use = lt >> 1;
+      if (!mbar_wait(&tfull[b], use & 1)) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (*abort_flag) break;
+      const int m0 = tm0(t), n0 = tn0(t);
+      const int m = m0 + q * 32 + lane;
+      const uint32_t base = tmem + (uint32_t)(b * COLS) + ((uint32_t)(q * 32) << 16);
+      const int nch = (min(BN, N - n0) + 31) / 32;
+      for (int c = h; c < nch; c += 2) {
+        float v[32];
+        tc_ld32(base + (uint32_t)(32 * c), v);
+        if (m < M) t32_epilogue(ep, m, n0 + 32 * c, N, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, 2 * COLS);
+  }
+}
+
+static bool make_tmap_f32(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                          uint32_t box_inner, uint32_t box_outer) {
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+static bool launch_tf32(const GemmArgs& g, const float* B, int ldb, cudaStream_t st, int* d_err, std::string* why) {
+  static bool attr_set[kMaxDevices] = {};
+  const int dev = current_device();
+  constexpr int smem = t32_smem_bytes<BN>();
+  static_assert(smem <= kTcSmemMax, "tf32 GEMM shared memory");
+  if (!smem_opt_in(gemm_tf32_kernel<BN>, smem, attr_set, dev, why)) return false;
+  CUtensorMap ta, tb;
+  if (!make_tmap_f32(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)g.lda * 4, kT32BK, 128) ||
+      !make_tmap_f32(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 4, kT32BK, BN)) {
+    if (why) *why = "cuTensorMapEncodeTiled failed (tf32 operands)";
+    return false;
+  }
+  const int tiles = ((g.M + 127) / 128) * ((g.N + BN - 1) / BN);
+  const int nsm = num_sms(dev);
+  const int grid = tiles < nsm ? tiles : nsm;
+  gemm_tf32_kernel<BN><<<grid, kT32Threads, smem, st>>>(ta, tb, make_epi(g), g.M, g.N, g.K, d_err);
+  return true;
+}
+
+bool gemm_tc_tf32(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why) {
+  if (g.M <= 0 || g.N <= 0) return true;
+  if (!gemm_tc_init(why)) return false;
+  if (g.A2 || g.Bover || g.b_row0 || !(g.epi == EPI_FWD_SILU || g.epi == EPI_F32 || g.epi == EPI_BWD_SILU ||
+                                       g.epi == EPI_LINEAR)) {
+    if (why) *why = "tf32 GEMM: unsupported operand form or epilogue";
+    return false;
+  }
+  const float* B = g.trans ? g.W->f32T : g.W->f32;
+  const int ldb = g.trans ? g.W->ldT : g.W->ld;
+  if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (g.lda % 4) ||
+      (ldb % 4)) {
+    if (why) *why = "tf32 GEMM operands must be 16-byte aligned with pitches a multiple of 4 elements";
+    return false;
+  }
+  const int tiles = (g.N + 255) / 256;
+  int bn = (g.N + tiles - 1) / tiles;
+  bn = (bn + 31) / 32 * 32;
+  switch (bn) {
+    case 32: return launch_tf32<32>(g, B, ldb, st, d_err, why);
+    case 64: return launch_tf32<64>(g, B, ldb, st, d_err, why);
+    case 96: return launch_tf32<96>(g, B, ldb, st, d_err, why);
+    case 128: return launch_tf32<128>(g, B, ldb, st, d_err, why);
+    case 160: return launch_tf32<160>(g, B, ldb, st, d_err, why);
+    case 192: return launch_tf32<192>(g, B, ldb, st, d_err, why);
+    case 224: return launch_tf32<224>(g, B, ldb, st, d_err, why);
+    default: return launch_tf32<256>(g, B, ldb, st, d_err, why);
+  }
+}
+
 }  // namespace alg

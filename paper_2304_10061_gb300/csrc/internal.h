@@ -137,6 +137,8 @@ struct GemmArgs {
 void gemm_simt_f32(const GemmArgs& g, cudaStream_t st);
 bool gemm_tc_bf16(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
 bool gemm_tc_init(std::string* why);
+// float32 operands read as TF32 by tcgen05 kind::tf32, float32 epilogues (FWD_SILU, F32, BWD_SILU, LINEAR)
+bool gemm_tc_tf32(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
 bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why);
 
 // scan / utilities

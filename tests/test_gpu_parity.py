@@ -98,7 +98,33 @@ def test_bf16_matches_oracle(name):
     assert err["w_rel"] < 5e-2, err
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+# TF32 path (float32 storage, tcgen05 kind::tf32 GEMMs): operands keep 10 of
+# float32's 23 mantissa bits (relative rounding <= 2^-10), 4x finer than bf16's
+# 7, so its gates are a quarter of the BF16 path's.
+@pytest.mark.parametrize("name", list(CASES))
+def test_tf32_matches_oracle(name):
+    arch, w, s = CASES[name]
+    res, edges = _run(arch, w, s, "tf32")
+    eo, (E0, Ea0, F0, W0) = _oracle(name)
+    assert_same_edges(edges, eo)
+    err = errors(res["E_atom"], res["F"], res["virial"][0], Ea0, F0, W0)
+    assert err["f_rms"] < BF16_F_RMS / 4, err
+    assert err["f_max"] < 10 * BF16_F_RMS / 4, err
+    assert err["e_rel"] < 2.5e-3, err
+    assert err["w_rel"] < 1.25e-2, err
+
+
+def test_tf32_error_between_fp32_and_bf16():
+    arch, w, s = CASES["c2arch_2000"]
+    _, (E0, Ea0, F0, W0) = _oracle("c2arch_2000")
+    e = {}
+    for prec in ("fp32", "tf32", "bf16"):
+        res, _ = _run(arch, w, s, prec)
+        e[prec] = errors(res["E_atom"], res["F"], res["virial"][0], Ea0, F0, W0)["f_rms"]
+    assert e["fp32"] < e["tf32"] < e["bf16"], e
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_chunked_equals_single_pass(prec):
     """Rows split over many chunks (ragged tails) give bitwise the same result."""
     arch, w, s = CASES["c2arch_2000"]
@@ -108,7 +134,7 @@ def test_chunked_equals_single_pass(prec):
         np.testing.assert_array_equal(a[k], b[k])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_deterministic(prec):
     arch, w, s = CASES["tiny2_lmax2_C8"]
     a, _ = _run(arch, w, s, prec)

@@ -196,6 +196,13 @@ allegro_status allegro_set_md_skin(allegro_ctx* ctx, double skin);
 allegro_status allegro_md_rebuilds(const allegro_ctx* ctx, int64_t* rebuilds);
 
 /*
+ * allegro_list_size -- atoms, edges and structures of the neighbour list the
+ * context holds (the last allegro_neighbors*, or the final positions of
+ * allegro_md_verlet); zeros when it holds none.  Any output may be NULL.
+ */
+allegro_status allegro_list_size(const allegro_ctx* ctx, int64_t* n_atoms, int64_t* n_edges, int32_t* n_struct);
+
+/*
  * allegro_get_neighbors -- copy the last neighbour list out, sorted by centre
  * atom i (rows in ascending i; order inside a row is deterministic but
  * unspecified).  i[cap], j[cap], shift[cap*3] int32 (any may be NULL);

@@ -178,8 +178,14 @@ class Allegro:
         self._check(self._L.allegro_md_verlet(self._ctx, n, _ptr(pos), _ptr(vel), _ptr(types), masses.ctypes.data,
                                               masses.size, _ptr(cell), _ptr(pbc), float(dt), int(n_steps),
                                               Ep.ctypes.data, Ek.ctypes.data))
-        self.n_atoms, self.n_struct = n, 1
+        self._sync_sizes()
         return Ep, Ek
+
+    def _sync_sizes(self):
+        """Atoms, edges and structures of the list the context holds."""
+        na, ne, ns = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+        self._check(self._L.allegro_list_size(self._ctx, ctypes.byref(na), ctypes.byref(ne), ctypes.byref(ns)))
+        self.n_atoms, self.n_edges, self.n_struct = int(na.value), int(ne.value), int(ns.value)
 
     def set_autotune(self, enable: bool = True):
         """Launch-configuration autotuner (chunk size, fused layer pairs, epilogue warps) per shape bucket."""

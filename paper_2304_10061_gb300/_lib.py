@@ -21,7 +21,7 @@ PREC = {"fp32": 0, "bf16": 1, "tf32": 2}
 EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_set_zbl", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
            "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_set_md_skin", "allegro_md_rebuilds",
-           "allegro_set_autotune", "allegro_set_graphs", "allegro_autotune_report",
+           "allegro_set_autotune", "allegro_set_graphs", "allegro_autotune_report", "allegro_list_size",
            "allegro_last_error",
            "allegro_destroy")
 
@@ -53,6 +53,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_md_verlet.argtypes = [vp, i64, dp, dp, dp, dp, i32, dp, dp, ctypes.c_double, i64, dp, dp]
     L.allegro_set_md_skin.argtypes = [vp, ctypes.c_double]
     L.allegro_set_autotune.argtypes = [vp, i32]
+    L.allegro_list_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
     L.allegro_set_graphs.argtypes = [vp, i32]
     L.allegro_autotune_report.argtypes = [vp, ctypes.c_char_p, sz]
     L.allegro_md_rebuilds.argtypes = [vp, ctypes.POINTER(i64)]

@@ -2015,6 +2015,14 @@ allegro_status allegro_md_rebuilds(const allegro_ctx* c, int64_t* rebuilds) {
   return ALLEGRO_OK;
 }
 
+allegro_status allegro_list_size(const allegro_ctx* c, int64_t* n_atoms, int64_t* n_edges, int32_t* n_struct) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (n_atoms) *n_atoms = c->have_nb ? c->n_atoms : 0;
+  if (n_edges) *n_edges = c->have_nb ? c->n_edges : 0;
+  if (n_struct) *n_struct = c->have_nb ? c->nstruct : 0;
+  return ALLEGRO_OK;
+}
+
 allegro_status allegro_get_neighbors(allegro_ctx* c, int32_t* i, int32_t* j, int32_t* shift, int64_t cap) {
   if (!c) return ALLEGRO_E_INVALID;
   if (!c->have_nb) return fail(c, ALLEGRO_E_STATE, "no neighbour list");

@@ -50,7 +50,10 @@ bool gemm_tc_init(std::string* why) {
 
 // 2-D bf16 tensor map: `inner` contiguous elements per row, `outer` rows,
 // rows `row_bytes` apart; box box_inner x box_outer, 128-byte swizzle,
-// out-of-bounds elements read as zero.
+// out-of-bounds elements read as zero.  L2 fills at 256-byte granularity when
+// the map covers whole rows, at 64 bytes when it covers only part of each row
+// of its array (the x columns of [x | s], 64 columns of a 256-wide buffer):
+// larger fills would pull in the columns that are not read.
 static bool make_tmap(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
                       uint32_t box_inner, uint32_t box_outer) {
   cuuint64_t dims[2] = {inner, outer};
@@ -59,7 +62,8 @@ static bool make_tmap(CUtensorMap* tm, const void* base, uint64_t inner, uint64_
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        inner * 2 < row_bytes ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -1664,7 +1668,8 @@ static bool make_tmap_f32(CUtensorMap* tm, const void* base, uint64_t inner, uin
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        inner * 4 < row_bytes ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }

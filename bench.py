@@ -427,6 +427,73 @@ def _precision_matrix(args, local, stream):
     return res
 
 
+def _paper_model(args, local, stream, n_atoms: int = 262144):
+    """The paper's production architecture (2 layers, 64 channels, l_max 2, two-body
+    [128, 256, 512, 1024], latent 3 x 1024, edge [128]) with its per-pair cutoffs and ZBL
+    term, seeded random weights, on a water-density box: step time, throughput and the
+    model's MLP FLOP rate, BF16 and TF32 (the paper's compute precision); force errors
+    against the FP64 oracle on a 512-atom box of the same density."""
+    import torch
+    from dataclasses import replace
+    from paper_2304_10061_gb300 import Allegro
+    from synth import ARCHS, SPECIES_Z, lattice_box, make_weights, paper_pair_cutoffs, weights_to_blob
+    arch = replace(ARCHS["paper"], pair_rc=paper_pair_cutoffs(), zbl_z=SPECIES_Z)
+    w = make_weights(arch, 1)
+    blob = weights_to_blob(arch, w)
+    s = lattice_box(n_atoms, (n_atoms / 0.1) ** (1.0 / 3.0), seed=9)
+    dev = f"cuda:{local}"
+    px = torch.tensor(s.pos, device=dev)
+    tx = torch.tensor(s.species, dtype=torch.int32, device=dev)
+    cx = torch.tensor(s.cell, device=dev)
+    res = {"atoms": s.n_atoms, "architecture": "2 layers, 64 channels, l_max 2, two-body [128,256,512,1024], "
+                                               "latent [1024,1024,1024], edge [128], per-pair cutoffs, ZBL",
+           "model_flops_per_edge": model_flops_per_edge(arch),
+           "paper_context": "paper: 1,119,744-atom water on 64 A100 nodes (256 GPUs) at 20.3 steps/s, about "
+                            "8.9e4 atom-steps/s per A100 (whole LAMMPS MD step, TF32)"}
+    # force errors of the MLP precision: the ZBL term (exact up to float32 rounding) would dominate
+    # RMS|F| at the lattice's closest contacts, so the error sample runs without it
+    small = lattice_box(512, (512 / 0.1) ** (1.0 / 3.0), seed=10)
+    ref = None
+    if not args.skip_cpu:
+        from oracle.allegro import AllegroOracle
+        a0 = replace(arch, zbl_z=None)
+        i, j, S = _edges(a0, small)
+        ref = AllegroOracle(a0, w).energy_forces(small.pos, small.species, small.cell, i, j, S)
+    for prec in ("bf16", "tf32"):
+        m = Allegro(blob, precision=prec, device=local)
+        m.set_stream(stream.cuda_stream)
+        m.set_pair_cutoffs(arch.pair_rc)
+        m.set_zbl(SPECIES_Z)
+        out = dict(E=torch.empty(1, dtype=torch.float64, device=dev),
+                   E_atom=torch.empty(s.n_atoms, dtype=torch.float64, device=dev),
+                   F=torch.empty(s.n_atoms, 3, dtype=torch.float64, device=dev),
+                   virial=torch.empty(1, 3, 3, dtype=torch.float64, device=dev))
+        for _ in range(2):
+            m.neighbors(px, tx, cx)
+            m.energy_forces(out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        K = 4
+        a.record(stream)
+        for _ in range(K):
+            m.neighbors(px, tx, cx)
+            m.energy_forces(out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / K
+        rec = {"ms_per_step": ms, "atom_steps_per_s": s.n_atoms / (ms * 1e-3), "edges": m.n_edges,
+               "model_tflops_per_s": res["model_flops_per_edge"] * m.n_edges / (ms * 1e-3) / 1e12}
+        if ref is not None:
+            m.set_zbl(None)
+            m.neighbors(small.pos, small.species, small.cell)
+            o = m.energy_forces()
+            rec["force_err_vs_fp64_512_atoms_no_zbl"] = _force_errors(o["F"].cpu().numpy(), o["E"].item(), ref[2],
+                                                                      ref[0])
+        res[prec] = rec
+        m.close()
+    return res
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores: each step one bounded sample of the workload."""
     rank, ws, _, dist = _dist()
@@ -665,6 +732,8 @@ def run_ours(args):
         # water-density box (float64 final sums throughout; weights and activations float32 for the
         # TF32 and FP32 rows), and each setting's force error against the FP64 oracle
         extra["table_iv_3072_atoms"] = _precision_matrix(args, local, stream)
+        # the paper's production architecture (1024-wide MLPs, per-pair cutoffs, ZBL)
+        extra["paper_model_262144_atoms"] = _paper_model(args, local, stream)
         # the headline box under the paper's per-ordered-species-pair cutoffs
         if arch.pair_rc is None:
             extra["pair_cutoffs_1M_atoms" if args.config == "c4" and not args.atoms else "pair_cutoffs"] = \

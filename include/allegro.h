@@ -65,7 +65,10 @@ typedef enum {
  *   precision: an allegro_precision.
  *   device: CUDA device ordinal.  out: receives the context.
  * Supported models: 1 or 2 layers, l_max 1 or 2, channels a power of two from
- * 8 to 128, MLP widths up to 512.  Others return ALLEGRO_E_INVALID.
+ * 8 to 128, MLP widths up to 1024 (the paper's production model: two-body
+ * [128, 256, 512, 1024], latent 3 x 1024; with the BF16 path, MLPs wider than
+ * 256 need channels x (l_max + 1) a multiple of 64).  Others return
+ * ALLEGRO_E_INVALID.
  */
 allegro_status allegro_create(const void* weights_blob, size_t blob_bytes,
                               const int32_t* species_map, int32_t n_types,

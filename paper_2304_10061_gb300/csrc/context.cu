@@ -904,8 +904,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   io.Y = w.Y; io.W01 = w.W01; io.ld01 = w.ld_W01; io.w2 = w.w2; io.ld2 = w.ld_w2; io.G1 = w.G1; io.G2 = w.G2;
 
   const int S = a.S(), C = a.C;
-  // BF16 path: adjoint heads and the edge energy live in the tcgen05 GEMM epilogues
-  const bool fused = (c->prec == ALLEGRO_PREC_BF16);
+  // BF16 path: adjoint heads and the edge energy live in the tcgen05 GEMM
+  // epilogues, which take whole rows of at most 256 columns; wider MLPs (the
+  // paper's 1024-wide production model) run them as the separate elementwise
+  // kernels of the float32 paths, with the K-concatenated head GEMMs writing
+  // a float32 xbar
+  const bool bf16 = (c->prec == ALLEGRO_PREC_BF16);
+  const bool fused = bf16 && a.tb.back() <= 256 && a.lat.back() <= 256;
   // algorithmic bytes of the row kernels (per edge, per atom), float32 features
   auto row_scope = [&](const char* name, double per_edge, double per_atom) {
     return ProfScope(c, name, 0.0, (double)Ec * per_edge + (double)Ac * per_atom);
@@ -1060,7 +1065,9 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   };
   // BF16 path with a K-concatenated head map: the latent MLP adjoint writes only the s columns of
   // D; the head GEMM forms the x columns from [wbar | zbar] directly
-  auto kcat = [&](int L) { return fused && c->headB[L - 1] != nullptr; };
+  auto kcat = [&](int L) { return bf16 && c->headB[L - 1] != nullptr; };
+  if (bf16 && !fused && (!kcat(1) || (nl == 2 && !kcat(2))))
+    return fail(c, ALLEGRO_E_INVALID, "BF16 path with MLPs wider than 256 needs 64-aligned env-weight widths");
   // D (the latent inputs' adjoint) is stored in the activation type: EPI_LINEAR
   const void* zlat[2] = {nullptr, nullptr};
   if ((s = back_mlp(c->lat[nl - 1], w.Zlat[nl - 1], w.ld_Zlat, nlat, w.D[nl - 1], w.ld_D[nl - 1],
@@ -1082,7 +1089,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
     // xbar^1 = wbar^2 . env2 + D[1][:, :K1], then the adjoint head of x^1 = u silu(z)
     GemmArgs head1;
     const GemmArgs* head1p = nullptr;
-    if (kcat(2)) {
+    if (kcat(2) && !fused) {
+      // wide MLPs: xbar^1 in float32 from the K-concatenated GEMM, the head below
+      head1 = mk(w.wbar2, w.ld_wbar2, c->headK[1], c->env2, true, EPI_F32, w.xbar, w.ld_xbar, a.lat.back());
+      head1.A2 = zlat[1]; head1.lda2 = w.ld_H; head1.K1 = c->headK1[1];
+      head1.Bover = c->headB[1]; head1.ldb_over = c->headLd[1];
+      if ((s = run1(head1)) != ALLEGRO_OK) return s;
+    } else if (kcat(2)) {
       head1 = mk(w.wbar2, w.ld_wbar2, c->headK[1], c->env2, true, EPI_HEAD, w.H[0], w.ld_H, a.lat.back(),
                  w.Zlat[0][nlat - 1], w.ld_Zlat[nlat - 1], w.u, nullptr, 0, w.ubar);
       head1.A2 = zlat[1]; head1.lda2 = w.ld_H; head1.K1 = c->headK1[1];
@@ -1113,7 +1126,13 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   // xbar^0 = [wbar^0 | wbar^1] . [W_emb ; W_env1] + D[0][:, :K0], then the head of x^0 = u silu(z)
   GemmArgs head0;
   bool head0_pending = false;
-  if (kcat(1)) {
+  if (kcat(1) && !fused) {
+    // wide MLPs: xbar^0 in float32 from the K-concatenated GEMM, the head below
+    head0 = mk(w.wbar01, w.ld_wbar01, c->headK[0], c->w01, true, EPI_F32, w.xbar, w.ld_xbar, a.tb.back());
+    head0.A2 = zlat[0]; head0.lda2 = w.ld_H; head0.K1 = c->headK1[0];
+    head0.Bover = c->headB[0]; head0.ldb_over = c->headLd[0];
+    if ((s = run1(head0)) != ALLEGRO_OK) return s;
+  } else if (kcat(1)) {
     head0 = mk(w.wbar01, w.ld_wbar01, c->headK[0], c->w01, true, EPI_HEAD, w.H[0], w.ld_H, a.tb.back(),
                w.Ztb[ntb - 1], w.ld_Ztb[ntb - 1], w.u, nullptr, 0, w.ubar);
     head0.A2 = zlat[0]; head0.lda2 = w.ld_H; head0.K1 = c->headK1[0];

@@ -438,9 +438,6 @@ void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, 
 template void edge_energy<float>(int, int, const float*, int, const float*, float*, cudaStream_t);
 template void edge_energy<bf16>(int, int, const bf16*, int, const float*, float*, cudaStream_t);
 
-// Per atom i (float64): Etilde_i = sigma_Z E_i + mu_Z with E_i = sum_{row i} E_ij;
-// F_i = sum_{e in row i} g_e - sum_{e with j_e = i} g_e  (g_e = dE/dd_e);
-// per-atom virial W_i = - sum_{e in row i} d_e (x) g_e.
 // ZBL repulsion of one ordered edge (Sec. "Training details": a Ziegler-
 // Biersack-Littmark term is added to the potential).  The universal ZBL pair
 // energy k_e Z_a Z_b / r phi(r / a_s), phi(x) = sum_k c_k exp(-d_k x) (the
@@ -476,6 +473,10 @@ __device__ __forceinline__ void zbl_edge(float r, float2 zp, float inv_rc, const
   dedr = a * (dphi * zp.y * u + phi * du - phi * u * ir);
 }
 
+// Per atom i (float64): Etilde_i = sigma_Z E_i + mu_Z with E_i = sum_{row i} E_ij;
+// F_i = sum_{e in row i} g_e - sum_{e with j_e = i} g_e  (g_e = dE/dd_e);
+// per-atom virial W_i = - sum_{e in row i} d_e (x) g_e; with the ZBL term its energy
+// joins Etilde_i and its dE/dd joins g_e in both gathers.
 __global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_ptr,
                                    const int* __restrict__ col_edge, const float* __restrict__ Ee,
                                    const float* __restrict__ g, const double* __restrict__ ed,

@@ -20,7 +20,7 @@ typedef __nv_bfloat16 bf16;
 constexpr int kMaxLmax = 2;
 constexpr int kMaxS = (kMaxLmax + 1) * (kMaxLmax + 1);   // spherical-harmonic components
 constexpr int kMaxChannels = 128;
-constexpr int kMaxWidth = 512;
+constexpr int kMaxWidth = 1024;
 constexpr int kMaxSpecies = 64;
 constexpr int kMaxBessel = 16;
 

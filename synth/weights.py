@@ -77,6 +77,11 @@ ARCHS: Dict[str, Arch] = {
     # 23.5k / 1M-atom cases: 2 layers, l_max=2, 64 channels
     "c2": Arch(n_species=5, lmax=2, n_layers=2, channels=64, two_body=(64, 128, 256),
                latent=(256, 256), edge=(128,)),
+    # the paper's production model (Sec. "Training details"): 2 layers of 64 tensor features,
+    # l_max 2, two-body MLP [128, 256, 512, 1024], latent MLP [1024, 1024, 1024], edge MLP with
+    # one hidden layer of 128, no nonlinearity; per-pair cutoffs and ZBL on the water/protein mix
+    "paper": Arch(n_species=5, lmax=2, n_layers=2, channels=64, two_body=(128, 256, 512, 1024),
+                  latent=(1024, 1024, 1024), edge=(128,)),
     # 4M-atom case: 3 layers, l_max=3, 128 channels, latent 2x512
     "c5": Arch(n_species=5, lmax=3, n_layers=3, channels=128, two_body=(64, 128, 512),
                latent=(512, 512), edge=(128,)),

@@ -23,6 +23,8 @@ L1X2 = Arch(n_species=2, lmax=1, n_layers=2, channels=32, two_body=(64,), latent
 C128 = Arch(n_species=2, lmax=2, n_layers=2, channels=128, two_body=(64, 128), latent=(128,), edge=())
 # dense rows (~85 neighbours): rows longer than one staged segment of the row kernels
 DENSE = Arch(n_species=3, lmax=2, n_layers=2, channels=16, two_body=(32,), latent=(32,), edge=())
+# 1024-wide MLPs (the paper's production widths): the BF16 path's heads and edge energy leave the GEMM epilogues
+WIDE = Arch(n_species=3, lmax=2, n_layers=2, channels=64, two_body=(128, 1024), latent=(1024, 1024), edge=(128,))
 
 
 def _cases():
@@ -36,6 +38,8 @@ def _cases():
     s128.species = s128.species % 2
     sd = lattice_box(400, (400 / 0.32) ** (1 / 3), seed=10)
     sd.species = sd.species % 3
+    sw = lattice_box(250, (250 / 0.1) ** (1 / 3), seed=11)
+    sw.species = sw.species % 3
     return {
         "c1": (a1, w1, s1),
         "tiny2_lmax2_C8": (TINY2, make_weights(TINY2, 3), st),
@@ -44,6 +48,7 @@ def _cases():
         "c2arch_2000": (ARCHS["c2"], make_weights(ARCHS["c2"], 1), s2),
         "C128_lmax2": (C128, make_weights(C128, 7), s128),
         "dense_rows_85": (DENSE, make_weights(DENSE, 8), sd),
+        "wide_1024": (WIDE, make_weights(WIDE, 9), sw),
     }
 
 

@@ -142,6 +142,25 @@ allegro_status allegro_neighbors(allegro_ctx* ctx, int64_t n_atoms, const double
                                  int64_t* n_edges_out);
 
 /*
+ * allegro_neighbors_local -- the neighbour list of one sub-domain of a spatial
+ * decomposition (Sec. "Optimized LAMMPS-Kokkos implementation": strict
+ * locality lets each rank evaluate its own atoms with a ghost halo of width
+ * r_c).  Atoms [0, n_local) are the sub-domain's own atoms and the only
+ * centres; atoms [n_local, n_atoms) are ghosts (copies of other sub-domains'
+ * atoms, already shifted by the periodic image they stand for), which appear
+ * only as neighbours j.  Same pair rule and arguments as allegro_neighbors.
+ * allegro_energy_forces then returns E_total = the sum of the local atoms'
+ * energies, E_atom = 0 for ghosts, F for every atom (a ghost's force is its
+ * share of the local energies, to be added to the atom it copies), and the
+ * virial of the local centres' edges.  Summed over sub-domains whose local
+ * atoms partition the system and whose ghosts cover r_c around them, these
+ * equal the single-domain results.
+ */
+allegro_status allegro_neighbors_local(allegro_ctx* ctx, int64_t n_local, int64_t n_atoms, const double* pos,
+                                       const int32_t* types, const double* cell, const uint8_t* pbc,
+                                       int64_t* n_edges_out);
+
+/*
  * allegro_neighbors_batched -- many independent structures in one packed
  * list.  Structure b holds atoms [atom_offsets[b], atom_offsets[b+1]);
  * atom_offsets[n_struct+1] int64 (host or device).  cells[n_struct*9] or

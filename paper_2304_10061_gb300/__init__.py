@@ -134,6 +134,21 @@ class Allegro:
         self.n_atoms, self.n_edges, self.n_struct = n, int(ne.value), 1
         return self.n_edges
 
+    def neighbors_local(self, n_local: int, pos, types, cell=None, pbc=None) -> int:
+        """One sub-domain of a spatial decomposition: atoms [0, n_local) are centres, the
+        rest ghosts (neighbours only)."""
+        pos = _as(pos, np.float64)
+        types = _as(types, np.int32)
+        cell = _as(cell, np.float64)
+        pbc = _as(pbc, np.uint8)
+        n = int(pos.shape[0])
+        ne = ctypes.c_int64(0)
+        self._keep = (pos, types, cell, pbc)
+        self._check(self._L.allegro_neighbors_local(self._ctx, int(n_local), n, _ptr(pos), _ptr(types), _ptr(cell),
+                                                    _ptr(pbc), ctypes.byref(ne)))
+        self.n_atoms, self.n_edges, self.n_struct = n, int(ne.value), 1
+        return self.n_edges
+
     def neighbors_batched(self, offsets, pos, types, cells=None, pbc=None) -> int:
         offsets = _as(offsets, np.int64)
         pos = _as(pos, np.float64)

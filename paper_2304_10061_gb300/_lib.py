@@ -22,6 +22,7 @@ EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",
            "allegro_profile", "allegro_profile_report", "allegro_neighbors_noalloc", "allegro_md_verlet", "allegro_set_md_skin", "allegro_md_rebuilds",
            "allegro_set_autotune", "allegro_set_graphs", "allegro_autotune_report", "allegro_list_size",
+           "allegro_neighbors_local",
            "allegro_last_error",
            "allegro_destroy")
 
@@ -44,6 +45,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.allegro_set_zbl.argtypes = [vp, dp, i32]
     L.allegro_neighbors.argtypes = [vp, i64, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_neighbors_batched.argtypes = [vp, i32, dp, dp, dp, dp, dp, ctypes.POINTER(i64)]
+    L.allegro_neighbors_local.argtypes = [vp, i64, i64, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.allegro_energy_forces.argtypes = [vp, dp, dp, dp, dp]
     L.allegro_get_neighbors.argtypes = [vp, dp, dp, dp, i64]
     L.allegro_profile.argtypes = [vp, i32]

@@ -134,6 +134,7 @@ struct allegro_ctx {
   // state of the last neighbour build
   bool have_nb = false;
   int64_t n_atoms = 0, n_edges = 0;
+  int64_t n_centres = 0;                   // atoms [0, n_centres) are centres (the rest are ghosts)
   int nstruct = 0;
   bool batched = false;
   std::vector<int> h_row_ptr;              // host copy of row_ptr (for chunking)
@@ -741,6 +742,7 @@ allegro_status finish_neighbors(allegro_ctx* c, int n, int64_t E) {
     return fail(c, ALLEGRO_E_INVALID, "a type is outside the species map or a position is not finite");
   if (err & kErrNeighbor) return fail(c, ALLEGRO_E_CUDA, "internal: neighbour fill pass disagreed with its count");
   c->n_atoms = n;
+  c->n_centres = n;
   c->n_edges = E;
   c->have_nb = true;
   return ALLEGRO_OK;
@@ -1234,7 +1236,7 @@ allegro_status run_plan(allegro_ctx* c, const Plan& p, const WS& w, bool backwar
   }
   {
     ProfScope ps(c, "atom_reduce", 0.0, (double)E * (backward ? 60.0 : 4.0) + (double)n * (backward ? 128.0 : 16.0));
-    atom_reduce(n, c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_Ee, c->d_g, c->d_ed, c->d_species, c->d_sigma,
+    atom_reduce(n, (int)std::min<int64_t>(c->n_centres, n), c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_Ee, c->d_g, c->d_ed, c->d_species, c->d_sigma,
                 c->d_mu, backward, c->d_Eatom, c->d_F, c->d_Wat, c->d_ei, c->d_ej, c->arch, c->stream);
   }
   {
@@ -1261,6 +1263,7 @@ allegro_status evaluate_once(allegro_ctx* c, bool backward) {
   allegro_ctx::GraphKey key;
   key.bounds = p.bounds;
   for (int b : p.bounds) key.bounds.push_back(c->h_row_ptr[b]);   // edge offsets of the chunks too
+  key.bounds.push_back((int)c->n_centres);
   key.ptrs = {c->d_row_ptr, c->d_col_ptr, c->d_col_edge, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_Ee, c->d_g,
               c->d_species, c->d_Eatom, c->d_F, c->d_Wat, c->d_offs, c->d_Eout, c->d_Wout, c->d_err,
               c->d_red_scratch, c->ws, c->arch.pair_basis, c->arch.zbl, c->d_atom_struct};
@@ -1584,7 +1587,7 @@ allegro_status allegro_reserve(allegro_ctx* c, int64_t atom_cap, int64_t edge_ca
 // only when `use_pair` is set.
 static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double* pos, const int32_t* types,
                                    const double* cell, const uint8_t* pbc, int64_t* n_edges_out, double radius,
-                                   bool use_pair) {
+                                   bool use_pair, int64_t n_centres = -1) {
   if (!c) return ALLEGRO_E_INVALID;
   c->have_nb = false;
   if (n_atoms < 0 || n_atoms > 1000000000LL) return fail(c, ALLEGRO_E_INVALID, "bad n_atoms");
@@ -1616,6 +1619,7 @@ static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double
     hpbc[0] = hpbc[1] = hpbc[2] = 1;
   }
   CellGrid g{};
+  g.n_centres = (n_centres < 0 || n_centres > n) ? n : (int)n_centres;
   const double rc = radius, rcm = rc * (1.0 + 1e-6);
   const double* pair_rc2 = use_pair ? c->arch.pair_rc2 : nullptr;
   memcpy(c->h_cell, hcell, sizeof hcell);
@@ -1729,6 +1733,7 @@ static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
   if ((s = finish_neighbors(c, n, hE)) != ALLEGRO_OK) return s;
+  c->n_centres = g.n_centres;
   if (n_edges_out) *n_edges_out = hE;
   return ALLEGRO_OK;
 }
@@ -1737,6 +1742,14 @@ allegro_status allegro_neighbors(allegro_ctx* c, int64_t n_atoms, const double* 
                                  const double* cell, const uint8_t* pbc, int64_t* n_edges_out) {
   if (!c) return ALLEGRO_E_INVALID;
   return build_single(c, n_atoms, pos, types, cell, pbc, n_edges_out, c->arch.rc, true);
+}
+
+allegro_status allegro_neighbors_local(allegro_ctx* c, int64_t n_local, int64_t n_atoms, const double* pos,
+                                       const int32_t* types, const double* cell, const uint8_t* pbc,
+                                       int64_t* n_edges_out) {
+  if (!c) return ALLEGRO_E_INVALID;
+  if (n_local < 0 || n_local > n_atoms) return fail(c, ALLEGRO_E_INVALID, "n_local must be in [0, n_atoms]");
+  return build_single(c, n_atoms, pos, types, cell, pbc, n_edges_out, c->arch.rc, true, n_local);
 }
 
 allegro_status allegro_neighbors_batched(allegro_ctx* c, int32_t n_struct, const int64_t* atom_offsets,

@@ -477,7 +477,7 @@ __device__ __forceinline__ void zbl_edge(float r, float2 zp, float inv_rc, const
 // F_i = sum_{e in row i} g_e - sum_{e with j_e = i} g_e  (g_e = dE/dd_e);
 // per-atom virial W_i = - sum_{e in row i} d_e (x) g_e; with the ZBL term its energy
 // joins Etilde_i and its dE/dd joins g_e in both gathers.
-__global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_ptr,
+__global__ void atom_reduce_kernel(int n, int n_centres, const int* __restrict__ row_ptr, const int* __restrict__ col_ptr,
                                    const int* __restrict__ col_edge, const float* __restrict__ Ee,
                                    const float* __restrict__ g, const double* __restrict__ ed,
                                    const int* __restrict__ species, const double* __restrict__ sigma,
@@ -514,7 +514,7 @@ __global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const
       W[6] -= d2 * gx; W[7] -= d2 * gy; W[8] -= d2 * gz;
     }
   }
-  E_atom[i] = sigma[z] * Ei + mu[z] + Ez;
+  E_atom[i] = (i < n_centres) ? sigma[z] * Ei + mu[z] + Ez : 0.0;
   if (want_forces) {
     for (int k = col_ptr[i]; k < col_ptr[i + 1]; ++k) {
       size_t e = (size_t)col_edge[k];
@@ -535,12 +535,12 @@ __global__ void atom_reduce_kernel(int n, const int* __restrict__ row_ptr, const
   }
 }
 
-void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
+void atom_reduce(int n, int n_centres, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
                  const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
                  bool want_forces, double* E_atom, double* F, double* Wat, const int* ei, const int* ej,
                  const Arch& a, cudaStream_t st) {
   if (n <= 0) return;
-  atom_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, col_ptr, col_edge, Ee, g, ed, species, sigma,
+  atom_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, n_centres, row_ptr, col_ptr, col_edge, Ee, g, ed, species, sigma,
                                                       mu, want_forces, E_atom, F, Wat, ei, ej,
                                                       reinterpret_cast<const float2*>(a.zbl), make_basis(a));
 }

@@ -154,6 +154,7 @@ struct CellGrid {
   int n[3];           // cells per axis
   int R[3];           // stencil radius per axis
   double lo[3], span[3];   // non-periodic axes: frac range mapped onto the grid
+  int n_centres;      // atoms [0, n_centres) are centres; the rest (ghosts) only neighbours
 };
 void nb_bin(const double* pos, int n, const CellGrid& g, int* cell_of, int* wrap, int* cell_count,
             cudaStream_t st);
@@ -213,7 +214,9 @@ template <typename T>
 void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, cudaStream_t st);
 // float64 per-atom energies sigma_Z E_i + mu_Z (+ the ZBL term when a.zbl is set), forces by row and
 // column gathers of dE/dd, per-atom virial
-void atom_reduce(int n, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
+// atoms [n_centres, n) are ghosts: energy 0 (their own environments are incomplete); forces from the
+// column gather (their share of the local centres' energies)
+void atom_reduce(int n, int n_centres, const int* row_ptr, const int* col_ptr, const int* col_edge, const float* Ee,
                  const float* g, const double* ed, const int* species, const double* sigma, const double* mu,
                  bool want_forces, double* E_atom, double* F, double* Wat, const int* ei, const int* ej,
                  const Arch& a, cudaStream_t st);

@@ -403,6 +403,10 @@ __global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = sorted[t];
+  if (i >= g.n_centres) {   // ghost atoms (spatial decomposition) are neighbours only, never centres
+    if (!fill) count[i] = 0;
+    return;
+  }
   const int ci = cell_of[i];
   int c[3];
   c[2] = ci % g.n[2];

@@ -258,5 +258,13 @@ double cg_racah(int j1, int m1, int j2, int m2, int j3, int m3);
 void coupling_real(int l1, int l2, int l3, std::vector<double>& out);   // [(2l1+1)(2l2+1)(2l3+1)]
 void fused_layer_tensor(int lmax, const float* theta_raw, std::vector<double>& W, int& n_in, int& n_out,
                         bool last);
+// any number of layers: irreps (l, p = +1 / -1) of V^0..V^nl, and the fused tensor of one layer
+struct Irrep {
+  int l, p;
+};
+void layer_irreps(int lmax, int nl, std::vector<std::vector<Irrep>>& irs);
+int irreps_dim(const std::vector<Irrep>& v);
+void layer_tensor(int lmax, const std::vector<Irrep>& in, const std::vector<Irrep>& out, const float* theta_raw,
+                  std::vector<double>& W);
 
 }  // namespace alg

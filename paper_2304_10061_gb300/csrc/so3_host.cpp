@@ -147,4 +147,96 @@ void fused_layer_tensor(int lmax, const float* theta_raw, std::vector<double>& W
   }
 }
 
+// ---------------------------------------------------------------------------
+// Models with more than two layers: features of the middle layers carry
+// irreps (l, p) of either parity.  Layer L's outputs are the irreps (lo, po),
+// lo <= l_max, produced by (l1, p1) x (l2, (-1)^l2) from its inputs that can
+// still reach the scalar 0e in the remaining layers; the last layer keeps 0e
+// only.  Irreps are ordered by l, then p = +1 before p = -1, each taking
+// 2l + 1 consecutive components of the strided layout.
+// ---------------------------------------------------------------------------
+static void sort_unique(std::vector<Irrep>& v) {
+  std::vector<Irrep> out;
+  for (int l = 0; l <= 64; ++l)
+    for (int p : {1, -1})
+      for (const Irrep& x : v)
+        if (x.l == l && x.p == p) {
+          out.push_back(x);
+          break;
+        }
+  v.swap(out);
+}
+
+static std::vector<Irrep> tp_outputs(const std::vector<Irrep>& in, int lmax) {
+  std::vector<Irrep> out;
+  for (const Irrep& a : in)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int lo = std::abs(a.l - l2); lo <= std::min(a.l + l2, lmax); ++lo)
+        out.push_back({lo, a.p * ((l2 & 1) ? -1 : 1)});
+  sort_unique(out);
+  return out;
+}
+
+static bool can_reach_scalar(const Irrep& ir, int steps, int lmax) {
+  if (steps == 0) return ir.l == 0 && ir.p == 1;
+  for (const Irrep& o : tp_outputs({ir}, lmax))
+    if (can_reach_scalar(o, steps - 1, lmax)) return true;
+  return false;
+}
+
+void layer_irreps(int lmax, int nl, std::vector<std::vector<Irrep>>& irs) {
+  irs.clear();
+  std::vector<Irrep> v0;
+  for (int l = 0; l <= lmax; ++l) v0.push_back({l, (l & 1) ? -1 : 1});
+  irs.push_back(v0);
+  for (int L = 1; L <= nl; ++L) {
+    std::vector<Irrep> keep;
+    for (const Irrep& o : tp_outputs(irs.back(), lmax))
+      if (can_reach_scalar(o, nl - L, lmax)) keep.push_back(o);
+    irs.push_back(keep);
+  }
+}
+
+int irreps_dim(const std::vector<Irrep>& v) {
+  int d = 0;
+  for (const Irrep& x : v) d += 2 * x.l + 1;
+  return d;
+}
+
+// W[a][b][c] over dim(in) x S x dim(out) for the layer in -> out.
+void layer_tensor(int lmax, const std::vector<Irrep>& in, const std::vector<Irrep>& out, const float* theta_raw,
+                  std::vector<double>& W) {
+  const int S = (lmax + 1) * (lmax + 1), lm = lmax + 1;
+  const int din = irreps_dim(in), dout = irreps_dim(out);
+  W.assign((size_t)din * S * dout, 0.0);
+  auto pidx = [](int p) { return p == 1 ? 0 : 1; };
+  std::vector<int> off_in, off_out;
+  for (int o = 0, k = 0; k < (int)in.size(); o += 2 * in[k].l + 1, ++k) off_in.push_back(o);
+  for (int o = 0, k = 0; k < (int)out.size(); o += 2 * out[k].l + 1, ++k) off_out.push_back(o);
+  for (int ko = 0; ko < (int)out.size(); ++ko) {
+    const int lo = out[ko].l, po = out[ko].p;
+    int npaths = 0;
+    for (const Irrep& a : in)
+      for (int l2 = 0; l2 <= lmax; ++l2)
+        if (lo >= std::abs(a.l - l2) && lo <= a.l + l2 && po == a.p * ((l2 & 1) ? -1 : 1)) ++npaths;
+    for (int ki = 0; ki < (int)in.size(); ++ki) {
+      const int l1 = in[ki].l, p1 = in[ki].p;
+      for (int l2 = 0; l2 <= lmax; ++l2) {
+        if (!(lo >= std::abs(l1 - l2) && lo <= l1 + l2 && po == p1 * ((l2 & 1) ? -1 : 1))) continue;
+        const size_t idx = ((((size_t)lo * 2 + pidx(po)) * lm + l1) * 2 + pidx(p1)) * lm + l2;
+        const double th = (double)theta_raw[idx] / std::sqrt((double)npaths);
+        std::vector<double> Cc;
+        coupling_real(l1, l2, lo, Cc);
+        const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * lo + 1;
+        for (int m1 = 0; m1 < d1; ++m1)
+          for (int m2 = 0; m2 < d2; ++m2)
+            for (int m3 = 0; m3 < d3; ++m3) {
+              const int a = off_in[ki] + m1, b = l2 * l2 + m2, c = off_out[ko] + m3;
+              W[((size_t)a * S + b) * dout + c] += th * Cc[(m1 * d2 + m2) * d3 + m3];
+            }
+      }
+    }
+  }
+}
+
 }  // namespace alg

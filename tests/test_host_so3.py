@@ -32,6 +32,30 @@ double cg_racah(int j1, int m1, int j2, int m2, int j3, int m3);
 void coupling_real(int l1, int l2, int l3, std::vector<double>& out);
 void fused_layer_tensor(int lmax, const float* theta_raw, std::vector<double>& W, int& n_in, int& n_out, bool last);
 }
+namespace alg {
+struct Irrep { int l, p; };
+void layer_irreps(int lmax, int nl, std::vector<std::vector<Irrep>>& irs);
+int irreps_dim(const std::vector<Irrep>& v);
+void layer_tensor(int lmax, const std::vector<Irrep>& in, const std::vector<Irrep>& out, const float* theta_raw,
+                  std::vector<double>& W);
+}
+extern "C" int t_irreps(int lmax, int nl, int L, int* lp, int cap) {
+  std::vector<std::vector<alg::Irrep>> irs;
+  alg::layer_irreps(lmax, nl, irs);
+  const auto& v = irs[L];
+  if ((int)v.size() * 2 > cap) return -1;
+  for (size_t k = 0; k < v.size(); ++k) { lp[2 * k] = v[k].l; lp[2 * k + 1] = v[k].p; }
+  return (int)v.size();
+}
+extern "C" int t_layer(int lmax, int nl, int L, const float* theta, double* out, int cap) {
+  std::vector<std::vector<alg::Irrep>> irs;
+  alg::layer_irreps(lmax, nl, irs);
+  std::vector<double> W;
+  alg::layer_tensor(lmax, irs[L - 1], irs[L], theta, W);
+  if ((int)W.size() > cap) return -1;
+  for (size_t i = 0; i < W.size(); ++i) out[i] = W[i];
+  return (int)W.size();
+}
 extern "C" double t_cg(int j1, int m1, int j2, int m2, int j3, int m3) {
   return alg::cg_racah(j1, m1, j2, m2, j3, m3);
 }
@@ -72,6 +96,11 @@ def lib(tmp_path_factory):
     L.t_cg.argtypes = [ctypes.c_int] * 6
     L.t_coupling.restype = ctypes.c_int
     L.t_coupling.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    L.t_irreps.restype = ctypes.c_int
+    L.t_irreps.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.t_layer.restype = ctypes.c_int
+    L.t_layer.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_int]
     L.t_fused.restype = ctypes.c_int
     L.t_fused.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                           ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -158,3 +187,24 @@ def test_sparsity_rule_is_the_oracle_pattern():
     rule = np.array([[[_allowed(a, b, c) for c in range(9)] for b in range(9)] for a in range(9)])
     assert int(rule.sum()) == 83
     assert (nz == rule).all()
+
+
+@pytest.mark.parametrize("lmax,nl", [(1, 3), (2, 3), (3, 3), (3, 2), (2, 2)])
+def test_general_layer_irreps_and_tensors_match_oracle(lib, lmax, nl):
+    """Irreps of every layer (pseudo-irreps in the middle layers of 3-layer models) and
+    the fused tensors between them, as the host builds them, equal the oracle's."""
+    irs = so3.layer_irreps(lmax, nl)
+    buf = np.zeros(2 * 64, dtype=np.int32)
+    for L in range(nl + 1):
+        k = lib.t_irreps(lmax, nl, L, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), buf.size)
+        got = [(int(buf[2 * q]), int(buf[2 * q + 1])) for q in range(k)]
+        assert got == irs[L], (L, got, irs[L])
+    lm = lmax + 1
+    rng = np.random.default_rng(300 + 10 * lmax + nl)
+    for L in range(1, nl + 1):
+        theta = rng.standard_normal((lm, 2, lm, 2, lm)).astype(np.float32)
+        ref = so3.fused_path_tensor(theta.astype(np.float64), irs[L - 1], irs[L], lmax)
+        out = np.zeros(ref.size)
+        k = lib.t_layer(lmax, nl, L, theta.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dp(out), out.size)
+        assert k == ref.size
+        np.testing.assert_allclose(out.reshape(ref.shape), ref, rtol=0, atol=1e-12, err_msg=str(L))

@@ -64,7 +64,8 @@ typedef enum {
  *       other value must equal it (the radial basis and envelope vanish there).
  *   precision: an allegro_precision.
  *   device: CUDA device ordinal.  out: receives the context.
- * Supported models: 1 or 2 layers, l_max 1 or 2, channels a power of two from
+ * Supported models: 1 to 3 layers, l_max 1 to 3 (three-layer models carry
+ * pseudo-parity features in their middle layers), channels a power of two from
  * 8 to 128, MLP widths up to 1024 (the paper's production model: two-body
  * [128, 256, 512, 1024], latent 3 x 1024; with the BF16 path, MLPs wider than
  * 256 need channels x (l_max + 1) a multiple of 64).  Others return

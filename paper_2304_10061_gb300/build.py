@@ -21,8 +21,8 @@ OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(OUT_DIR, "liballegro_gb300.so")
 
-SOURCES = ["context.cu", "neighbors.cu", "edge_kernels.cu", "row_kernels.cu", "gemm_simt.cu", "gemm_tc.cu",
-           "so3_host.cpp", "noalloc.cu"]
+SOURCES = ["context.cu", "neighbors.cu", "edge_kernels.cu", "row_kernels.cu", "row_generic.cu", "gemm_simt.cu",
+           "gemm_tc.cu", "so3_host.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]

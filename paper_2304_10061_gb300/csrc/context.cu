@@ -117,12 +117,19 @@ struct allegro_ctx {
   // model on the device
   std::vector<Lin> tb;                     // two-body layers
   Lin w01;                                 // [embedding ; env weights of layer 1]
-  Lin env2;                                // env weights of layer 2 (two-layer models)
+  Lin env2;                                // env weights of layer 2 (two- and three-layer models)
+  Lin env3;                                // env weights of layer 3 (three-layer models)
+  // models the specialised row kernels do not take (three layers, or l_max 3): the
+  // generic row path with the layer tensors as nonzero lists on the device
+  bool generic = false;
+  GenNz* d_nz[kGenMaxLayers + 1] = {};
+  int nnz[kGenMaxLayers + 1] = {};
+  int gdim[kGenMaxLayers + 1] = {};
   std::vector<std::vector<Lin>> lat;       // latent MLP of layers 1..nl
   // BF16 path: the adjoint of x^{L-1} in one GEMM over [wbar^L | zbar^L] (K-concatenated):
   // B[n][k] = W_env^L[k][n] for k < K1, W_lat^L_0[k - K1][n] after; null when K1 % 64 != 0
-  bf16* headB[2] = {nullptr, nullptr};
-  int headK1[2] = {0, 0}, headK[2] = {0, 0}, headLd[2] = {0, 0};
+  bf16* headB[kGenMaxLayers] = {nullptr, nullptr, nullptr};
+  int headK1[kGenMaxLayers] = {0, 0, 0}, headK[kGenMaxLayers] = {0, 0, 0}, headLd[kGenMaxLayers] = {0, 0, 0};
   float* d_v = nullptr;                    // folded edge-energy vector
   double* d_sigma = nullptr;
   double* d_mu = nullptr;
@@ -399,8 +406,10 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   for (int k = 0; k < nlat; ++k) a.lat.push_back(r.get<int32_t>());
   for (int k = 0; k < ned; ++k) a.edge.push_back(r.get<int32_t>());
   if (!r.ok) return fail(c, ALLEGRO_E_INVALID, "weights: truncated header");
-  if (a.nl < 1 || a.nl > 2) return fail(c, ALLEGRO_E_INVALID, "weights: %d layers (supported: 1 or 2)", a.nl);
-  if (a.lmax < 1 || a.lmax > kMaxLmax) return fail(c, ALLEGRO_E_INVALID, "weights: l_max %d (supported: 1, 2)", a.lmax);
+  if (a.nl < 1 || a.nl > kGenMaxLayers)
+    return fail(c, ALLEGRO_E_INVALID, "weights: %d layers (supported: 1 to 3)", a.nl);
+  if (a.lmax < 1 || a.lmax > kMaxLmax) return fail(c, ALLEGRO_E_INVALID, "weights: l_max %d (supported: 1 to 3)", a.lmax);
+  c->generic = (a.nl > 2 || a.lmax > 2);
   if (a.C < 8 || a.C > kMaxChannels || (a.C & (a.C - 1)))
     return fail(c, ALLEGRO_E_INVALID, "weights: %d channels (supported: powers of two 8..128)", a.C);
   if (a.ns < 1 || a.ns > kMaxSpecies || a.nb < 1 || a.nb > kMaxBessel || a.p < 2 || a.p > 16 || !(a.rc > 0) ||
@@ -456,7 +465,8 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   memcpy(W01.data(), Wemb.data(), Wemb.size() * 4);
   memcpy(W01.data() + Wemb.size(), Wenv[0].data(), Wenv[0].size() * 4);
   if ((s = upload_lin(c, W01, 2 * nw, a.tb.back(), c->w01)) != ALLEGRO_OK) return s;
-  if (a.nl == 2 && (s = upload_lin(c, Wenv[1], nw, a.lat.back(), c->env2)) != ALLEGRO_OK) return s;
+  if (a.nl >= 2 && (s = upload_lin(c, Wenv[1], nw, a.lat.back(), c->env2)) != ALLEGRO_OK) return s;
+  if (a.nl >= 3 && (s = upload_lin(c, Wenv[2], nw, a.lat.back(), c->env3)) != ALLEGRO_OK) return s;
   c->lat.assign(a.nl, std::vector<Lin>(nlat));
   for (int L = 1; L <= a.nl; ++L) {
     fan = a.Klat(L - 1) + a.C;
@@ -468,7 +478,7 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   // K-concatenated adjoint maps of x^0 (layer 1: [W_emb ; W_env1] with the latent layer 1_0)
   // and of x^1 (layer 2: W_env2 with the latent layer 2_0)
   for (int L = 1; L <= a.nl; ++L) {
-    const std::vector<float>& We = (L == 1) ? W01 : Wenv[1];
+    const std::vector<float>& We = (L == 1) ? W01 : Wenv[L - 1];
     const int K1 = (L == 1) ? 2 * nw : nw;
     const int Nx = a.Klat(L - 1), K2 = a.lat[0], fanl = a.Klat(L - 1) + a.C;
     if (K1 % 64 != 0) continue;
@@ -509,6 +519,36 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   const int S = a.S();
   memset(&c->tp, 0, sizeof(c->tp));
   c->tp.nu = (float)(1.0 / sqrt(a.ann));
+  if (c->generic) {
+    // the fused tensor of every layer between its irreps (pseudo-parity features in the
+    // middle layers), as a list of nonzeros for the generic row kernels
+    std::vector<std::vector<Irrep>> irs;
+    layer_irreps(a.lmax, a.nl, irs);
+    for (int L = 0; L <= a.nl; ++L) {
+      c->gdim[L] = irreps_dim(irs[L]);
+      if (c->gdim[L] > kGenMaxD) return fail(c, ALLEGRO_E_INVALID, "internal: layer %d has %d components", L, c->gdim[L]);
+    }
+    for (int L = 1; L <= a.nl; ++L) {
+      std::vector<double> W;
+      layer_tensor(a.lmax, irs[L - 1], irs[L], theta[L - 1].data(), W);
+      const int din = c->gdim[L - 1], dout = c->gdim[L];
+      std::vector<GenNz> nz;
+      double wmax = 0.0;
+      for (double x : W) wmax = std::max(wmax, fabs(x));
+      for (int aa = 0; aa < din; ++aa)
+        for (int b = 0; b < S; ++b)
+          for (int cc = 0; cc < dout; ++cc) {
+            const double v = W[((size_t)aa * S + b) * dout + cc];
+            if (fabs(v) > 1e-12 * wmax) nz.push_back({(unsigned char)aa, (unsigned char)b, (unsigned char)cc, 0, (float)v});
+          }
+      c->nnz[L] = (int)nz.size();
+      CUDA_TRY(c, cudaMalloc(&c->d_nz[L], std::max<size_t>(nz.size(), 1) * sizeof(GenNz)));
+      c->weight_allocs.push_back(c->d_nz[L]);
+      if (!nz.empty())
+        CUDA_TRY(c, cudaMemcpy(c->d_nz[L], nz.data(), nz.size() * sizeof(GenNz), cudaMemcpyHostToDevice));
+    }
+    return ALLEGRO_OK;
+  }
   int nin, nout;
   if (a.nl == 2) {
     std::vector<double> W;
@@ -545,17 +585,22 @@ struct WS {
   // activations (act = float or bf16) and float32 buffers, per chunk edge
   std::vector<void*> Ztb; std::vector<int> ld_Ztb;
   void* H[2]; int ld_H;
-  void* X[2]; int ld_X[2];
+  void* X[kGenMaxLayers]; int ld_X[kGenMaxLayers];
   void* Xlast; int ld_Xlast;
   std::vector<std::vector<void*>> Zlat; std::vector<int> ld_Zlat;
   void* W01; int ld_W01;     // [w0 | w1] (activation type)
   void* w2; int ld_w2;       // (activation type)
-  void* D[2]; int ld_D[2];   // adjoint of the latent MLP input [x | s], activation type
+  void* w3;                  // env weights of layer 3 (three-layer models; pitch ld_w2)
+  void* D[kGenMaxLayers]; int ld_D[kGenMaxLayers];   // adjoint of the latent MLP input [x | s], activation type
   void* wbar01; int ld_wbar01;
   void* wbar2; int ld_wbar2;
+  void* wbar3;               // (pitch ld_wbar2)
   float* xbar; int ld_xbar;
   float* Y; float* Ybar[2]; float* u; float* ubar; float* sig;
   float* G1; float* G2;
+  // generic row path: per atom Gamma^L, Q^L, Gammabar^L (L = 1..nl), Qbar scratch; per edge w^0bar
+  float* gG[kGenMaxLayers + 1]; float* gQ[kGenMaxLayers + 1]; float* gGb[kGenMaxLayers + 1];
+  float* gQb; float* w0bar;
 };
 
 // Lays the workspace out over `base` (or only measures it when base is null).
@@ -595,11 +640,25 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->ld_W01 = pad8(2 * nw);
   w->W01 = take((size_t)Ec * w->ld_W01 * act_bytes);
   w->ld_w2 = pad8(nw);
-  w->w2 = (a.nl == 2) ? take((size_t)Ec * w->ld_w2 * act_bytes) : nullptr;
+  w->w2 = (a.nl >= 2) ? take((size_t)Ec * w->ld_w2 * act_bytes) : nullptr;
+  w->w3 = (a.nl >= 3) ? take((size_t)Ec * w->ld_w2 * act_bytes) : nullptr;
   w->ld_wbar01 = pad8(2 * nw);
   w->wbar01 = take((size_t)Ec * w->ld_wbar01 * act_bytes);
   w->ld_wbar2 = pad8(nw);
-  w->wbar2 = (a.nl == 2) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
+  w->wbar2 = (a.nl >= 2) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
+  w->wbar3 = (a.nl >= 3) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
+  const bool generic = (a.nl > 2 || a.lmax > 2);
+  for (int L = 0; L <= kGenMaxLayers; ++L) w->gG[L] = w->gQ[L] = w->gGb[L] = nullptr;
+  w->gQb = w->w0bar = nullptr;
+  if (generic) {
+    for (int L = 1; L <= a.nl; ++L) {
+      w->gG[L] = (float*)take((size_t)Ac * a.C * S * 4);
+      w->gQ[L] = (float*)take((size_t)Ac * a.C * S * 4);
+      w->gGb[L] = (float*)take((size_t)Ac * a.C * S * 4);
+    }
+    w->gQb = (float*)take((size_t)Ac * a.C * S * 4);
+    w->w0bar = (float*)take((size_t)Ec * nw * 4);
+  }
   w->ld_xbar = pad8(std::max(a.tb.back(), a.lat.back()));
   w->xbar = (float*)take((size_t)Ec * w->ld_xbar * 4);
   w->Y = (float*)take((size_t)Ec * S * 4);
@@ -800,6 +859,7 @@ const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
     if (W == &c->tb[k]) n = "two_body." + std::to_string(k);
   if (W == &c->w01) n = "embed_env1";
   if (W == &c->env2) n = "env2";
+  if (W == &c->env3) n = "env3";
   for (size_t L = 0; L < c->lat.size(); ++L)
     for (size_t k = 0; k < c->lat[L].size(); ++k)
       if (W == &c->lat[L][k]) n = "latent." + std::to_string(L + 1) + "." + std::to_string(k);
@@ -1179,6 +1239,180 @@ allegro_status run_chunk(allegro_ctx* c, const WS& w, int a0, int a1, int e0, in
   return ALLEGRO_OK;
 }
 
+// One chunk through the generic row path (three layers, or l_max 3): the
+// environment sums and products of row_generic.cu, the MLPs as single GEMMs
+// with the heads and the edge energy as elementwise kernels (BF16: the heads'
+// K-concatenated GEMMs write a float32 xbar), any number of layers.
+template <typename T>
+allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0, int e1, bool backward) {
+  const Arch& a = c->arch;
+  cudaStream_t st = c->stream;
+  const int Ec = e1 - e0, Ac = a1 - a0;
+  if (Ec <= 0) return ALLEGRO_OK;
+  const int ntb = (int)a.tb.size(), nlat = (int)a.lat.size(), nl = a.nl, nw = a.n_w(), S = a.S();
+  const bool bf16 = (c->prec == ALLEGRO_PREC_BF16);
+  allegro_status s;
+  const double act = sizeof(T);
+  auto mk = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
+                void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const void* add = nullptr,
+                int ld_add = 0) {
+    GemmArgs g;
+    g.M = Ec; g.N = N; g.K = K; g.A = A; g.lda = lda; g.W = &W; g.trans = trans; g.epi = epi;
+    g.out = out; g.ldo = ldo; g.pre = pre; g.ldp = ldp; g.rowscale = rowscale; g.add = add; g.ld_add = ld_add;
+    g.v = c->d_v; g.rowsig = w.sig; g.epq = c->tune.epq_wide;
+    return g;
+  };
+  auto run1 = [&](const GemmArgs& g) {
+    const double outb = (g.epi == EPI_F32) ? 4.0 : act;
+    ProfScope ps(c, gemm_label(c, g.W, g.trans, g.epi), 2.0 * Ec * (double)g.N * g.K,
+                 (double)Ec * (g.K * act + g.N * outb + (g.pre ? g.N * act : 0.0)) + (double)g.N * g.K * act);
+    return gemm<T>(c, g);
+  };
+  // forward MLP layers [k0, nlay): SiLU, pre-activations kept, the last layer times u into last_out
+  auto fwd_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
+                     int k0, int nlay, const void* src, int ld_src, int Kin, void* last_out,
+                     int ld_last) -> allegro_status {
+    for (int k = k0; k < nlay; ++k) {
+      const bool last = (k == nlay - 1);
+      void* out = last ? last_out : w.H[(k - k0) & 1];
+      const int ldo = last ? ld_last : w.ld_H;
+      allegro_status r = run1(mk(src, ld_src, Kin, layers[k], false, EPI_FWD_SILU, out, ldo, layers[k].N, Z[k],
+                                 ldZ[k], last ? w.u : nullptr));
+      if (r != ALLEGRO_OK) return r;
+      src = out; ld_src = ldo; Kin = layers[k].N;
+    }
+    return ALLEGRO_OK;
+  };
+  // adjoint of an MLP from zbar of its last layer (in H[0]) to its input's adjoint, columns [col0, Kin)
+  auto back_mlp = [&](const std::vector<Lin>& layers, const std::vector<void*>& Z, const std::vector<int>& ldZ,
+                      void* dst, int ld_dst, int Kin, int col0, const void** zin) -> allegro_status {
+    int cur = 0;
+    for (int k = (int)layers.size() - 1; k >= 0; --k) {
+      const Lin& W = layers[k];
+      allegro_status r;
+      if (k >= 1) {
+        r = run1(mk(w.H[cur], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur ^ 1], w.ld_H, W.K, Z[k - 1], ldZ[k - 1]));
+        cur ^= 1;
+      } else {
+        void* dstc = col0 ? (void*)((char*)dst + (size_t)col0 * sizeof(T)) : dst;
+        GemmArgs g = mk(w.H[cur], w.ld_H, W.N, W, true, EPI_LINEAR, dstc, ld_dst, Kin - col0);
+        g.b_row0 = col0;
+        if (zin) *zin = w.H[cur];
+        r = run1(g);
+      }
+      if (r != ALLEGRO_OK) return r;
+    }
+    return ALLEGRO_OK;
+  };
+  const Lin* env[kGenMaxLayers + 1] = {nullptr, &c->w01, &c->env2, &c->env3};
+  void* wL[kGenMaxLayers + 1] = {w.W01, w.W01, w.w2, w.w3};
+  void* wbL[kGenMaxLayers + 1] = {w.wbar01, w.wbar01, w.wbar2, w.wbar3};
+  GenRowIO gio;
+  gio.a0 = a0; gio.na = Ac; gio.e0 = e0; gio.C = a.C; gio.S = S; gio.lmax = a.lmax; gio.nl = nl;
+  gio.row_ptr = c->d_row_ptr; gio.Y = w.Y; gio.nu = c->tp.nu; gio.Qb = w.gQb; gio.w0bar = w.w0bar;
+  gio.Ybar = w.Ybar[0];
+  for (int L = 0; L <= nl; ++L) {
+    gio.w[L] = wL[L];
+    gio.ldw[L] = (L <= 1) ? w.ld_W01 : w.ld_w2;
+    gio.wcol[L] = (L == 1) ? nw : 0;
+    gio.wbar[L] = wbL[L];
+    gio.ldwbar[L] = (L <= 1) ? w.ld_wbar01 : w.ld_wbar2;
+    gio.wbcol[L] = (L == 1) ? nw : 0;
+    gio.dim[L] = c->gdim[L];
+    if (L >= 1) {
+      gio.xs[L] = w.X[L - 1]; gio.ldxs[L] = w.ld_X[L - 1]; gio.xs_off[L] = a.Klat(L - 1);
+      gio.sbar[L] = w.D[L - 1]; gio.ldsbar[L] = w.ld_D[L - 1]; gio.sbar_off[L] = a.Klat(L - 1);
+      gio.G[L] = w.gG[L]; gio.Q[L] = w.gQ[L]; gio.Gb[L] = w.gGb[L];
+      gio.nz[L] = c->d_nz[L]; gio.nnz[L] = c->nnz[L];
+    }
+  }
+  // ---- forward ----
+  const bool tb_single = (ntb == 1);
+  {
+    ProfScope ps(c, "geom_fwd", 2.0 * Ec * a.tb[0] * (a.nb + 2),
+                 (double)Ec * (24 + 8 + 8 + S * 4 + 4 + 4 + 2.0 * a.tb[0] * act));
+    edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, c->d_sigma, w.sig,
+                     c->tb[0].f32T, c->tb[0].ldT, (T*)w.Ztb[0], w.ld_Ztb[0],
+                     (T*)(tb_single ? w.X[0] : w.H[1]), tb_single ? w.ld_X[0] : w.ld_H, tb_single, st);
+  }
+  if (ntb > 1 && (s = fwd_mlp(c->tb, w.Ztb, w.ld_Ztb, 1, ntb, w.H[1], w.ld_H, a.tb[0], w.X[0], w.ld_X[0])) != ALLEGRO_OK)
+    return s;
+  if ((s = run1(mk(w.X[0], w.ld_X[0], a.tb.back(), c->w01, false, EPI_LINEAR, w.W01, w.ld_W01, 2 * nw))) != ALLEGRO_OK)
+    return s;
+  for (int L = 1; L <= nl; ++L) {
+    if (L >= 2 &&
+        (s = run1(mk(w.X[L - 1], w.ld_X[L - 1], a.lat.back(), *env[L], false, EPI_LINEAR, wL[L], w.ld_w2, nw))) !=
+            ALLEGRO_OK)
+      return s;
+    {
+      ProfScope ps(c, "row_gen_fwd", 0.0, (double)Ec * (2.0 * nw * act + S * 4 + a.C * act) + (double)Ac * a.C * S * 8.0, 3);
+      gen_row_fwd<T>(gio, L, st);
+    }
+    void* dst = (L < nl) ? w.X[L] : w.Xlast;
+    const int ld_dst = (L < nl) ? w.ld_X[L] : w.ld_Xlast;
+    if ((s = fwd_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, 0, nlat, w.X[L - 1], w.ld_X[L - 1],
+                     a.Klat(L - 1) + a.C, dst, ld_dst)) != ALLEGRO_OK)
+      return s;
+  }
+  {
+    ProfScope ps(c, "edge_energy", 0.0, (double)Ec * (a.lat.back() * act + 4));
+    edge_energy<T>(Ec, a.lat.back(), (const T*)w.Xlast, w.ld_Xlast, c->d_v, c->d_Ee + e0, st);
+  }
+  if (!backward) return ALLEGRO_OK;
+  // ---- adjoint ----
+  {
+    ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * 2 * act + 16));
+    mlp_head_bwd<T>(Ec, a.lat.back(), nullptr, 0, c->d_v, c->d_ei, c->d_species, c->d_sigma, e0,
+                    (const T*)w.Zlat[nl - 1][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, true, (T*)w.H[0], w.ld_H,
+                    st);
+  }
+  for (int L = nl; L >= 1; --L) {
+    const bool kc = bf16 && c->headB[L - 1] != nullptr;
+    if (bf16 && !kc) return fail(c, ALLEGRO_E_INVALID, "BF16 generic path needs 64-aligned env-weight widths");
+    const void* zlat = nullptr;
+    if ((s = back_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, w.D[L - 1], w.ld_D[L - 1], a.Klat(L - 1) + a.C,
+                      kc ? a.Klat(L - 1) : 0, &zlat)) != ALLEGRO_OK)
+      return s;
+    {
+      ProfScope ps(c, "row_gen_bwd", 0.0, (double)Ec * (4.0 * nw * act + 2 * S * 4 + a.C * act) + (double)Ac * a.C * S * 16.0, 3);
+      gen_row_bwd<T>(gio, L, st);
+    }
+    // xbar of x^{L-1} = wbar^L . W_env^L (layer 1: [wbar^0 | wbar^1] . [W_emb ; W_env^1]) + its latent-input adjoint
+    const int K1 = (L == 1) ? 2 * nw : nw;
+    GemmArgs hd;
+    if (kc) {
+      hd = mk(wbL[L], (L == 1) ? w.ld_wbar01 : w.ld_wbar2, c->headK[L - 1], *env[L], true, EPI_F32, w.xbar,
+              w.ld_xbar, a.Klat(L - 1));
+      hd.A2 = zlat; hd.lda2 = w.ld_H; hd.K1 = c->headK1[L - 1];
+      hd.Bover = c->headB[L - 1]; hd.ldb_over = c->headLd[L - 1];
+    } else {
+      hd = mk(wbL[L], (L == 1) ? w.ld_wbar01 : w.ld_wbar2, K1, *env[L], true, EPI_F32, w.xbar, w.ld_xbar,
+              a.Klat(L - 1), nullptr, 0, nullptr, w.D[L - 1], w.ld_D[L - 1]);
+    }
+    if ((s = run1(hd)) != ALLEGRO_OK) return s;
+    const void* pre = (L == 1) ? w.Ztb[ntb - 1] : w.Zlat[L - 2][nlat - 1];
+    const int ldp = (L == 1) ? w.ld_Ztb[ntb - 1] : w.ld_Zlat[nlat - 1];
+    ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.Klat(L - 1) * (4 + 2 * act) + 12));
+    mlp_head_bwd<T>(Ec, a.Klat(L - 1), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
+                    (const T*)pre, ldp, w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);
+  }
+  int cur0 = 0;
+  for (int k = ntb - 1; k >= 1; --k) {
+    const Lin& W = c->tb[k];
+    if ((s = run1(mk(w.H[cur0], w.ld_H, W.N, W, true, EPI_BWD_SILU, w.H[cur0 ^ 1], w.ld_H, W.K, w.Ztb[k - 1],
+                     w.ld_Ztb[k - 1]))) != ALLEGRO_OK)
+      return s;
+    cur0 ^= 1;
+  }
+  {
+    ProfScope ps(c, "geom_bwd", 2.0 * Ec * a.tb[0] * a.nb, (double)Ec * (24 + a.tb[0] * act + 4 + S * 4 + 12));
+    YbarParts yb{{w.Ybar[0], nullptr}};
+    edge_geom_bwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, (const T*)w.H[cur0], w.ld_H,
+                     c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb, c->d_g, st);
+  }
+  return ALLEGRO_OK;
+}
+
 // Chunks of whole rows (each centre's environment sum complete inside one
 // chunk), at most `budget` edges each (0: the largest the memory allows).
 struct Plan {
@@ -1229,8 +1463,12 @@ allegro_status run_plan(allegro_ctx* c, const Plan& p, const WS& w, bool backwar
   for (size_t q = 0; q + 1 < p.bounds.size(); ++q) {
     int a0 = p.bounds[q], a1 = p.bounds[q + 1];
     int e0 = c->h_row_ptr[a0], e1 = c->h_row_ptr[a1];
-    s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk<bf16>(c, w, a0, a1, e0, e1, backward)
-                                       : run_chunk<float>(c, w, a0, a1, e0, e1, backward);
+    if (c->generic)
+      s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk_gen<bf16>(c, w, a0, a1, e0, e1, backward)
+                                         : run_chunk_gen<float>(c, w, a0, a1, e0, e1, backward);
+    else
+      s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk<bf16>(c, w, a0, a1, e0, e1, backward)
+                                         : run_chunk<float>(c, w, a0, a1, e0, e1, backward);
     if (s != ALLEGRO_OK) return s;
     CUDA_TRY(c, cudaGetLastError());
   }

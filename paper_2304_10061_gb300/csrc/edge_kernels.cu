@@ -11,6 +11,9 @@
 //   l=0: 1
 //   l=1: sqrt3 y, sqrt3 z, sqrt3 x
 //   l=2: sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2 - 1), sqrt15 xz, sqrt15/2 (x^2 - y^2)
+//   l=3: c3 y (3x^2 - y^2), 2 c2 xyz, c1 (15z^2 - 3) y, c0 z (5z^2 - 3), c1 (15z^2 - 3) x,
+//        c2 z (x^2 - y^2), c3 x (x^2 - 3y^2);  c0 = sqrt7/2, c1 = sqrt(7/6)/2,
+//        c2 = 15 sqrt(7/60), c3 = 15 sqrt(7/360)
 // Two-body input row: [onehot(Z_i) | onehot(Z_j) | B(r)].
 #include <cuda_runtime.h>
 
@@ -68,6 +71,21 @@ __device__ __forceinline__ void sh_eval(int lmax, float x, float y, float z, flo
     Y[4] = s15 * x * y; Y[5] = s15 * y * z; Y[6] = s5h * (3.0f * z * z - 1.0f);
     Y[7] = s15 * x * z; Y[8] = 0.5f * s15 * (x * x - y * y);
   }
+  if (lmax >= 3) {
+    // N_l|m| d^|m|P_3/dz^|m| A_m with the normalisation sqrt(7 (2 - d_m0) (3-|m|)! / (3+|m|)!)
+    const float c0 = 1.3228756555322954f;   // sqrt(7) / 2
+    const float c1 = 0.5400617248673217f;   // sqrt(7/6) / 2
+    const float c2 = 5.1234753829797990f;   // 15 sqrt(7/60)
+    const float c3 = 2.0916500663351889f;   // 15 sqrt(7/360)
+    const float f = 15.0f * z * z - 3.0f;
+    Y[9] = c3 * y * (3.0f * x * x - y * y);
+    Y[10] = 2.0f * c2 * x * y * z;
+    Y[11] = c1 * f * y;
+    Y[12] = c0 * z * (5.0f * z * z - 3.0f);
+    Y[13] = c1 * f * x;
+    Y[14] = c2 * z * (x * x - y * y);
+    Y[15] = c3 * x * (x * x - 3.0f * y * y);
+  }
 }
 
 // sum_a Ybar_a grad Y_a (gradient of the polynomial forms above w.r.t. (x, y, z))
@@ -79,6 +97,17 @@ __device__ __forceinline__ void sh_vjp(int lmax, float x, float y, float z, cons
     G[0] += s15 * (Yb[4] * y + Yb[7] * z + Yb[8] * x);
     G[1] += s15 * (Yb[4] * x + Yb[5] * z - Yb[8] * y);
     G[2] += s15 * (Yb[5] * y + Yb[7] * x) + 3.0f * s5 * Yb[6] * z;
+  }
+  if (lmax >= 3) {
+    const float c0 = 1.3228756555322954f, c1 = 0.5400617248673217f, c2 = 5.1234753829797990f,
+                c3 = 2.0916500663351889f;
+    const float f = 15.0f * z * z - 3.0f;
+    G[0] += c3 * Yb[9] * 6.0f * x * y + 2.0f * c2 * Yb[10] * y * z + c1 * Yb[13] * f +
+            c2 * Yb[14] * 2.0f * x * z + c3 * Yb[15] * 3.0f * (x * x - y * y);
+    G[1] += c3 * Yb[9] * 3.0f * (x * x - y * y) + 2.0f * c2 * Yb[10] * x * z + c1 * Yb[11] * f -
+            c2 * Yb[14] * 2.0f * y * z - c3 * Yb[15] * 6.0f * x * y;
+    G[2] += 2.0f * c2 * Yb[10] * x * y + c1 * Yb[11] * 30.0f * z * y + c0 * Yb[12] * f +
+            c1 * Yb[13] * 30.0f * z * x + c2 * Yb[14] * (x * x - y * y);
   }
 }
 
@@ -343,7 +372,8 @@ __global__ void __launch_bounds__(kGeomBlock)
   }
   // Ybar arrives in two partial arrays (from two row-kernel passes), summed in a fixed order
   float Yb[kMaxS];
-  for (int a = 0; a < bc.S; ++a) Yb[a] = yb.p[0][(size_t)e * bc.S + a] + yb.p[1][(size_t)e * bc.S + a];
+  for (int a = 0; a < bc.S; ++a)
+    Yb[a] = yb.p[0][(size_t)e * bc.S + a] + (yb.p[1] ? yb.p[1][(size_t)e * bc.S + a] : 0.0f);
   float G[3];
   sh_vjp(bc.lmax, x, y, z, Yb, G);
   const float rg = x * G[0] + y * G[1] + z * G[2];

@@ -17,7 +17,7 @@ namespace alg {
 typedef __nv_bfloat16 bf16;
 
 // Largest sizes the kernels are instantiated for.
-constexpr int kMaxLmax = 2;
+constexpr int kMaxLmax = 3;
 constexpr int kMaxS = (kMaxLmax + 1) * (kMaxLmax + 1);   // spherical-harmonic components
 constexpr int kMaxChannels = 128;
 constexpr int kMaxWidth = 1024;
@@ -76,7 +76,7 @@ struct TPConst {
 // two real harmonics carries only those |m|), and the sine/cosine type of m_c
 // (m < 0: sine) is the product of the types of m_a and m_b (sin sin and cos cos
 // give cos, sin cos gives sin).  The host checks every loaded tensor against it.
-__host__ __device__ constexpr int sh_l(int a) { return a < 1 ? 0 : (a < 4 ? 1 : 2); }
+__host__ __device__ constexpr int sh_l(int a) { return a < 1 ? 0 : (a < 4 ? 1 : (a < 9 ? 2 : 3)); }
 __host__ __device__ constexpr int sh_m(int a) { return a - sh_l(a) * sh_l(a) - sh_l(a); }
 __host__ __device__ constexpr int iabs_c(int x) { return x < 0 ? -x : x; }
 __host__ __device__ constexpr bool tp_nonzero(int a, int b, int c) {
@@ -248,6 +248,48 @@ struct RowIO {
   //   two layers: row_bwd_last -> Ybar[0], row_bwd_mid (second pass) -> Ybar[1]
   float* Ybar[2] = {nullptr, nullptr};
 };
+// ---- any number of layers (row_generic.cu) ----
+constexpr int kGenMaxLayers = 3;
+constexpr int kGenMaxD = 32;       // components of the largest feature (l_max 3, both parities: 31)
+struct GenNz {                     // a nonzero W[a][b][c] of a fused layer tensor
+  unsigned char a, b, c, pad;
+  float v;
+};
+struct GenRowIO {
+  int a0 = 0, na = 0, e0 = 0, C = 0, S = 0, lmax = 0, nl = 0;
+  const int* row_ptr = nullptr;
+  const float* Y = nullptr;                       // [Ec][S]
+  float nu = 1.0f;
+  // index L = 0 (embedding w^0) .. nl (env weights w^L): activation-type arrays, columns
+  // [col, col + C (l_max+1)) of rows `ld` apart
+  const void* w[kGenMaxLayers + 1] = {};
+  int ldw[kGenMaxLayers + 1] = {}, wcol[kGenMaxLayers + 1] = {};
+  void* wbar[kGenMaxLayers + 1] = {};
+  int ldwbar[kGenMaxLayers + 1] = {}, wbcol[kGenMaxLayers + 1] = {};
+  // L = 1..nl: s^L output (latent input's s columns) and its adjoint sbar^L
+  void* xs[kGenMaxLayers + 1] = {};
+  int ldxs[kGenMaxLayers + 1] = {}, xs_off[kGenMaxLayers + 1] = {};
+  const void* sbar[kGenMaxLayers + 1] = {};
+  int ldsbar[kGenMaxLayers + 1] = {}, sbar_off[kGenMaxLayers + 1] = {};
+  // L = 1..nl, per atom [na][C][S]: Gamma^L (nu applied), Q^L, Gammabar^L
+  float* G[kGenMaxLayers + 1] = {};
+  float* Q[kGenMaxLayers + 1] = {};
+  float* Gb[kGenMaxLayers + 1] = {};
+  float* Qb = nullptr;                            // [na][C][S] scratch
+  float* w0bar = nullptr;                         // [Ec][C][l_max+1] float32 accumulator
+  float* Ybar = nullptr;                          // [Ec][S]
+  // layer tensors W^k, k = 1..nl: nonzeros over dim[k-1] x S x dim[k]
+  const GenNz* nz[kGenMaxLayers + 1] = {};
+  int nnz[kGenMaxLayers + 1] = {};
+  int dim[kGenMaxLayers + 1] = {};                // dim[0] = S, dim[nl] = 1
+};
+// forward of layer L: Gamma^L, Q^L, s^L
+template <typename T>
+void gen_row_fwd(const GenRowIO& io, int L, cudaStream_t st);
+// adjoint of layer L (call for L = nl down to 1): Qbar^L, Gammabar^k (k <= L), wbar^L, w^0bar, Ybar
+template <typename T>
+void gen_row_bwd(const GenRowIO& io, int L, cudaStream_t st);
+
 template <typename T>
 void row_fwd(int layer, int nl, int lmax, const RowIO& io, const TPConst& tp, cudaStream_t st);
 template <typename T>

@@ -494,6 +494,65 @@ def _paper_model(args, local, stream, n_atoms: int = 262144):
     return res
 
 
+def _c5_run(args, local, stream, steps: int = 1):
+    """The 4,194,304-atom configuration (3 layers, l_max 3, 128 channels, latent 2 x 512) in BF16:
+    E + F + virial with a neighbour rebuild per step, the device memory the library holds, and
+    the force error of the same architecture against the FP64 oracle on a 256-atom box."""
+    import torch
+    from paper_2304_10061_gb300 import Allegro
+    from synth import lattice_box, make_config, weights_to_blob
+    s, arch, w = make_config("c5")
+    blob = weights_to_blob(arch, w)
+    dev = f"cuda:{local}"
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(local)
+    px = torch.tensor(s.pos, device=dev)
+    tx = torch.tensor(s.species, dtype=torch.int32, device=dev)
+    cx = torch.tensor(s.cell, device=dev)
+    out = dict(E=torch.empty(1, dtype=torch.float64, device=dev),
+               E_atom=torch.empty(s.n_atoms, dtype=torch.float64, device=dev),
+               F=torch.empty(s.n_atoms, 3, dtype=torch.float64, device=dev),
+               virial=torch.empty(1, 3, 3, dtype=torch.float64, device=dev))
+    m = Allegro(blob, precision="bf16", device=local)
+    m.set_stream(stream.cuda_stream)
+    m.neighbors(px, tx, cx)
+    m.energy_forces(out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        m.neighbors(px, tx, cx)
+        m.energy_forces(out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    free1, _ = torch.cuda.mem_get_info(local)
+    res = {"atoms": s.n_atoms, "edges": m.n_edges, "precision": "bf16",
+           "architecture": "3 layers, 128 channels, l_max 3, two-body [64,128,512], latent [512,512], edge [128]",
+           "model_flops_per_edge": model_flops_per_edge(arch), "steps": steps, "ms_per_step": ms,
+           "atom_steps_per_s": s.n_atoms / (ms * 1e-3),
+           "model_tflops_per_s": model_flops_per_edge(arch) * m.n_edges / (ms * 1e-3) / 1e12,
+           "device_gb_in_use": (free0 - free1) / 1e9, "device_gb_total": total / 1e9,
+           "memory_note": "device memory in use after the step minus before the inputs were placed (inputs, outputs "
+                          "and the library's buffers, which only grow, so this is the step's peak); edge activations "
+                          "live for one chunk of centre rows at a time",
+           "e_total": float(out["E"].item())}
+    m.close()
+    if not args.skip_cpu:
+        from oracle.allegro import AllegroOracle
+        small = lattice_box(256, (256 / 0.1) ** (1.0 / 3.0), seed=11)
+        i, j, S = _edges(arch, small)
+        ref = AllegroOracle(arch, w).energy_forces(small.pos, small.species, small.cell, i, j, S)
+        for prec in ("bf16", "fp32"):
+            mm = Allegro(blob, precision=prec, device=local)
+            mm.neighbors(small.pos, small.species, small.cell)
+            o = mm.energy_forces()
+            res[f"force_err_vs_fp64_256_atoms_{prec}"] = _force_errors(o["F"].cpu().numpy(), o["E"].item(), ref[2],
+                                                                       ref[0])
+            mm.close()
+    return res
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores: each step one bounded sample of the workload."""
     rank, ws, _, dist = _dist()
@@ -734,6 +793,8 @@ def run_ours(args):
         extra["table_iv_3072_atoms"] = _precision_matrix(args, local, stream)
         # the paper's production architecture (1024-wide MLPs, per-pair cutoffs, ZBL)
         extra["paper_model_262144_atoms"] = _paper_model(args, local, stream)
+        # the largest configuration: 3 layers, l_max 3, 128 channels on 4,194,304 atoms
+        extra["c5_4194304_atoms"] = _c5_run(args, local, stream)
         # the headline box under the paper's per-ordered-species-pair cutoffs
         if arch.pair_rc is None:
             extra["pair_cutoffs_1M_atoms" if args.config == "c4" and not args.atoms else "pair_cutoffs"] = \

@@ -124,6 +124,11 @@ struct allegro_ctx {
   bool generic = false;
   GenNz* d_nz[kGenMaxLayers + 1] = {};
   int nnz[kGenMaxLayers + 1] = {};
+  GenNz* d_nz0[kGenMaxLayers + 1] = {};     // entries with c == 0
+  int nnz0[kGenMaxLayers + 1] = {};
+  GenNz* d_nzb[kGenMaxLayers + 1] = {};     // all entries sorted by b
+  GenNz* d_nzc[kGenMaxLayers + 1] = {};     // all entries sorted by c
+  GenNz* d_nz0b[kGenMaxLayers + 1] = {};    // entries with c == 0 sorted by b
   int gdim[kGenMaxLayers + 1] = {};
   std::vector<std::vector<Lin>> lat;       // latent MLP of layers 1..nl
   // BF16 path: the adjoint of x^{L-1} in one GEMM over [wbar^L | zbar^L] (K-concatenated):
@@ -541,11 +546,27 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
             const double v = W[((size_t)aa * S + b) * dout + cc];
             if (fabs(v) > 1e-12 * wmax) nz.push_back({(unsigned char)aa, (unsigned char)b, (unsigned char)cc, 0, (float)v});
           }
+      std::vector<GenNz> nz0;
+      for (const GenNz& z : nz)
+        if (z.c == 0) nz0.push_back(z);
+      std::vector<GenNz> nzb(nz), nzc(nz), nz0b(nz0);
+      std::stable_sort(nz0b.begin(), nz0b.end(), [](const GenNz& x, const GenNz& y) { return x.b < y.b; });
+      std::stable_sort(nzb.begin(), nzb.end(), [](const GenNz& x, const GenNz& y) {
+        return x.b != y.b ? x.b < y.b : x.c < y.c;
+      });
+      std::stable_sort(nzc.begin(), nzc.end(), [](const GenNz& x, const GenNz& y) {
+        return x.c != y.c ? x.c < y.c : x.b < y.b;
+      });
       c->nnz[L] = (int)nz.size();
-      CUDA_TRY(c, cudaMalloc(&c->d_nz[L], std::max<size_t>(nz.size(), 1) * sizeof(GenNz)));
-      c->weight_allocs.push_back(c->d_nz[L]);
-      if (!nz.empty())
-        CUDA_TRY(c, cudaMemcpy(c->d_nz[L], nz.data(), nz.size() * sizeof(GenNz), cudaMemcpyHostToDevice));
+      c->nnz0[L] = (int)nz0.size();
+      const std::vector<GenNz>* lists[5] = {&nz, &nz0, &nzb, &nzc, &nz0b};
+      GenNz** dst[5] = {&c->d_nz[L], &c->d_nz0[L], &c->d_nzb[L], &c->d_nzc[L], &c->d_nz0b[L]};
+      for (int q = 0; q < 5; ++q) {
+        CUDA_TRY(c, cudaMalloc(dst[q], std::max<size_t>(lists[q]->size(), 1) * sizeof(GenNz)));
+        c->weight_allocs.push_back(*dst[q]);
+        if (!lists[q]->empty())
+          CUDA_TRY(c, cudaMemcpy(*dst[q], lists[q]->data(), lists[q]->size() * sizeof(GenNz), cudaMemcpyHostToDevice));
+      }
     }
     return ALLEGRO_OK;
   }
@@ -1319,11 +1340,14 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     gio.ldwbar[L] = (L <= 1) ? w.ld_wbar01 : w.ld_wbar2;
     gio.wbcol[L] = (L == 1) ? nw : 0;
     gio.dim[L] = c->gdim[L];
+    gio.dmax = std::max(gio.dmax, c->gdim[L]);
     if (L >= 1) {
       gio.xs[L] = w.X[L - 1]; gio.ldxs[L] = w.ld_X[L - 1]; gio.xs_off[L] = a.Klat(L - 1);
       gio.sbar[L] = w.D[L - 1]; gio.ldsbar[L] = w.ld_D[L - 1]; gio.sbar_off[L] = a.Klat(L - 1);
       gio.G[L] = w.gG[L]; gio.Q[L] = w.gQ[L]; gio.Gb[L] = w.gGb[L];
       gio.nz[L] = c->d_nz[L]; gio.nnz[L] = c->nnz[L];
+      gio.nz0[L] = c->d_nz0[L]; gio.nnz0[L] = c->nnz0[L];
+      gio.nzb[L] = c->d_nzb[L]; gio.nzc[L] = c->d_nzc[L]; gio.nz0b[L] = c->d_nz0b[L];
     }
   }
   // ---- forward ----

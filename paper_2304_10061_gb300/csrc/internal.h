@@ -278,10 +278,16 @@ struct GenRowIO {
   float* Qb = nullptr;                            // [na][C][S] scratch
   float* w0bar = nullptr;                         // [Ec][C][l_max+1] float32 accumulator
   float* Ybar = nullptr;                          // [Ec][S]
-  // layer tensors W^k, k = 1..nl: nonzeros over dim[k-1] x S x dim[k]
+  // layer tensors W^k, k = 1..nl: nonzeros over dim[k-1] x S x dim[k], sorted by a, then b, then c
   const GenNz* nz[kGenMaxLayers + 1] = {};
   int nnz[kGenMaxLayers + 1] = {};
+  const GenNz* nz0[kGenMaxLayers + 1] = {};      // the entries with c == 0 (a chain's first step on e_0)
+  int nnz0[kGenMaxLayers + 1] = {};
+  const GenNz* nzb[kGenMaxLayers + 1] = {};      // the nonzeros sorted by b, then by c (nnz entries)
+  const GenNz* nzc[kGenMaxLayers + 1] = {};      // the nonzeros sorted by c, then by b
+  const GenNz* nz0b[kGenMaxLayers + 1] = {};     // the c == 0 entries sorted by b (nnz0 entries)
   int dim[kGenMaxLayers + 1] = {};                // dim[0] = S, dim[nl] = 1
+  int dmax = 0;                                   // the largest dim[k]
 };
 // forward of layer L: Gamma^L, Q^L, s^L
 template <typename T>

@@ -120,15 +120,9 @@ struct allegro_ctx {
   Lin env2;                                // env weights of layer 2 (two- and three-layer models)
   Lin env3;                                // env weights of layer 3 (three-layer models)
   // models the specialised row kernels do not take (three layers, or l_max 3): the
-  // generic row path with the layer tensors as nonzero lists on the device
+  // generic row path: the layer tensors' values in the kernels' order
   bool generic = false;
-  GenNz* d_nz[kGenMaxLayers + 1] = {};
-  int nnz[kGenMaxLayers + 1] = {};
-  GenNz* d_nz0[kGenMaxLayers + 1] = {};     // entries with c == 0
-  int nnz0[kGenMaxLayers + 1] = {};
-  GenNz* d_nzb[kGenMaxLayers + 1] = {};     // all entries sorted by b
-  GenNz* d_nzc[kGenMaxLayers + 1] = {};     // all entries sorted by c
-  GenNz* d_nz0b[kGenMaxLayers + 1] = {};    // entries with c == 0 sorted by b
+  std::vector<float> gen_vals;
   int gdim[kGenMaxLayers + 1] = {};
   std::vector<std::vector<Lin>> lat;       // latent MLP of layers 1..nl
   // BF16 path: the adjoint of x^{L-1} in one GEMM over [wbar^L | zbar^L] (K-concatenated):
@@ -526,48 +520,18 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   c->tp.nu = (float)(1.0 / sqrt(a.ann));
   if (c->generic) {
     // the fused tensor of every layer between its irreps (pseudo-parity features in the
-    // middle layers), as a list of nonzeros for the generic row kernels
+    // middle layers), packed in the generic row kernels' order
     std::vector<std::vector<Irrep>> irs;
     layer_irreps(a.lmax, a.nl, irs);
     for (int L = 0; L <= a.nl; ++L) {
       c->gdim[L] = irreps_dim(irs[L]);
       if (c->gdim[L] > kGenMaxD) return fail(c, ALLEGRO_E_INVALID, "internal: layer %d has %d components", L, c->gdim[L]);
     }
-    for (int L = 1; L <= a.nl; ++L) {
-      std::vector<double> W;
-      layer_tensor(a.lmax, irs[L - 1], irs[L], theta[L - 1].data(), W);
-      const int din = c->gdim[L - 1], dout = c->gdim[L];
-      std::vector<GenNz> nz;
-      double wmax = 0.0;
-      for (double x : W) wmax = std::max(wmax, fabs(x));
-      for (int aa = 0; aa < din; ++aa)
-        for (int b = 0; b < S; ++b)
-          for (int cc = 0; cc < dout; ++cc) {
-            const double v = W[((size_t)aa * S + b) * dout + cc];
-            if (fabs(v) > 1e-12 * wmax) nz.push_back({(unsigned char)aa, (unsigned char)b, (unsigned char)cc, 0, (float)v});
-          }
-      std::vector<GenNz> nz0;
-      for (const GenNz& z : nz)
-        if (z.c == 0) nz0.push_back(z);
-      std::vector<GenNz> nzb(nz), nzc(nz), nz0b(nz0);
-      std::stable_sort(nz0b.begin(), nz0b.end(), [](const GenNz& x, const GenNz& y) { return x.b < y.b; });
-      std::stable_sort(nzb.begin(), nzb.end(), [](const GenNz& x, const GenNz& y) {
-        return x.b != y.b ? x.b < y.b : x.c < y.c;
-      });
-      std::stable_sort(nzc.begin(), nzc.end(), [](const GenNz& x, const GenNz& y) {
-        return x.c != y.c ? x.c < y.c : x.b < y.b;
-      });
-      c->nnz[L] = (int)nz.size();
-      c->nnz0[L] = (int)nz0.size();
-      const std::vector<GenNz>* lists[5] = {&nz, &nz0, &nzb, &nzc, &nz0b};
-      GenNz** dst[5] = {&c->d_nz[L], &c->d_nz0[L], &c->d_nzb[L], &c->d_nzc[L], &c->d_nz0b[L]};
-      for (int q = 0; q < 5; ++q) {
-        CUDA_TRY(c, cudaMalloc(dst[q], std::max<size_t>(lists[q]->size(), 1) * sizeof(GenNz)));
-        c->weight_allocs.push_back(*dst[q]);
-        if (!lists[q]->empty())
-          CUDA_TRY(c, cudaMemcpy(*dst[q], lists[q]->data(), lists[q]->size() * sizeof(GenNz), cudaMemcpyHostToDevice));
-      }
-    }
+    std::vector<std::vector<double>> Ws(a.nl + 1);
+    for (int L = 1; L <= a.nl; ++L) layer_tensor(a.lmax, irs[L - 1], irs[L], theta[L - 1].data(), Ws[L]);
+    std::string why;
+    if (!gen_pack_values(a.lmax, a.nl, irs, Ws, c->gen_vals, why))
+      return fail(c, ALLEGRO_E_INVALID, "internal: %s", why.c_str());
     return ALLEGRO_OK;
   }
   int nin, nout;
@@ -1332,6 +1296,7 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
   gio.a0 = a0; gio.na = Ac; gio.e0 = e0; gio.C = a.C; gio.S = S; gio.lmax = a.lmax; gio.nl = nl;
   gio.row_ptr = c->d_row_ptr; gio.Y = w.Y; gio.nu = c->tp.nu; gio.Qb = w.gQb; gio.w0bar = w.w0bar;
   gio.Ybar = w.Ybar[0];
+  gio.vals = c->gen_vals.data();
   for (int L = 0; L <= nl; ++L) {
     gio.w[L] = wL[L];
     gio.ldw[L] = (L <= 1) ? w.ld_W01 : w.ld_w2;
@@ -1340,14 +1305,10 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     gio.ldwbar[L] = (L <= 1) ? w.ld_wbar01 : w.ld_wbar2;
     gio.wbcol[L] = (L == 1) ? nw : 0;
     gio.dim[L] = c->gdim[L];
-    gio.dmax = std::max(gio.dmax, c->gdim[L]);
     if (L >= 1) {
       gio.xs[L] = w.X[L - 1]; gio.ldxs[L] = w.ld_X[L - 1]; gio.xs_off[L] = a.Klat(L - 1);
       gio.sbar[L] = w.D[L - 1]; gio.ldsbar[L] = w.ld_D[L - 1]; gio.sbar_off[L] = a.Klat(L - 1);
       gio.G[L] = w.gG[L]; gio.Q[L] = w.gQ[L]; gio.Gb[L] = w.gGb[L];
-      gio.nz[L] = c->d_nz[L]; gio.nnz[L] = c->nnz[L];
-      gio.nz0[L] = c->d_nz0[L]; gio.nnz0[L] = c->nnz0[L];
-      gio.nzb[L] = c->d_nzb[L]; gio.nzc[L] = c->d_nzc[L]; gio.nz0b[L] = c->d_nz0b[L];
     }
   }
   // ---- forward ----

@@ -251,10 +251,6 @@ struct RowIO {
 // ---- any number of layers (row_generic.cu) ----
 constexpr int kGenMaxLayers = 3;
 constexpr int kGenMaxD = 32;       // components of the largest feature (l_max 3, both parities: 31)
-struct GenNz {                     // a nonzero W[a][b][c] of a fused layer tensor
-  unsigned char a, b, c, pad;
-  float v;
-};
 struct GenRowIO {
   int a0 = 0, na = 0, e0 = 0, C = 0, S = 0, lmax = 0, nl = 0;
   const int* row_ptr = nullptr;
@@ -278,17 +274,18 @@ struct GenRowIO {
   float* Qb = nullptr;                            // [na][C][S] scratch
   float* w0bar = nullptr;                         // [Ec][C][l_max+1] float32 accumulator
   float* Ybar = nullptr;                          // [Ec][S]
-  // layer tensors W^k, k = 1..nl: nonzeros over dim[k-1] x S x dim[k], sorted by a, then b, then c
-  const GenNz* nz[kGenMaxLayers + 1] = {};
-  int nnz[kGenMaxLayers + 1] = {};
-  const GenNz* nz0[kGenMaxLayers + 1] = {};      // the entries with c == 0 (a chain's first step on e_0)
-  int nnz0[kGenMaxLayers + 1] = {};
-  const GenNz* nzb[kGenMaxLayers + 1] = {};      // the nonzeros sorted by b, then by c (nnz entries)
-  const GenNz* nzc[kGenMaxLayers + 1] = {};      // the nonzeros sorted by c, then by b
-  const GenNz* nz0b[kGenMaxLayers + 1] = {};     // the c == 0 entries sorted by b (nnz0 entries)
+  // layer tensors W^k, k = 1..nl: their values (host memory) at the candidate nonzeros that
+  // gen_pack_values lists, layers 1..nl concatenated; the kernels take them as launch parameters
+  const float* vals = nullptr;
   int dim[kGenMaxLayers + 1] = {};                // dim[0] = S, dim[nl] = 1
-  int dmax = 0;                                   // the largest dim[k]
 };
+struct Irrep;
+// The values of the layer tensors W[k] (k = 1..nl, dense float64 over dim(irs[k-1]) x S x
+// dim(irs[k])) at the generic kernels' candidate nonzeros, in their order; false (with the
+// reason) when the model is outside the generic kernels' set or a nonzero lies outside the
+// candidates.
+bool gen_pack_values(int lmax, int nl, const std::vector<std::vector<Irrep>>& irs,
+                     const std::vector<std::vector<double>>& W, std::vector<float>& vals, std::string& why);
 // forward of layer L: Gamma^L, Q^L, s^L
 template <typename T>
 void gen_row_fwd(const GenRowIO& io, int L, cudaStream_t st);

@@ -28,12 +28,23 @@
 // sums are register accumulations over the row (deterministic), the channel
 // sums of Ybar are block reductions in a fixed order; l_max is a template
 // parameter, so every per-edge vector lives in registers.  Chain kernels: one
-// thread per (atom, channel); every thread's vectors in shared memory
-// ([component][thread], conflict-free); the nonzero lists (read by all threads
-// alike, so broadcast from L1) sorted by the output index of each sum, the
-// running sum in a register.
+// thread per (atom, channel), unrolled at compile time over the candidate
+// nonzeros of the layer tensors.  Which entries of a fused tensor can be
+// nonzero is fixed by l_max and the layer irreps: the paths allowed by the
+// triangle and parity rules, and within a path's real coupling block the
+// entries with |m3| = |m1| + |m2| or ||m1| - |m2||, whose sine/cosine types
+// multiply to the block's type ((-1)^(l1+l2+l3): real harmonics with m < 0 are
+// the sine type).  So every vector index is a compile-time constant (the
+// vectors live in registers) and the tensor values are launch parameters
+// (constant-bank operands of the multiply-adds); the host checks that every
+// nonzero of the model's tensors is a candidate.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -64,37 +75,186 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return t;
 }
 
-constexpr int kChainThreads = 64;   // (atom, channel) pairs per block of the chain kernels
+constexpr int kChainThreads = 128;   // (atom, channel) pairs per block of the chain kernels
 
-// A thread's vectors in shared memory, [component][thread] (conflict-free):
-// `ng` slots of S components (the environments Gamma^k) first, then slots of
-// D components (the largest feature dimension of the model).
-struct Vecs {
-  float* base;
-  int tid, S, ng, D;
-  __device__ __forceinline__ float& at(int slot, int i) const {
-    const int off = slot < ng ? slot * S : ng * S + (slot - ng) * D;
-    return base[(size_t)(off + i) * kChainThreads + tid];
-  }
+// ---- the layer irreps and candidate nonzeros at compile time ----
+struct IrSet {               // irreps (l, parity), sorted by l, even before odd
+  int n = 0;
+  int l[8] = {};
+  int p[8] = {};
 };
 
-// sum over the entries of a nonzero list sorted by its `key` component, flushed per key
-// run: out(key, sum of term(entry)) once per distinct key, in list order
-template <typename Key, typename Term, typename Out>
-__device__ __forceinline__ void sorted_sum(const GenNz* z, int n, Key&& key, Term&& term, Out&& out) {
-  int run = -1;
-  float acc = 0.0f;
-  for (int q = 0; q < n; ++q) {
-    const GenNz zz = z[q];
-    const int k = key(zz);
-    if (k != run) {
-      if (run >= 0) out(run, acc);
-      run = k;
-      acc = 0.0f;
-    }
-    acc += term(zz);
+__host__ __device__ constexpr int iabs(int x) { return x < 0 ? -x : x; }
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+
+__host__ __device__ constexpr IrSet ir_natural(int lmax) {
+  IrSet s{};
+  for (int l = 0; l <= lmax; ++l) {
+    s.l[s.n] = l;
+    s.p[s.n] = (l & 1) ? -1 : 1;
+    ++s.n;
   }
-  if (run >= 0) out(run, acc);
+  return s;
+}
+
+// the irreps of the products of `in` with the harmonics up to l_max, truncated at l_max
+__host__ __device__ constexpr IrSet ir_products(const IrSet& in, int lmax) {
+  bool has[kMaxLmax + 1][2] = {};
+  for (int k = 0; k < in.n; ++k)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int lo = iabs(in.l[k] - l2); lo <= imin(in.l[k] + l2, lmax); ++lo)
+        has[lo][in.p[k] * ((l2 & 1) ? -1 : 1) == 1 ? 0 : 1] = true;
+  IrSet s{};
+  for (int l = 0; l <= lmax; ++l)
+    for (int q = 0; q < 2; ++q)
+      if (has[l][q]) {
+        s.l[s.n] = l;
+        s.p[s.n] = q ? -1 : 1;
+        ++s.n;
+      }
+  return s;
+}
+
+// can (l, p) reach the scalar 0e in `steps` more products?
+__host__ __device__ constexpr bool ir_reaches_scalar(int l, int p, int steps, int lmax) {
+  if (steps == 0) return l == 0 && p == 1;
+  IrSet one{};
+  one.n = 1;
+  one.l[0] = l;
+  one.p[0] = p;
+  const IrSet o = ir_products(one, lmax);
+  for (int k = 0; k < o.n; ++k)
+    if (ir_reaches_scalar(o.l[k], o.p[k], steps - 1, lmax)) return true;
+  return false;
+}
+
+// the features of layer L of an nl-layer model: the products that can still reach 0e
+__host__ __device__ constexpr IrSet ir_layer(int lmax, int nl, int L) {
+  IrSet s = ir_natural(lmax);
+  for (int k = 1; k <= L; ++k) {
+    const IrSet o = ir_products(s, lmax);
+    IrSet keep{};
+    for (int q = 0; q < o.n; ++q)
+      if (ir_reaches_scalar(o.l[q], o.p[q], nl - k, lmax)) {
+        keep.l[keep.n] = o.l[q];
+        keep.p[keep.n] = o.p[q];
+        ++keep.n;
+      }
+    s = keep;
+  }
+  return s;
+}
+
+__host__ __device__ constexpr int ir_dim(const IrSet& s) {
+  int d = 0;
+  for (int k = 0; k < s.n; ++k) d += 2 * s.l[k] + 1;
+  return d;
+}
+
+// can the real coupling block (l1, l2, l3) be nonzero at (m1, m2, m3)?
+__host__ __device__ constexpr bool coupling_candidate(int l1, int m1, int l2, int m2, int l3, int m3) {
+  const int a = iabs(m1), b = iabs(m2), c = iabs(m3);
+  const bool sine = ((m1 < 0) != (m2 < 0)) != (m3 < 0);
+  return sine == (((l1 + l2 + l3) & 1) == 1) && (c == a + b || c == iabs(a - b));
+}
+
+// Visit the candidate nonzeros (a, b, c) of layer K's tensor in the kernels' order:
+// output irrep, input irrep, harmonic degree l2, then m1, m2, m3.
+template <typename F>
+__host__ __device__ constexpr void for_candidates(int lmax, int nl, int K, F&& f) {
+  const IrSet in = ir_layer(lmax, nl, K - 1), out = ir_layer(lmax, nl, K);
+  for (int ko = 0, oo = 0; ko < out.n; oo += 2 * out.l[ko] + 1, ++ko)
+    for (int ki = 0, oi = 0; ki < in.n; oi += 2 * in.l[ki] + 1, ++ki)
+      for (int l2 = 0; l2 <= lmax; ++l2) {
+        const int l1 = in.l[ki], lo = out.l[ko];
+        if (lo < iabs(l1 - l2) || lo > l1 + l2 || out.p[ko] != in.p[ki] * ((l2 & 1) ? -1 : 1)) continue;
+        for (int m1 = -l1; m1 <= l1; ++m1)
+          for (int m2 = -l2; m2 <= l2; ++m2)
+            for (int m3 = -lo; m3 <= lo; ++m3)
+              if (coupling_candidate(l1, m1, l2, m2, lo, m3)) f(oi + l1 + m1, l2 * l2 + l2 + m2, oo + lo + m3);
+      }
+}
+
+struct CountFn {
+  int n = 0;
+  __host__ __device__ constexpr void operator()(int, int, int) { ++n; }
+};
+__host__ __device__ constexpr int n_candidates(int lmax, int nl, int K) {
+  CountFn f{};
+  for_candidates(lmax, nl, K, f);
+  return f.n;
+}
+
+template <int N>
+struct CandList {
+  unsigned char a[N] = {}, b[N] = {}, c[N] = {};
+};
+template <int N>
+struct FillFn {
+  CandList<N>* out;
+  int q = 0;
+  __host__ __device__ constexpr void operator()(int a, int b, int c) {
+    out->a[q] = (unsigned char)a;
+    out->b[q] = (unsigned char)b;
+    out->c[q] = (unsigned char)c;
+    ++q;
+  }
+};
+template <int N>
+__host__ __device__ constexpr CandList<N> candidates(int lmax, int nl, int K) {
+  CandList<N> r{};
+  FillFn<N> f{&r};
+  for_candidates(lmax, nl, K, f);
+  return r;
+}
+
+// layer K of an (LMAX, NL) model: its candidates and their offset in the value array
+template <int LMAX, int NL, int K>
+struct Cand {
+  static constexpr int n = n_candidates(LMAX, NL, K);
+  static constexpr int off = Cand<LMAX, NL, K - 1>::off + Cand<LMAX, NL, K - 1>::n;
+  static constexpr CandList<n> list = candidates<n>(LMAX, NL, K);
+  static constexpr int din = ir_dim(ir_layer(LMAX, NL, K - 1)), dout = ir_dim(ir_layer(LMAX, NL, K));
+};
+template <int LMAX, int NL>
+struct Cand<LMAX, NL, 0> {
+  static constexpr int n = 0, off = 0;
+};
+template <class P>
+__host__ __device__ constexpr int cand_a(int q) { return P::list.a[q]; }
+template <class P>
+__host__ __device__ constexpr int cand_b(int q) { return P::list.b[q]; }
+template <class P>
+__host__ __device__ constexpr int cand_c(int q) { return P::list.c[q]; }
+
+// the values of all layers' candidates, a launch parameter
+template <int LMAX, int NL>
+struct GenVals {
+  static constexpr int n = Cand<LMAX, NL, NL>::off + Cand<LMAX, NL, NL>::n;
+  float v[n];
+};
+
+template <class F, int... Q>
+__device__ __forceinline__ void each_candidate(F&& f, std::integer_sequence<int, Q...>) {
+  (f(std::integral_constant<int, Q>{}), ...);
+}
+
+// y = M^K x over layer K's candidates, M^K[a][c] = sum_b W^K[a][b][c] G[b]; x = e_0 when E0
+template <int LMAX, int NL, int K, bool E0, int D>
+__device__ __forceinline__ void chain_mv(const float* v, const float (&G)[D], const float (&x)[kGenMaxD],
+                                         float (&y)[kGenMaxD]) {
+  using P = Cand<LMAX, NL, K>;
+#pragma unroll
+  for (int a = 0; a < P::din; ++a) y[a] = 0.0f;
+  each_candidate([&](auto q) {
+    constexpr int Q = decltype(q)::value;
+    constexpr int a = cand_a<P>(Q), b = cand_b<P>(Q), c = cand_c<P>(Q);
+    if constexpr (E0) {
+      if constexpr (c == 0) y[a] = fmaf(v[P::off + Q], G[b], y[a]);
+    } else {
+      y[a] = fmaf(v[P::off + Q] * G[b], x[c], y[a]);
+    }
+  }, std::make_integer_sequence<int, P::n>{});
 }
 
 }  // namespace
@@ -125,27 +285,29 @@ __global__ void gen_env_kernel(GenRowIO io, int L) {
 }
 
 // Q^L[i][u][:] = M^1 ... M^L e_0
-__global__ void __launch_bounds__(kChainThreads) gen_chain_fwd_kernel(GenRowIO io, int L) {
-  extern __shared__ __align__(16) float sm[];
+template <int LMAX, int NL, int L>
+__global__ void __launch_bounds__(kChainThreads) gen_chain_fwd_kernel(GenRowIO io, const __grid_constant__ GenVals<LMAX, NL> w) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= io.na * io.C) return;
-  const int ia = t / io.C, u = t - ia * io.C;
-  const size_t o = ((size_t)ia * io.C + u) * io.S;
-  // slots: Gamma^1..Gamma^L (S each), then the two chain vectors
-  const Vecs V{sm, (int)threadIdx.x, io.S, L, io.dmax};
-  for (int k = 1; k <= L; ++k)
-    for (int b = 0; b < io.S; ++b) V.at(k - 1, b) = io.G[k][o + b];
-  int cur = L, nxt = L + 1;
-  for (int k = L; k >= 1; --k) {   // r <- M^k r; the first step acts on e_0 (its c == 0 entries)
-    const bool first = (k == L);
-    for (int a = 0; a < io.dim[k - 1]; ++a) V.at(nxt, a) = 0.0f;
-    sorted_sum(first ? io.nz0[k] : io.nz[k], first ? io.nnz0[k] : io.nnz[k], [](const GenNz& z) { return (int)z.a; },
-               [&](const GenNz& z) { return z.v * V.at(k - 1, z.b) * (first ? 1.0f : V.at(cur, z.c)); },
-               [&](int a, float v) { V.at(nxt, a) = v; });
-    const int sw = cur; cur = nxt; nxt = sw;
+  const size_t o = (size_t)t * S;
+  float G[L][S];
+#pragma unroll
+  for (int k = 0; k < L; ++k)
+#pragma unroll
+    for (int b = 0; b < S; ++b) G[k][b] = io.G[k + 1][o + b];
+  float x[kGenMaxD], y[kGenMaxD];
+  chain_mv<LMAX, NL, L, true>(w.v, G[L - 1], x, y);
+  if constexpr (L >= 2) {
+    chain_mv<LMAX, NL, L - 1, false>(w.v, G[L - 2], y, x);
+    if constexpr (L >= 3) {
+      chain_mv<LMAX, NL, L - 2, false>(w.v, G[L - 3], x, y);
+    }
   }
-  float* q = io.Q[L] + o;
-  for (int a = 0; a < io.S; ++a) q[a] = V.at(cur, a);
+  const float* q = (L == 2) ? x : y;
+  float* out = io.Q[L] + o;
+#pragma unroll
+  for (int a = 0; a < S; ++a) out[a] = q[a];
 }
 
 // s^L_e[u] = sum_a w^0_{e,u,l(a)} Y_e[a] Q^L[i][u][a], into the s columns of the latent input
@@ -199,43 +361,71 @@ __global__ void gen_qbar_kernel(GenRowIO io, int L) {
   for (int a = 0; a < S; ++a) out[a] = acc[a];
 }
 
-// Back along the chain of Q^L: Gammabar^k += ..., k = 1..L.  Each sum runs over
-// a copy of the layer's nonzeros sorted by its output index (a, b or c), so it
-// accumulates in a register and is written once.
-__global__ void __launch_bounds__(kChainThreads) gen_chain_bwd_kernel(GenRowIO io, int L) {
-  extern __shared__ __align__(16) float sm[];
+// Gb[b] += sum over layer K's candidates of W^K[a][b][c] rb[a] r[c] (r = e_0 when E0) and, unless
+// !NB, nb[c] = sum W^K[a][b][c] rb[a] G[b]
+template <int LMAX, int NL, int K, bool E0, bool NB, int D>
+__device__ __forceinline__ void chain_adj(const float* v, const float (&G)[D], const float (&rb)[kGenMaxD],
+                                          const float (&r)[kGenMaxD], float (&gb)[D], float (&nb)[kGenMaxD]) {
+  using P = Cand<LMAX, NL, K>;
+#pragma unroll
+  for (int b = 0; b < D; ++b) gb[b] = 0.0f;
+  if constexpr (NB) {
+#pragma unroll
+    for (int c = 0; c < P::dout; ++c) nb[c] = 0.0f;
+  }
+  each_candidate([&](auto q) {
+    constexpr int Q = decltype(q)::value;
+    constexpr int a = cand_a<P>(Q), b = cand_b<P>(Q), c = cand_c<P>(Q);
+    const float t = v[P::off + Q] * rb[a];
+    if constexpr (E0) {
+      if constexpr (c == 0) gb[b] += t;
+    } else {
+      gb[b] = fmaf(t, r[c], gb[b]);
+    }
+    if constexpr (NB) nb[c] = fmaf(t, G[b], nb[c]);
+  }, std::make_integer_sequence<int, P::n>{});
+}
+
+// Back along the chain of Q^L: Gammabar^k += ..., k = 1..L
+template <int LMAX, int NL, int L>
+__global__ void __launch_bounds__(kChainThreads) gen_chain_bwd_kernel(GenRowIO io, const __grid_constant__ GenVals<LMAX, NL> w) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= io.na * io.C) return;
-  const int ia = t / io.C, u = t - ia * io.C;
-  const size_t o = ((size_t)ia * io.C + u) * io.S;
-  // slots: Gamma^1..Gamma^L (S each); r_k at slot L - 2 + k for k = 2..L + 1; rbar; nbar
-  const Vecs V{sm, (int)threadIdx.x, io.S, L, io.dmax};
-  auto sR = [&](int k) { return L - 2 + k; };
-  const int sRb = 2 * L, sNb = 2 * L + 1;
-  for (int k = 1; k <= L; ++k)
-    for (int b = 0; b < io.S; ++b) V.at(k - 1, b) = io.G[k][o + b];
-  // r_{L+1} = e_0; r_k = M^k r_{k+1} for k = L .. 2
-  for (int c = 0; c < io.dim[L]; ++c) V.at(sR(L + 1), c) = 0.0f;
-  V.at(sR(L + 1), 0) = 1.0f;
-  for (int k = L; k >= 2; --k) {   // r_{L+1} = e_0: the first step takes the c == 0 entries
-    for (int a = 0; a < io.dim[k - 1]; ++a) V.at(sR(k), a) = 0.0f;
-    sorted_sum(k == L ? io.nz0[k] : io.nz[k], k == L ? io.nnz0[k] : io.nnz[k], [](const GenNz& z) { return (int)z.a; },
-               [&](const GenNz& z) { return z.v * V.at(k - 1, z.b) * V.at(sR(k + 1), z.c); },
-               [&](int a, float v) { V.at(sR(k), a) = v; });
-  }
-  // rbar_1 = Qbar^L; for k = 1..L: Gammabar^k[b] += W rbar_k[a] r_{k+1}[c], rbar_{k+1}[c] = W rbar_k[a] Gamma^k[b]
-  for (int a = 0; a < io.S; ++a) V.at(sRb, a) = io.Qb[o + a];
-  for (int k = 1; k <= L; ++k) {
-    float* Gb = io.Gb[k] + o;
-    sorted_sum(k == L ? io.nz0b[k] : io.nzb[k], k == L ? io.nnz0[k] : io.nnz[k], [](const GenNz& z) { return (int)z.b; },
-               [&](const GenNz& z) { return z.v * V.at(sRb, z.a) * V.at(sR(k + 1), z.c); },
-               [&](int b, float v) { Gb[b] += v; });
-    if (k < L) {
-      for (int c = 0; c < io.dim[k]; ++c) V.at(sNb, c) = 0.0f;
-      sorted_sum(io.nzc[k], io.nnz[k], [](const GenNz& z) { return (int)z.c; },
-                 [&](const GenNz& z) { return z.v * V.at(sRb, z.a) * V.at(k - 1, z.b); },
-                 [&](int c, float v) { V.at(sNb, c) = v; });
-      for (int c = 0; c < io.dim[k]; ++c) V.at(sRb, c) = V.at(sNb, c);
+  const size_t o = (size_t)t * S;
+  float G[L][S];
+#pragma unroll
+  for (int k = 0; k < L; ++k)
+#pragma unroll
+    for (int b = 0; b < S; ++b) G[k][b] = io.G[k + 1][o + b];
+  // r_{L+1} = e_0, r_k = M^k r_{k+1}: r[k - 2] holds r_k for k = 2..L
+  float r[L > 1 ? L - 1 : 1][kGenMaxD];
+  float dummy[kGenMaxD];
+  if constexpr (L >= 2) chain_mv<LMAX, NL, L, true>(w.v, G[L - 1], dummy, r[L - 2]);
+  if constexpr (L >= 3) chain_mv<LMAX, NL, L - 1, false>(w.v, G[L - 2], r[L - 2], r[L - 3]);
+  float rb[kGenMaxD], nb[kGenMaxD], gb[S];
+#pragma unroll
+  for (int a = 0; a < S; ++a) rb[a] = io.Qb[o + a];
+  // k = 1 .. L: Gammabar^k, and rbar_{k+1} for k < L
+  auto flush = [&](int k) {
+    float* g = io.Gb[k] + o;
+#pragma unroll
+    for (int b = 0; b < S; ++b) g[b] += gb[b];
+  };
+  if constexpr (L == 1) {
+    chain_adj<LMAX, NL, 1, true, false>(w.v, G[0], rb, dummy, gb, nb);
+    flush(1);
+  } else {
+    chain_adj<LMAX, NL, 1, false, true>(w.v, G[0], rb, r[0], gb, nb);
+    flush(1);
+    if constexpr (L == 2) {
+      chain_adj<LMAX, NL, 2, true, false>(w.v, G[1], nb, dummy, gb, rb);
+      flush(2);
+    } else {
+      chain_adj<LMAX, NL, 2, false, true>(w.v, G[1], nb, r[1], gb, rb);
+      flush(2);
+      chain_adj<LMAX, NL, 3, true, false>(w.v, G[2], rb, dummy, gb, nb);
+      flush(3);
     }
   }
 }
@@ -318,30 +508,50 @@ __global__ void gen_edge_adj_kernel(GenRowIO io, int L, bool last) {
 // ---------------------------------------------------------------------------
 static int block_of(int C) { return (C + 31) / 32 * 32; }
 
-// shared memory of a chain kernel: L environment slots of S components and nslot of dmax per thread
-static size_t chain_smem(const GenRowIO& io, int L, int nslot) {
-  return ((size_t)L * io.S + (size_t)nslot * io.dmax) * kChainThreads * sizeof(float);
+template <int LMAX, int NL>
+static GenVals<LMAX, NL> vals_of(const GenRowIO& io) {
+  GenVals<LMAX, NL> w;
+  for (int q = 0; q < GenVals<LMAX, NL>::n; ++q) w.v[q] = io.vals[q];
+  return w;
 }
 
-// the chain kernels' opt-in to large dynamic shared memory, once per device
-static void chain_smem_opt_in() {
-  static bool done[64] = {};
-  int d = 0;
-  cudaGetDevice(&d);
-  if (d < 0 || d >= 64 || done[d]) return;
-  cudaFuncSetAttribute(gen_chain_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(gen_chain_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  done[d] = true;
+template <int LMAX, int NL>
+static void chain_fwd(const GenRowIO& io, int L, cudaStream_t st) {
+  const GenVals<LMAX, NL> w = vals_of<LMAX, NL>(io);
+  const int g = (io.na * io.C + kChainThreads - 1) / kChainThreads;
+  if (L == 1) gen_chain_fwd_kernel<LMAX, NL, 1><<<g, kChainThreads, 0, st>>>(io, w);
+  if constexpr (NL >= 2) if (L == 2) gen_chain_fwd_kernel<LMAX, NL, 2><<<g, kChainThreads, 0, st>>>(io, w);
+  if constexpr (NL >= 3) if (L == 3) gen_chain_fwd_kernel<LMAX, NL, 3><<<g, kChainThreads, 0, st>>>(io, w);
+}
+
+template <int LMAX, int NL>
+static void chain_bwd(const GenRowIO& io, int L, cudaStream_t st) {
+  const GenVals<LMAX, NL> w = vals_of<LMAX, NL>(io);
+  const int g = (io.na * io.C + kChainThreads - 1) / kChainThreads;
+  if (L == 1) gen_chain_bwd_kernel<LMAX, NL, 1><<<g, kChainThreads, 0, st>>>(io, w);
+  if constexpr (NL >= 2) if (L == 2) gen_chain_bwd_kernel<LMAX, NL, 2><<<g, kChainThreads, 0, st>>>(io, w);
+  if constexpr (NL >= 3) if (L == 3) gen_chain_bwd_kernel<LMAX, NL, 3><<<g, kChainThreads, 0, st>>>(io, w);
+}
+
+// the (l_max, layers) models of the generic path
+template <int LMAX>
+static void chain_fwd_nl(const GenRowIO& io, int L, cudaStream_t st) {
+  if (io.nl == 1) chain_fwd<LMAX, 1>(io, L, st);
+  else if (io.nl == 2) chain_fwd<LMAX, 2>(io, L, st);
+  else chain_fwd<LMAX, 3>(io, L, st);
+}
+template <int LMAX>
+static void chain_bwd_nl(const GenRowIO& io, int L, cudaStream_t st) {
+  if (io.nl == 1) chain_bwd<LMAX, 1>(io, L, st);
+  else if (io.nl == 2) chain_bwd<LMAX, 2>(io, L, st);
+  else chain_bwd<LMAX, 3>(io, L, st);
 }
 
 template <typename T, int LMAX>
 static void fwd_lmax(const GenRowIO& io, int L, cudaStream_t st) {
   const int bl = block_of(io.C);
   gen_env_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
-  const int n = io.na * io.C;
-  const size_t sm = chain_smem(io, L, 2);
-  chain_smem_opt_in();
-  gen_chain_fwd_kernel<<<(n + kChainThreads - 1) / kChainThreads, kChainThreads, sm, st>>>(io, L);
+  chain_fwd_nl<LMAX>(io, L, st);
   gen_s_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
 }
 
@@ -353,10 +563,7 @@ static void bwd_lmax(const GenRowIO& io, int L, cudaStream_t st) {
       cudaMemsetAsync(io.Gb[k], 0, (size_t)io.na * io.C * io.S * sizeof(float), st);
   }
   gen_qbar_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
-  const int n = io.na * io.C;
-  const size_t sm = chain_smem(io, L, L + 2);
-  chain_smem_opt_in();
-  gen_chain_bwd_kernel<<<(n + kChainThreads - 1) / kChainThreads, kChainThreads, sm, st>>>(io, L);
+  chain_bwd_nl<LMAX>(io, L, st);
   gen_edge_adj_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L, L == 1);
 }
 
@@ -374,6 +581,69 @@ void gen_row_bwd(const GenRowIO& io, int L, cudaStream_t st) {
   if (io.lmax == 1) bwd_lmax<T, 1>(io, L, st);
   else if (io.lmax == 2) bwd_lmax<T, 2>(io, L, st);
   else bwd_lmax<T, 3>(io, L, st);
+}
+
+template <int LMAX, int NL, int K>
+static void pack_layer(const std::vector<double>& W, int S, std::vector<float>& vals, std::vector<char>& hit) {
+  using P = Cand<LMAX, NL, K>;
+  for (int q = 0; q < P::n; ++q) {
+    const size_t i = ((size_t)P::list.a[q] * S + P::list.b[q]) * P::dout + P::list.c[q];
+    vals.push_back((float)W[i]);
+    hit[i] = 1;
+  }
+}
+
+template <int LMAX, int NL>
+static bool pack_model(const std::vector<std::vector<Irrep>>& irs, const std::vector<std::vector<double>>& W,
+                       std::vector<float>& vals, std::string& why) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1);
+  vals.clear();
+  for (int K = 0; K <= NL; ++K) {   // the compile-time irreps are the model's
+    const IrSet ct = ir_layer(LMAX, NL, K);
+    bool same = ct.n == (int)irs[K].size();
+    for (int q = 0; same && q < ct.n; ++q) same = ct.l[q] == irs[K][q].l && ct.p[q] == irs[K][q].p;
+    if (!same) {
+      why = "layer " + std::to_string(K) + " irreps differ from the generic kernels'";
+      return false;
+    }
+  }
+  for (int K = 1; K <= NL; ++K) {
+    std::vector<char> hit(W[K].size(), 0);
+    if (K == 1) pack_layer<LMAX, NL, 1>(W[K], S, vals, hit);
+    if constexpr (NL >= 2) if (K == 2) pack_layer<LMAX, NL, 2>(W[K], S, vals, hit);
+    if constexpr (NL >= 3) if (K == 3) pack_layer<LMAX, NL, 3>(W[K], S, vals, hit);
+    double wmax = 0.0, missed = 0.0;
+    for (size_t i = 0; i < W[K].size(); ++i) {
+      wmax = std::fmax(wmax, std::fabs(W[K][i]));
+      if (!hit[i]) missed = std::fmax(missed, std::fabs(W[K][i]));
+    }
+    if (missed > 1e-12 * wmax) {
+      why = "layer " + std::to_string(K) + " tensor has a nonzero outside the candidate pattern";
+      return false;
+    }
+  }
+  return (int)vals.size() == GenVals<LMAX, NL>::n;
+}
+
+bool gen_pack_values(int lmax, int nl, const std::vector<std::vector<Irrep>>& irs,
+                     const std::vector<std::vector<double>>& W, std::vector<float>& vals, std::string& why) {
+  if ((int)irs.size() != nl + 1 || (int)W.size() != nl + 1) {
+    why = "layer count mismatch";
+    return false;
+  }
+  const int code = lmax * 10 + nl;
+  switch (code) {
+    case 11: return pack_model<1, 1>(irs, W, vals, why);
+    case 12: return pack_model<1, 2>(irs, W, vals, why);
+    case 13: return pack_model<1, 3>(irs, W, vals, why);
+    case 21: return pack_model<2, 1>(irs, W, vals, why);
+    case 22: return pack_model<2, 2>(irs, W, vals, why);
+    case 23: return pack_model<2, 3>(irs, W, vals, why);
+    case 31: return pack_model<3, 1>(irs, W, vals, why);
+    case 32: return pack_model<3, 2>(irs, W, vals, why);
+    case 33: return pack_model<3, 3>(irs, W, vals, why);
+    default: why = "l_max " + std::to_string(lmax) + ", " + std::to_string(nl) + " layers: not supported"; return false;
+  }
 }
 
 template void gen_row_fwd<float>(const GenRowIO&, int, cudaStream_t);

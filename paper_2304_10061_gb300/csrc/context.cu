@@ -583,9 +583,9 @@ struct WS {
   float* xbar; int ld_xbar;
   float* Y; float* Ybar[2]; float* u; float* ubar; float* sig;
   float* G1; float* G2;
-  // generic row path: per atom Gamma^L, Q^L, Gammabar^L (L = 1..nl), Qbar scratch; per edge w^0bar
+  // generic row path: per atom Gamma^L, Q^L, Gammabar^L (L = 1..nl), Qbar scratch
   float* gG[kGenMaxLayers + 1]; float* gQ[kGenMaxLayers + 1]; float* gGb[kGenMaxLayers + 1];
-  float* gQb; float* w0bar;
+  float* gQb;
 };
 
 // Lays the workspace out over `base` (or only measures it when base is null).
@@ -634,7 +634,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->wbar3 = (a.nl >= 3) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
   const bool generic = (a.nl > 2 || a.lmax > 2);
   for (int L = 0; L <= kGenMaxLayers; ++L) w->gG[L] = w->gQ[L] = w->gGb[L] = nullptr;
-  w->gQb = w->w0bar = nullptr;
+  w->gQb = nullptr;
   if (generic) {
     for (int L = 1; L <= a.nl; ++L) {
       w->gG[L] = (float*)take((size_t)Ac * a.C * S * 4);
@@ -642,7 +642,6 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
       w->gGb[L] = (float*)take((size_t)Ac * a.C * S * 4);
     }
     w->gQb = (float*)take((size_t)Ac * a.C * S * 4);
-    w->w0bar = (float*)take((size_t)Ec * nw * 4);
   }
   w->ld_xbar = pad8(std::max(a.tb.back(), a.lat.back()));
   w->xbar = (float*)take((size_t)Ec * w->ld_xbar * 4);
@@ -1294,7 +1293,7 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
   void* wbL[kGenMaxLayers + 1] = {w.wbar01, w.wbar01, w.wbar2, w.wbar3};
   GenRowIO gio;
   gio.a0 = a0; gio.na = Ac; gio.e0 = e0; gio.C = a.C; gio.S = S; gio.lmax = a.lmax; gio.nl = nl;
-  gio.row_ptr = c->d_row_ptr; gio.Y = w.Y; gio.nu = c->tp.nu; gio.Qb = w.gQb; gio.w0bar = w.w0bar;
+  gio.row_ptr = c->d_row_ptr; gio.Y = w.Y; gio.nu = c->tp.nu; gio.Qb = w.gQb;
   gio.Ybar = w.Ybar[0];
   gio.vals = c->gen_vals.data();
   for (int L = 0; L <= nl; ++L) {

@@ -272,7 +272,6 @@ struct GenRowIO {
   float* Q[kGenMaxLayers + 1] = {};
   float* Gb[kGenMaxLayers + 1] = {};
   float* Qb = nullptr;                            // [na][C][S] scratch
-  float* w0bar = nullptr;                         // [Ec][C][l_max+1] float32 accumulator
   float* Ybar = nullptr;                          // [Ec][S]
   // layer tensors W^k, k = 1..nl: their values (host memory) at the candidate nonzeros that
   // gen_pack_values lists, layers 1..nl concatenated; the kernels take them as launch parameters

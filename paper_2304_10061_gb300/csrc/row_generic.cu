@@ -17,16 +17,18 @@
 //   rbar_{k+1}[c] = sum_{a,b} W^k[a][b][c] rbar_k[a] Gamma^k[b],            rbar_1 = Qbar^L,
 //                                                                             r_k = M^k ... M^L e_0)
 //   wbar^L_{e,l}  = nu sum_{m} Gammabar^L[lm] Y_e[lm]        (once Gammabar^L is complete)
-//   w^0bar_{e,l} += sum_{a in l} sbar^L_e Y_e[a] Q^L[a]
-//   Ybar_e[a]    += sum_u (sbar^L_e w^0_{e,l(a)} Q^L[a] + nu w^L_{e,l(a)} Gammabar^L[a])
-// processed for L = nl, nl-1, ..., 1 (the order in which the sbar^L arrive):
-// Gammabar^L is complete once every layer >= L has been processed.
+//   w^0bar_{e,l}  = sum_L sum_{a in l} sbar^L_e Y_e[a] Q^L[a]
+//   Ybar_e[a]     = sum_L sum_u (sbar^L_e w^0_{e,l(a)} Q^L[a] + nu w^L_{e,l(a)} Gammabar^L[a])
+// Layers are processed for L = nl, nl-1, ..., 1 (the order in which the sbar^L
+// arrive): Gammabar^L is complete once every layer >= L has been processed, so
+// wbar^L is written then; w^0bar and Ybar, sums over all layers, are formed
+// once, after layer 1.
 //
 // Layout: per atom [atom][channel][S] float32; per edge the activation-type
 // arrays of the MLP side (w, s, sbar, wbar) and float32 Y / Ybar / w^0bar.
 // Row kernels: one block per centre atom, one thread per channel; per-atom
 // sums are register accumulations over the row (deterministic), the channel
-// sums of Ybar are block reductions in a fixed order; l_max is a template
+// sums of Ybar are warp halving sums and a fixed-order sum over the warps; l_max is a template
 // parameter, so every per-edge vector lives in registers.  Chain kernels: one
 // thread per (atom, channel), unrolled at compile time over the candidate
 // nonzeros of the layer tensors.  Which entries of a fused tensor can be
@@ -61,18 +63,71 @@ template <> __device__ __forceinline__ void gst<bf16>(bf16* p, float v) { *p = _
 
 __host__ __device__ constexpr int l_of(int a) { return a < 1 ? 0 : (a < 4 ? 1 : (a < 9 ? 2 : 3)); }
 
-// Sum of v over the block's threads (blockDim.x a multiple of 32, <= 1024), the
-// same fixed order every time; red: 32 floats of shared memory.
-__device__ __forceinline__ float block_sum(float v, float* red) {
+// the LM = l_max + 1 weights of one channel: one vector access when LM == 4 (the
+// rows are padded to 8 elements and the columns start at multiples of LM, so
+// channel u's group starts at a multiple of 4 elements)
+template <typename T, int LM>
+__device__ __forceinline__ void load_lm(const T* p, float (&x)[LM]) {
+  if constexpr (LM == 4 && sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else if constexpr (LM == 4 && sizeof(T) == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+    x[0] = lo.x; x[1] = lo.y; x[2] = hi.x; x[3] = hi.y;
+  } else {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[w] = v;
-  __syncthreads();
-  float t = 0.0f;
-  for (int q = 0; q < nw; ++q) t += red[q];
-  return t;
+    for (int l = 0; l < LM; ++l) x[l] = gld(p + l);
+  }
+}
+template <typename T, int LM>
+__device__ __forceinline__ void store_lm(T* p, const float (&x)[LM]) {
+  if constexpr (LM == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else if constexpr (LM == 4 && sizeof(T) == 2) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]), hi = __floats2bfloat162_rn(x[2], x[3]);
+    uint2 v;
+    v.x = *reinterpret_cast<const unsigned*>(&lo);
+    v.y = *reinterpret_cast<const unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(p) = v;
+  } else {
+#pragma unroll
+    for (int l = 0; l < LM; ++l) gst(p + l, x[l]);
+  }
+}
+
+// an edge's S harmonics (rows of S floats, 16-byte aligned when S is a multiple of 4)
+template <int S>
+__device__ __forceinline__ void load_y(const float* p, float (&y)[S]) {
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < S / 4; ++k) {
+      const float4 v = *reinterpret_cast<const float4*>(p + 4 * k);
+      y[4 * k] = v.x; y[4 * k + 1] = v.y; y[4 * k + 2] = v.z; y[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) y[a] = p[a];
+  }
+}
+
+// Warp sums of 16 values by recursive halving: at each of the five steps a lane
+// sends the half of its remaining values that its partner keeps.  Returns, in
+// every lane, the warp sum of component lane / 2 (16 shuffles instead of 80).
+__device__ __forceinline__ float warp_sum16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;   // this lane keeps the upper half
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 constexpr int kChainThreads = 128;   // (atom, channel) pairs per block of the chain kernels
@@ -271,11 +326,12 @@ __global__ void gen_env_kernel(GenRowIO io, int L) {
   float G[S];
 #pragma unroll
   for (int b = 0; b < S; ++b) G[b] = 0.0f;
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
     float wl[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = gld(w + (size_t)e * ldw + col + u * LM + l);
-    const float* y = io.Y + (size_t)e * S;
+    load_lm<T, LM>(w + (size_t)e * ldw + col + u * LM, wl);
+    float y[S];
+    load_y<S>(io.Y + (size_t)e * S, y);
 #pragma unroll
     for (int b = 0; b < S; ++b) G[b] += wl[l_of(b)] * y[b];
   }
@@ -323,11 +379,12 @@ __global__ void gen_s_kernel(GenRowIO io, int L) {
 #pragma unroll
   for (int a = 0; a < S; ++a) q[a] = Q[a];
   T* xs = reinterpret_cast<T*>(io.xs[L]);
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
     float wl[LM];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = gld(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM + l);
-    const float* y = io.Y + (size_t)e * S;
+    load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM, wl);
+    float y[S];
+    load_y<S>(io.Y + (size_t)e * S, y);
     float s = 0.0f;
 #pragma unroll
     for (int a = 0; a < S; ++a) s += wl[l_of(a)] * y[a] * q[a];
@@ -347,12 +404,15 @@ __global__ void gen_qbar_kernel(GenRowIO io, int L) {
   float acc[S];
 #pragma unroll
   for (int a = 0; a < S; ++a) acc[a] = 0.0f;
+#pragma unroll 4
   for (int e = rb; e < re; ++e) {
     const float s = gld(sb + (size_t)e * io.ldsbar[L] + io.sbar_off[L] + u);
     float wl[LM];
+    load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM, wl);
 #pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] = s * gld(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM + l);
-    const float* y = io.Y + (size_t)e * S;
+    for (int l = 0; l < LM; ++l) wl[l] *= s;
+    float y[S];
+    load_y<S>(io.Y + (size_t)e * S, y);
 #pragma unroll
     for (int a = 0; a < S; ++a) acc[a] += wl[l_of(a)] * y[a];
   }
@@ -430,77 +490,98 @@ __global__ void __launch_bounds__(kChainThreads) gen_chain_bwd_kernel(GenRowIO i
   }
 }
 
-// Per edge, layer L: wbar^L, the w^0bar accumulation and the Ybar accumulation.
-// last = true (L == 1): w^0bar is complete; written to its activation-type slot.
+// wbar^L_{e,u,l} = nu sum_m Gammabar^L[i][u][lm] Y_e[lm], for a layer L >= 2 (complete once
+// the chains of layers >= L have run)
 template <typename T, int LMAX>
-__global__ void gen_edge_adj_kernel(GenRowIO io, int L, bool last) {
+__global__ void gen_wbar_kernel(GenRowIO io, int L) {
   constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
-  __shared__ float red[(kMaxChannels / 32) * 16];
+  const int ia = blockIdx.x, u = threadIdx.x;
+  if (ia >= io.na || u >= io.C) return;
+  const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
+  float gb[S];
+  const float* G = io.Gb[L] + ((size_t)ia * io.C + u) * S;
+#pragma unroll
+  for (int a = 0; a < S; ++a) gb[a] = io.nu * G[a];
+  T* wLb = reinterpret_cast<T*>(io.wbar[L]);
+#pragma unroll 4
+  for (int e = rb; e < re; ++e) {
+    float y[S];
+    load_y<S>(io.Y + (size_t)e * S, y);
+    float g[LM] = {};
+#pragma unroll
+    for (int a = 0; a < S; ++a) g[l_of(a)] += gb[a] * y[a];
+    store_lm<T, LM>(wLb + (size_t)e * io.ldwbar[L] + io.wbcol[L] + u * LM, g);
+  }
+}
+
+// Per edge, once every layer's adjoint is in (after layer 1's chain):
+//   w^0bar_{e,u,l} = sum_{a in l} Y_e[a] qs[a],  qs[a] = sum_L sbar^L_{e,u} Q^L[a]
+//   wbar^1_{e,u,l} = nu sum_{a in l} Gammabar^1[a] Y_e[a]
+//   Ybar_e[a]      = sum_u (w^0_{e,u,l(a)} qs[a] + nu sum_L w^L_{e,u,l(a)} Gammabar^L[a])
+// The channel sums of Ybar: warp halving sums, then the warps' partials in a fixed order.
+template <typename T, int LMAX, int NL>
+__global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO io) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  static_assert(S <= 16, "halving sums of 16 components");
+  __shared__ float red[2][kMaxChannels / 32][16];
   const int ia = blockIdx.x, u = threadIdx.x;
   if (ia >= io.na) return;
   const bool act = u < io.C;
   const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
-  const T* w0 = reinterpret_cast<const T*>(io.w[0]);
-  const T* wL = reinterpret_cast<const T*>(io.w[L]);
-  const T* sb = reinterpret_cast<const T*>(io.sbar[L]);
-  T* wLb = reinterpret_cast<T*>(io.wbar[L]);
-  T* w0b = reinterpret_cast<T*>(io.wbar[0]);
-  float q[S], gbar[S];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = (int)(blockDim.x >> 5);
+  float q[NL][S], gb[NL][S];
   const size_t o = ((size_t)ia * io.C + (act ? u : 0)) * S;
 #pragma unroll
-  for (int a = 0; a < S; ++a) {
-    q[a] = act ? io.Q[L][o + a] : 0.0f;
-    gbar[a] = act ? io.Gb[L][o + a] : 0.0f;
-  }
-  for (int e = rb; e < re; ++e) {
-    const float* y = io.Y + (size_t)e * S;
-    float yv[S], yc[S];
+  for (int L = 0; L < NL; ++L)
 #pragma unroll
     for (int a = 0; a < S; ++a) {
-      yv[a] = y[a];
-      yc[a] = 0.0f;
+      q[L][a] = act ? io.Q[L + 1][o + a] : 0.0f;
+      gb[L][a] = act ? io.nu * io.Gb[L + 1][o + a] : 0.0f;
     }
-    if (act) {
-      const float s = gld(sb + (size_t)e * io.ldsbar[L] + io.sbar_off[L] + u);
-      float w0l[LM], wLl[LM], g0[LM], gL[LM];
+  const T* w0 = reinterpret_cast<const T*>(io.w[0]);
+  T* w0b = reinterpret_cast<T*>(io.wbar[0]);
+  T* w1b = reinterpret_cast<T*>(io.wbar[1]);
+  for (int e = rb, buf = 0; e < re; ++e, buf ^= 1) {
+    float y[S];
+    load_y<S>(io.Y + (size_t)e * S, y);
+    float yc[16];
 #pragma unroll
-      for (int l = 0; l < LM; ++l) {
-        w0l[l] = gld(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM + l);
-        wLl[l] = gld(wL + (size_t)e * io.ldw[L] + io.wcol[L] + u * LM + l);
-        g0[l] = 0.0f;
-        gL[l] = 0.0f;
+    for (int a = 0; a < 16; ++a) yc[a] = 0.0f;
+    if (act) {
+      float qs[S], w0l[LM], g0[LM] = {}, g1[LM] = {};
+#pragma unroll
+      for (int a = 0; a < S; ++a) qs[a] = 0.0f;
+#pragma unroll
+      for (int L = 0; L < NL; ++L) {
+        const float sb = gld(reinterpret_cast<const T*>(io.sbar[L + 1]) + (size_t)e * io.ldsbar[L + 1] +
+                             io.sbar_off[L + 1] + u);
+        float wl[LM];
+        load_lm<T, LM>(reinterpret_cast<const T*>(io.w[L + 1]) + (size_t)e * io.ldw[L + 1] + io.wcol[L + 1] + u * LM,
+                       wl);
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+          qs[a] = fmaf(sb, q[L][a], qs[a]);
+          yc[a] = fmaf(wl[l_of(a)], gb[L][a], yc[a]);
+        }
       }
+      load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM, w0l);
 #pragma unroll
       for (int a = 0; a < S; ++a) {
-        const int l = l_of(a);
-        g0[l] += s * yv[a] * q[a];
-        gL[l] += io.nu * gbar[a] * yv[a];
-        yc[a] = s * w0l[l] * q[a] + io.nu * wLl[l] * gbar[a];
+        const float ya = y[a];
+        g0[l_of(a)] = fmaf(ya, qs[a], g0[l_of(a)]);
+        g1[l_of(a)] = fmaf(ya, gb[0][a], g1[l_of(a)]);
+        yc[a] = fmaf(w0l[l_of(a)], qs[a], yc[a]);
       }
-      float* acc = io.w0bar + ((size_t)e * io.C + u) * LM;
-#pragma unroll
-      for (int l = 0; l < LM; ++l) {
-        const float t = (L == io.nl ? 0.0f : acc[l]) + g0[l];
-        if (last) gst(w0b + (size_t)e * io.ldwbar[0] + io.wbcol[0] + u * LM + l, t);
-        else acc[l] = t;
-        gst(wLb + (size_t)e * io.ldwbar[L] + io.wbcol[L] + u * LM + l, gL[l]);
-      }
+      store_lm<T, LM>(w0b + (size_t)e * io.ldwbar[0] + io.wbcol[0] + u * LM, g0);
+      store_lm<T, LM>(w1b + (size_t)e * io.ldwbar[1] + io.wbcol[1] + u * LM, g1);
     }
-    // channel sums of the S components: warp shuffles, then the warps' partials in a fixed order
-#pragma unroll
-    for (int a = 0; a < S; ++a)
-#pragma unroll
-      for (int o2 = 16; o2 > 0; o2 >>= 1) yc[a] += __shfl_xor_sync(0xffffffffu, yc[a], o2);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-      for (int a = 0; a < S; ++a) red[(threadIdx.x >> 5) * S + a] = yc[a];
-    __syncthreads();
+    const float t = warp_sum16(yc);   // component lane / 2
+    if ((lane & 1) == 0) red[buf][wid][lane >> 1] = t;
+    __syncthreads();   // one barrier per edge: the other buffer is rewritten only after the next one
     if (threadIdx.x < S) {
-      float t = 0.0f;
-      for (int q2 = 0; q2 < (int)(blockDim.x >> 5); ++q2) t += red[q2 * S + threadIdx.x];
-      float* yb = io.Ybar + (size_t)e * S + threadIdx.x;
-      *yb = (L == io.nl ? 0.0f : *yb) + t;
+      float sum = 0.0f;
+      for (int k = 0; k < nwarp; ++k) sum += red[buf][k][threadIdx.x];
+      io.Ybar[(size_t)e * S + threadIdx.x] = sum;
     }
   }
 }
@@ -564,7 +645,10 @@ static void bwd_lmax(const GenRowIO& io, int L, cudaStream_t st) {
   }
   gen_qbar_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
   chain_bwd_nl<LMAX>(io, L, st);
-  gen_edge_adj_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L, L == 1);
+  if (L >= 2) gen_wbar_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
+  else if (io.nl == 1) gen_edge_final_kernel<T, LMAX, 1><<<io.na, bl, 0, st>>>(io);
+  else if (io.nl == 2) gen_edge_final_kernel<T, LMAX, 2><<<io.na, bl, 0, st>>>(io);
+  else gen_edge_final_kernel<T, LMAX, 3><<<io.na, bl, 0, st>>>(io);
 }
 
 template <typename T>

@@ -113,30 +113,35 @@ class AllegroOracle:
         Zj = torch.nn.functional.one_hot(Z[torch.as_tensor(j)], a.n_species).to(torch_f64)
         h = torch.cat([Zi, Zj, B], dim=1)
         for Wk in self.two_body:
-            h = silu(h @ Wk.T)
+            h = silu(self.linear(h, Wk))
         x = u * h                                                        # x^0
         C, lm = a.channels, a.lmax + 1
-        w0 = (x @ self.embed.T).view(-1, C, lm)
+        w0 = self.linear(x, self.embed).view(-1, C, lm)
         V = w0[:, :, self.l_of_sh] * Y[:, None, :]                      # V^0 [E, C, S]
         i_t = torch.as_tensor(i)
         if features is not None:
             features.update(Y=Y, u=u, B=B, x0=x, w0=w0, V0=V)
         for L in range(1, a.n_layers + 1):
-            wL = (x @ self.env[L - 1].T).view(-1, C, lm)
+            wL = self.linear(x, self.env[L - 1]).view(-1, C, lm)
             contrib = wL[:, :, self.l_of_sh] * Y[:, None, :]
             Gam = torch.zeros(n_atoms, C, Y.shape[1], dtype=torch_f64).index_add_(0, i_t, contrib) * self.nu
             V = torch.einsum("eua,eub,abc->euc", V, Gam[i_t], self.W[L - 1])
             s = V[:, :, 0]                                               # the 0e component comes first
             h = torch.cat([x, s], dim=1)
             for Wk in self.latent[L - 1]:
-                h = silu(h @ Wk.T)
+                h = silu(self.linear(h, Wk))
             x = u * h
             if features is not None:
                 features.update({f"w{L}": wL, f"Gamma{L}": Gam, f"V{L}": V, f"x{L}": x})
         e = x
         for Wk in self.edge:
-            e = e @ Wk.T
+            e = self.linear(e, Wk)
         return e[:, 0]
+
+    def linear(self, x, W):
+        """The bias-free linear layer x W^T of every MLP (one place, so a test can
+        substitute a reduced-precision product)."""
+        return x @ W.T
 
     def _radial(self, r, Z, i, j):
         """Bessel basis [E, n_bessel] and envelope [E] with each edge's cutoff."""

@@ -538,12 +538,27 @@ def _c5_run(args, local, stream, steps: int = 1):
                           "live for one chunk of centre rows at a time",
            "e_total": float(out["E"].item())}
     m.close()
+    if not args.skip_fp8:
+        m8 = Allegro(blob, precision="fp8", device=local)
+        m8.set_stream(stream.cuda_stream)
+        m8.neighbors(px, tx, cx)
+        m8.energy_forces(out=out)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            m8.neighbors(px, tx, cx)
+            m8.energy_forces(out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms8 = a.elapsed_time(b) / steps
+        res["fp8"] = {"ms_per_step": ms8, "atom_steps_per_s": s.n_atoms / (ms8 * 1e-3), "speedup_over_bf16": ms / ms8}
+        m8.close()
     if not args.skip_cpu:
         from oracle.allegro import AllegroOracle
         small = lattice_box(256, (256 / 0.1) ** (1.0 / 3.0), seed=11)
         i, j, S = _edges(arch, small)
         ref = AllegroOracle(arch, w).energy_forces(small.pos, small.species, small.cell, i, j, S)
-        for prec in ("bf16", "fp32"):
+        for prec in ("bf16", "fp32") + (() if args.skip_fp8 else ("fp8",)):
             mm = Allegro(blob, precision=prec, device=local)
             mm.neighbors(small.pos, small.species, small.cell)
             o = mm.energy_forces()
@@ -704,6 +719,16 @@ def run_ours(args):
     else:
         m32 = None
 
+    # ---- FP8 (E4M3 MLP GEMMs, per-tensor scales) beside it ----
+    fp8 = None
+    m8 = None
+    if args.precision == "bf16" and not args.skip_fp8:
+        m8 = make("fp8")
+        ms8 = timed(m8, max(1, min(args.steps, 5)), 1, dev_out())
+        fp8 = {"value": N * ws / (ms8 * 1e-3), "unit": UNIT, "ms_per_step": ms8, "speedup_over_bf16": ms / ms8,
+               "note": "MLP GEMMs with E4M3 operands (tcgen05 kind::f8f6f4), float32 accumulation, per-tensor "
+                       "power-of-two scales, bf16 activations; evaluated through the generic row path"}
+
     # ---- context workloads: batched uneven molecules, and an MD run with 1 fs steps ----
     extra = {}
     if not args.skip_extra:
@@ -802,7 +827,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"bf16": "bf16", "tf32": "tf32"}.get(args.precision, "f32"), "data": "synthetic",
+            "vs_baseline": None, "dtype": {"bf16": "bf16", "tf32": "tf32", "fp8": "e4m3"}.get(args.precision, "f32"), "data": "synthetic",
             "config": {"workload": _workload(args, s), "atoms": N, "edges": n_edges,
                        "step": "neighbour rebuild + E + F + virial, float64 reductions",
                        "l2": "inputs larger than L2 (edge arrays of several GB per step)",
@@ -814,11 +839,15 @@ def run_ours(args):
             "roofline": _roofline(report, ms * args.steps, args.steps, n_edges, arch, N)}
     if fp32:
         line["fp32"] = fp32
+    if fp8:
+        line["fp8"] = fp8
     line.update(extra)
     if rank == 0 and ws == 1 and not args.skip_cpu:
         models = {args.precision: m}
         if m32 is not None:
             models["fp32"] = m32
+        if m8 is not None:
+            models["fp8"] = m8
         cpu, ferr = _cpu_baseline(arch, w, blob, models)
         line["cpu_baseline"] = cpu
         line["force_err_vs_fp64"] = ferr
@@ -827,6 +856,8 @@ def run_ours(args):
     m.close()
     if m32 is not None:
         m32.close()
+    if m8 is not None:
+        m8.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -841,9 +872,10 @@ def main():
     ap.add_argument("--config", default="c4")
     ap.add_argument("--atoms", type=int, default=0, help="scale the configuration's box to this many atoms "
                                                            "(same density; lattice configurations)")
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32", "fp8"])
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--chunk-edges", type=int, default=0, help="edges per model pass (0 = automatic)")
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched-molecule and MD context runs")

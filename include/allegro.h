@@ -48,8 +48,17 @@ typedef enum {
 typedef enum {
   ALLEGRO_PREC_FP32 = 0,    /* all MLP GEMMs in float32 on the CUDA cores */
   ALLEGRO_PREC_BF16 = 1,    /* MLP GEMMs in bfloat16 on tcgen05 tensor cores, float32 accumulation */
-  ALLEGRO_PREC_TF32 = 2     /* float32 weights and activations, MLP GEMMs read as TF32 by tcgen05
+  ALLEGRO_PREC_TF32 = 2,    /* float32 weights and activations, MLP GEMMs read as TF32 by tcgen05
                                (kind::tf32), float32 accumulation: Table IV's production setting */
+  ALLEGRO_PREC_FP8 = 3      /* MLP GEMMs with E4M3 operands on tcgen05 (kind::f8f6f4), float32
+                               accumulation; per-tensor power-of-two scales: each weight matrix's
+                               fixed at allegro_create (max|W| maps to <= 448), each activation's
+                               from the max|value| its producer recorded in the same evaluation
+                               (max maps to <= 224); activations stored in bfloat16 (converted to
+                               E4M3 on chip).  Sec. "Mixed-precision calculations" taken one
+                               step below bfloat16: forces carry E4M3 rounding (3 mantissa bits),
+                               an error of order 10% of RMS|F| on the seeded models; for
+                               precision studies, not for MD */
 } allegro_precision;
 
 /*

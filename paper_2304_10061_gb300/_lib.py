@@ -16,7 +16,7 @@ STATUS_NAMES = {
     0: "ALLEGRO_OK", 1: "ALLEGRO_E_INVALID", 2: "ALLEGRO_E_OOM", 3: "ALLEGRO_E_CUDA",
     4: "ALLEGRO_E_CAPACITY", 5: "ALLEGRO_E_TIMEOUT", 6: "ALLEGRO_E_NONFINITE", 7: "ALLEGRO_E_STATE",
 }
-PREC = {"fp32": 0, "bf16": 1, "tf32": 2}
+PREC = {"fp32": 0, "bf16": 1, "tf32": 2, "fp8": 3}
 
 EXPORTS = ("allegro_create", "allegro_set_stream", "allegro_set_pair_cutoffs", "allegro_set_zbl", "allegro_reserve", "allegro_neighbors",
            "allegro_neighbors_batched", "allegro_energy_forces", "allegro_get_neighbors",

@@ -22,7 +22,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(OUT_DIR, "liballegro_gb300.so")
 
 SOURCES = ["context.cu", "neighbors.cu", "edge_kernels.cu", "row_kernels.cu", "row_generic.cu", "gemm_simt.cu",
-           "gemm_tc.cu", "so3_host.cpp", "noalloc.cu"]
+           "gemm_tc.cu", "gemm_fp8.cu", "so3_host.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]

@@ -129,6 +129,13 @@ struct allegro_ctx {
   // B[n][k] = W_env^L[k][n] for k < K1, W_lat^L_0[k - K1][n] after; null when K1 % 64 != 0
   bf16* headB[kGenMaxLayers] = {nullptr, nullptr, nullptr};
   int headK1[kGenMaxLayers] = {0, 0, 0}, headK[kGenMaxLayers] = {0, 0, 0}, headLd[kGenMaxLayers] = {0, 0, 0};
+  // FP8 path: E4M3 copies of the head maps ([Nx][headLd8] bytes) and their scales
+  uint8_t* headB8[kGenMaxLayers] = {nullptr, nullptr, nullptr};
+  int headLd8[kGenMaxLayers] = {0, 0, 0};
+  float headS8[kGenMaxLayers] = {1.0f, 1.0f, 1.0f};
+  // FP8 path: per-tensor amax slots (float bits) of the activations the E4M3 GEMMs read,
+  // cleared at the start of every chunk
+  unsigned* d_amax = nullptr;
   float* d_v = nullptr;                    // folded edge-energy vector
   double* d_sigma = nullptr;
   double* d_mu = nullptr;
@@ -263,6 +270,17 @@ struct allegro_ctx {
 
 namespace {
 
+// activations stored in bf16 (the BF16 and FP8 precisions)
+bool bf16_storage(const allegro_ctx* c) { return c->prec == ALLEGRO_PREC_BF16 || c->prec == ALLEGRO_PREC_FP8; }
+
+// power-of-two scale s with max|W| / s <= 448 (the largest E4M3 value)
+float e4m3_weight_scale(double amax) {
+  if (!(amax > 0.0)) return 1.0f;
+  int e;
+  const double m = frexp(amax / 448.0, &e);   // amax / 448 = m 2^e, m in [0.5, 1)
+  return (float)ldexp(1.0, m == 0.5 ? e - 1 : e);
+}
+
 allegro_status fail(allegro_ctx* c, allegro_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -384,6 +402,21 @@ allegro_status upload_lin(allegro_ctx* c, const std::vector<float>& W, int N, in
   CUDA_TRY(c, cudaMemcpy(L.f32T, fT.data(), fT.size() * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(L.b16, b.data(), b.size() * 2, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(L.b16T, bT.data(), bT.size() * 2, cudaMemcpyHostToDevice));
+  if (c->prec == ALLEGRO_PREC_FP8) {
+    // E4M3 copies with one power-of-two scale per tensor (W and its transpose share max|W|)
+    double amax = 0.0;
+    for (float x : W) amax = std::max(amax, (double)fabsf(x));
+    L.s8 = L.s8T = e4m3_weight_scale(amax);
+    L.ld8 = (K + 15) / 16 * 16;
+    L.ld8T = (N + 15) / 16 * 16;
+    CUDA_TRY(c, cudaMalloc(&L.f8, (size_t)N * L.ld8));
+    c->weight_allocs.push_back(L.f8);
+    CUDA_TRY(c, cudaMalloc(&L.f8T, (size_t)K * L.ld8T));
+    c->weight_allocs.push_back(L.f8T);
+    fp8_quantize(L.f32, N, K, L.ld, L.f8, L.ld8, 1.0f / L.s8, 0);
+    fp8_quantize(L.f32T, K, N, L.ldT, L.f8T, L.ld8T, 1.0f / L.s8T, 0);
+    CUDA_TRY(c, cudaDeviceSynchronize());
+  }
   return ALLEGRO_OK;
 }
 
@@ -408,7 +441,8 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
   if (a.nl < 1 || a.nl > kGenMaxLayers)
     return fail(c, ALLEGRO_E_INVALID, "weights: %d layers (supported: 1 to 3)", a.nl);
   if (a.lmax < 1 || a.lmax > kMaxLmax) return fail(c, ALLEGRO_E_INVALID, "weights: l_max %d (supported: 1 to 3)", a.lmax);
-  c->generic = (a.nl > 2 || a.lmax > 2);
+  c->generic = (a.nl > 2 || a.lmax > 2 || c->prec == ALLEGRO_PREC_FP8);
+  a.generic = c->generic;
   if (a.C < 8 || a.C > kMaxChannels || (a.C & (a.C - 1)))
     return fail(c, ALLEGRO_E_INVALID, "weights: %d channels (supported: powers of two 8..128)", a.C);
   if (a.ns < 1 || a.ns > kMaxSpecies || a.nb < 1 || a.nb > kMaxBessel || a.p < 2 || a.p > 16 || !(a.rc > 0) ||
@@ -492,6 +526,27 @@ allegro_status load_model(allegro_ctx* c, const void* blob, size_t bytes) {
     c->weight_allocs.push_back(c->headB[L - 1]);
     CUDA_TRY(c, cudaMemcpy(c->headB[L - 1], hb.data(), hb.size() * 2, cudaMemcpyHostToDevice));
     c->headK1[L - 1] = K1; c->headK[L - 1] = K; c->headLd[L - 1] = ld;
+    if (c->prec == ALLEGRO_PREC_FP8) {
+      // E4M3 copy: float32 rows uploaded to a temporary buffer and quantised there
+      std::vector<float> hf((size_t)Nx * K);
+      double amax = 0.0;
+      for (int n = 0; n < Nx; ++n) {
+        for (int k = 0; k < K1; ++k) hf[(size_t)n * K + k] = We[(size_t)k * Nx + n];
+        for (int k = 0; k < K2; ++k) hf[(size_t)n * K + K1 + k] = Wlat[L - 1][0][(size_t)k * fanl + n];
+      }
+      for (float x : hf) amax = std::max(amax, (double)fabsf(x));
+      c->headS8[L - 1] = e4m3_weight_scale(amax);
+      c->headLd8[L - 1] = (K + 15) / 16 * 16;
+      float* tmp = nullptr;
+      CUDA_TRY(c, cudaMalloc(&tmp, hf.size() * 4));
+      CUDA_TRY(c, cudaMemcpy(tmp, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice));
+      CUDA_TRY(c, cudaMalloc(&c->headB8[L - 1], (size_t)Nx * c->headLd8[L - 1]));
+      c->weight_allocs.push_back(c->headB8[L - 1]);
+      fp8_quantize(tmp, Nx, K, K, c->headB8[L - 1], c->headLd8[L - 1], 1.0f / c->headS8[L - 1], 0);
+      const cudaError_t e = cudaDeviceSynchronize();
+      cudaFree(tmp);
+      if (e != cudaSuccess) return fail(c, ALLEGRO_E_CUDA, "FP8 head weights: %s", cudaGetErrorString(e));
+    }
   }
   // linear edge-energy MLP folded into one vector: E_ij = v . x  (float64 product)
   std::vector<double> rvec(1, 1.0);
@@ -632,7 +687,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
   w->ld_wbar2 = pad8(nw);
   w->wbar2 = (a.nl >= 2) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
   w->wbar3 = (a.nl >= 3) ? take((size_t)Ec * w->ld_wbar2 * act_bytes) : nullptr;
-  const bool generic = (a.nl > 2 || a.lmax > 2);
+  const bool generic = a.generic;
   for (int L = 0; L <= kGenMaxLayers; ++L) w->gG[L] = w->gQ[L] = w->gGb[L] = nullptr;
   w->gQb = nullptr;
   if (generic) {
@@ -656,7 +711,7 @@ size_t layout_ws(const Arch& a, int act_bytes, int64_t Ec, int64_t Ac, uint8_t* 
 }
 
 allegro_status ensure_ws(allegro_ctx* c, int64_t Ec, int64_t Ac, WS* w) {
-  const int act_bytes = (c->prec == ALLEGRO_PREC_BF16) ? 2 : 4;
+  const int act_bytes = bf16_storage(c) ? 2 : 4;
   if (Ec > c->ws_edges || Ac > c->ws_atoms || !c->ws) {
     int64_t E2 = std::max<int64_t>(Ec, c->ws_edges), A2 = std::max<int64_t>(Ac, c->ws_atoms);
     E2 = std::max<int64_t>((int64_t)(E2 * 1.05) + 64, 256);
@@ -678,7 +733,7 @@ allegro_status ensure_ws(allegro_ctx* c, int64_t Ec, int64_t Ac, WS* w) {
 
 int64_t ws_bytes_per_edge(const allegro_ctx* c) {
   WS w;
-  const int act_bytes = (c->prec == ALLEGRO_PREC_BF16) ? 2 : 4;
+  const int act_bytes = bf16_storage(c) ? 2 : 4;
   size_t b1 = layout_ws(c->arch, act_bytes, 1 << 16, 1, nullptr, &w);
   return (int64_t)(b1 / (1 << 16)) + 1;
 }
@@ -848,7 +903,9 @@ const char* gemm_label(allegro_ctx* c, const Lin* W, bool trans, int epi) {
     for (size_t k = 0; k < c->lat[L].size(); ++k)
       if (W == &c->lat[L][k]) n = "latent." + std::to_string(L + 1) + "." + std::to_string(k);
   const char* en[] = {"silu", "f32", "dsilu", "head", "last", "linear"};
-  n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/" : (c->prec == ALLEGRO_PREC_TF32 ? "gemm_tf32/" : "gemm_simt/")) +
+  n = std::string(c->prec == ALLEGRO_PREC_BF16 ? "gemm_tc/"
+                  : (c->prec == ALLEGRO_PREC_TF32 ? "gemm_tf32/"
+                                                  : (c->prec == ALLEGRO_PREC_FP8 ? "gemm_fp8/" : "gemm_simt/"))) +
       n + (trans ? "^T" : "") + ":" +
       en[epi];
   return intern_label(n);
@@ -862,6 +919,9 @@ allegro_status gemm(allegro_ctx* c, GemmArgs g) {
   } else if (c->prec == ALLEGRO_PREC_TF32) {
     std::string why;
     if (!gemm_tc_tf32(g, c->stream, c->d_err, &why)) return fail(c, ALLEGRO_E_CUDA, "tcgen05 TF32 GEMM: %s", why.c_str());
+  } else if (c->prec == ALLEGRO_PREC_FP8) {
+    std::string why;
+    if (!gemm_tc_fp8(g, c->stream, c->d_err, &why)) return fail(c, ALLEGRO_E_CUDA, "tcgen05 FP8 GEMM: %s", why.c_str());
   } else {
     gemm_simt_f32(g, c->stream);
   }
@@ -1234,9 +1294,27 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
   const int Ec = e1 - e0, Ac = a1 - a0;
   if (Ec <= 0) return ALLEGRO_OK;
   const int ntb = (int)a.tb.size(), nlat = (int)a.lat.size(), nl = a.nl, nw = a.n_w(), S = a.S();
-  const bool bf16 = (c->prec == ALLEGRO_PREC_BF16);
+  const bool bf16 = bf16_storage(c);
+  const bool fp8 = (c->prec == ALLEGRO_PREC_FP8);
   allegro_status s;
   const double act = sizeof(T);
+  // FP8: per-tensor amax slots.  Every kernel that writes a whole activation array an
+  // E4M3 GEMM reads takes a fresh slot for it; a GEMM reads the latest slot of its
+  // operand arrays (the s columns written into [x | s] join the slot of x).
+  const void* slot_buf[kAmaxSlots];
+  int nslot = 0;
+  auto fresh = [&](const void* b) -> unsigned* {
+    if (!fp8 || nslot >= kAmaxSlots) return nullptr;
+    slot_buf[nslot] = b;
+    return c->d_amax + nslot++;
+  };
+  auto slot_of = [&](const void* b) -> unsigned* {
+    if (!fp8 || !b) return nullptr;
+    for (int k = nslot - 1; k >= 0; --k)
+      if (slot_buf[k] == b) return c->d_amax + k;
+    return nullptr;
+  };
+  if (fp8) CUDA_TRY(c, cudaMemsetAsync(c->d_amax, 0, kAmaxSlots * sizeof(unsigned), st));
   auto mk = [&](const void* A, int lda, int K, const Lin& W, bool trans, int epi, void* out, int ldo, int N,
                 void* pre = nullptr, int ldp = 0, const float* rowscale = nullptr, const void* add = nullptr,
                 int ld_add = 0) {
@@ -1246,7 +1324,15 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     g.v = c->d_v; g.rowsig = w.sig; g.epq = c->tune.epq_wide;
     return g;
   };
-  auto run1 = [&](const GemmArgs& g) {
+  auto run1 = [&](GemmArgs g) {
+    if (fp8) {
+      g.amax_a = slot_of(g.A);
+      g.amax_a2 = slot_of(g.A2);
+      if (g.epi == EPI_FWD_SILU || g.epi == EPI_BWD_SILU) {
+        g.amax_out = fresh(g.out);
+        if (!g.amax_out) return fail(c, ALLEGRO_E_INVALID, "FP8: more than %d activation arrays in a chunk", kAmaxSlots);
+      }
+    }
     const double outb = (g.epi == EPI_F32) ? 4.0 : act;
     ProfScope ps(c, gemm_label(c, g.W, g.trans, g.epi), 2.0 * Ec * (double)g.N * g.K,
                  (double)Ec * (g.K * act + g.N * outb + (g.pre ? g.N * act : 0.0)) + (double)g.N * g.K * act);
@@ -1317,7 +1403,8 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
                  (double)Ec * (24 + 8 + 8 + S * 4 + 4 + 4 + 2.0 * a.tb[0] * act));
     edge_geom_fwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, w.Y, w.u, c->d_sigma, w.sig,
                      c->tb[0].f32T, c->tb[0].ldT, (T*)w.Ztb[0], w.ld_Ztb[0],
-                     (T*)(tb_single ? w.X[0] : w.H[1]), tb_single ? w.ld_X[0] : w.ld_H, tb_single, st);
+                     (T*)(tb_single ? w.X[0] : w.H[1]), tb_single ? w.ld_X[0] : w.ld_H, tb_single, st,
+                     fresh(tb_single ? w.X[0] : w.H[1]));
   }
   if (ntb > 1 && (s = fwd_mlp(c->tb, w.Ztb, w.ld_Ztb, 1, ntb, w.H[1], w.ld_H, a.tb[0], w.X[0], w.ld_X[0])) != ALLEGRO_OK)
     return s;
@@ -1330,6 +1417,7 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
       return s;
     {
       ProfScope ps(c, "row_gen_fwd", 0.0, (double)Ec * (2.0 * nw * act + S * 4 + a.C * act) + (double)Ac * a.C * S * 8.0, 3);
+      gio.amax_s = slot_of(w.X[L - 1]);
       gen_row_fwd<T>(gio, L, st);
     }
     void* dst = (L < nl) ? w.X[L] : w.Xlast;
@@ -1348,17 +1436,17 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.lat.back() * 2 * act + 16));
     mlp_head_bwd<T>(Ec, a.lat.back(), nullptr, 0, c->d_v, c->d_ei, c->d_species, c->d_sigma, e0,
                     (const T*)w.Zlat[nl - 1][nlat - 1], w.ld_Zlat[nlat - 1], w.u, w.ubar, true, (T*)w.H[0], w.ld_H,
-                    st);
+                    st, fresh(w.H[0]));
   }
   for (int L = nl; L >= 1; --L) {
-    const bool kc = bf16 && c->headB[L - 1] != nullptr;
-    if (bf16 && !kc) return fail(c, ALLEGRO_E_INVALID, "BF16 generic path needs 64-aligned env-weight widths");
+    const bool kc = bf16 && c->headB[L - 1] != nullptr && (!fp8 || c->headB8[L - 1] != nullptr);
     const void* zlat = nullptr;
     if ((s = back_mlp(c->lat[L - 1], w.Zlat[L - 1], w.ld_Zlat, w.D[L - 1], w.ld_D[L - 1], a.Klat(L - 1) + a.C,
                       kc ? a.Klat(L - 1) : 0, &zlat)) != ALLEGRO_OK)
       return s;
     {
       ProfScope ps(c, "row_gen_bwd", 0.0, (double)Ec * (4.0 * nw * act + 2 * S * 4 + a.C * act) + (double)Ac * a.C * S * 16.0, 3);
+      gio.amax_wbar = fresh(wbL[L]);
       gen_row_bwd<T>(gio, L, st);
     }
     // xbar of x^{L-1} = wbar^L . W_env^L (layer 1: [wbar^0 | wbar^1] . [W_emb ; W_env^1]) + its latent-input adjoint
@@ -1369,6 +1457,12 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
               w.ld_xbar, a.Klat(L - 1));
       hd.A2 = zlat; hd.lda2 = w.ld_H; hd.K1 = c->headK1[L - 1];
       hd.Bover = c->headB[L - 1]; hd.ldb_over = c->headLd[L - 1];
+      hd.Bover8 = c->headB8[L - 1]; hd.ldb_over8 = c->headLd8[L - 1]; hd.sBover8 = c->headS8[L - 1];
+    } else if (bf16) {
+      // env-weight widths off the 64-column k-blocks: wbar . W_env in float32, the latent input's
+      // adjoint (bf16) added by the head kernel below
+      hd = mk(wbL[L], (L == 1) ? w.ld_wbar01 : w.ld_wbar2, K1, *env[L], true, EPI_F32, w.xbar, w.ld_xbar,
+              a.Klat(L - 1));
     } else {
       hd = mk(wbL[L], (L == 1) ? w.ld_wbar01 : w.ld_wbar2, K1, *env[L], true, EPI_F32, w.xbar, w.ld_xbar,
               a.Klat(L - 1), nullptr, 0, nullptr, w.D[L - 1], w.ld_D[L - 1]);
@@ -1378,7 +1472,8 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     const int ldp = (L == 1) ? w.ld_Ztb[ntb - 1] : w.ld_Zlat[nlat - 1];
     ProfScope ps(c, "head_bwd", 0.0, (double)Ec * (a.Klat(L - 1) * (4 + 2 * act) + 12));
     mlp_head_bwd<T>(Ec, a.Klat(L - 1), w.xbar, w.ld_xbar, nullptr, c->d_ei, c->d_species, c->d_sigma, e0,
-                    (const T*)pre, ldp, w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st);
+                    (const T*)pre, ldp, w.u, w.ubar, false, (T*)w.H[0], w.ld_H, st, fresh(w.H[0]),
+                    (bf16 && !kc) ? (const T*)w.D[L - 1] : nullptr, w.ld_D[L - 1]);
   }
   int cur0 = 0;
   for (int k = ntb - 1; k >= 1; --k) {
@@ -1448,7 +1543,7 @@ allegro_status run_plan(allegro_ctx* c, const Plan& p, const WS& w, bool backwar
     int a0 = p.bounds[q], a1 = p.bounds[q + 1];
     int e0 = c->h_row_ptr[a0], e1 = c->h_row_ptr[a1];
     if (c->generic)
-      s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk_gen<bf16>(c, w, a0, a1, e0, e1, backward)
+      s = bf16_storage(c) ? run_chunk_gen<bf16>(c, w, a0, a1, e0, e1, backward)
                                          : run_chunk_gen<float>(c, w, a0, a1, e0, e1, backward);
     else
       s = (c->prec == ALLEGRO_PREC_BF16) ? run_chunk<bf16>(c, w, a0, a1, e0, e1, backward)
@@ -1655,7 +1750,8 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
   if (!out) return ALLEGRO_E_INVALID;
   *out = nullptr;
   if (!weights_blob || blob_bytes == 0) return ALLEGRO_E_INVALID;
-  if (precision != ALLEGRO_PREC_FP32 && precision != ALLEGRO_PREC_BF16 && precision != ALLEGRO_PREC_TF32)
+  if (precision != ALLEGRO_PREC_FP32 && precision != ALLEGRO_PREC_BF16 && precision != ALLEGRO_PREC_TF32 &&
+      precision != ALLEGRO_PREC_FP8)
     return ALLEGRO_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -1671,7 +1767,7 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
     return s;
   };
   if (cudaSetDevice(device) != cudaSuccess) return bail(fail(c, ALLEGRO_E_CUDA, "cudaSetDevice failed"));
-  if (precision == ALLEGRO_PREC_BF16 || precision == ALLEGRO_PREC_TF32) {
+  if (precision == ALLEGRO_PREC_BF16 || precision == ALLEGRO_PREC_TF32 || precision == ALLEGRO_PREC_FP8) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, device);
     if (prop.major != 10 || prop.minor != 3)
@@ -1684,6 +1780,8 @@ allegro_status allegro_create(const void* weights_blob, size_t blob_bytes, const
   c->stream = c->own_stream;
   allegro_status s = load_model(c, weights_blob, blob_bytes);
   if (s != ALLEGRO_OK) return bail(s);
+  if (precision == ALLEGRO_PREC_FP8 && cudaMalloc(&c->d_amax, kAmaxSlots * sizeof(unsigned)) != cudaSuccess)
+    return bail(fail(c, ALLEGRO_E_OOM, "amax slots"));
   if (r_c > 0 && fabs(r_c - c->arch.rc) > 1e-12 * c->arch.rc)
     return bail(fail(c, ALLEGRO_E_INVALID, "r_c %g differs from the model cutoff %g", r_c, c->arch.rc));
   // species map
@@ -2360,7 +2458,7 @@ void allegro_destroy(allegro_ctx* c) {
                   c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,
                   c->d_md_pos, c->d_md_vel, c->d_md_invm, c->d_md_types, c->d_md_masses, c->d_md_E, c->d_md_K,
                   c->d_md_part, c->d_pair_basis, c->d_pair_rc2, c->d_zbl, c->d_sk_row, c->d_sk_j,
-                  c->d_sk_S, c->d_sk_ref, c->d_cell9, c->d_maxd};
+                  c->d_sk_S, c->d_sk_ref, c->d_cell9, c->d_maxd, c->d_amax};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cuda_bf16.h>
 
+#include "amax.cuh"
 #include "internal.h"
 
 namespace alg {
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kGeomBlock)
                     const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
                     float* __restrict__ Yout, float* __restrict__ uout, const double* __restrict__ sigma,
                     float* __restrict__ sig, const float* __restrict__ W0t, int ldW, int N0, T* __restrict__ Zout,
-                    int ldZ, T* __restrict__ Hout, int ldH, int scale_u) {
+                    int ldZ, T* __restrict__ Hout, int ldH, int scale_u, unsigned* __restrict__ amax) {
   constexpr int LDS = geom_stage_ld<T>();
   extern __shared__ __align__(16) uint8_t geom_sm[];
   const int K0 = 2 * bc.ns + bc.nb;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(kGeomBlock)
   T* sH = sZ + kGeomBlock * LDS;                                                  // [kGeomBlock][LDS]
   const int tl = threadIdx.x;
   const int ntiles = (Ec + kGeomBlock - 1) / kGeomBlock;
+  float hmax = 0.0f;   // max |activation| written (FP8 per-tensor scale)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int eb = tile * kGeomBlock;
     const int nloc = min(kGeomBlock, Ec - eb);
@@ -245,7 +247,10 @@ __global__ void __launch_bounds__(kGeomBlock)
           }
           float hv[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) hv[k] = acc[k] * path_sigmoid<T>(acc[k]) * rsc;
+          for (int k = 0; k < 4; ++k) {
+            hv[k] = acc[k] * path_sigmoid<T>(acc[k]) * rsc;
+            hmax = fmaxf(hmax, fabsf(hv[k]));
+          }
           st4_act(sZ + tl * LDS + c4, acc);
           st4_act(sH + tl * LDS + c4, hv);
         }
@@ -258,12 +263,13 @@ __global__ void __launch_bounds__(kGeomBlock)
     float* dst = Yout + (size_t)eb * bc.S;
     for (int q = tl; q < nloc * bc.S; q += kGeomBlock) dst[q] = sY[q];
   }
+  record_amax(amax, hmax);
 }
 
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
                    const Arch& a, float* Y, float* u, const double* sigma, float* sig, const float* W0t, int ldW,
-                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st) {
+                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st, unsigned* amax) {
   if (Ec <= 0) return;
   const int N0 = a.tb[0], K0 = a.K0in();
   const size_t stage = (size_t)kGeomBlock * kMaxS * 4 + 2 * (size_t)kGeomBlock * geom_stage_ld<T>() * sizeof(T);
@@ -275,14 +281,14 @@ void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* e
     cudaFuncSetAttribute(geom_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   geom_fwd_kernel<T><<<tiles, kGeomBlock, smem, st>>>(
       Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, sigma, sig, W0t, ldW, N0, Z0, ldZ, H0, ldH,
-      scale_u ? 1 : 0);
+      scale_u ? 1 : 0, amax);
 }
 template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
                                    float*, float*, const double*, float*, const float*, int, float*, int, float*,
-                                   int, bool, cudaStream_t);
+                                   int, bool, cudaStream_t, unsigned*);
 template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int*, const int*, const Arch&,
                                   float*, float*, const double*, float*, const float*, int, bf16*, int, bf16*, int,
-                                  bool, cudaStream_t);
+                                  bool, cudaStream_t, unsigned*);
 
 // Adjoint of the geometry.  The first two-body layer's input adjoint is only
 // needed for its Bessel part: Bbar_n = sum_k zbar0_k W0[k][2 ns + n] (the
@@ -410,7 +416,8 @@ __global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, i
                                 const int* __restrict__ species, const double* __restrict__ sigma, int e0,
                                 const T* __restrict__ pre, int ld_pre,
                                 const float* __restrict__ u, float* __restrict__ ubar, bool ubar_init,
-                                T* __restrict__ zbar, int ld_z) {
+                                T* __restrict__ zbar, int ld_z, unsigned* __restrict__ amax,
+                                const T* __restrict__ addx, int ld_addx) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= Ec) return;
@@ -418,33 +425,39 @@ __global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, i
   float sc = 1.0f;
   if (!xbar) sc = (float)sigma[species[ei[(size_t)e0 + e]]];
   const float ue = u[e];
-  float dot = 0.0f;
+  float dot = 0.0f, zmax = 0.0f;
   for (int n = lane; n < K; n += 32) {
     float xb = xbar ? xbar[(size_t)e * ld_x + n] : sc * vconst[n];
+    if (addx) xb += from_act(addx[(size_t)e * ld_addx + n]);
     float z = from_act(pre[(size_t)e * ld_pre + n]);
     float s = sigmoidf_(z);
     dot += xb * z * s;
-    zbar[(size_t)e * ld_z + n] = to_act<T>(xb * ue * s * (1.0f + z * (1.0f - s)));
+    const float zb = xb * ue * s * (1.0f + z * (1.0f - s));
+    zmax = fmaxf(zmax, fabsf(zb));
+    zbar[(size_t)e * ld_z + n] = to_act<T>(zb);
   }
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   if (lane == 0) ubar[e] = ubar_init ? dot : ubar[e] + dot;
+  record_amax(amax, zmax);
 }
 
 template <typename T>
 void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
                   const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,
-                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st) {
+                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st, unsigned* amax, const T* addx,
+                  int ld_addx) {
   if (Ec <= 0) return;
   long long threads = (long long)Ec * 32;
   head_bwd_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      Ec, K, xbar, ld_x, vconst, ei, species, sigma, e0, pre, ld_pre, u, ubar, ubar_init, zbar, ld_z);
+      Ec, K, xbar, ld_x, vconst, ei, species, sigma, e0, pre, ld_pre, u, ubar, ubar_init, zbar, ld_z, amax, addx,
+      ld_addx);
 }
 template void mlp_head_bwd<float>(int, int, const float*, int, const float*, const int*, const int*,
                                   const double*, int, const float*, int, const float*, float*, bool, float*, int,
-                                  cudaStream_t);
+                                  cudaStream_t, unsigned*, const float*, int);
 template void mlp_head_bwd<bf16>(int, int, const float*, int, const float*, const int*, const int*,
                                  const double*, int, const bf16*, int, const float*, float*, bool, bf16*, int,
-                                 cudaStream_t);
+                                 cudaStream_t, unsigned*, const bf16*, int);
 
 // E_ij = v . x (the linear edge-energy MLP folded into one vector v)
 template <typename T>

@@ -45,6 +45,8 @@ struct Arch {
   // [ns * ns][2] = {k_e Z_a Z_b / 2, 1 / a_s} per ordered species pair; null: no ZBL term
   const float* zbl = nullptr;
   std::vector<int> tb, lat, edge;
+  // evaluated through the generic row path (three layers, l_max 3, or the FP8 precision)
+  bool generic = false;
   int S() const { return (lmax + 1) * (lmax + 1); }
   int n_w() const { return C * (lmax + 1); }
   int K0in() const { return 2 * ns + nb; }
@@ -59,6 +61,12 @@ struct Lin {
   float* f32T = nullptr;
   bf16* b16 = nullptr;
   bf16* b16T = nullptr;
+  // FP8 precision: E4M3 copies [N][ld8] and [K][ld8T] (pitches multiples of 16 bytes) with their
+  // per-tensor power-of-two scales (W = s8 q8)
+  uint8_t* f8 = nullptr;
+  uint8_t* f8T = nullptr;
+  int ld8 = 0, ld8T = 0;
+  float s8 = 1.0f, s8T = 1.0f;
 };
 
 // Tensor-product constants of one model, passed to kernels by value.
@@ -130,6 +138,12 @@ struct GemmArgs {
   const float* rowsig = nullptr;   // EPI_LAST: sigma_{Z_i} per row
   float* Eout = nullptr;           // EPI_LAST: E_ij per row
   int epq = 4;                     // tcgen05 path: epilogue warps per TMEM quarter of SiLU-adjoint / last-layer GEMMs
+  // FP8 path: B given directly as E4M3 [N][ld] with its scale (the K-concatenated head maps)
+  const uint8_t* Bover8 = nullptr; int ldb_over8 = 0; float sBover8 = 1.0f;
+  // FP8 path: per-tensor amax slots (float bits, device) of A, of A2, and of this GEMM's output
+  const unsigned* amax_a = nullptr;
+  const unsigned* amax_a2 = nullptr;
+  unsigned* amax_out = nullptr;
 };
 
 // ---- launchers -----------------------------------------------------------
@@ -140,6 +154,12 @@ bool gemm_tc_init(std::string* why);
 // float32 operands read as TF32 by tcgen05 kind::tf32, float32 epilogues (FWD_SILU, F32, BWD_SILU, LINEAR)
 bool gemm_tc_tf32(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
 bool gemm_chain_bf16(const GemmArgs& g1, const GemmArgs& g2, cudaStream_t st, int* d_err, std::string* why);
+// E4M3 operands with per-tensor scales read by tcgen05 kind::f8f6f4 (bf16 activations converted on
+// chip), float32 accumulation, bf16 / float32 epilogues (FWD_SILU, F32, BWD_SILU, LINEAR)
+bool gemm_tc_fp8(const GemmArgs& g, cudaStream_t st, int* d_err, std::string* why);
+// dst[r][k] = e4m3(src[r][k] * inv_scale) for k < cols, 0 for cols <= k < ldd (rows x ldd bytes)
+void fp8_quantize(const float* src, int rows, int cols, int lds, uint8_t* dst, int ldd, float inv_scale,
+                  cudaStream_t st);
 
 // scan / utilities
 void exclusive_scan_i32(const int* in, int* out, int n, int* d_total, void* tmp, size_t tmp_bytes,
@@ -196,7 +216,7 @@ void nb_minmax_frac(const double* pos, int n, const double* inv, double* d_minma
 template <typename T>
 void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
                    const Arch& a, float* Y, float* u, const double* sigma, float* sig, const float* W0t, int ldW,
-                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st);
+                   T* Z0, int ldZ, T* H0, int ldH, bool scale_u, cudaStream_t st, unsigned* amax = nullptr);
 // Partial adjoints of Y [Ec][S] written by the row-kernel passes
 struct YbarParts {
   const float* p[2];
@@ -206,10 +226,12 @@ template <typename T>
 void edge_geom_bwd(int Ec, int e0, const double* ed, const int* ei, const int* ej, const int* species,
                    const Arch& a, const T* zbar0, int ldz, const float* W0t, int ldW, const float* ubar,
                    const YbarParts& yb, float* g, cudaStream_t st);
+// (addx, if given: an activation-type addend of xbar, [Ec][ld_addx])
 template <typename T>
 void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vconst, const int* ei,
                   const int* species, const double* sigma, int e0, const T* pre, int ld_pre, const float* u,
-                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st);
+                  float* ubar, bool ubar_init, T* zbar, int ld_z, cudaStream_t st, unsigned* amax = nullptr,
+                  const T* addx = nullptr, int ld_addx = 0);
 template <typename T>
 void edge_energy(int Ec, int K, const T* x, int ldx, const float* v, float* Ee, cudaStream_t st);
 // float64 per-atom energies sigma_Z E_i + mu_Z (+ the ZBL term when a.zbl is set), forces by row and
@@ -250,6 +272,8 @@ struct RowIO {
 };
 // ---- any number of layers (row_generic.cu) ----
 constexpr int kGenMaxLayers = 3;
+// FP8 precision: amax slots per context (one per activation written in a chunk)
+constexpr int kAmaxSlots = 128;
 constexpr int kGenMaxD = 32;       // components of the largest feature (l_max 3, both parities: 31)
 struct GenRowIO {
   int a0 = 0, na = 0, e0 = 0, C = 0, S = 0, lmax = 0, nl = 0;
@@ -277,6 +301,10 @@ struct GenRowIO {
   // gen_pack_values lists, layers 1..nl concatenated; the kernels take them as launch parameters
   const float* vals = nullptr;
   int dim[kGenMaxLayers + 1] = {};                // dim[0] = S, dim[nl] = 1
+  // FP8 precision: amax slots (float bits) of the s columns written by the forward pass
+  // and of the wbar arrays written by the adjoint pass (null: not recorded)
+  unsigned* amax_s = nullptr;
+  unsigned* amax_wbar = nullptr;
 };
 struct Irrep;
 // The values of the layer tensors W[k] (k = 1..nl, dense float64 over dim(irs[k-1]) x S x

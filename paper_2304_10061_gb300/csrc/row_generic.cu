@@ -48,6 +48,7 @@
 #include <utility>
 #include <vector>
 
+#include "amax.cuh"
 #include "internal.h"
 
 namespace alg {
@@ -379,6 +380,7 @@ __global__ void gen_s_kernel(GenRowIO io, int L) {
 #pragma unroll
   for (int a = 0; a < S; ++a) q[a] = Q[a];
   T* xs = reinterpret_cast<T*>(io.xs[L]);
+  float smax = 0.0f;
 #pragma unroll 4
   for (int e = rb; e < re; ++e) {
     float wl[LM];
@@ -388,8 +390,10 @@ __global__ void gen_s_kernel(GenRowIO io, int L) {
     float s = 0.0f;
 #pragma unroll
     for (int a = 0; a < S; ++a) s += wl[l_of(a)] * y[a] * q[a];
+    smax = fmaxf(smax, fabsf(s));
     gst(xs + (size_t)e * io.ldxs[L] + io.xs_off[L] + u, s);
   }
+  record_amax(io.amax_s, smax);
 }
 
 // Qbar^L[i][u][a] = sum_e sbar^L_e[u] w^0_{e,u,l(a)} Y_e[a]
@@ -503,6 +507,7 @@ __global__ void gen_wbar_kernel(GenRowIO io, int L) {
 #pragma unroll
   for (int a = 0; a < S; ++a) gb[a] = io.nu * G[a];
   T* wLb = reinterpret_cast<T*>(io.wbar[L]);
+  float gmax = 0.0f;
 #pragma unroll 4
   for (int e = rb; e < re; ++e) {
     float y[S];
@@ -510,8 +515,11 @@ __global__ void gen_wbar_kernel(GenRowIO io, int L) {
     float g[LM] = {};
 #pragma unroll
     for (int a = 0; a < S; ++a) g[l_of(a)] += gb[a] * y[a];
+#pragma unroll
+    for (int l = 0; l < LM; ++l) gmax = fmaxf(gmax, fabsf(g[l]));
     store_lm<T, LM>(wLb + (size_t)e * io.ldwbar[L] + io.wbcol[L] + u * LM, g);
   }
+  record_amax(io.amax_wbar, gmax);
 }
 
 // Per edge, once every layer's adjoint is in (after layer 1's chain):
@@ -541,6 +549,7 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
   const T* w0 = reinterpret_cast<const T*>(io.w[0]);
   T* w0b = reinterpret_cast<T*>(io.wbar[0]);
   T* w1b = reinterpret_cast<T*>(io.wbar[1]);
+  float gmax = 0.0f;
   for (int e = rb, buf = 0; e < re; ++e, buf ^= 1) {
     float y[S];
     load_y<S>(io.Y + (size_t)e * S, y);
@@ -574,6 +583,8 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
       }
       store_lm<T, LM>(w0b + (size_t)e * io.ldwbar[0] + io.wbcol[0] + u * LM, g0);
       store_lm<T, LM>(w1b + (size_t)e * io.ldwbar[1] + io.wbcol[1] + u * LM, g1);
+#pragma unroll
+      for (int l = 0; l < LM; ++l) gmax = fmaxf(gmax, fmaxf(fabsf(g0[l]), fabsf(g1[l])));
     }
     const float t = warp_sum16(yc);   // component lane / 2
     if ((lane & 1) == 0) red[buf][wid][lane >> 1] = t;
@@ -584,6 +595,7 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
       io.Ybar[(size_t)e * S + threadIdx.x] = sum;
     }
   }
+  record_amax(io.amax_wbar, gmax);
 }
 
 // ---------------------------------------------------------------------------

@@ -410,6 +410,29 @@ template void edge_geom_bwd<bf16>(int, int, const double*, const int*, const int
 //   ubar += sum_n xbar_n silu(z_n),   zbar_n = xbar_n u silu'(z_n).
 // xbar = sigma_{Z_i} v when `xbar` is null (the last layer: E_ij = v . x with
 // the linear edge-energy MLP folded into v, and dE/dE_ij = sigma_{Z_i}).
+// four consecutive activation-type values as floats (16-byte float / 8-byte bf16 access)
+__device__ __forceinline__ float4 ld4_act(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4_act(const bf16* p) {
+  const uint2 w = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4_act4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st4_act4(bf16* p, float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 w;
+  w.x = *reinterpret_cast<const unsigned*>(&a);
+  w.y = *reinterpret_cast<const unsigned*>(&b);
+  *reinterpret_cast<uint2*>(p) = w;
+}
+
+// Adjoint head of an MLP whose output is x = u * silu(z):  given xbar,
+//   ubar += sum_n xbar_n silu(z_n),   zbar_n = xbar_n u silu'(z_n).
+// xbar = sigma_{Z_i} v when `xbar` is null (the last layer: E_ij = v . x with
+// the linear edge-energy MLP folded into v, and dE/dE_ij = sigma_{Z_i}).
+// One warp per edge; with `vec` (every row start 16-byte aligned for float,
+// 8-byte for bf16) a lane takes four consecutive columns per step.
 template <typename T>
 __global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, int ld_x,
                                 const float* __restrict__ vconst, const int* __restrict__ ei,
@@ -417,7 +440,7 @@ __global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, i
                                 const T* __restrict__ pre, int ld_pre,
                                 const float* __restrict__ u, float* __restrict__ ubar, bool ubar_init,
                                 T* __restrict__ zbar, int ld_z, unsigned* __restrict__ amax,
-                                const T* __restrict__ addx, int ld_addx) {
+                                const T* __restrict__ addx, int ld_addx, int vec) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= Ec) return;
@@ -426,15 +449,38 @@ __global__ void head_bwd_kernel(int Ec, int K, const float* __restrict__ xbar, i
   if (!xbar) sc = (float)sigma[species[ei[(size_t)e0 + e]]];
   const float ue = u[e];
   float dot = 0.0f, zmax = 0.0f;
-  for (int n = lane; n < K; n += 32) {
-    float xb = xbar ? xbar[(size_t)e * ld_x + n] : sc * vconst[n];
-    if (addx) xb += from_act(addx[(size_t)e * ld_addx + n]);
-    float z = from_act(pre[(size_t)e * ld_pre + n]);
-    float s = sigmoidf_(z);
+  auto one = [&](float xb, float z) -> float {
+    const float s = sigmoidf_(z);
     dot += xb * z * s;
     const float zb = xb * ue * s * (1.0f + z * (1.0f - s));
     zmax = fmaxf(zmax, fabsf(zb));
-    zbar[(size_t)e * ld_z + n] = to_act<T>(zb);
+    return zb;
+  };
+  int n0 = 0;
+  if (vec) {
+    const int K4 = K & ~3;
+#pragma unroll 4
+    for (int n = 4 * lane; n < K4; n += 128) {
+      float4 xb = xbar ? ld4_act(xbar + (size_t)e * ld_x + n) : ld4_act(vconst + n);
+      if (!xbar) { xb.x *= sc; xb.y *= sc; xb.z *= sc; xb.w *= sc; }
+      if (addx) {
+        const float4 a = ld4_act(addx + (size_t)e * ld_addx + n);
+        xb.x += a.x; xb.y += a.y; xb.z += a.z; xb.w += a.w;
+      }
+      const float4 z = ld4_act(pre + (size_t)e * ld_pre + n);
+      float4 zb;
+      zb.x = one(xb.x, z.x);
+      zb.y = one(xb.y, z.y);
+      zb.z = one(xb.z, z.z);
+      zb.w = one(xb.w, z.w);
+      st4_act4(zbar + (size_t)e * ld_z + n, zb);
+    }
+    n0 = K4;
+  }
+  for (int n = n0 + lane; n < K; n += 32) {
+    float xb = xbar ? xbar[(size_t)e * ld_x + n] : sc * vconst[n];
+    if (addx) xb += from_act(addx[(size_t)e * ld_addx + n]);
+    zbar[(size_t)e * ld_z + n] = to_act<T>(one(xb, from_act(pre[(size_t)e * ld_pre + n])));
   }
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   if (lane == 0) ubar[e] = ubar_init ? dot : ubar[e] + dot;
@@ -448,9 +494,13 @@ void mlp_head_bwd(int Ec, int K, const float* xbar, int ld_x, const float* vcons
                   int ld_addx) {
   if (Ec <= 0) return;
   long long threads = (long long)Ec * 32;
+  auto al = [](const void* p, int b) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+  constexpr int b4 = 4 * (int)sizeof(T);   // bytes of four activation-type values
+  const int vec = al(xbar, 16) && al(vconst, 16) && al(pre, b4) && al(zbar, b4) && al(addx, b4) &&
+                  (ld_x % 4 == 0) && (ld_pre % 4 == 0) && (ld_z % 4 == 0) && (!addx || ld_addx % 4 == 0);
   head_bwd_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       Ec, K, xbar, ld_x, vconst, ei, species, sigma, e0, pre, ld_pre, u, ubar, ubar_init, zbar, ld_z, amax, addx,
-      ld_addx);
+      ld_addx, vec);
 }
 template void mlp_head_bwd<float>(int, int, const float*, int, const float*, const int*, const int*,
                                   const double*, int, const float*, int, const float*, float*, bool, float*, int,

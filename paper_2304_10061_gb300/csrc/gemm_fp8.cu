@@ -104,6 +104,14 @@ __device__ __forceinline__ unsigned f8_amax_bits(const unsigned* a, const unsign
   return x > y ? x : y;
 }
 
+// sigmoid(z) = (1 + tanh(z / 2)) / 2 with the hardware tanh approximation (relative
+// error ~2^-11, far below the E4M3 rounding of the products)
+__device__ __forceinline__ float f8_sigmoid(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return fmaf(0.5f, t, 0.5f);
+}
+
 // 32 consecutive columns [n, n + 32) of row m (v already times sA sB): the epilogue of
 // the bf16-storage path with plain stores; returns max|output| of an activation output
 // (0 for the float32 output)
@@ -142,7 +150,7 @@ __device__ __forceinline__ float f8_epilogue(const EpiParams& ep, int m, int n, 
     }
     const float rs = ep.rowscale ? ep.rowscale[m] : 1.0f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = v[j] * epi_sigmoid(v[j]) * rs;
+    for (int j = 0; j < 32; ++j) v[j] = v[j] * f8_sigmoid(v[j]) * rs;
   } else if (ep.epi == EPI_BWD_SILU) {
     const bf16* zp = reinterpret_cast<const bf16*>(ep.pre) + (size_t)m * ep.ldp + n;
     float z[32];
@@ -154,7 +162,7 @@ __device__ __forceinline__ float f8_epilogue(const EpiParams& ep, int m, int n, 
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      const float sg = epi_sigmoid(z[j]);
+      const float sg = f8_sigmoid(z[j]);
       v[j] = v[j] * sg * (1.0f + z[j] * (1.0f - sg));
     }
   }
@@ -389,8 +397,10 @@ __global__ void __launch_bounds__(kF8Threads, 1)
           const uint8_t* stg = sS + s2 * kF8StgBytes;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
+            // item -> (row, unit): eight consecutive lanes take eight consecutive rows of one
+            // unit, so their 16-byte reads and writes fall on eight different bank groups
             const int it = ct + 128 * i;
-            const int row = it >> 2, cc = it & 3, sw = row & 7;
+            const int row = (it & 7) + 8 * (it >> 5), cc = (it >> 3) & 3, sw = row & 7;
             const uint4 lo = *reinterpret_cast<const uint4*>(stg + row * 128 + (((2 * cc) ^ sw) << 4));
             const uint4 hi = *reinterpret_cast<const uint4*>(stg + row * 128 + (((2 * cc + 1) ^ sw) << 4));
             *reinterpret_cast<uint4*>(a8 + row * 128 + (((4 * h + cc) ^ sw) << 4)) = f8_convert16(lo, hi, invA);

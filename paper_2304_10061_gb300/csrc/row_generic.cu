@@ -531,7 +531,10 @@ template <typename T, int LMAX, int NL>
 __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO io) {
   constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
   static_assert(S <= 16, "halving sums of 16 components");
-  __shared__ float red[2][kMaxChannels / 32][16];
+  // per-warp channel partials of Ybar for batches of kEdgeBatch edges, double-buffered:
+  // one barrier per batch
+  constexpr int kEdgeBatch = 8;
+  __shared__ float red[2][kEdgeBatch][kMaxChannels / 32][16];
   const int ia = blockIdx.x, u = threadIdx.x;
   if (ia >= io.na) return;
   const bool act = u < io.C;
@@ -550,7 +553,17 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
   T* w0b = reinterpret_cast<T*>(io.wbar[0]);
   T* w1b = reinterpret_cast<T*>(io.wbar[1]);
   float gmax = 0.0f;
-  for (int e = rb, buf = 0; e < re; ++e, buf ^= 1) {
+  // the batch's sums over the warps, in a fixed order: thread t takes edge t / S, component t % S
+  auto flush = [&](int eb, int nb, int buf) {
+    for (int t = threadIdx.x; t < nb * S; t += blockDim.x) {
+      const int j = t / S, a = t - j * S;
+      float sum = 0.0f;
+      for (int k = 0; k < nwarp; ++k) sum += red[buf][j][k][a];
+      io.Ybar[(size_t)(eb + j) * S + a] = sum;
+    }
+  };
+  for (int e = rb, buf = 0; e < re; ++e) {
+    const int j = (e - rb) % kEdgeBatch;
     float y[S];
     load_y<S>(io.Y + (size_t)e * S, y);
     float yc[16];
@@ -587,12 +600,12 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
       for (int l = 0; l < LM; ++l) gmax = fmaxf(gmax, fmaxf(fabsf(g0[l]), fabsf(g1[l])));
     }
     const float t = warp_sum16(yc);   // component lane / 2
-    if ((lane & 1) == 0) red[buf][wid][lane >> 1] = t;
-    __syncthreads();   // one barrier per edge: the other buffer is rewritten only after the next one
-    if (threadIdx.x < S) {
-      float sum = 0.0f;
-      for (int k = 0; k < nwarp; ++k) sum += red[buf][k][threadIdx.x];
-      io.Ybar[(size_t)e * S + threadIdx.x] = sum;
+    if ((lane & 1) == 0) red[buf][j][wid][lane >> 1] = t;
+    if (j == kEdgeBatch - 1 || e == re - 1) {
+      // one barrier per batch: the other buffer is rewritten only after the next one
+      __syncthreads();
+      flush(e - j, j + 1, buf);
+      buf ^= 1;
     }
   }
   record_amax(io.amax_wbar, gmax);

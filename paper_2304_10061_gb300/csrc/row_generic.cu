@@ -26,10 +26,13 @@
 //
 // Layout: per atom [atom][channel][S] float32; per edge the activation-type
 // arrays of the MLP side (w, s, sbar, wbar) and float32 Y / Ybar / w^0bar.
-// Row kernels: one block per centre atom, one thread per channel; per-atom
-// sums are register accumulations over the row (deterministic), the channel
-// sums of Ybar are warp halving sums and a fixed-order sum over the warps; l_max is a template
-// parameter, so every per-edge vector lives in registers.  Chain kernels: one
+// Row kernels: one warp per centre atom with C / 32 channels per lane (the
+// environment sums, s, Qbar, the upper layers' wbar: a lane's harmonics loads
+// serve all its channels), or, for the per-edge adjoint that combines every
+// layer, one block per centre atom and one thread per channel; per-atom sums
+// are register accumulations over the row (deterministic), the channel sums of
+// Ybar are warp halving sums and a fixed-order sum over the warps; l_max is a
+// template parameter, so every per-edge vector lives in registers.  Chain kernels: one
 // thread per (atom, channel), unrolled at compile time over the candidate
 // nonzeros of the layer tensors.  Which entries of a fused tensor can be
 // nonzero is fixed by l_max and the layer irreps: the paths allowed by the
@@ -315,32 +318,6 @@ __device__ __forceinline__ void chain_mv(const float* v, const float (&G)[D], co
 
 }  // namespace
 
-// Gamma^L[i][u][b] = nu sum_{e in row i} w^L[e][u][l(b)] Y[e][b]
-template <typename T, int LMAX>
-__global__ void gen_env_kernel(GenRowIO io, int L) {
-  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
-  const int ia = blockIdx.x, u = threadIdx.x;
-  if (ia >= io.na || u >= io.C) return;
-  const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
-  const T* w = reinterpret_cast<const T*>(io.w[L]);
-  const int ldw = io.ldw[L], col = io.wcol[L];
-  float G[S];
-#pragma unroll
-  for (int b = 0; b < S; ++b) G[b] = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    float wl[LM];
-    load_lm<T, LM>(w + (size_t)e * ldw + col + u * LM, wl);
-    float y[S];
-    load_y<S>(io.Y + (size_t)e * S, y);
-#pragma unroll
-    for (int b = 0; b < S; ++b) G[b] += wl[l_of(b)] * y[b];
-  }
-  float* out = io.G[L] + ((size_t)ia * io.C + u) * S;
-#pragma unroll
-  for (int b = 0; b < S; ++b) out[b] = G[b] * io.nu;
-}
-
 // Q^L[i][u][:] = M^1 ... M^L e_0
 template <int LMAX, int NL, int L>
 __global__ void __launch_bounds__(kChainThreads) gen_chain_fwd_kernel(GenRowIO io, const __grid_constant__ GenVals<LMAX, NL> w) {
@@ -365,64 +342,6 @@ __global__ void __launch_bounds__(kChainThreads) gen_chain_fwd_kernel(GenRowIO i
   float* out = io.Q[L] + o;
 #pragma unroll
   for (int a = 0; a < S; ++a) out[a] = q[a];
-}
-
-// s^L_e[u] = sum_a w^0_{e,u,l(a)} Y_e[a] Q^L[i][u][a], into the s columns of the latent input
-template <typename T, int LMAX>
-__global__ void gen_s_kernel(GenRowIO io, int L) {
-  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
-  const int ia = blockIdx.x, u = threadIdx.x;
-  if (ia >= io.na || u >= io.C) return;
-  const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
-  const T* w0 = reinterpret_cast<const T*>(io.w[0]);
-  float q[S];
-  const float* Q = io.Q[L] + ((size_t)ia * io.C + u) * S;
-#pragma unroll
-  for (int a = 0; a < S; ++a) q[a] = Q[a];
-  T* xs = reinterpret_cast<T*>(io.xs[L]);
-  float smax = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    float wl[LM];
-    load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM, wl);
-    float y[S];
-    load_y<S>(io.Y + (size_t)e * S, y);
-    float s = 0.0f;
-#pragma unroll
-    for (int a = 0; a < S; ++a) s += wl[l_of(a)] * y[a] * q[a];
-    smax = fmaxf(smax, fabsf(s));
-    gst(xs + (size_t)e * io.ldxs[L] + io.xs_off[L] + u, s);
-  }
-  record_amax(io.amax_s, smax);
-}
-
-// Qbar^L[i][u][a] = sum_e sbar^L_e[u] w^0_{e,u,l(a)} Y_e[a]
-template <typename T, int LMAX>
-__global__ void gen_qbar_kernel(GenRowIO io, int L) {
-  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
-  const int ia = blockIdx.x, u = threadIdx.x;
-  if (ia >= io.na || u >= io.C) return;
-  const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
-  const T* w0 = reinterpret_cast<const T*>(io.w[0]);
-  const T* sb = reinterpret_cast<const T*>(io.sbar[L]);
-  float acc[S];
-#pragma unroll
-  for (int a = 0; a < S; ++a) acc[a] = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    const float s = gld(sb + (size_t)e * io.ldsbar[L] + io.sbar_off[L] + u);
-    float wl[LM];
-    load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + io.wcol[0] + u * LM, wl);
-#pragma unroll
-    for (int l = 0; l < LM; ++l) wl[l] *= s;
-    float y[S];
-    load_y<S>(io.Y + (size_t)e * S, y);
-#pragma unroll
-    for (int a = 0; a < S; ++a) acc[a] += wl[l_of(a)] * y[a];
-  }
-  float* out = io.Qb + ((size_t)ia * io.C + u) * S;
-#pragma unroll
-  for (int a = 0; a < S; ++a) out[a] = acc[a];
 }
 
 // Gb[b] += sum over layer K's candidates of W^K[a][b][c] rb[a] r[c] (r = e_0 when E0) and, unless
@@ -492,34 +411,6 @@ __global__ void __launch_bounds__(kChainThreads) gen_chain_bwd_kernel(GenRowIO i
       flush(3);
     }
   }
-}
-
-// wbar^L_{e,u,l} = nu sum_m Gammabar^L[i][u][lm] Y_e[lm], for a layer L >= 2 (complete once
-// the chains of layers >= L have run)
-template <typename T, int LMAX>
-__global__ void gen_wbar_kernel(GenRowIO io, int L) {
-  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
-  const int ia = blockIdx.x, u = threadIdx.x;
-  if (ia >= io.na || u >= io.C) return;
-  const int rb = io.row_ptr[io.a0 + ia] - io.e0, re = io.row_ptr[io.a0 + ia + 1] - io.e0;
-  float gb[S];
-  const float* G = io.Gb[L] + ((size_t)ia * io.C + u) * S;
-#pragma unroll
-  for (int a = 0; a < S; ++a) gb[a] = io.nu * G[a];
-  T* wLb = reinterpret_cast<T*>(io.wbar[L]);
-  float gmax = 0.0f;
-#pragma unroll 4
-  for (int e = rb; e < re; ++e) {
-    float y[S];
-    load_y<S>(io.Y + (size_t)e * S, y);
-    float g[LM] = {};
-#pragma unroll
-    for (int a = 0; a < S; ++a) g[l_of(a)] += gb[a] * y[a];
-#pragma unroll
-    for (int l = 0; l < LM; ++l) gmax = fmaxf(gmax, fabsf(g[l]));
-    store_lm<T, LM>(wLb + (size_t)e * io.ldwbar[L] + io.wbcol[L] + u * LM, g);
-  }
-  record_amax(io.amax_wbar, gmax);
 }
 
 // Per edge, once every layer's adjoint is in (after layer 1's chain):
@@ -612,7 +503,178 @@ __global__ void __launch_bounds__(kMaxChannels) gen_edge_final_kernel(GenRowIO i
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Warp-per-atom forms of the per-edge row kernels (environment sums, s, Qbar,
+// wbar of the upper layers): one warp owns a centre atom's row, lane t the CPL
+// channels t, t + 32, ... (CPL = C / 32, at least 1; lanes past C idle), so
+// each per-channel load or store of the warp covers 32 consecutive channels
+// (one contiguous span of the edge's row).  A lane's harmonics loads serve all
+// its CPL channels.
+// ---------------------------------------------------------------------------
+constexpr int kGenWarps = 4;   // atoms (warps) per block
+
+struct GenLane {
+  int ia, lane, rb, re;
+  bool act;
+};
+template <int CPL>
+__device__ __forceinline__ bool gen_lane(const GenRowIO& io, GenLane& g) {
+  g.ia = blockIdx.x * kGenWarps + (threadIdx.x >> 5);
+  g.lane = threadIdx.x & 31;
+  if (g.ia >= io.na) return false;
+  g.act = g.lane < io.C;
+  g.rb = io.row_ptr[io.a0 + g.ia] - io.e0;
+  g.re = io.row_ptr[io.a0 + g.ia + 1] - io.e0;
+  return true;
+}
+
+// Gamma^L[i][u][b] = nu sum_{e in row i} w^L[e][u][l(b)] Y[e][b]
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kGenWarps) gen_env_w_kernel(GenRowIO io, int L) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  GenLane g;
+  if (!gen_lane<CPL>(io, g) || !g.act) return;
+  const T* __restrict__ w = reinterpret_cast<const T*>(io.w[L]) + io.wcol[L] + g.lane * LM;
+  const float* __restrict__ Y = io.Y;
+  const int ldw = io.ldw[L];
+  float G[CPL][S];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int b = 0; b < S; ++b) G[c][b] = 0.0f;
+#pragma unroll 2
+  for (int e = g.rb; e < g.re; ++e) {
+    float y[S];
+    load_y<S>(Y + (size_t)e * S, y);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      float wl[LM];
+      load_lm<T, LM>(w + (size_t)e * ldw + 32 * c * LM, wl);
+#pragma unroll
+      for (int b = 0; b < S; ++b) G[c][b] = fmaf(wl[l_of(b)], y[b], G[c][b]);
+    }
+  }
+  float* out = io.G[L] + ((size_t)g.ia * io.C + g.lane) * S;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int b = 0; b < S; ++b) out[32 * c * S + b] = G[c][b] * io.nu;
+}
+
+// s^L_e[u] = sum_a w^0_{e,u,l(a)} Y_e[a] Q^L[i][u][a], into the s columns of the latent input
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kGenWarps) gen_s_w_kernel(GenRowIO io, int L) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  GenLane g;
+  if (!gen_lane<CPL>(io, g) || !g.act) return;
+  const T* __restrict__ w0 = reinterpret_cast<const T*>(io.w[0]) + io.wcol[0] + g.lane * LM;
+  const float* __restrict__ Y = io.Y;
+  float q[CPL][S];
+  const float* Q = io.Q[L] + ((size_t)g.ia * io.C + g.lane) * S;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int a = 0; a < S; ++a) q[c][a] = Q[32 * c * S + a];
+  T* __restrict__ xs = reinterpret_cast<T*>(io.xs[L]) + io.xs_off[L] + g.lane;
+  const int ldw0 = io.ldw[0], ldxs = io.ldxs[L];
+  float smax = 0.0f;
+  // the loads of an edge's weights and harmonics are all issued before its stores
+#pragma unroll 2
+  for (int e = g.rb; e < g.re; ++e) {
+    float y[S], wl[CPL][LM];
+    load_y<S>(Y + (size_t)e * S, y);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) load_lm<T, LM>(w0 + (size_t)e * ldw0 + 32 * c * LM, wl[c]);
+    float sv[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      sv[c] = 0.0f;
+#pragma unroll
+      for (int a = 0; a < S; ++a) sv[c] = fmaf(wl[c][l_of(a)] * y[a], q[c][a], sv[c]);
+      smax = fmaxf(smax, fabsf(sv[c]));
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) gst(xs + (size_t)e * ldxs + 32 * c, sv[c]);
+  }
+  record_amax(io.amax_s, smax);
+}
+
+// Qbar^L[i][u][a] = sum_e sbar^L_e[u] w^0_{e,u,l(a)} Y_e[a]
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kGenWarps) gen_qbar_w_kernel(GenRowIO io, int L) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  GenLane g;
+  if (!gen_lane<CPL>(io, g) || !g.act) return;
+  const T* __restrict__ w0 = reinterpret_cast<const T*>(io.w[0]) + io.wcol[0] + g.lane * LM;
+  const T* __restrict__ sb = reinterpret_cast<const T*>(io.sbar[L]) + io.sbar_off[L] + g.lane;
+  const float* __restrict__ Y = io.Y;
+  float acc[CPL][S];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int a = 0; a < S; ++a) acc[c][a] = 0.0f;
+#pragma unroll 2
+  for (int e = g.rb; e < g.re; ++e) {
+    float y[S];
+    load_y<S>(Y + (size_t)e * S, y);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const float sv = gld(sb + (size_t)e * io.ldsbar[L] + 32 * c);
+      float wl[LM];
+      load_lm<T, LM>(w0 + (size_t)e * io.ldw[0] + 32 * c * LM, wl);
+#pragma unroll
+      for (int a = 0; a < S; ++a) acc[c][a] = fmaf(wl[l_of(a)] * sv, y[a], acc[c][a]);
+    }
+  }
+  float* out = io.Qb + ((size_t)g.ia * io.C + g.lane) * S;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int a = 0; a < S; ++a) out[32 * c * S + a] = acc[c][a];
+}
+
+// wbar^L_{e,u,l} = nu sum_m Gammabar^L[i][u][lm] Y_e[lm], for a layer L >= 2
+template <typename T, int LMAX, int CPL>
+__global__ void __launch_bounds__(32 * kGenWarps) gen_wbar_w_kernel(GenRowIO io, int L) {
+  constexpr int S = (LMAX + 1) * (LMAX + 1), LM = LMAX + 1;
+  GenLane g;
+  if (!gen_lane<CPL>(io, g) || !g.act) return;
+  float gb[CPL][S];
+  const float* G = io.Gb[L] + ((size_t)g.ia * io.C + g.lane) * S;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int a = 0; a < S; ++a) gb[c][a] = io.nu * G[32 * c * S + a];
+  T* __restrict__ wLb = reinterpret_cast<T*>(io.wbar[L]) + io.wbcol[L] + g.lane * LM;
+  const float* __restrict__ Y = io.Y;
+  float gmax = 0.0f;
+#pragma unroll 2
+  for (int e = g.rb; e < g.re; ++e) {
+    float y[S];
+    load_y<S>(Y + (size_t)e * S, y);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      float o[LM] = {};
+#pragma unroll
+      for (int a = 0; a < S; ++a) o[l_of(a)] = fmaf(gb[c][a], y[a], o[l_of(a)]);
+#pragma unroll
+      for (int l = 0; l < LM; ++l) gmax = fmaxf(gmax, fabsf(o[l]));
+      store_lm<T, LM>(wLb + (size_t)e * io.ldwbar[L] + 32 * c * LM, o);
+    }
+  }
+  record_amax(io.amax_wbar, gmax);
+}
+
 static int block_of(int C) { return (C + 31) / 32 * 32; }
+
+// the warp-per-atom kernels at CPL = C / 32 channels per lane (C a power of two, 8..128)
+#define GEN_W_LAUNCH(KERNEL, ...)                                                     \
+  do {                                                                                \
+    const dim3 grid_((io.na + kGenWarps - 1) / kGenWarps), block_(32 * kGenWarps);    \
+    if (io.C >= 128) KERNEL<T, LMAX, 4><<<grid_, block_, 0, st>>>(__VA_ARGS__);       \
+    else if (io.C >= 64) KERNEL<T, LMAX, 2><<<grid_, block_, 0, st>>>(__VA_ARGS__);   \
+    else KERNEL<T, LMAX, 1><<<grid_, block_, 0, st>>>(__VA_ARGS__);                   \
+  } while (0)
 
 template <int LMAX, int NL>
 static GenVals<LMAX, NL> vals_of(const GenRowIO& io) {
@@ -655,10 +717,9 @@ static void chain_bwd_nl(const GenRowIO& io, int L, cudaStream_t st) {
 
 template <typename T, int LMAX>
 static void fwd_lmax(const GenRowIO& io, int L, cudaStream_t st) {
-  const int bl = block_of(io.C);
-  gen_env_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
+  GEN_W_LAUNCH(gen_env_w_kernel, io, L);
   chain_fwd_nl<LMAX>(io, L, st);
-  gen_s_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
+  GEN_W_LAUNCH(gen_s_w_kernel, io, L);
 }
 
 template <typename T, int LMAX>
@@ -668,9 +729,9 @@ static void bwd_lmax(const GenRowIO& io, int L, cudaStream_t st) {
     for (int k = 1; k <= io.nl; ++k)
       cudaMemsetAsync(io.Gb[k], 0, (size_t)io.na * io.C * io.S * sizeof(float), st);
   }
-  gen_qbar_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
+  GEN_W_LAUNCH(gen_qbar_w_kernel, io, L);
   chain_bwd_nl<LMAX>(io, L, st);
-  if (L >= 2) gen_wbar_kernel<T, LMAX><<<io.na, bl, 0, st>>>(io, L);
+  if (L >= 2) GEN_W_LAUNCH(gen_wbar_w_kernel, io, L);
   else if (io.nl == 1) gen_edge_final_kernel<T, LMAX, 1><<<io.na, bl, 0, st>>>(io);
   else if (io.nl == 2) gen_edge_final_kernel<T, LMAX, 2><<<io.na, bl, 0, st>>>(io);
   else gen_edge_final_kernel<T, LMAX, 3><<<io.na, bl, 0, st>>>(io);

@@ -29,6 +29,7 @@ FP8_W = 16 * 5e-2
 
 L3X3 = Arch(n_species=2, lmax=3, n_layers=3, channels=16, two_body=(32,), latent=(64,), edge=(8,))
 L1X2 = Arch(n_species=2, lmax=1, n_layers=2, channels=32, two_body=(64,), latent=(64, 96), edge=(16, 8))
+L3X3C128 = Arch(n_species=2, lmax=3, n_layers=3, channels=128, two_body=(64,), latent=(64,), edge=(16,))
 
 
 def _cases():
@@ -38,11 +39,14 @@ def _cases():
     s3.species = s3.species % 2
     sl = lattice_box(500, (500 / 0.1) ** (1 / 3), seed=8)
     sl.species = sl.species % 2
+    s3c = lattice_box(120, (120 / 0.1) ** (1 / 3), seed=14)
+    s3c.species = s3c.species % 2
     return {
         "c1": (a1, w1, s1),
         "c2arch_1000": (ARCHS["c2"], make_weights(ARCHS["c2"], 1), s2),
         "three_layers_lmax3": (L3X3, make_weights(L3X3, 10), s3),
         "lmax1_two_layers": (L1X2, make_weights(L1X2, 6), sl),
+        "three_layers_lmax3_C128": (L3X3C128, make_weights(L3X3C128, 13), s3c),
     }
 
 

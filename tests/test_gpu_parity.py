@@ -29,6 +29,8 @@ WIDE = Arch(n_species=3, lmax=2, n_layers=2, channels=64, two_body=(128, 1024), 
 L3X3 = Arch(n_species=2, lmax=3, n_layers=3, channels=16, two_body=(32,), latent=(64,), edge=(8,))
 L2X3 = Arch(n_species=3, lmax=2, n_layers=3, channels=64, two_body=(32, 64), latent=(64, 64), edge=())
 L3X2 = Arch(n_species=2, lmax=3, n_layers=2, channels=32, two_body=(64,), latent=(64,), edge=(16,))
+# 128 channels on the generic path: four channels per lane in its warp-per-atom kernels
+L3X3C128 = Arch(n_species=2, lmax=3, n_layers=3, channels=128, two_body=(64,), latent=(64,), edge=(16,))
 
 
 def _cases():
@@ -48,6 +50,8 @@ def _cases():
     s3.species = s3.species % 2
     s3b = lattice_box(240, (240 / 0.1) ** (1 / 3), seed=13)
     s3b.species = s3b.species % 3
+    s3c = lattice_box(120, (120 / 0.1) ** (1 / 3), seed=14)
+    s3c.species = s3c.species % 2
     return {
         "c1": (a1, w1, s1),
         "tiny2_lmax2_C8": (TINY2, make_weights(TINY2, 3), st),
@@ -60,6 +64,7 @@ def _cases():
         "three_layers_lmax3": (L3X3, make_weights(L3X3, 10), s3),
         "three_layers_lmax2": (L2X3, make_weights(L2X3, 11), s3b),
         "two_layers_lmax3": (L3X2, make_weights(L3X2, 12), s3),
+        "three_layers_lmax3_C128": (L3X3C128, make_weights(L3X3C128, 13), s3c),
     }
 
 

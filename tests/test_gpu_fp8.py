@@ -122,3 +122,85 @@ def test_fp8_chunked_within_gate():
     err = errors(res["E_atom"], res["F"], res["virial"][0], Ea0, F0, W0)
     pred = errors(Ea8, F8, W8, Ea0, F0, W0)
     assert err["f_rms"] < 2.0 * pred["f_rms"], (err, pred)
+
+
+def test_fp8_degenerate_systems():
+    """Empty input, one atom without neighbours, isolated atoms beside a bonded pair."""
+    import torch
+    arch, w, _ = CASES["c1"]
+    m = lib_model(weights_to_blob(arch, w), precision="fp8")
+    m.neighbors(np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 10)
+    out = m.energy_forces()
+    assert out["E"].item() == 0.0 and out["F"].numel() == 0
+    m.neighbors(np.array([[1.0, 2.0, 3.0]]), np.array([1], np.int32), np.eye(3) * 20)
+    out = m.energy_forces()
+    assert out["E"].item() == pytest.approx(w["mu"][1], abs=1e-12)
+    assert torch.all(out["F"] == 0)
+    pos = np.array([[0.0, 0, 0], [1.5, 0, 0], [20, 0, 0], [0, 20, 0]])
+    m.neighbors(pos, np.array([0, 1, 1, 0], np.int32), None)
+    out = m.energy_forces()
+    i, j, S = neighbor_list(pos, None, [False] * 3, 4.0)
+    E0, Ea0, F0, W0 = AllegroOracle(arch, w).energy_forces(pos, [0, 1, 1, 0], None, i, j, S)
+    err = errors(out["E_atom"].cpu().numpy(), out["F"].cpu().numpy(), None, Ea0, F0, W0)
+    assert err["e_rel"] < FP8_E and err["f_max"] < FP8_F_MAX, err
+    m.close()
+
+
+def test_fp8_batched_molecules_per_structure():
+    """Packed uneven molecules: per-molecule energies and forces within the FP8 gates."""
+    from synth import molecule_batch
+    from synth.structures import pack
+    arch, w = ARCHS["c2"], make_weights(ARCHS["c2"], 1)
+    mols = molecule_batch(48, seed=2)
+    pos, spec, offs = pack(mols)
+    m = lib_model(weights_to_blob(arch, w), precision="fp8")
+    m.neighbors_batched(offs, pos, spec)
+    out = {k: v.cpu().numpy() for k, v in m.energy_forces().items()}
+    m.close()
+    orc = AllegroOracle(arch, w)
+    for b in (0, 17, 47):
+        mb = mols[b]
+        i, j, S = neighbor_list(mb.pos, None, mb.pbc, 4.0)
+        E0, Ea0, F0, W0 = orc.energy_forces(mb.pos, mb.species, None, i, j, S)
+        sl = slice(offs[b], offs[b + 1])
+        err = errors(out["E_atom"][sl], out["F"][sl], out["virial"][b], Ea0, F0, W0)
+        assert err["f_rms"] < FP8_F_RMS and err["e_rel"] < FP8_E, (b, err)
+
+
+def test_fp8_graph_replay_equals_eager():
+    """The amax slots are cleared inside the captured work: replays equal eager launches bitwise."""
+    arch, w, s = CASES["c2arch_1000"]
+    blob = weights_to_blob(arch, w)
+    eager = lib_model(blob, precision="fp8")
+    eager.neighbors(s.pos, s.species, s.cell)
+    ref = {k: v.cpu().numpy() for k, v in eager.energy_forces().items()}
+    g = lib_model(blob, precision="fp8")
+    g.set_graphs(True)
+    g.neighbors(s.pos, s.species, s.cell)
+    for _ in range(4):
+        o = {k: v.cpu().numpy() for k, v in g.energy_forces().items()}
+        for k in ref:
+            np.testing.assert_array_equal(o[k], ref[k])
+    assert g.autotune_report()["graph_replays"] >= 2
+    eager.close()
+    g.close()
+
+
+def test_fp8_pair_cutoffs_and_zbl():
+    """The per-pair cutoff table and the ZBL term (float32 arithmetic outside the GEMMs) on the FP8 path."""
+    from dataclasses import replace
+    from synth import SPECIES_Z, paper_pair_cutoffs
+    arch = replace(Arch(n_species=5, lmax=2, n_layers=2, channels=16, two_body=(32,), latent=(32,), edge=(8,),
+                        zbl_z=SPECIES_Z), pair_rc=paper_pair_cutoffs())
+    w = make_weights(arch, 23)
+    s = lattice_box(800, (800 / 0.1) ** (1 / 3), seed=42)
+    m = lib_model(weights_to_blob(arch, w), precision="fp8")
+    m.set_pair_cutoffs(np.asarray(arch.pair_rc))
+    m.set_zbl(SPECIES_Z)
+    m.neighbors(s.pos, s.species, s.cell)
+    out = {k: v.cpu().numpy() for k, v in m.energy_forces().items()}
+    m.close()
+    ed = neighbor_list(s.pos, s.cell, s.pbc, 4.0, species=s.species, pair_rc=arch.pair_rc)
+    E0, Ea0, F0, W0 = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, *ed)
+    err = errors(out["E_atom"], out["F"], out["virial"][0], Ea0, F0, W0)
+    assert err["f_rms"] < FP8_F_RMS and err["e_rel"] < FP8_E and err["w_rel"] < FP8_W, err

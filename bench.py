@@ -687,6 +687,26 @@ def run_ours(args):
     n_edges = m.n_edges
     ms_max, value = aggregate(N, ms, ws, dist, dev)
 
+    # ---- energy + forces + virial alone on a fixed neighbour list, eager and CUDA-graph replay ----
+    ef_only = {}
+    for graphs in (False, True):
+        m.set_graphs(graphs)
+        m.neighbors(pos, types, cell)
+        for _ in range(3):
+            m.energy_forces(out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kf = max(1, min(args.steps, 5))
+        a.record(stream)
+        for _ in range(kf):
+            m.energy_forces(out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        msf = a.elapsed_time(b) / kf
+        ef_only["graph_replay" if graphs else "eager"] = {"ms_per_step": msf, "atom_steps_per_s": N / (msf * 1e-3)}
+    m.set_graphs(False)
+    ef_only["note"] = "energy + forces + virial on the list built once (no neighbour rebuild in the step)"
+
     # ---- end to end: pinned host inputs, host outputs, every step ----
     hpos = torch.tensor(s.pos).pin_memory()
     htypes = torch.tensor(s.species, dtype=torch.int32).pin_memory()
@@ -837,6 +857,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches1 - launches0),
             "roofline": _roofline(report, ms * args.steps, args.steps, n_edges, arch, N)}
+    line["ef_only"] = ef_only
     if fp32:
         line["fp32"] = fp32
     if fp8:

@@ -1303,8 +1303,13 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
   // operand arrays (the s columns written into [x | s] join the slot of x).
   const void* slot_buf[kAmaxSlots];
   int nslot = 0;
+  bool slots_exhausted = false;   // reported after the chunk (the kernels ran without a record)
   auto fresh = [&](const void* b) -> unsigned* {
-    if (!fp8 || nslot >= kAmaxSlots) return nullptr;
+    if (!fp8) return nullptr;
+    if (nslot >= kAmaxSlots) {
+      slots_exhausted = true;
+      return nullptr;
+    }
     slot_buf[nslot] = b;
     return c->d_amax + nslot++;
   };
@@ -1430,6 +1435,8 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     ProfScope ps(c, "edge_energy", 0.0, (double)Ec * (a.lat.back() * act + 4));
     edge_energy<T>(Ec, a.lat.back(), (const T*)w.Xlast, w.ld_Xlast, c->d_v, c->d_Ee + e0, st);
   }
+  if (slots_exhausted)
+    return fail(c, ALLEGRO_E_INVALID, "FP8: more than %d activation arrays in a chunk", kAmaxSlots);
   if (!backward) return ALLEGRO_OK;
   // ---- adjoint ----
   {
@@ -1489,6 +1496,8 @@ allegro_status run_chunk_gen(allegro_ctx* c, const WS& w, int a0, int a1, int e0
     edge_geom_bwd<T>(Ec, e0, c->d_ed, c->d_ei, c->d_ej, c->d_species, a, (const T*)w.H[cur0], w.ld_H,
                      c->tb[0].f32T, c->tb[0].ldT, w.ubar, yb, c->d_g, st);
   }
+  if (slots_exhausted)
+    return fail(c, ALLEGRO_E_INVALID, "FP8: more than %d activation arrays in a chunk", kAmaxSlots);
   return ALLEGRO_OK;
 }
 

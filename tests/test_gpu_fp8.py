@@ -204,3 +204,31 @@ def test_fp8_pair_cutoffs_and_zbl():
     E0, Ea0, F0, W0 = AllegroOracle(arch, w).energy_forces(s.pos, s.species, s.cell, *ed)
     err = errors(out["E_atom"], out["F"], out["virial"][0], Ea0, F0, W0)
     assert err["f_rms"] < FP8_F_RMS and err["e_rel"] < FP8_E and err["w_rel"] < FP8_W, err
+
+
+def test_fp8_md_and_autotune():
+    """Velocity-Verlet steps on the FP8 path stay finite and move the atoms; the autotuner's
+    configuration (its chunk sizes give each chunk its own activation scales) stays within the
+    gates."""
+    from synth import SPECIES_MASSES
+    arch, w, s = CASES["c1"]
+    m = lib_model(weights_to_blob(arch, w), precision="fp8")
+    type_masses = np.array(SPECIES_MASSES[:2])
+    rng = np.random.default_rng(3)
+    vel = rng.normal(size=(s.n_atoms, 3)) * np.sqrt(0.0257 * 9.648533212e-3 / type_masses[s.species][:, None])
+    pos = s.pos.copy()
+    Ep, Ek = m.md_verlet(pos, vel, s.species, type_masses, dt=0.5, n_steps=10, cell=s.cell)
+    m.close()
+    assert np.all(np.isfinite(Ep + Ek)) and np.all(np.isfinite(pos))
+    assert not np.array_equal(pos, s.pos)
+    arch, w, s = CASES["c2arch_1000"]
+    _, (E0, Ea0, F0, W0), (E8, Ea8, F8, W8) = _reference("c2arch_1000")
+    m = lib_model(weights_to_blob(arch, w), precision="fp8")
+    m.set_autotune(True)
+    m.neighbors(s.pos, s.species, s.cell)
+    for _ in range(2):
+        out = {k: v.cpu().numpy() for k, v in m.energy_forces().items()}
+    m.close()
+    err = errors(out["E_atom"], out["F"], out["virial"][0], Ea0, F0, W0)
+    pred = errors(Ea8, F8, W8, Ea0, F0, W0)
+    assert err["f_rms"] < 2.0 * pred["f_rms"] and err["e_rel"] < FP8_E, (err, pred)

@@ -90,7 +90,7 @@ struct Cap {
   int64_t v = 0;
 };
 struct Caps {
-  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat, pos4, pw;
+  Cap pos, types, species, row_ptr, col_ptr, count, cell_of, wrap, sorted, atom_struct, Eatom, F, Wat, pos4, pw, wraps;
   Cap ej, ei, eS, ed, col_edge, Ee, g;
   Cap cc, cs, ccur;
   Cap offs, cells, pbc, nimg, Eout, Wout;
@@ -168,6 +168,7 @@ struct allegro_ctx {
   int* d_wrap = nullptr;
   int* d_sorted = nullptr;
   float4* d_pos4 = nullptr;                // wrapped float32 positions in cell order
+  int4* d_wraps = nullptr;                 // wrap counts in cell order
   double* d_pw = nullptr;                  // wrapped float64 positions in cell order [3 n]
   int* d_atom_struct = nullptr;
   double* d_Eatom = nullptr;
@@ -754,6 +755,7 @@ allegro_status stage_atoms(allegro_ctx* c, int64_t n, const double* pos, const i
   CUDA_TRY(c, grow(c->d_wrap, k.wrap, 3 * need));
   CUDA_TRY(c, grow(c->d_sorted, k.sorted, need));
   CUDA_TRY(c, grow(c->d_pos4, k.pos4, need));
+  CUDA_TRY(c, grow(c->d_wraps, k.wraps, need));
   CUDA_TRY(c, grow(c->d_pw, k.pw, 3 * need));
   CUDA_TRY(c, grow(c->d_atom_struct, k.atom_struct, need));
   CUDA_TRY(c, grow(c->d_Eatom, k.Eatom, need));
@@ -2020,7 +2022,7 @@ static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double
     CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cursor, 0, (size_t)(ncell + 1) * 4, st));
     nb_place(c->d_cell_of, n, c->d_cell_start, c->d_cell_cursor, c->d_sorted, st);
     nb_sort_cells(c->d_cell_start, (int)ncell, c->d_sorted, st);
-    nb_pos4(c->d_pos, c->d_species, n, g, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, st);
+    nb_pos4(c->d_pos, c->d_species, n, g, c->d_wrap, c->d_sorted, c->d_pos4, c->d_pw, c->d_wraps, st);
   }
   // Error band of the float32 prefilter: bound X on |wrapped coordinate| and
   // |image offset|, per-component error <= 8 ulp(X), squared-distance error
@@ -2044,7 +2046,7 @@ static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double
   const double rc2 = rc * rc;
   {
     ProfScope ps(c, "nb_search_count", 0.0, (double)n * 64, 4);
-    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
+    nb_search(false, c->d_pos, n, g, c->d_cell_of, c->d_wraps, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
               band, pair_rc2, c->arch.ns, c->d_count,
               nullptr, nullptr, nullptr, nullptr, nullptr, c->d_err, st);
     exclusive_scan_i32(c->d_count, c->d_row_ptr, n, nullptr, c->d_scan_tmp, c->scan_tmp_cap, st);
@@ -2057,7 +2059,7 @@ static allegro_status build_single(allegro_ctx* c, int64_t n_atoms, const double
   if ((s = ensure_edges(c, hE)) != ALLEGRO_OK) return s;
   {
     ProfScope ps(c, "nb_search_fill", 0.0, (double)hE * 44 + (double)n * 64);
-    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wrap, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
+    nb_search(true, c->d_pos, n, g, c->d_cell_of, c->d_wraps, c->d_cell_start, c->d_sorted, c->d_pos4, c->d_pw, rc2,
               band, pair_rc2, c->arch.ns, nullptr,
               c->d_row_ptr, c->d_ej, c->d_ei, c->d_eS, c->d_ed, c->d_err, st);
   }
@@ -2467,7 +2469,7 @@ void allegro_destroy(allegro_ctx* c) {
                   c->d_Wout, c->d_scan_tmp, c->d_err, c->d_total, c->d_minmax, c->d_red_scratch, c->ws,
                   c->d_md_pos, c->d_md_vel, c->d_md_invm, c->d_md_types, c->d_md_masses, c->d_md_E, c->d_md_K,
                   c->d_md_part, c->d_pair_basis, c->d_pair_rc2, c->d_zbl, c->d_sk_row, c->d_sk_j,
-                  c->d_sk_S, c->d_sk_ref, c->d_cell9, c->d_maxd, c->d_amax};
+                  c->d_sk_S, c->d_sk_ref, c->d_cell9, c->d_maxd, c->d_amax, c->d_wraps};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

@@ -182,12 +182,14 @@ void nb_place(const int* cell_of, int n, const int* cell_start, int* cell_cursor
               cudaStream_t st);
 void nb_sort_cells(const int* cell_start, int n_cells, int* sorted, cudaStream_t st);
 // pos4[s].w carries the model species of atom sorted[s] (its bits)
+// pos4 / pw / wraps: wrapped float32 (with the species bits) and float64 positions and the
+// wrap counts, all in cell order
 void nb_pos4(const double* pos, const int* species, int n, const CellGrid& g, const int* wrap, const int* sorted,
-             float4* pos4, double* pw, cudaStream_t st);
+             float4* pos4, double* pw, int4* wraps, cudaStream_t st);
 // pair_rc2: null, or device [ns * ns] squared cutoffs per ordered species pair
 // (each <= rc2, the search radius; `band` is the prefilter band of rc2)
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
+               const int4* wraps, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
                double rc2, float band, const double* pair_rc2, int ns, int* count, const int* row_ptr, int* ej,
                int* ei, int* eS, double* ed, int* d_err, cudaStream_t st);
 void nb_bruteforce_batched(bool fill, const double* pos, const int64_t* offs, int nstruct,

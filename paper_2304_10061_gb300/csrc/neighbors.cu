@@ -365,7 +365,7 @@ void nb_max_disp2(const double* pos, const double* ref, int n, unsigned long lon
 // the displacements of accepted edges.
 __global__ void pos4_kernel(const double* __restrict__ pos, const int* __restrict__ species, int n, CellGrid g,
                             const int* __restrict__ wrap, const int* __restrict__ sorted,
-                            float4* __restrict__ pos4, double* __restrict__ pw) {
+                            float4* __restrict__ pos4, double* __restrict__ pw, int4* __restrict__ wraps) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int j = sorted[s];
@@ -380,6 +380,7 @@ __global__ void pos4_kernel(const double* __restrict__ pos, const int* __restric
   pw[3 * (size_t)s] = p[0];
   pw[3 * (size_t)s + 1] = p[1];
   pw[3 * (size_t)s + 2] = p[2];
+  wraps[s] = make_int4(wrap[3 * (size_t)j], wrap[3 * (size_t)j + 1], wrap[3 * (size_t)j + 2], 0);
 }
 
 // Neighbour search.  A float32 prefilter on the wrapped positions decides
@@ -391,129 +392,213 @@ __global__ void pos4_kernel(const double* __restrict__ pos, const int* __restric
 // from the exact test inside the band, else (pw_j + q . cell) - pw_i from the
 // float64 wrapped positions (the same vector up to float64 rounding; the
 // edge's image shift is S = q - w_j + w_i).
-template <bool fill>
-__global__ void search_kernel( const double* __restrict__ pos, int n, CellGrid g,
-                              const int* __restrict__ cell_of, const int* __restrict__ wrap,
-                              const int* __restrict__ cell_start, const int* __restrict__ sorted,
-                              const float4* __restrict__ pos4, const double* __restrict__ pw, double rc2, float band,
-                              const double* __restrict__ pair_rc2, int ns,
-                              int* __restrict__ count, const int* __restrict__ row_ptr,
-                              int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS,
-                              double* __restrict__ ed, int* __restrict__ d_err) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int i = sorted[t];
-  if (i >= g.n_centres) {   // ghost atoms (spatial decomposition) are neighbours only, never centres
-    if (!fill) count[i] = 0;
-    return;
+// The fill pass writes through shared memory: a lane records each accepted
+// candidate of its row (cell-order index s, image q, whether it took the exact
+// test) in its warp's staging area, then the warp writes the 32 rows one after
+// another with its lanes on consecutive edges of a row, so each store covers
+// consecutive addresses (a row per lane would scatter every store over 32
+// rows).  Edges past kFillStage in a row are written by their lane directly.
+constexpr int kSearchThreads = 128;
+constexpr int kFillStage = 32;
+
+// The displacement of pair_test (the same float64 operations in the same order).
+__device__ __forceinline__ void pair_disp(const double* __restrict__ pi, const double* __restrict__ pj,
+                                          const double* cell, int S0, int S1, int S2, double d[3]) {
+  double s0 = (double)S0, s1 = (double)S1, s2 = (double)S2;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    double off = __dadd_rn(__dadd_rn(__dmul_rn(s0, cell[0 * 3 + x]), __dmul_rn(s1, cell[1 * 3 + x])),
+                           __dmul_rn(s2, cell[2 * 3 + x]));
+    d[x] = __dsub_rn(__dadd_rn(pj[x], off), pi[x]);
   }
-  const int ci = cell_of[i];
-  int c[3];
-  c[2] = ci % g.n[2];
-  c[1] = (ci / g.n[2]) % g.n[1];
-  c[0] = ci / (g.n[2] * g.n[1]);
-  const int wi0 = wrap[3 * (size_t)i], wi1 = wrap[3 * (size_t)i + 1], wi2 = wrap[3 * (size_t)i + 2];
-  const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
-  const float4 pi4 = pos4[t];
-  const double pwi[3] = {pw[3 * (size_t)t], pw[3 * (size_t)t + 1], pw[3 * (size_t)t + 2]};
-  const float rc2f = (float)rc2;
-  const float lo2 = rc2f - band, hi2 = rc2f + band;
-  // per-ordered-pair cutoffs: row of the centre's species (the band of the largest
-  // cutoff bounds the float32 error of every smaller one)
-  const double* prow = pair_rc2 ? pair_rc2 + (size_t)__float_as_int(pi4.w) * ns : nullptr;
-  float cf[9];
+}
+
+// image q (three signed 9-bit fields) and the exact-test flag of a staged edge
+__device__ __forceinline__ int pack_q(int q0, int q1, int q2, bool exact) {
+  return (q0 & 511) | ((q1 & 511) << 9) | ((q2 & 511) << 18) | (exact ? (1 << 27) : 0);
+}
+__device__ __forceinline__ int unpack_q(int v, int f) { return ((v >> (9 * f)) << 23) >> 23; }
+
+template <bool fill>
+__global__ void __launch_bounds__(kSearchThreads) search_kernel(
+    const double* __restrict__ pos, int n, CellGrid g, const int* __restrict__ cell_of,
+    const int4* __restrict__ wraps, const int* __restrict__ cell_start, const int* __restrict__ sorted,
+    const float4* __restrict__ pos4, const double* __restrict__ pw, double rc2, float band,
+    const double* __restrict__ pair_rc2, int ns, int* __restrict__ count, const int* __restrict__ row_ptr,
+    int* __restrict__ ej, int* __restrict__ ei, int* __restrict__ eS, double* __restrict__ ed,
+    int* __restrict__ d_err) {
+  __shared__ int2 stage[fill ? kSearchThreads : 1][fill ? kFillStage : 1];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = t < n;
+  const int i = act ? sorted[t] : 0;
+  if (act && i >= g.n_centres) {   // ghost atoms (spatial decomposition) are neighbours only, never centres
+    if (!fill) count[i] = 0;
+    act = false;
+  }
+  if constexpr (!fill) {
+    if (!act) return;
+  }
+  int4 wi = make_int4(0, 0, 0, 0);
+  double pi[3] = {0.0, 0.0, 0.0}, pwi[3] = {0.0, 0.0, 0.0};
+  int k = 0, base = 0, cap = 0;
+  if (act) {
+    const int ci = cell_of[i];
+    int c[3];
+    c[2] = ci % g.n[2];
+    c[1] = (ci / g.n[2]) % g.n[1];
+    c[0] = ci / (g.n[2] * g.n[1]);
+    wi = wraps[t];   // cell-order copies of the wrap counts: coalesced with pos4
 #pragma unroll
-  for (int k = 0; k < 9; ++k) cf[k] = (float)g.cell[k];
-  int k = 0;
-  const int base = fill ? row_ptr[i] : 0;
-  const int cap = fill ? (row_ptr[i + 1] - base) : 0;
-  for (int d0 = -g.R[0]; d0 <= g.R[0]; ++d0) {
-    int cc0 = c[0] + d0, q0 = 0;
-    if (g.pbc[0]) { q0 = floordiv(cc0, g.n[0]); cc0 -= q0 * g.n[0]; }
-    else if (cc0 < 0 || cc0 >= g.n[0]) continue;
-    for (int d1 = -g.R[1]; d1 <= g.R[1]; ++d1) {
-      int cc1 = c[1] + d1, q1 = 0;
-      if (g.pbc[1]) { q1 = floordiv(cc1, g.n[1]); cc1 -= q1 * g.n[1]; }
-      else if (cc1 < 0 || cc1 >= g.n[1]) continue;
-      for (int d2 = -g.R[2]; d2 <= g.R[2]; ++d2) {
-        int cc2 = c[2] + d2, q2 = 0;
-        if (g.pbc[2]) { q2 = floordiv(cc2, g.n[2]); cc2 -= q2 * g.n[2]; }
-        else if (cc2 < 0 || cc2 >= g.n[2]) continue;
-        const int cell = (cc0 * g.n[1] + cc1) * g.n[2] + cc2;
-        const int b = cell_start[cell], e = cell_start[cell + 1];
-        // image offset of this stencil cell (float32), relative to i
-        const float ox = (float)q0 * cf[0] + (float)q1 * cf[3] + (float)q2 * cf[6] - pi4.x;
-        const float oy = (float)q0 * cf[1] + (float)q1 * cf[4] + (float)q2 * cf[7] - pi4.y;
-        const float oz = (float)q0 * cf[2] + (float)q1 * cf[5] + (float)q2 * cf[8] - pi4.z;
-        // float64 image offset (fill pass only; zero away from the box faces)
-        double qoff[3] = {0.0, 0.0, 0.0};
-        if (fill && (q0 | q1 | q2)) {
+    for (int x = 0; x < 3; ++x) {
+      pi[x] = pos[3 * (size_t)i + x];
+      pwi[x] = pw[3 * (size_t)t + x];
+    }
+    const float4 pi4 = pos4[t];
+    const float rc2f = (float)rc2;
+    const float lo2 = rc2f - band, hi2 = rc2f + band;
+    // per-ordered-pair cutoffs: row of the centre's species (the band of the largest
+    // cutoff bounds the float32 error of every smaller one)
+    const double* prow = pair_rc2 ? pair_rc2 + (size_t)__float_as_int(pi4.w) * ns : nullptr;
+    float cf[9];
 #pragma unroll
-          for (int x = 0; x < 3; ++x)
-            qoff[x] = (double)q0 * g.cell[x] + (double)q1 * g.cell[3 + x] + (double)q2 * g.cell[6 + x];
-        }
-        for (int s = b; s < e; ++s) {
-          const float4 pj = pos4[s];
-          const float dx = pj.x + ox, dy = pj.y + oy, dz = pj.z + oz;
-          const float r2f = dx * dx + dy * dy + dz * dz;
-          if (r2f > hi2) continue;
-          double rc2p = rc2;
-          float lo2p = lo2;
-          if (prow) {
-            rc2p = prow[__float_as_int(pj.w)];
-            const float rc2pf = (float)rc2p;
-            if (r2f > rc2pf + band) continue;
-            lo2p = rc2pf - band;
-          }
-          const int j = sorted[s];
-          int S0 = g.pbc[0] ? q0 - wrap[3 * (size_t)j] + wi0 : 0;
-          int S1 = g.pbc[1] ? q1 - wrap[3 * (size_t)j + 1] + wi1 : 0;
-          int S2 = g.pbc[2] ? q2 - wrap[3 * (size_t)j + 2] + wi2 : 0;
-          if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
-          double d[3];
-          if (r2f >= lo2p) {
-            if (!pair_test(pi, pos + 3 * (size_t)j, g.cell, S0, S1, S2, rc2p, d)) continue;
-          } else if constexpr (fill) {
-#pragma unroll
-            for (int x = 0; x < 3; ++x) d[x] = (pw[3 * (size_t)s + x] + qoff[x]) - pwi[x];
-          }
-          if (fill) {
-            if (k < cap) {
-              size_t o = (size_t)base + k;
-              ej[o] = j;
-              ei[o] = i;
-              eS[3 * o] = S0; eS[3 * o + 1] = S1; eS[3 * o + 2] = S2;
-              ed[3 * o] = d[0]; ed[3 * o + 1] = d[1]; ed[3 * o + 2] = d[2];
+    for (int q = 0; q < 9; ++q) cf[q] = (float)g.cell[q];
+    base = fill ? row_ptr[i] : 0;
+    cap = fill ? (row_ptr[i + 1] - base) : 0;
+    for (int d0 = -g.R[0]; d0 <= g.R[0]; ++d0) {
+      int cc0 = c[0] + d0, q0 = 0;
+      if (g.pbc[0]) { q0 = floordiv(cc0, g.n[0]); cc0 -= q0 * g.n[0]; }
+      else if (cc0 < 0 || cc0 >= g.n[0]) continue;
+      for (int d1 = -g.R[1]; d1 <= g.R[1]; ++d1) {
+        int cc1 = c[1] + d1, q1 = 0;
+        if (g.pbc[1]) { q1 = floordiv(cc1, g.n[1]); cc1 -= q1 * g.n[1]; }
+        else if (cc1 < 0 || cc1 >= g.n[1]) continue;
+        for (int d2 = -g.R[2]; d2 <= g.R[2]; ++d2) {
+          int cc2 = c[2] + d2, q2 = 0;
+          if (g.pbc[2]) { q2 = floordiv(cc2, g.n[2]); cc2 -= q2 * g.n[2]; }
+          else if (cc2 < 0 || cc2 >= g.n[2]) continue;
+          const int cell = (cc0 * g.n[1] + cc1) * g.n[2] + cc2;
+          const int b = cell_start[cell], e = cell_start[cell + 1];
+          // image offset of this stencil cell (float32), relative to i
+          const float ox = (float)q0 * cf[0] + (float)q1 * cf[3] + (float)q2 * cf[6] - pi4.x;
+          const float oy = (float)q0 * cf[1] + (float)q1 * cf[4] + (float)q2 * cf[7] - pi4.y;
+          const float oz = (float)q0 * cf[2] + (float)q1 * cf[5] + (float)q2 * cf[8] - pi4.z;
+          for (int s = b; s < e; ++s) {
+            const float4 pj = pos4[s];
+            const float dx = pj.x + ox, dy = pj.y + oy, dz = pj.z + oz;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            if (r2f > hi2) continue;
+            double rc2p = rc2;
+            float lo2p = lo2;
+            if (prow) {
+              rc2p = prow[__float_as_int(pj.w)];
+              const float rc2pf = (float)rc2p;
+              if (r2f > rc2pf + band) continue;
+              lo2p = rc2pf - band;
             }
+            const int4 wj = wraps[s];
+            const int S0 = g.pbc[0] ? q0 - wj.x + wi.x : 0;
+            const int S1 = g.pbc[1] ? q1 - wj.y + wi.y : 0;
+            const int S2 = g.pbc[2] ? q2 - wj.z + wi.z : 0;
+            if (s == t && S0 == 0 && S1 == 0 && S2 == 0) continue;   // (s = t: j = i)
+            const bool exact = r2f >= lo2p;
+            double d[3];
+            if (exact && !pair_test(pi, pos + 3 * (size_t)sorted[s], g.cell, S0, S1, S2, rc2p, d)) continue;
+            if constexpr (fill) {
+              if (k < kFillStage) {
+                stage[threadIdx.x][k] = make_int2(s, pack_q(q0, q1, q2, exact));
+              } else if (k < cap) {
+                // past the staging area: this lane writes the edge itself
+                if (!exact) {
+#pragma unroll
+                  for (int x = 0; x < 3; ++x) {
+                    const double qoff = (q0 | q1 | q2) ? ((double)q0 * g.cell[x] + (double)q1 * g.cell[3 + x]) +
+                                                             (double)q2 * g.cell[6 + x]
+                                                       : 0.0;
+                    d[x] = (pw[3 * (size_t)s + x] + qoff) - pwi[x];
+                  }
+                }
+                const size_t o = (size_t)base + k;
+                ej[o] = sorted[s];
+                ei[o] = i;
+                eS[3 * o] = S0; eS[3 * o + 1] = S1; eS[3 * o + 2] = S2;
+                ed[3 * o] = d[0]; ed[3 * o + 1] = d[1]; ed[3 * o + 2] = d[2];
+              }
+            }
+            ++k;
           }
-          ++k;
         }
       }
     }
   }
-  if (fill) {
-    if (k != cap) atomicOr(d_err, kErrNeighbor);
-  } else {
+  if constexpr (!fill) {
     count[i] = k;
+  } else {
+    if (act && k != cap) atomicOr(d_err, kErrNeighbor);
+    __syncwarp();
+    // the warp's rows one after another, lanes on consecutive edges
+    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
+    const int nst = act ? min(min(k, cap), kFillStage) : 0;
+    for (int r = 0; r < 32; ++r) {
+      const int nr = __shfl_sync(0xffffffffu, nst, r);
+      if (nr == 0) continue;
+      const int ir = __shfl_sync(0xffffffffu, i, r);
+      const int br = __shfl_sync(0xffffffffu, base, r);
+      const int wx = __shfl_sync(0xffffffffu, wi.x, r), wy = __shfl_sync(0xffffffffu, wi.y, r),
+                wz = __shfl_sync(0xffffffffu, wi.z, r);
+      double pir[3], pwr[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        pir[x] = __shfl_sync(0xffffffffu, pi[x], r);
+        pwr[x] = __shfl_sync(0xffffffffu, pwi[x], r);
+      }
+      for (int kk = lane; kk < nr; kk += 32) {
+        const int2 en = stage[w0 + r][kk];
+        const int s = en.x;
+        const int q0 = unpack_q(en.y, 0), q1 = unpack_q(en.y, 1), q2 = unpack_q(en.y, 2);
+        const bool exact = (en.y >> 27) & 1;
+        const int j = sorted[s];
+        const int4 wj = wraps[s];
+        const int S0 = g.pbc[0] ? q0 - wj.x + wx : 0;
+        const int S1 = g.pbc[1] ? q1 - wj.y + wy : 0;
+        const int S2 = g.pbc[2] ? q2 - wj.z + wz : 0;
+        double d[3];
+        if (exact) {
+          pair_disp(pir, pos + 3 * (size_t)j, g.cell, S0, S1, S2, d);
+        } else {
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const double qoff = (q0 | q1 | q2) ? ((double)q0 * g.cell[x] + (double)q1 * g.cell[3 + x]) +
+                                                     (double)q2 * g.cell[6 + x]
+                                               : 0.0;
+            d[x] = (pw[3 * (size_t)s + x] + qoff) - pwr[x];
+          }
+        }
+        const size_t o = (size_t)br + kk;
+        ej[o] = j;
+        ei[o] = ir;
+        eS[3 * o] = S0; eS[3 * o + 1] = S1; eS[3 * o + 2] = S2;
+        ed[3 * o] = d[0]; ed[3 * o + 1] = d[1]; ed[3 * o + 2] = d[2];
+      }
+    }
   }
 }
 
 void nb_pos4(const double* pos, const int* species, int n, const CellGrid& g, const int* wrap, const int* sorted,
-             float4* pos4, double* pw, cudaStream_t st) {
+             float4* pos4, double* pw, int4* wraps, cudaStream_t st) {
   if (n <= 0) return;
-  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, species, n, g, wrap, sorted, pos4, pw);
+  pos4_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, species, n, g, wrap, sorted, pos4, pw, wraps);
 }
 
 void nb_search(bool fill, const double* pos, int n, const CellGrid& g, const int* cell_of,
-               const int* wrap, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
+               const int4* wraps, const int* cell_start, const int* sorted, const float4* pos4, const double* pw,
                double rc2, float band, const double* pair_rc2, int ns, int* count, const int* row_ptr, int* ej,
                int* ei, int* eS, double* ed, int* d_err, cudaStream_t st) {
   if (n <= 0) return;
   if (fill)
-    search_kernel<true><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
+    search_kernel<true><<<(n + kSearchThreads - 1) / kSearchThreads, kSearchThreads, 0, st>>>(pos, n, g, cell_of, wraps, cell_start, sorted, pos4, pw, rc2,
                                                          band, pair_rc2, ns, count, row_ptr, ej, ei, eS, ed, d_err);
   else
-    search_kernel<false><<<(n + 127) / 128, 128, 0, st>>>(pos, n, g, cell_of, wrap, cell_start, sorted, pos4, pw, rc2,
+    search_kernel<false><<<(n + kSearchThreads - 1) / kSearchThreads, kSearchThreads, 0, st>>>(pos, n, g, cell_of, wraps, cell_start, sorted, pos4, pw, rc2,
                                                           band, pair_rc2, ns, count, row_ptr, ej, ei, eS, ed, d_err);
 }
 

@@ -166,7 +166,8 @@ __device__ __forceinline__ void copy_rows_out(const T* src, int lds, T* dst, int
   }
 }
 
-template <typename T>
+// AMAX: record max|activation| for the FP8 per-tensor scale (the other paths skip the work)
+template <typename T, bool AMAX>
 __global__ void __launch_bounds__(kGeomBlock)
     geom_fwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
                     const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
@@ -216,9 +217,18 @@ __global__ void __launch_bounds__(kGeomBlock)
       }
       uout[e] = u;
       if (sig) sig[e] = (float)sigma[zi];
+      // sin(n pi x) for n = 1..nb by the angle-addition recurrence from one
+      // sincospi: (s, c)_{n+1} = (s_n c_1 + c_n s_1, c_n c_1 - s_n s_1)
+      float s1, c1;
+      sincospif(xr, &s1, &c1);
+      float sn = s1, cn = c1;
 #pragma unroll
-      for (int n = 0; n < kMaxBessel; ++n)
-        B[n] = (n < bc.nb) ? pb.y * sinpif((float)(n + 1) * xr) * ir32 : 0.0f;
+      for (int n = 0; n < kMaxBessel; ++n) {
+        B[n] = (n < bc.nb) ? pb.y * sn * ir32 : 0.0f;
+        const float s2 = fmaf(sn, c1, cn * s1);
+        cn = fmaf(cn, c1, -(sn * s1));
+        sn = s2;
+      }
     }
     const float rsc = scale_u ? u : 1.0f;
     for (int c0 = 0; c0 < N0; c0 += kGeomCols) {
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(kGeomBlock)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             hv[k] = acc[k] * path_sigmoid<T>(acc[k]) * rsc;
-            hmax = fmaxf(hmax, fabsf(hv[k]));
+            if constexpr (AMAX) hmax = fmaxf(hmax, fabsf(hv[k]));
           }
           st4_act(sZ + tl * LDS + c4, acc);
           st4_act(sH + tl * LDS + c4, hv);
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kGeomBlock)
     float* dst = Yout + (size_t)eb * bc.S;
     for (int q = tl; q < nloc * bc.S; q += kGeomBlock) dst[q] = sY[q];
   }
-  record_amax(amax, hmax);
+  if constexpr (AMAX) record_amax(amax, hmax);
 }
 
 template <typename T>
@@ -277,11 +287,14 @@ void edge_geom_fwd(int Ec, int e0, const double* ed, const int* ei, const int* e
   // one tile per block, 32 weight columns staged per pass (measured faster than persistent
   // blocks holding all of W0t)
   const size_t smem = stage + (size_t)K0 * kGeomWPad * 4;
-  if (smem > 48 * 1024)   // many species: opt in to more than the default dynamic shared memory
-    cudaFuncSetAttribute(geom_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  geom_fwd_kernel<T><<<tiles, kGeomBlock, smem, st>>>(
-      Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, sigma, sig, W0t, ldW, N0, Z0, ldZ, H0, ldH,
-      scale_u ? 1 : 0, amax);
+  auto launch = [&](auto kern) {
+    if (smem > 48 * 1024)   // many species: opt in to more than the default dynamic shared memory
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<tiles, kGeomBlock, smem, st>>>(Ec, e0, ed, ei, ej, species, make_basis(a), Y, u, sigma, sig, W0t, ldW, N0,
+                                          Z0, ldZ, H0, ldH, scale_u ? 1 : 0, amax);
+  };
+  if (amax) launch(geom_fwd_kernel<T, true>);
+  else launch(geom_fwd_kernel<T, false>);
 }
 template void edge_geom_fwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,
                                    float*, float*, const double*, float*, const float*, int, float*, int, float*,
@@ -294,8 +307,9 @@ template void edge_geom_fwd<bf16>(int, int, const double*, const int*, const int
 // needed for its Bessel part: Bbar_n = sum_k zbar0_k W0[k][2 ns + n] (the
 // one-hot species inputs carry no geometry), formed here from zbar0 and the
 // Bessel rows of W0t held in shared memory.
+constexpr int kGeomBwdBlocksPerSM = 8;
 template <typename T>
-__global__ void __launch_bounds__(kGeomBlock)
+__global__ void __launch_bounds__(kGeomBlock, kGeomBwdBlocksPerSM)
     geom_bwd_kernel(int Ec, int e0, const double* __restrict__ ed, const int* __restrict__ ei,
                     const int* __restrict__ ej, const int* __restrict__ species, BasisConst bc,
                     const T* __restrict__ zbar0,
@@ -307,85 +321,94 @@ __global__ void __launch_bounds__(kGeomBlock)
     wb_sm[q] = W0t[(size_t)(2 * bc.ns + n) * ldW + k];
   }
   __syncthreads();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Ec) return;
-  const size_t eg = (size_t)e0 + e;
-  const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
-  // float32 geometry from the exact float64 displacement
-  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-  const float r2 = fx * fx + fy * fy + fz * fz;
-  const float ir32 = rsqrtf(r2);
-  const float r = r2 * ir32;
-  const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
-  const float2 pb = pair_basis(bc, bc.pair ? species[ei[eg]] : 0, bc.pair ? species[ej[eg]] : 0);
-  const float inv_rc = pb.x, pref = pb.y;
-  const float xr = r * inv_rc;
-  // Bbar = zbar0 . W0[:, 2 ns:]
-  float Bb[kMaxBessel];
-#pragma unroll
-  for (int n = 0; n < kMaxBessel; ++n) Bb[n] = 0.0f;
-  const T* zr = zbar0 + (size_t)e * ldz;
-  constexpr int V = 16 / (int)sizeof(T);   // elements per 16-byte vector
-  int k0 = 0;
-  if ((ldz * (int)sizeof(T)) % 16 == 0 && N0 % 4 == 0) {   // 16-byte aligned rows: vector loads
-    for (; k0 + V <= N0; k0 += V) {
-      const uint4 q = *reinterpret_cast<const uint4*>(zr + k0);
-      const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-      float zk[V];
-      if constexpr (sizeof(T) == 2) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          zk[2 * t] = __uint_as_float(wv[t] << 16);
-          zk[2 * t + 1] = __uint_as_float(wv[t] & 0xffff0000u);
+  // persistent blocks (a few per SM): the Bessel rows are staged once per block
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ec; e += gridDim.x * blockDim.x) {
+    const size_t eg = (size_t)e0 + e;
+    const double dx = ed[3 * eg], dy = ed[3 * eg + 1], dz = ed[3 * eg + 2];
+    // float32 geometry from the exact float64 displacement
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float r2 = fx * fx + fy * fy + fz * fz;
+    const float ir32 = rsqrtf(r2);
+    const float r = r2 * ir32;
+    const float x = fx * ir32, y = fy * ir32, z = fz * ir32;
+    const float2 pb = pair_basis(bc, bc.pair ? species[ei[eg]] : 0, bc.pair ? species[ej[eg]] : 0);
+    const float inv_rc = pb.x, pref = pb.y;
+    const float xr = r * inv_rc;
+    // Bbar = zbar0 . W0[:, 2 ns:]
+    float Bb[kMaxBessel];
+  #pragma unroll
+    for (int n = 0; n < kMaxBessel; ++n) Bb[n] = 0.0f;
+    const T* zr = zbar0 + (size_t)e * ldz;
+    constexpr int V = 16 / (int)sizeof(T);   // elements per 16-byte vector
+    int k0 = 0;
+    if ((ldz * (int)sizeof(T)) % 16 == 0 && N0 % 4 == 0) {   // 16-byte aligned rows: vector loads
+      for (; k0 + V <= N0; k0 += V) {
+        const uint4 q = *reinterpret_cast<const uint4*>(zr + k0);
+        const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+        float zk[V];
+        if constexpr (sizeof(T) == 2) {
+  #pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            zk[2 * t] = __uint_as_float(wv[t] << 16);
+            zk[2 * t + 1] = __uint_as_float(wv[t] & 0xffff0000u);
+          }
+        } else {
+  #pragma unroll
+          for (int t = 0; t < 4; ++t) zk[t] = __uint_as_float(wv[t]);
         }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) zk[t] = __uint_as_float(wv[t]);
-      }
-#pragma unroll
-      for (int n = 0; n < kMaxBessel; ++n) {
-        if (n < bc.nb) {
-#pragma unroll
-          for (int v4 = 0; v4 < V; v4 += 4) {   // weight rows are float4-aligned (N0 % 4 == 0 on this path)
-            const float4 wv4 = *reinterpret_cast<const float4*>(wb_sm + n * N0 + k0 + v4);
-            Bb[n] += zk[v4] * wv4.x + zk[v4 + 1] * wv4.y + zk[v4 + 2] * wv4.z + zk[v4 + 3] * wv4.w;
+  #pragma unroll
+        for (int n = 0; n < kMaxBessel; ++n) {
+          if (n < bc.nb) {
+  #pragma unroll
+            for (int v4 = 0; v4 < V; v4 += 4) {   // weight rows are float4-aligned (N0 % 4 == 0 on this path)
+              const float4 wv4 = *reinterpret_cast<const float4*>(wb_sm + n * N0 + k0 + v4);
+              Bb[n] += zk[v4] * wv4.x + zk[v4 + 1] * wv4.y + zk[v4 + 2] * wv4.z + zk[v4 + 3] * wv4.w;
+            }
           }
         }
       }
     }
+    for (int k = k0; k < N0; ++k) {
+      const float zk = to_f32(zr[k]);
+  #pragma unroll
+      for (int n = 0; n < kMaxBessel; ++n)
+        if (n < bc.nb) Bb[n] += zk * wb_sm[n * N0 + k];
+    }
+    // dE/dr from the Bessel basis and the envelope
+    float dEdr = 0.0f;
+    {
+      // sin, cos(n pi x) for n = 1..nb by the angle-addition recurrence from one sincospi
+      float s1, c1;
+      sincospif(xr, &s1, &c1);
+      float sn = s1, cn = c1;
+  #pragma unroll
+      for (int n = 1; n <= kMaxBessel; ++n) {
+        if (n > bc.nb) break;
+        const float kk = (float)n * 3.14159265358979323846f * inv_rc;
+        const float dB = pref * (kk * cn * r - sn) * ir32 * ir32;
+        dEdr += Bb[n - 1] * dB;
+        const float s2 = fmaf(sn, c1, cn * s1);
+        cn = fmaf(cn, c1, -(sn * s1));
+        sn = s2;
+      }
+    }
+    if (xr < 1.0f) {
+      const float xp1 = ipow(xr, bc.p - 1);
+      const float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
+      dEdr += ubar[e] * du * inv_rc;
+    }
+    // Ybar arrives in two partial arrays (from two row-kernel passes), summed in a fixed order
+    float Yb[kMaxS];
+  #pragma unroll
+    for (int a = 0; a < kMaxS; ++a)
+      Yb[a] = (a < bc.S) ? yb.p[0][(size_t)e * bc.S + a] + (yb.p[1] ? yb.p[1][(size_t)e * bc.S + a] : 0.0f) : 0.0f;
+    float G[3];
+    sh_vjp(bc.lmax, x, y, z, Yb, G);
+    const float rg = x * G[0] + y * G[1] + z * G[2];
+    g[3 * eg] = x * dEdr + (G[0] - x * rg) * ir32;
+    g[3 * eg + 1] = y * dEdr + (G[1] - y * rg) * ir32;
+    g[3 * eg + 2] = z * dEdr + (G[2] - z * rg) * ir32;
   }
-  for (int k = k0; k < N0; ++k) {
-    const float zk = to_f32(zr[k]);
-#pragma unroll
-    for (int n = 0; n < kMaxBessel; ++n)
-      if (n < bc.nb) Bb[n] += zk * wb_sm[n * N0 + k];
-  }
-  // dE/dr from the Bessel basis and the envelope
-  float dEdr = 0.0f;
-#pragma unroll
-  for (int n = 1; n <= kMaxBessel; ++n) {
-    if (n > bc.nb) break;
-    float sn, cn;
-    sincospif((float)n * xr, &sn, &cn);
-    const float kk = (float)n * 3.14159265358979323846f * inv_rc;
-    const float dB = pref * (kk * cn * r - sn) * ir32 * ir32;
-    dEdr += Bb[n - 1] * dB;
-  }
-  if (xr < 1.0f) {
-    const float xp1 = ipow(xr, bc.p - 1);
-    const float du = xp1 * (-(float)bc.p * bc.c0 + xr * ((float)(bc.p + 1) * bc.c1 - (float)(bc.p + 2) * bc.c2 * xr));
-    dEdr += ubar[e] * du * inv_rc;
-  }
-  // Ybar arrives in two partial arrays (from two row-kernel passes), summed in a fixed order
-  float Yb[kMaxS];
-  for (int a = 0; a < bc.S; ++a)
-    Yb[a] = yb.p[0][(size_t)e * bc.S + a] + (yb.p[1] ? yb.p[1][(size_t)e * bc.S + a] : 0.0f);
-  float G[3];
-  sh_vjp(bc.lmax, x, y, z, Yb, G);
-  const float rg = x * G[0] + y * G[1] + z * G[2];
-  g[3 * eg] = x * dEdr + (G[0] - x * rg) * ir32;
-  g[3 * eg + 1] = y * dEdr + (G[1] - y * rg) * ir32;
-  g[3 * eg + 2] = z * dEdr + (G[2] - z * rg) * ir32;
 }
 
 template <typename T>
@@ -396,7 +419,12 @@ void edge_geom_bwd(int Ec, int e0, const double* ed, const int* ei, const int* e
   const size_t smem = (size_t)a.nb * a.tb[0] * 4;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(geom_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  geom_bwd_kernel<T><<<(Ec + kGeomBlock - 1) / kGeomBlock, kGeomBlock, smem, st>>>(
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (Ec + kGeomBlock - 1) / kGeomBlock;
+  const int grid = std::min(tiles, std::max(nsm, 1) * kGeomBwdBlocksPerSM);
+  geom_bwd_kernel<T><<<grid, kGeomBlock, smem, st>>>(
       Ec, e0, ed, ei, ej, species, make_basis(a), zbar0, ldz, W0t, ldW, a.tb[0], ubar, yb, g);
 }
 template void edge_geom_bwd<float>(int, int, const double*, const int*, const int*, const int*, const Arch&,

@@ -247,19 +247,26 @@ __global__ void __launch_bounds__(kGeomBlock)
         for (int c4 = 0; c4 < kGeomCols; c4 += 4) {
           const float4 a = *reinterpret_cast<const float4*>(wi + c4);
           const float4 b = *reinterpret_cast<const float4*>(wj + c4);
-          float acc[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+          // column pairs in packed fp32 (FFMA2 / FMUL2: each half the ordinary
+          // IEEE fp32 fma / multiply, so the results equal the scalar ones)
+          float2 z01 = make_float2(a.x + b.x, a.y + b.y), z23 = make_float2(a.z + b.z, a.w + b.w);
 #pragma unroll
           for (int n = 0; n < kMaxBessel; ++n) {
             if (n < bc.nb) {
               const float4 w = *reinterpret_cast<const float4*>(wb + n * WP + c4);
-              acc[0] += B[n] * w.x; acc[1] += B[n] * w.y; acc[2] += B[n] * w.z; acc[3] += B[n] * w.w;
+              const float2 bn = make_float2(B[n], B[n]);
+              z01 = __ffma2_rn(bn, make_float2(w.x, w.y), z01);
+              z23 = __ffma2_rn(bn, make_float2(w.z, w.w), z23);
             }
           }
-          float hv[4];
+          const float2 rs2 = make_float2(rsc, rsc);
+          const float2 h01 = __fmul2_rn(__fmul2_rn(z01, make_float2(path_sigmoid<T>(z01.x), path_sigmoid<T>(z01.y))), rs2);
+          const float2 h23 = __fmul2_rn(__fmul2_rn(z23, make_float2(path_sigmoid<T>(z23.x), path_sigmoid<T>(z23.y))), rs2);
+          const float acc[4] = {z01.x, z01.y, z23.x, z23.y};
+          const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
+          if constexpr (AMAX) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            hv[k] = acc[k] * path_sigmoid<T>(acc[k]) * rsc;
-            if constexpr (AMAX) hmax = fmaxf(hmax, fabsf(hv[k]));
+            for (int k = 0; k < 4; ++k) hmax = fmaxf(hmax, fabsf(hv[k]));
           }
           st4_act(sZ + tl * LDS + c4, acc);
           st4_act(sH + tl * LDS + c4, hv);

@@ -757,24 +757,42 @@ def run_ours(args):
         import numpy as np
         mols = molecule_batch(2048, seed=2)
         mpos, mspec, moffs = pack(mols)
-        bt = {}
+        bt, bt_ef, tuned = {}, {}, {}
         for prec in (args.precision, "fp32"):
+            # the batched-inference configuration: launch configuration autotuned on the first
+            # evaluation of the shape, then the evaluation replayed as one CUDA graph
             mb = make(prec)
+            mb.set_autotune(True)
+            mb.set_graphs(True)
             mb.neighbors_batched(moffs, mpos, mspec)
-            mb.energy_forces()
+            for _ in range(3):                       # tune, capture, replay
+                mb.energy_forces()
             torch.cuda.synchronize()
+            nrep = 10
             t0 = time.perf_counter()
-            for _ in range(3):
+            for _ in range(nrep):                    # whole step: host inputs, list rebuild, E + F + virial
                 mb.neighbors_batched(moffs, mpos, mspec)
                 mb.energy_forces()
             torch.cuda.synchronize()
-            bt[prec] = len(mpos) * 3 / (time.perf_counter() - t0)
+            bt[prec] = len(mpos) * nrep / (time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            for _ in range(nrep):                    # E + F + virial on the list built once
+                mb.energy_forces()
+            torch.cuda.synchronize()
+            bt_ef[prec] = len(mpos) * nrep / (time.perf_counter() - t0)
+            rep = mb.autotune_report()
+            tuned[prec] = {"configuration": rep["current"], "graph_replays": rep["graph_replays"],
+                           "kernels_per_graph": rep["graph_kernels"]}
             ne = mb.n_edges
             mb.close()
         extra["batched_2048_molecules"] = {
             "atoms": int(len(mpos)), "edges": int(ne), "unit": UNIT, args.precision: bt[args.precision],
-            "fp32": bt["fp32"], "note": "2048 gas-phase molecules of 8-64 atoms in one packed edge list, "
-                                        "per-molecule E/F/virial; host inputs each step"}
+            "fp32": bt["fp32"],
+            "ef_only": {args.precision: bt_ef[args.precision], "fp32": bt_ef["fp32"]},
+            "autotuned": tuned,
+            "note": "2048 gas-phase molecules of 8-64 atoms in one packed edge list, per-molecule E/F/virial; "
+                    "autotuned launch configuration, evaluation replayed as a CUDA graph; the step rebuilds "
+                    "the list from host inputs each time, ef_only evaluates the list built once"}
         s2, _, _ = make_config("c2")
         masses = np.array([1.008, 15.999, 12.011, 14.007, 32.06])
         rng = np.random.default_rng(0)

@@ -260,8 +260,10 @@ __global__ void __launch_bounds__(kGeomBlock)
             }
           }
           const float2 rs2 = make_float2(rsc, rsc);
-          const float2 h01 = __fmul2_rn(__fmul2_rn(z01, make_float2(path_sigmoid<T>(z01.x), path_sigmoid<T>(z01.y))), rs2);
-          const float2 h23 = __fmul2_rn(__fmul2_rn(z23, make_float2(path_sigmoid<T>(z23.x), path_sigmoid<T>(z23.y))), rs2);
+          const float2 g01 = make_float2(path_sigmoid<T>(z01.x), path_sigmoid<T>(z01.y));
+          const float2 g23 = make_float2(path_sigmoid<T>(z23.x), path_sigmoid<T>(z23.y));
+          const float2 h01 = __fmul2_rn(__fmul2_rn(z01, g01), rs2);
+          const float2 h23 = __fmul2_rn(__fmul2_rn(z23, g23), rs2);
           const float acc[4] = {z01.x, z01.y, z23.x, z23.y};
           const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
           if constexpr (AMAX) {

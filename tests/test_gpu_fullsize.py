@@ -3,7 +3,9 @@ one by one (strict locality: E_i needs only atom i's row; F_k needs the rows of
 k and of every atom that has k as a neighbour).
 
   23,552-atom box (2 layers, l_max 2, 64 channels)   float32 and BF16
-  1,048,576-atom box (same model, the benchmarked workload)   float32 and BF16
+  1,048,576-atom box (same model, the benchmarked workload)   float32 and BF16,
+      TF32 (the paper's production setting), and BF16 under the paper's
+      per-ordered-species-pair cutoff table
   4,194,304-atom box (3 layers, l_max 3, 128 channels)   BF16, as benchmarked
   2048 packed gas-phase molecules (2 layers, l_max 2, 64 channels)   float32 and
       BF16 with the autotuner and CUDA-graph replay on, as benchmarked; sampled
@@ -15,15 +17,20 @@ import pytest
 from gpu_util import BF16_F_RMS, FP32_E, FP32_F, FP32_W, errors, lib_model
 from oracle.allegro import AllegroOracle
 from oracle.neighbors import neighbor_list
-from synth import make_config, weights_to_blob
+from dataclasses import replace
+
+from synth import make_config, paper_pair_cutoffs, weights_to_blob
 from synth.structures import pack
 
 pytestmark = pytest.mark.gpu
 
 
-def _sampled_check(name, prec, n_e=48, n_f=12):
+def _sampled_check(name, prec, n_e=48, n_f=12, pair_rc=None):
     s, arch, w = make_config(name)
     m = lib_model(weights_to_blob(arch, w), precision=prec)
+    if pair_rc is not None:
+        m.set_pair_cutoffs(np.asarray(pair_rc))
+        arch = replace(arch, pair_rc=pair_rc)
     m.neighbors(s.pos, s.species, s.cell)
     out = m.energy_forces()
     Ea = out["E_atom"].cpu().numpy()
@@ -35,14 +42,14 @@ def _sampled_check(name, prec, n_e=48, n_f=12):
     orc = AllegroOracle(arch, w)
     # energies of sampled centres
     ce = np.sort(rng.choice(s.n_atoms, n_e, replace=False))
-    i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c, centers=ce)
+    i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c, centers=ce, species=s.species, pair_rc=pair_rc)
     _, Ea0, _, _ = orc.energy_forces(s.pos, s.species, s.cell, i, j, S, centers=ce)
     scale = np.sqrt((Ea ** 2).mean())
     e_err = np.abs(Ea[ce] - Ea0[ce]) / np.maximum(np.abs(Ea0[ce]), scale)
     # forces on sampled atoms: all rows that contain k, plus k's own row
     fk = np.sort(rng.choice(s.n_atoms, n_f, replace=False))
     rows = np.unique(np.concatenate([fk, gi[np.isin(gj, fk)]]))
-    i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c, centers=rows)
+    i, j, S = neighbor_list(s.pos, s.cell, s.pbc, arch.r_c, centers=rows, species=s.species, pair_rc=pair_rc)
     _, _, F0, _ = orc.energy_forces(s.pos, s.species, s.cell, i, j, S, centers=rows)
     rms = np.sqrt((F ** 2).mean())
     dF = F[fk] - F0[fk]
@@ -63,6 +70,24 @@ def test_fullsize_fp32(name):
 @pytest.mark.parametrize("name", ["c2", "c4"])
 def test_fullsize_bf16(name):
     e_err, dF, rms, net, W = _sampled_check(name, "bf16")
+    assert np.sqrt((dF ** 2).mean()) < BF16_F_RMS * rms
+    assert e_err.max() < 1e-2
+    assert net < 1e-4
+
+
+def test_fullsize_c4_tf32():
+    """The 1M-atom box on the TF32 path (float32 storage, tcgen05 kind::tf32 GEMMs), gated
+    like the other reduced-precision GEMM path."""
+    e_err, dF, rms, net, W = _sampled_check("c4", "tf32")
+    assert np.sqrt((dF ** 2).mean()) < BF16_F_RMS * rms
+    assert e_err.max() < 1e-2
+    assert net < 1e-4
+
+
+def test_fullsize_c4_pair_cutoffs_bf16():
+    """The 1M-atom box under the paper's per-ordered-species-pair cutoff table, BF16 path:
+    the oracle's rows use the same table."""
+    e_err, dF, rms, net, W = _sampled_check("c4", "bf16", pair_rc=paper_pair_cutoffs(default=4.0))
     assert np.sqrt((dF ** 2).mean()) < BF16_F_RMS * rms
     assert e_err.max() < 1e-2
     assert net < 1e-4

@@ -19,8 +19,10 @@ Contents and the passages they follow (arXiv 2304.10061):
              (Sec. "Mixed-precision calculations"); forces and virial by
              torch autograd.
   verlet     velocity-Verlet integration (Sec. "Problem Overview").
+  zbl        the ZBL screened nuclear repulsion of the production potential
+             (Sec. "Training details").
 
-Where the paper is silent the oracle follows the readings listed in the
-design document of this repository (basis, envelope, normalisations, path
-weights, sign conventions); each is restated in the docstring that uses it.
+Where the paper is silent the oracle takes one stated reading (basis,
+envelope, normalisations, path weights, sign conventions), restated in the
+docstring of the function that uses it.
 """
